@@ -1,0 +1,211 @@
+/*
+ * lvb.h -- C-ABI of liblvb, a GB300 (sm_103a) local Verlet buffer broad
+ * phase for soft-sphere DEM, after "Local Verlet buffer approach for
+ * broad-phase interaction detection in Discrete Element Method"
+ * (arXiv 2208.13770).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Particle arrays are float4 records in structure-of-arrays form, passed
+ *   as `const float*` to 16-byte-aligned DEVICE memory:
+ *     pos_r : (x, y, z, r)          position [m] and radius [m]
+ *     vel   : (vx, vy, vz, unused)  velocity [m/s]
+ *     acc   : (ax, ay, az, unused)  acceleration [m/s^2]
+ *   n records each, particle i at float offset 4*i.
+ * - Output buffers of the lvb_get_* / dem_get_* calls may be host or device
+ *   memory; the library detects which (cudaPointerGetAttributes) and copies
+ *   into them.  The caller owns every buffer it passes; the library never
+ *   keeps a caller pointer beyond the call.
+ * - All work is enqueued on the context's CUDA stream (`void* stream` is a
+ *   cudaStream_t; NULL is the legacy default stream).  Calls that only
+ *   enqueue return before the GPU finishes; caller buffers must stay valid
+ *   until the stream reaches that point.
+ * - Return value: 0 (LVB_OK) or a negative LVB_E* code; no exception, exit
+ *   or device trap crosses this boundary.  Errors found on the device (a
+ *   non-finite position, a full cell, a full pair store) are sticky: they
+ *   are returned by lvb_sync and by every later call that synchronises
+ *   (the lvb_get_* family, lvb_stats), and the context's list is invalid
+ *   from the step that raised them on.
+ * - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Definitions (binary32, round to nearest, no fused multiply-add):
+ *   |a - b|^2 = ((dx*dx + dy*dy) + dz*dz) with d = a - b per component.
+ *   R_NL,i    = r_i + skin_i                            (Eq. bounding_sphere)
+ *   flag_i    : |x_i - xref_i|^2 > skin_i * skin_i    (Eq. update; xref_i is
+ *               the position of i at its last list update)
+ *   pair {i,j}: |xref_i - xref_j|^2 <= (R_NL,i + R_NL,j)^2
+ *               (Def. verletlist and Eq. broad_phase, on reference positions)
+ *   contact   : delta_ij = (r_i + r_j) - sqrt(|x_i - x_j|^2) > 0 (Eq. delta)
+ */
+#ifndef LVB_H
+#define LVB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LVB_OK          0
+#define LVB_EINVAL     (-1)  /* bad argument (NULL, n <= 0, misaligned, bad enum, box) */
+#define LVB_ENOMEM     (-2)  /* device allocation failed */
+#define LVB_ECAPACITY  (-3)  /* caller's output buffer too small: the needed
+                                size is written to the count argument */
+#define LVB_EDEVICE    (-4)  /* a CUDA call failed */
+#define LVB_ENAN       (-5)  /* a non-finite position or radius was seen */
+#define LVB_EOVERFLOW  (-6)  /* an internal fixed-capacity store overflowed
+                                (cell slots or pair store); list invalid */
+#define LVB_ESTATE     (-7)  /* call not valid in the context's state */
+
+/* Skin policies (Sec. "The local skin parameter" and Sec. Results). */
+#define LVB_SKIN_GLOBAL           0  /* skin = value (uniform; the paper's
+                                        constant-skin comparator) */
+#define LVB_SKIN_DIAMETER_FACTOR  1  /* skin = value * (2 r_i) */
+#define LVB_SKIN_PAPER_KVDT       2  /* skin = (value * |v_i|) * dt with
+                                        value = K, Eq. skin_formulus1 */
+#define LVB_SKIN_LEARNED          3  /* skin proposed by the skin network
+                                        (lvb_mlp.h); needs vel and acc */
+
+/* When the list is updated (Def. autoverlet and its per-particle form). */
+#define LVB_TRIGGER_PARTIAL 0  /* only flagged particles update xref/skin and
+                                  get their rows rebuilt (local buffer) */
+#define LVB_TRIGGER_GLOBAL  1  /* any flag => every particle updates and the
+                                  whole list is rebuilt (Def. autoverlet) */
+#define LVB_TRIGGER_ALWAYS  2  /* every step is a full rebuild ("without
+                                  Verlet buffer" when the skin is 0) */
+
+typedef struct lvb_ctx lvb_ctx;
+
+typedef struct {
+    int32_t kind;        /* LVB_SKIN_* */
+    float value;         /* s_g [m], alpha [-] or K [steps], by kind */
+    float dt;            /* time step for LVB_SKIN_PAPER_KVDT [s] */
+    const void *mlp;     /* LVB_SKIN_LEARNED: device pointer to packed
+                            weights (lvb_mlp.h layout); else NULL */
+} lvb_skin_policy;
+
+typedef struct {
+    float lo[3];         /* box lower corner [m] */
+    float hi[3];         /* box upper corner [m]; hi > lo per axis */
+} lvb_box;
+
+typedef struct {
+    int64_t n;               /* particles */
+    int64_t steps;           /* lvb_step calls completed */
+    int64_t rebuild_steps;   /* steps at which at least one particle updated */
+    int64_t flagged_total;   /* sum over steps of |flagged| */
+    int64_t updated_total;   /* sum over steps of particles whose xref/skin
+                                were updated (= flagged_total in PARTIAL mode) */
+    int64_t last_flagged;    /* |flagged| at the last step */
+    int64_t entries;         /* symmetric list entries (2 x pairs) */
+    int64_t pairs;           /* unordered pairs in the list */
+    int64_t relayouts;       /* row-store re-layouts (a row outgrew its slack) */
+    int64_t cell_capacity;   /* slots per cell */
+    int64_t row_store_capacity; /* entries the row store can hold */
+    float cell_edge;         /* L [m] */
+    float rnl_max;           /* cap H on R_NL = r + skin [m] */
+    int32_t grid[3];         /* cells per axis */
+    int32_t pad;
+} lvb_stats;
+
+/*
+ * lvb_init -- build the context and the first list (Algorithm 1 on the
+ * extended spheres) at the given positions, which become every particle's
+ * reference position.
+ *
+ *   out         : receives the context.
+ *   n           : particles, 1 <= n < 2^31.
+ *   pos_r       : device float4 (x, y, z, r), n records; radii are read
+ *                 here and kept fixed for the life of the context.
+ *   box         : the domain.  Positions outside it are binned into the
+ *                 boundary cells (correct, but slow if many leave it).
+ *   skin        : skin policy.
+ *   trigger     : LVB_TRIGGER_*.
+ *   cell_factor : cell edge L = cell_factor * (largest diameter)
+ *                 * (1 + 2^-7), cell_factor >= 1.  Every skin is capped so
+ *                 that R_NL <= H = L/2 * (1 - 2^-8) (the cap of Eq.
+ *                 skin_formulus_mincell, read as R_NL bounded by half a
+ *                 cell so the 27-cell stencil sees every pair).
+ *   vel         : device float4 velocities, needed by LVB_SKIN_PAPER_KVDT
+ *                 and LVB_SKIN_LEARNED; may be NULL otherwise.
+ *   acc         : device float4 accelerations, needed by LVB_SKIN_LEARNED;
+ *                 may be NULL otherwise.
+ *   stream      : cudaStream_t for all work of this context.
+ * Synchronises the stream.  Errors: EINVAL, ENOMEM, ENAN, EDEVICE.
+ */
+int lvb_init(lvb_ctx **out, int64_t n, const float *pos_r, const lvb_box *box,
+             const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
+             const float *vel, const float *acc, void *stream);
+
+/*
+ * lvb_step -- one step of the automatic Verlet update at the positions
+ * pos_r (same n and radii as at init):
+ *   1. flag every particle whose displacement since its reference position
+ *      exceeds its skin (Eq. update);
+ *   2. update reference position and skin of the flagged particles
+ *      (PARTIAL), of all particles if any is flagged (GLOBAL), or of all
+ *      (ALWAYS);
+ *   3. re-bin the updated particles in the linked-cell grid and rebuild
+ *      exactly the list rows that change.
+ * After the step the list equals the pair set defined above on the current
+ * (xref, skin) of all particles.  vel/acc as for lvb_init.
+ * Enqueues only (no synchronisation).  Errors: EINVAL, EDEVICE; device-side
+ * errors are reported by lvb_sync.
+ */
+int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *acc);
+
+/* lvb_sync -- wait for the context's stream and return the sticky device
+ * error (LVB_OK, LVB_ENAN or LVB_EOVERFLOW). */
+int lvb_sync(lvb_ctx *ctx);
+
+/*
+ * lvb_get_pairs -- the list as a compacted symmetric CSR: row i holds every
+ * j with {i, j} in the list, ascending; row_ptr has n + 1 entries.
+ * cap is the capacity of col.  If the list has more entries than cap,
+ * returns LVB_ECAPACITY with *n_entries set and row_ptr filled.
+ * Synchronises.
+ */
+int lvb_get_pairs(lvb_ctx *ctx, int32_t *row_ptr, int32_t *col, int64_t cap,
+                  int64_t *n_entries);
+
+/* lvb_get_pairs_ij -- the list as unordered pairs i < j, sorted by (i, j).
+ * Same capacity rule as lvb_get_pairs.  Synchronises. */
+int lvb_get_pairs_ij(lvb_ctx *ctx, int32_t *pi, int32_t *pj, int64_t cap,
+                     int64_t *n_pairs);
+
+/*
+ * lvb_get_contacts -- narrow phase (Eq. delta) on the list at positions
+ * pos_r: every pair i < j of the list with delta_ij > 0, sorted by (i, j),
+ * with delta_ij (binary32 formula above).  Same capacity rule.
+ * Synchronises.
+ */
+int lvb_get_contacts(lvb_ctx *ctx, const float *pos_r, int32_t *ci, int32_t *cj,
+                     float *delta, int64_t cap, int64_t *n_contacts);
+
+/* lvb_get_flags -- flags of the last step as a bitmask, bit (i % 32) of
+ * word i / 32; ceil(n/32) words.  *n_flagged = number of set bits.
+ * Synchronises. */
+int lvb_get_flags(lvb_ctx *ctx, uint32_t *bits, int64_t *n_flagged);
+
+/* lvb_get_ref -- per-particle reference state (xref, yref, zref, skin),
+ * n float4 records.  Synchronises. */
+int lvb_get_ref(lvb_ctx *ctx, float *ref4);
+
+/* lvb_stats -- counters and geometry of the context.  Synchronises. */
+int lvb_stats(lvb_ctx *ctx, lvb_stats *out);
+
+/* lvb_set_stream -- move the context to another stream (no copy). */
+int lvb_set_stream(lvb_ctx *ctx, void *stream);
+
+/* lvb_destroy -- free the context (synchronises its stream first). */
+int lvb_destroy(lvb_ctx *ctx);
+
+/* lvb_strerror -- static description of a status code. */
+const char *lvb_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LVB_H */

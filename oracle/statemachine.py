@@ -1,0 +1,78 @@
+"""The automatic Verlet update (Def. autoverlet) as a plain state machine.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Per-particle state is the reference position at the particle's last broad
+phase and its skin, ``ref = (xref, yref, zref, skin)``.  Each step, given the
+current positions (and velocities when the skin policy needs them):
+
+1. flags  F = { p : |x_p - xref_p| > skin_p }           (Eq. update)
+2. reference update, by trigger mode
+   * ``TRIGGER_PARTIAL`` -- only p in F take xref_p = x_p and a fresh skin
+     (the per-particle extension of the scheme; the pair set it yields is
+     still correct by the triangle-inequality argument of Theorem 1,
+     because every unflagged particle is within its skin of its own xref);
+   * ``TRIGGER_GLOBAL``  -- if F is not empty every particle is updated: the
+     paper's scheme, which re-executes the whole broad phase (Def.
+     autoverlet);
+   * ``TRIGGER_ALWAYS``  -- every particle every step: the broad phase
+     "without Verlet buffer" that the paper compares against (Sec. Results).
+3. pair set  P = { i < j : |xref_i - xref_j| <= R_NL,i + R_NL,j }
+   (Def. verletlist / Eq. broad_phase), recomputed from scratch from the
+   stored (xref, skin) -- it depends only on that state, not on history.
+4. contacts  C = { (i, j) in P : delta_ij > 0 }            (Eq. delta)
+
+The skin of a particle is fixed at its own update (reading: the paper's
+K*v*dt rule uses the velocity of the step at which the list is built).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import (SKIN_GLOBAL, SKIN_DIAMETER_FACTOR, SKIN_PAPER_KVDT, SKIN_LEARNED,  # noqa: F401
+               flags as _flags, skin as _skin, pairs as _pairs, contacts as _contacts)
+
+TRIGGER_PARTIAL, TRIGGER_GLOBAL, TRIGGER_ALWAYS = 0, 1, 2
+
+
+class OracleLVB:
+    def __init__(self, pos4, skin_kind, skin_value, dt, H, trigger=TRIGGER_PARTIAL,
+                 vel4=None, proposal=None):
+        pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
+        self.n = len(pos4)
+        self.kind, self.value, self.dt, self.H = int(skin_kind), np.float32(skin_value), \
+            np.float32(dt), np.float32(H)
+        self.trigger = int(trigger)
+        self.rad = pos4[:, 3].copy()
+        self.ref = np.zeros((self.n, 4), dtype=np.float32)
+        self.ref[:, :3] = pos4[:, :3]
+        self.ref[:, 3] = _skin(self.kind, self.value, self.dt, self.H, pos4, vel4, proposal)
+        self.pi, self.pj = _pairs(self.ref, self.rad)
+        self.steps = 0
+        self.updates = 0          # particle reference updates (sum over steps of |U|)
+        self.rebuild_steps = 0    # steps at which at least one reference changed
+
+    def step(self, pos4, vel4=None, proposal=None):
+        """Advance one step; returns (flags, updated) boolean arrays."""
+        pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
+        f = _flags(pos4, self.ref)
+        if self.trigger == TRIGGER_PARTIAL:
+            upd = f.copy()
+        elif self.trigger == TRIGGER_GLOBAL:
+            upd = np.full(self.n, bool(f.any()))
+        else:
+            upd = np.ones(self.n, dtype=bool)
+        if upd.any():
+            idx = np.nonzero(upd)[0]
+            self.ref[idx, :3] = pos4[idx, :3]
+            v = None if vel4 is None else np.ascontiguousarray(vel4, dtype=np.float32)[idx]
+            prop = None if proposal is None else np.asarray(proposal, dtype=np.float32)[idx]
+            self.ref[idx, 3] = _skin(self.kind, self.value, self.dt, self.H, pos4[idx], v, prop)
+            self.pi, self.pj = _pairs(self.ref, self.rad)
+            self.rebuild_steps += 1
+            self.updates += len(idx)
+        self.steps += 1
+        return f, upd
+
+    def contacts(self, pos4):
+        return _contacts(self.pi, self.pj, pos4)
