@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the local Verlet buffer broad phase on one GB300.
+
+Workload: the 200,000-particle polydisperse settling box (radii U[0.5, 2] mm,
+rho 2500, linear spring-dashpot k_n = 1e4, e = 0.7, velocity Verlet
+dt = 1e-6 s, local skin 0.1 d_i, cell edge 1.25 d_max), run through the
+library's DEM driver.  A "step" is one DEM step: integrate, broad phase
+(displacement check + partial rebuild), narrow phase and forces.  The L2
+cache (129 MB) is flushed with a 256 MB write before every timed step, and
+each phase is bracketed by CUDA events on the stream it runs on.
+
+value    = broad-phase particle-steps/s = N * K / (sum of broad-phase times)
+e2e      = the same metric through the C-ABI with host buffers: per step the
+           positions are copied from pinned host memory, lvb_step runs, and
+           the step's flags are read back (all inside the timed region)
+roofline = the dominant kernel's algorithmic bytes / its event-timed
+           duration, against the measured HBM copy bandwidth
+cpu_baseline = the CPU oracle on a bounded sample of the same scene
+
+`--impl reference` times the CPU oracle alone (the reference arm).
+Multi-GPU (torchrun): every rank runs its own replica of the scene (weak
+scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "broad-phase particle-steps/s and % HBM roofline; rebuild fraction; vs global buffer"
+WORKLOAD = ("settling box: 200,000 polydisperse spheres r~U[0.5,2] mm, rho 2500, LSD k_n 1e4 "
+            "e 0.7, velocity Verlet dt 1e-6 s, local skin 0.1 d_i, cell 1.25 d_max")
+L2_FLUSH_BYTES = 256 << 20
+T0_SAMPLE = 10_000        # oracle samples start mid-run (step 10,000 of 20,000)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _scene(rank):
+    from paper_2208_13770_gb300 import scenes
+    return scenes.settling(seed=scenes.SEED_BASE + 1 + rank)
+
+
+def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, flush,
+             record=None):
+    """Runs warmup + steps DEM steps with per-phase CUDA events.  Returns
+    per-phase total ms, stats and the (optional) recorded window."""
+    dem = lvb.DEM(scene, trigger=trigger, skin_kind=skin_kind, skin_value=skin_value)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        dem.step()
+    torch.cuda.synchronize()
+    st0 = dem.lvb.stats()
+    tot = np.zeros(3)
+    batch = 256
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(batch)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    rec = None
+    if record is not None:
+        start, m = record
+        rec = {"pos": torch.empty((m, scene.n, 4), dtype=torch.float32, pin_memory=True),
+               "start": start, "m": m}
+        dpos = dem.device_pos_tensor(torch)
+    t_all0.record(stream)
+    done = 0
+    while done < steps:
+        nb = min(batch, steps - done)
+        for b in range(nb):
+            k = done + b
+            if rec is not None and k == rec["start"]:
+                torch.cuda.synchronize()
+                rec["ref"] = dem.lvb.ref()
+                rec["pos0"] = dem.state()[0]
+            flush.zero_()
+            e = evs[b]
+            e[0].record(stream)
+            dem.phase(lvb.DEM_PHASE_INTEGRATE)
+            e[1].record(stream)
+            dem.phase(lvb.DEM_PHASE_BROAD)
+            e[2].record(stream)
+            dem.phase(lvb.DEM_PHASE_FORCES)
+            e[3].record(stream)
+            if rec is not None and rec["start"] <= k < rec["start"] + rec["m"]:
+                rec["pos"][k - rec["start"]].copy_(dpos, non_blocking=True)
+        torch.cuda.synchronize()
+        for b in range(nb):
+            e = evs[b]
+            tot += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+        done += nb
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    wall_ms = t_all0.elapsed_time(t_all1)
+    rc = dem.sync()
+    if rc != 0:
+        raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
+    st1 = dem.lvb.stats()
+    out = {"phase_ms": tot, "wall_ms": wall_ms, "stats0": st0, "stats1": st1, "rec": rec}
+    dem.close()
+    return out
+
+
+def _e2e(lvb, torch, scene, rec):
+    """Broad phase through the C-ABI with host buffers: per step a pinned
+    host -> device copy of the positions, lvb_step, and a device -> host
+    read of the flags (lvb_get_flags synchronises)."""
+    dev = torch.empty((scene.n, 4), dtype=torch.float32, device="cuda")
+    ref = torch.from_numpy(rec["ref"]).cuda()
+    dev.copy_(torch.from_numpy(rec["pos0"]))
+    ctx = lvb.LVB(dev, scene.lo, scene.hi, scene.skin_kind, scene.skin_value, scene.dt,
+                  lvb.LVB_TRIGGER_PARTIAL, scene.cell_factor, ref=ref)
+    m = rec["m"]
+    words = np.zeros((scene.n + 31) // 32, dtype=np.uint32)
+    nf = lvb.ctypes.c_int64(0)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    flagged = 0
+    for k in range(m):
+        dev.copy_(rec["pos"][k], non_blocking=True)
+        ctx.step(dev)
+        rc = lvb.lvb_get_flags(ctx.ctx, words.ctypes.data, lvb.ctypes.byref(nf))
+        if rc:
+            raise RuntimeError(lvb.lvb_strerror(rc))
+        flagged += nf.value
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return {"value": scene.n * m / dt, "unit": "particle-steps/s",
+            "h2d_bytes_per_step": scene.n * 16, "d2h_bytes_per_step": words.nbytes + 8,
+            "steps": m, "flagged": int(flagged)}
+
+
+def _oracle_sample(scene, t0_steps, m_steps, n_sub=None, time_budget=None, stride=10):
+    """Times the CPU oracle's broad phase (flags, reference update, pair set
+    by Algorithm 1) on a bounded sample of the scene: the n_sub lowest
+    particles, moving in free fall (the settling cloud is dilute, so free
+    fall is its motion between rare contacts), from step t0 for m steps.
+    The reference state at t0 is prepared (untimed) by the oracle's own
+    flag/skin updates every `stride` steps from step 0, without list builds."""
+    import oracle
+    from oracle.statemachine import OracleLVB
+    pos0 = scene.pos
+    if n_sub is not None and n_sub < scene.n:
+        idx = np.argsort(pos0[:, 2], kind="stable")[:n_sub]
+        idx.sort()
+    else:
+        idx = np.arange(scene.n)
+    p0 = pos0[idx].astype(np.float64)
+    v0 = scene.vel[idx].astype(np.float64)
+    g = np.asarray(scene.gravity, dtype=np.float64)
+    dt = scene.dt
+
+    def at(step):
+        t = step * dt
+        out = np.empty((len(idx), 4), dtype=np.float32)
+        out[:, :3] = p0[:, :3] + v0[:, :3] * t + 0.5 * g * t * t
+        out[:, 3] = p0[:, 3]
+        return out
+
+    rmax = float(np.float32(scene.pos[:, 3].max()))
+    L = scene.cell_factor * 2.0 * rmax * (1 + 2 ** -7)
+    H = np.float32(0.5 * L * (1 - 2 ** -8))
+    first = at(0)
+    ref = first.copy()
+    ref[:, 3] = oracle.skin(scene.skin_kind, scene.skin_value, dt, H, first)
+    for k in list(range(stride, t0_steps, stride)) + [t0_steps]:   # fast-forward
+        p = at(k)
+        f = oracle.flags(p, ref)
+        if f.any():
+            ref[f, :3] = p[f, :3]
+            ref[f, 3] = oracle.skin(scene.skin_kind, scene.skin_value, dt, H, p[f])
+    sm = OracleLVB(at(t0_steps), scene.skin_kind, scene.skin_value, dt, H, ref4=ref)
+    snaps = [at(t0_steps + 1 + k) for k in range(m_steps)]
+    t = time.perf_counter()
+    done = 0
+    for p in snaps:
+        sm.step(p)
+        done += 1
+        if time_budget is not None and time.perf_counter() - t > time_budget:
+            break
+    el = time.perf_counter() - t
+    return {"value": len(idx) * done / el, "particles": int(len(idx)), "steps": done,
+            "seconds": el, "updates": int(sm.updates), "rebuild_steps": int(sm.rebuild_steps)}
+
+
+def _cpu_info():
+    model = "unknown"
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "arch": os.uname().machine}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return 0
+    scene = _scene(0)
+    # size the per-step sample so that warmup + steps fit in ~150 s
+    probe = _oracle_sample(scene, T0_SAMPLE, 3, n_sub=20_000)
+    per_particle = 1.0 / probe["value"]
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n_sub = int(max(1000, min(scene.n, budget / per_particle)))
+    res = _oracle_sample(scene, T0_SAMPLE, args.steps + args.warmup, n_sub=n_sub)
+    v = res["value"]
+    sample = ("oracle broad phase (flags, skins, pair set by linked cells) on the %d lowest "
+              "particles of the settling box in free fall, steps %d..%d" %
+              (res["particles"], T0_SAMPLE + 1, T0_SAMPLE + res["steps"]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * res["seconds"] / max(1, res["steps"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": scene.n},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": sample, "host": _cpu_info()},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_native(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2208_13770_gb300 import lvb
+    hbm_peak, peak_kind = _peaks()
+    scene = _scene(rank)
+    n = scene.n
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    m_e2e = min(args.e2e_steps, args.steps)
+    rec_start = max(0, args.steps // 2 - m_e2e // 2)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        loc = _run_dem(lvb, torch, scene, lvb.LVB_TRIGGER_PARTIAL, scene.skin_kind,
+                       scene.skin_value, args.steps, args.warmup, flush,
+                       record=(rec_start, m_e2e))
+    torch.cuda.synchronize()
+    bp_ms = float(loc["phase_ms"][1])
+    if world > 1:
+        t = torch.tensor([bp_ms, float(loc["phase_ms"].sum())], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        bp_ms, step_ms_tot = float(t[0]), float(t[1])
+    else:
+        step_ms_tot = float(loc["phase_ms"].sum())
+    value = world * n * args.steps / (bp_ms * 1e-3)
+
+    # global-buffer variant: uniform skin 0.1 * mean diameter, any flag
+    # rebuilds the whole list (Def. autoverlet)
+    dmean = float(2.0 * scene.pos[:, 3].astype(np.float64).mean())
+    glob = _run_dem(lvb, torch, scene, lvb.LVB_TRIGGER_GLOBAL, lvb.LVB_SKIN_GLOBAL,
+                    0.1 * dmean, args.steps, args.warmup, flush)
+    g_bp_ms = float(glob["phase_ms"][1])
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return 0
+
+    e2e = _e2e(lvb, torch, scene, loc["rec"])
+    e2e["value"] *= world
+
+    s0, s1 = loc["stats0"], loc["stats1"]
+    flagged = s1["flagged_total"] - s0["flagged_total"]
+    upd = s1["updated_total"] - s0["updated_total"]
+    gs0, gs1 = glob["stats0"], glob["stats1"]
+    g_rebuild_steps = gs1["rebuild_steps"] - gs0["rebuild_steps"]
+    entries = s1["entries"]
+    row_len = entries / n
+    K = args.steps
+    ph = loc["phase_ms"] / K
+    # algorithmic bytes per step (one launch each of the phase kernels)
+    F = flagged / K
+    bytes_bp = 32.0 * n + n / 8.0 + F * (64.0 + 8.0 * row_len)
+    bytes_forces = n * (16.0 * 4 + 12.0 + 32.0) + 4.0 * entries
+    bytes_integrate = n * (16.0 * 4 + 32.0)
+    kern = {"k_forces (narrow phase + forces)": (ph[2], bytes_forces),
+            "k_integrate": (ph[0], bytes_integrate),
+            "broad phase (check + partial rebuild, %d launches)" % s1["launches_per_step"]:
+                (ph[1], bytes_bp)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    t_ms, b = kern[dom]
+    achieved = b / (t_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": None, "bytes_per_launch": b, "ms_per_launch": t_ms}
+    bp_ach = bytes_bp / (ph[1] * 1e-3) / 1e9
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        res = _oracle_sample(scene, T0_SAMPLE, 60, time_budget=25.0)
+        cpu = {"value": res["value"], "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle broad phase on all %d particles in free fall, steps "
+                         "%d..%d (%.1f s); reference state fast-forwarded by the oracle"
+                         % (res["particles"], T0_SAMPLE + 1, T0_SAMPLE + res["steps"],
+                            res["seconds"]),
+               "host": _cpu_info()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": step_ms_tot / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "dt": scene.dt, "skin": "0.1 d_i",
+                   "trigger": "partial (local buffer)", "l2": "flushed before every timed step "
+                   "(256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "broad_phase": {"ms_per_step": ph[1], "achieved_gbs": bp_ach,
+                        "frac_hbm": bp_ach / hbm_peak, "bytes_per_step": bytes_bp},
+        "phases_ms_per_step": {"integrate": ph[0], "broad": ph[1], "forces": ph[2]},
+        "full_step_particle_steps_per_s": world * n * K / (step_ms_tot * 1e-3),
+        "rebuild_fraction": upd / (n * K),
+        "flagged_per_step": F,
+        "global_buffer": {"value": world * n * K / (g_bp_ms * 1e-3),
+                          "rebuild_step_fraction": g_rebuild_steps / K,
+                          "skin": "uniform 0.1 * mean diameter = %.3g m" % (0.1 * dmean),
+                          "ms_per_step": float(glob["phase_ms"].sum()) / K},
+        "speedup_vs_global": g_bp_ms / bp_ms,
+        "list": {"entries": entries, "mean_row": row_len, "relayouts": s1["relayouts"]},
+        "e2e": e2e,
+        "gpu_launches": K * (2 + s1["launches_per_step"]),
+        "clocks": clk.summary(),
+        "timed_region_ms_incl_flush": loc["wall_ms"],
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

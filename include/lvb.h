@@ -13,8 +13,8 @@
  *     acc   : (ax, ay, az, unused)  acceleration [m/s^2]
  *   n records each, particle i at float offset 4*i.
  * - Output buffers of the lvb_get_* / dem_get_* calls may be host or device
- *   memory; the library detects which (cudaPointerGetAttributes) and copies
- *   into them.  The caller owns every buffer it passes; the library never
+ *   memory: the library copies into them with cudaMemcpyDefault (unified
+ *   addressing tells the two apart).  The caller owns every buffer it passes; the library never
  *   keeps a caller pointer beyond the call.
  * - All work is enqueued on the context's CUDA stream (`void* stream` is a
  *   cudaStream_t; NULL is the legacy default stream).  Calls that only
@@ -103,11 +103,17 @@ typedef struct {
     int64_t relayouts;       /* row-store re-layouts (a row outgrew its slack) */
     int64_t cell_capacity;   /* slots per cell */
     int64_t row_store_capacity; /* entries the row store can hold */
+    int64_t kernels_executed;  /* kernels of this context run on the device
+                                  (including the DEM driver's, if any) */
+    int64_t small_path_steps;  /* steps whose rebuild ran in one block */
+    int64_t small_max;       /* flagged counts up to this use the one-block
+                                rebuild (LVB_OPT_SMALL_MAX) */
+    int64_t graphs;          /* 1 if steps replay a CUDA graph */
     float cell_edge;         /* L [m] */
     float rnl_max;           /* cap H on R_NL = r + skin [m] */
     int32_t grid[3];         /* cells per axis */
     int32_t pad;
-} lvb_stats;
+} lvb_stats_t;
 
 /*
  * lvb_init -- build the context and the first list (Algorithm 1 on the
@@ -139,6 +145,20 @@ int lvb_init(lvb_ctx **out, int64_t n, const float *pos_r, const lvb_box *box,
              const float *vel, const float *acc, void *stream);
 
 /*
+ * lvb_init_resume -- as lvb_init, but every particle's reference state is
+ * taken from ref4 (device float4 (xref, yref, zref, skin), n records, e.g.
+ * saved by lvb_get_ref) instead of being set from pos_r and the policy;
+ * pos_r still supplies the radii.  The list is built on those references,
+ * so a run resumes exactly where the saved context stood (the list is a
+ * function of the reference state alone, Def. verletlist).  Each skin must
+ * be finite, >= 0 and within the cap max(0, H - r) of the new context, else
+ * LVB_EINVAL.
+ */
+int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *ref4,
+                    const lvb_box *box, const lvb_skin_policy *skin, int32_t trigger,
+                    float cell_factor, const float *vel, const float *acc, void *stream);
+
+/*
  * lvb_step -- one step of the automatic Verlet update at the positions
  * pos_r (same n and radii as at init):
  *   1. flag every particle whose displacement since its reference position
@@ -154,6 +174,19 @@ int lvb_init(lvb_ctx **out, int64_t n, const float *pos_r, const lvb_box *box,
  * errors are reported by lvb_sync.
  */
 int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *acc);
+
+/* Options of lvb_set_option. */
+#define LVB_OPT_GRAPH     0  /* 1 (default): each lvb_step replays a CUDA graph
+                                whose conditional nodes skip the rebuild work
+                                a step does not need; 0: direct launches.  A
+                                call made while the stream is being captured
+                                always launches directly. */
+#define LVB_OPT_SMALL_MAX 1  /* steps with at most this many flagged particles
+                                (default 128) rebuild in a single block */
+
+/* lvb_set_option -- set an LVB_OPT_* value (synchronises if a cached graph
+ * has to be rebuilt).  Errors: EINVAL. */
+int lvb_set_option(lvb_ctx *ctx, int32_t option, int64_t value);
 
 /* lvb_sync -- wait for the context's stream and return the sticky device
  * error (LVB_OK, LVB_ENAN or LVB_EOVERFLOW). */
@@ -193,7 +226,7 @@ int lvb_get_flags(lvb_ctx *ctx, uint32_t *bits, int64_t *n_flagged);
 int lvb_get_ref(lvb_ctx *ctx, float *ref4);
 
 /* lvb_stats -- counters and geometry of the context.  Synchronises. */
-int lvb_stats(lvb_ctx *ctx, lvb_stats *out);
+int lvb_stats(lvb_ctx *ctx, lvb_stats_t *out);
 
 /* lvb_set_stream -- move the context to another stream (no copy). */
 int lvb_set_stream(lvb_ctx *ctx, void *stream);

@@ -1,0 +1,115 @@
+/*
+ * lvb_dem.h -- C-ABI of the DEM driver that runs on top of the local Verlet
+ * buffer broad phase (lvb.h): velocity Verlet integration and a normal-only
+ * linear spring-dashpot contact law, with the contact search on the list.
+ *
+ * The paper's runs use velocity Verlet and a linear spring-dashpot model
+ * (Sec. Methodology); the loop is its XDEM flow chart with the list-validity
+ * gate before the broad phase (Sec. "XDEM flow chart", Fig.
+ * xdemw_flow_chart): integrate, broad phase (skipped per particle while its
+ * list rows stay valid), narrow phase on the list, forces, integrate.
+ *
+ * One step, with state (x, v, a) on the device (binary32):
+ *   x'  = x + v dt + a dt^2 / 2            (positions; then the broad phase
+ *   v*  = v + a dt                           runs at x', with v* as the
+ *                                            velocity seen by the skin rule)
+ *   F   = sum over list partners j with delta_ij > 0 of
+ *         (k_n delta_ij - gamma_ij v_n,ij) n_ij, plus walls
+ *         delta_ij = r_i + r_j - |x'_i - x'_j|   (Eq. delta; evaluated with
+ *                    compensated binary32 arithmetic, error ~1e-16 m)
+ *         n_ij = (x'_i - x'_j)/|x'_i - x'_j|, v_n,ij = (v*_i - v*_j) . n_ij
+ *         gamma_ij = 2 zeta sqrt(m_eff k_n), zeta = -ln e / sqrt(pi^2+ln^2 e),
+ *         m_eff = m_i m_j / (m_i + m_j), m = rho 4/3 pi r^3
+ *   a'  = F/m + g,   v' = v + (a + a') dt / 2
+ * Walls use the same law with m_eff = m_i: box planes (wall_kind 1), a drum
+ * of radius R about the y axis through (drum_cx, drum_cz) with end caps at
+ * the box's y planes (kind 2; the wall moves tangentially, which a normal-
+ * only law does not see), or specular reflection at the box planes (kind 3,
+ * meant for runs without contacts or gravity).
+ *
+ * Pointers follow lvb.h: device float4 records in, host or device buffers
+ * out, errors as LVB_* codes.
+ */
+#ifndef LVB_DEM_H
+#define LVB_DEM_H
+
+#include <stdint.h>
+
+#include "lvb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DEM_WALL_NONE     0
+#define DEM_WALL_BOX      1
+#define DEM_WALL_DRUM     2
+#define DEM_WALL_SPECULAR 3
+
+typedef struct {
+    float kn;             /* normal stiffness [N/m] */
+    float restitution;    /* e in (0, 1] */
+    float rho;            /* density [kg/m^3] */
+    float g[3];           /* gravity [m/s^2] */
+    int32_t wall_kind;    /* DEM_WALL_* */
+    int32_t clamp_tensile;/* 1: a negative (attractive) normal force is set to 0 */
+    float drum_cx, drum_cz, drum_R, drum_omega;
+    int32_t contacts_on;  /* 0: particles do not interact (ballistic runs) */
+    int32_t pad;
+} dem_params;
+
+typedef struct dem_ctx dem_ctx;
+
+/* Phases of one step, for callers that time them separately. */
+#define DEM_PHASE_INTEGRATE 0   /* x', v* */
+#define DEM_PHASE_BROAD     1   /* lvb_step at x' (check + partial rebuild) */
+#define DEM_PHASE_FORCES    2   /* narrow phase on the list, forces, a', v' */
+
+/*
+ * dem_init -- copy the initial state into library-owned device memory, build
+ * the broad phase (lvb_init) at x0 and evaluate a0 = F(x0, v0)/m + g.
+ *   pos_r, vel : device float4 (x, y, z, r) and (vx, vy, vz, -), n records.
+ *   prm        : physics; dt > 0 the time step [s].
+ *   box, skin, trigger, cell_factor : as lvb_init.
+ * Synchronises.  Errors: EINVAL, ENOMEM, ENAN, EDEVICE.
+ */
+int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
+             const dem_params *prm, float dt, const lvb_box *box,
+             const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
+             void *stream);
+
+/* dem_advance -- enqueue `steps` full steps (no synchronisation).  Chunks of
+ * steps are replayed from a CUDA graph captured on first use. */
+int dem_advance(dem_ctx *ctx, int64_t steps);
+
+/* dem_phase -- enqueue one phase (DEM_PHASE_*) of a step; a step is the
+ * three phases in order. */
+int dem_phase(dem_ctx *ctx, int32_t phase);
+
+/* dem_get_state -- copy out x (pos_r, with radii), v, a and v* (float4
+ * records; any pointer may be NULL).  Synchronises. */
+int dem_get_state(dem_ctx *ctx, float *pos_r, float *vel, float *acc, float *vstar);
+
+/* dem_set_state -- overwrite x, v, a (host or device float4 records; radii
+ * in pos_r must equal the initial ones).  The broad phase keeps its
+ * reference state, so the next step's check sees the new positions. */
+int dem_set_state(dem_ctx *ctx, const float *pos_r, const float *vel, const float *acc);
+
+/* dem_lvb -- the broad-phase context the driver owns (valid until
+ * dem_destroy), for lvb_get_* and lvb_stats. */
+int dem_lvb(dem_ctx *ctx, lvb_ctx **out);
+
+/* dem_device_state -- device pointers of the state arrays (float4 records),
+ * owned by the context; for callers that read them in place. */
+int dem_device_state(dem_ctx *ctx, float **pos_r, float **vel, float **acc, float **vstar);
+
+/* dem_sync -- wait for the stream; returns the broad phase's sticky error. */
+int dem_sync(dem_ctx *ctx);
+
+int dem_destroy(dem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LVB_DEM_H */

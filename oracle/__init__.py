@@ -81,10 +81,10 @@ def _configure(L):
             f.restype = i64
         L.orc_dem_forces.argtypes = [i64, p, p, ctypes.POINTER(DemParams), p]
         L.orc_dem_forces.restype = ctypes.c_int
-        L.orc_dem_forces64.argtypes = [i64, p, p, p, ctypes.POINTER(DemParams), p]
+        L.orc_dem_forces64.argtypes = [i64, p, p, p, ctypes.POINTER(DemParams), p, p]
         L.orc_dem_forces64.restype = ctypes.c_int
         L.orc_dem_step64.argtypes = [i64, p, p, p, p, ctypes.c_double,
-                                     ctypes.POINTER(DemParams), p, p, p, p, p, p]
+                                     ctypes.POINTER(DemParams), p, p, p, p, p, p, p]
         L.orc_dem_step64.restype = ctypes.c_int
         L.orc_improvement_pct.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_improvement_pct.restype = ctypes.c_double
@@ -258,28 +258,30 @@ def _d3(a):
     return None if a is None else np.ascontiguousarray(np.asarray(a)[:, :3], dtype=np.float64)
 
 
-def dem_step64(x, v, a, r, dt, P, xf=None, vf=None):
+def dem_step64(x, v, a, r, dt, P, xf=None, vf=None, with_fmag=False):
     """One velocity-Verlet step on a binary64 state (x, v, a: (n, 3); r: (n,)).
     xf / vf replace x' / v* as the state at which forces are evaluated.
-    Returns (x', v*, a', v'), each (n, 3) binary64."""
+    Returns (x', v*, a', v'), each (n, 3) binary64, plus the per-particle
+    scale of the summed force terms when with_fmag."""
     x, v, a, xf, vf = _d3(x), _d3(v), _d3(a), _d3(xf), _d3(vf)
     r = np.ascontiguousarray(r, dtype=np.float64)
     n = len(x)
     outs = [np.zeros((n, 3), dtype=np.float64) for _ in range(4)]
+    fmag = np.zeros(n, dtype=np.float64) if with_fmag else None
     rc = lib().orc_dem_step64(n, _ptr(x), _ptr(v), _ptr(a), _ptr(r), float(dt), ctypes.byref(P),
-                              _ptr(xf), _ptr(vf), *[_ptr(o) for o in outs])
+                              _ptr(xf), _ptr(vf), *[_ptr(o) for o in outs], _ptr(fmag))
     if rc != 0:
         raise MemoryError("oracle step failed")
-    return tuple(outs)
+    return tuple(outs) + ((fmag,) if with_fmag else ())
 
 
-def dem_step(x4, v4, a4, dt, P, x_in=None, vstar_in=None):
+def dem_step(x4, v4, a4, dt, P, x_in=None, vstar_in=None, with_fmag=False):
     """One step from the binary32 state (float4 records) of the code under
-    test, widened exactly.  Returns (x', v*, a', v') in binary64."""
+    test, widened exactly.  Returns (x', v*, a', v'[, fmag]) in binary64."""
     x4, v4, a4 = _f32x4(x4), _f32x4(v4), _f32x4(a4)
     return dem_step64(x4, v4, a4, x4[:, 3], dt, P,
                       None if x_in is None else _f32x4(x_in),
-                      None if vstar_in is None else _f32x4(vstar_in))
+                      None if vstar_in is None else _f32x4(vstar_in), with_fmag=with_fmag)
 
 
 def improvement_pct(t_without, t_case):

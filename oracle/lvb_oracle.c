@@ -470,9 +470,10 @@ static double lsd_force(const orc_dem_params *P, double dl, double vn, double me
  * far above the binary32 rounding of any position.
  * force: 3n doubles (contact + wall forces, no gravity). */
 ORC_API int orc_dem_forces64(int64_t n, const double *x, const double *r, const double *v,
-                             const orc_dem_params *P, double *force)
+                             const orc_dem_params *P, double *force, double *fmag)
 {
     memset(force, 0, (size_t)n * 3 * sizeof(double));
+    if (fmag) memset(fmag, 0, (size_t)n * sizeof(double));
     if (P->contacts_on && n > 1) {
         float *ref = (float *)malloc((size_t)n * 4 * sizeof(float));
         float *rad = (float *)malloc((size_t)n * sizeof(float));
@@ -518,6 +519,11 @@ ORC_API int orc_dem_forces64(int64_t n, const double *x, const double *r, const 
                 force[3 * i + c] += f * nrm[c];
                 force[3 * j + c] -= f * nrm[c];
             }
+            if (fmag) {   /* scale of the terms summed into F_i, F_j */
+                double sc = fabs(P->kn * dl) + fabs(f - P->kn * dl);
+                fmag[i] += sc;
+                fmag[j] += sc;
+            }
         }
         free(ci); free(cj);
     }
@@ -531,9 +537,17 @@ ORC_API int orc_dem_forces64(int64_t n, const double *x, const double *r, const 
                 double xc = x[3 * i + c];
                 double vc = v[3 * i + c];
                 double dlo = ri - (xc - P->lo[c]);     /* lower plane, normal +e_c */
-                if (dlo > 0.0) force[3 * i + c] += lsd_force(P, dlo, vc, m);
+                if (dlo > 0.0) {
+                    double f = lsd_force(P, dlo, vc, m);
+                    force[3 * i + c] += f;
+                    if (fmag) fmag[i] += fabs(P->kn * dlo) + fabs(f - P->kn * dlo);
+                }
                 double dhi = ri - (P->hi[c] - xc);     /* upper plane, normal -e_c */
-                if (dhi > 0.0) force[3 * i + c] -= lsd_force(P, dhi, -vc, m);
+                if (dhi > 0.0) {
+                    double f = lsd_force(P, dhi, -vc, m);
+                    force[3 * i + c] -= f;
+                    if (fmag) fmag[i] += fabs(P->kn * dhi) + fabs(f - P->kn * dhi);
+                }
             }
             if (P->wall_kind == 2) {
                 double ex = x[3 * i + 0] - P->drum_center[0];
@@ -547,6 +561,7 @@ ORC_API int orc_dem_forces64(int64_t n, const double *x, const double *r, const 
                     double f = lsd_force(P, dl, vn, m);
                     force[3 * i + 0] += f * nx;
                     force[3 * i + 2] += f * nz;
+                    if (fmag) fmag[i] += fabs(P->kn * dl) + fabs(f - P->kn * dl);
                 }
             }
         }
@@ -569,7 +584,7 @@ ORC_API int orc_dem_forces(int64_t n, const float *x4, const float *v4,
         }
         r[i] = x4[4 * i + 3];
     }
-    int rc = orc_dem_forces64(n, x, r, v, P, force);
+    int rc = orc_dem_forces64(n, x, r, v, P, force, NULL);
     free(x); free(v); free(r);
     return rc;
 }
@@ -581,15 +596,20 @@ ORC_API int orc_dem_forces(int64_t n, const float *x4, const float *v4,
  *   a' = F(x', v*)/m + g,         v' = v + (a + a') dt / 2.
  * With wall_kind 3 (specular box, meant for runs without contacts or
  * gravity) a coordinate that left [lo + r, hi - r] is mirrored back and its
- * velocity component negated.
+ * velocity components v' and v* are negated (v* is the velocity the
+ * particle has at its new, mirrored position).
  * xf / vf, when given (3n each), replace x' and v* as the state at which
  * forces are evaluated (the oracle "fed" the state of the code under test,
  * so that trajectories cannot drift apart).
- * All arrays are binary64, 3n (r: n). */
+ * fmag (n, optional): per particle, the sum over its contacts of
+ * |k_n delta| + |damping term| -- the scale of the terms summed into F,
+ * against which a binary32 evaluation's rounding is judged.
+ * All arrays are binary64, 3n (r, fmag: n). */
 ORC_API int orc_dem_step64(int64_t n, const double *x, const double *v, const double *a,
                            const double *r, double dt, const orc_dem_params *P,
                            const double *xf, const double *vf,
-                           double *x_out, double *vstar_out, double *a_out, double *v_out)
+                           double *x_out, double *vstar_out, double *a_out, double *v_out,
+                           double *fmag)
 {
     for (int64_t k = 0; k < 3 * n; ++k) {
         x_out[k] = x[k] + v[k] * dt + 0.5 * a[k] * dt * dt;
@@ -597,7 +617,7 @@ ORC_API int orc_dem_step64(int64_t n, const double *x, const double *v, const do
     }
     double *F = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     if (!F) return -1;
-    int rc = orc_dem_forces64(n, xf ? xf : x_out, r, vf ? vf : vstar_out, P, F);
+    int rc = orc_dem_forces64(n, xf ? xf : x_out, r, vf ? vf : vstar_out, P, F, fmag);
     if (rc != 0) { free(F); return rc; }
     for (int64_t i = 0; i < n; ++i) {
         double m = mass_of(r[i], P->rho);
@@ -612,8 +632,11 @@ ORC_API int orc_dem_step64(int64_t n, const double *x, const double *v, const do
             for (int c = 0; c < 3; ++c) {
                 double lo = P->lo[c] + r[i], hi = P->hi[c] - r[i];
                 double xc = x_out[3 * i + c];
-                if (xc < lo) { x_out[3 * i + c] = 2.0 * lo - xc; v_out[3 * i + c] = -v_out[3 * i + c]; }
-                else if (xc > hi) { x_out[3 * i + c] = 2.0 * hi - xc; v_out[3 * i + c] = -v_out[3 * i + c]; }
+                if (xc < lo || xc > hi) {
+                    x_out[3 * i + c] = 2.0 * (xc < lo ? lo : hi) - xc;
+                    v_out[3 * i + c] = -v_out[3 * i + c];
+                    vstar_out[3 * i + c] = -vstar_out[3 * i + c];
+                }
             }
         }
     }

@@ -37,16 +37,19 @@ TRIGGER_PARTIAL, TRIGGER_GLOBAL, TRIGGER_ALWAYS = 0, 1, 2
 
 class OracleLVB:
     def __init__(self, pos4, skin_kind, skin_value, dt, H, trigger=TRIGGER_PARTIAL,
-                 vel4=None, proposal=None):
+                 vel4=None, proposal=None, ref4=None):
         pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
         self.n = len(pos4)
         self.kind, self.value, self.dt, self.H = int(skin_kind), np.float32(skin_value), \
             np.float32(dt), np.float32(H)
         self.trigger = int(trigger)
         self.rad = pos4[:, 3].copy()
-        self.ref = np.zeros((self.n, 4), dtype=np.float32)
-        self.ref[:, :3] = pos4[:, :3]
-        self.ref[:, 3] = _skin(self.kind, self.value, self.dt, self.H, pos4, vel4, proposal)
+        if ref4 is not None:      # resume from a saved reference state
+            self.ref = np.array(ref4, dtype=np.float32, copy=True)
+        else:
+            self.ref = np.zeros((self.n, 4), dtype=np.float32)
+            self.ref[:, :3] = pos4[:, :3]
+            self.ref[:, 3] = _skin(self.kind, self.value, self.dt, self.H, pos4, vel4, proposal)
         self.pi, self.pj = _pairs(self.ref, self.rad)
         self.steps = 0
         self.updates = 0          # particle reference updates (sum over steps of |U|)

@@ -1,0 +1,448 @@
+// lvb_dem.cu -- DEM driver on the local Verlet buffer list (include/lvb_dem.h).
+//
+// Per step: k_integrate (x', v*), lvb_step at x' (displacement check and
+// partial rebuild), k_forces (narrow phase on the list rows, linear
+// spring-dashpot, walls, a', v').  Forces are accumulated per row of the
+// symmetric list, so each pair is evaluated once from each side and no
+// atomics are needed; both evaluations give exactly opposite forces.
+//
+// The overlap delta = r_i + r_j - |x_i - x_j| is a small difference of large
+// numbers: at 0.3 m coordinates a binary32 position carries ~3e-8 m of
+// rounding while a resting overlap under k_n = 1e4 N/m is ~1e-8 m.  So the
+// distance is evaluated exactly-rounded-ish in compensated binary32
+// (error-free TwoSum / TwoProduct transformations, Knuth and Dekker), which
+// brings its error to ~1e-16 m at the cost of ~30 FP32 operations per
+// contact -- far cheaper on this part than binary64.
+#include "lvb_internal.cuh"
+#include "lvb_dem.h"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+using namespace lvb;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNumSMs = 152;
+
+struct DemDev {
+    int n;
+    float dt, half_dt, half_dt2;
+    float kn, two_zeta, g[3];
+    int wall_kind, clamp_tensile, contacts_on;
+    float lo[3], hi[3];
+    float drum_cx, drum_cz, drum_R;
+    float4 *pos, *vel, *acc, *vstar;   // vstar.w = 1 / m
+    RowsView rows;
+};
+
+// exact a - b = s + e (TwoSum on a and -b)
+__device__ __forceinline__ void two_diff(float a, float b, float &s, float &e)
+{
+    s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
+}
+
+// exact a + b = s + e
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// |h + l| for a 3-vector given as high + low parts: returns s0 (rounded
+// sqrt of the leading sum) and corr with |h + l| = s0 + corr to ~2^-46.
+__device__ __forceinline__ void norm_dd(const float h[3], const float l[3], float &s0, float &corr)
+{
+    float p0 = __fmul_rn(h[0], h[0]), p1 = __fmul_rn(h[1], h[1]), p2 = __fmul_rn(h[2], h[2]);
+    float e0 = fmaf(h[0], h[0], -p0), e1 = fmaf(h[1], h[1], -p1), e2 = fmaf(h[2], h[2], -p2);
+    float s, t, u, w;
+    two_sum(p0, p1, s, t);
+    two_sum(s, p2, u, w);
+    float lo = t + w + (e0 + e1 + e2) +
+               2.0f * (h[0] * l[0] + h[1] * l[1] + h[2] * l[2]);
+    s0 = __fsqrt_rn(u);
+    const float rem = fmaf(-s0, s0, u) + lo;     // fma remainder is exact
+    corr = s0 > 0.0f ? rem / (2.0f * s0) : 0.0f;
+}
+
+__device__ __forceinline__ float lsd(const DemDev &d, float dl, float vn, float meff)
+{
+    const float gam = d.two_zeta * sqrtf(meff * d.kn);
+    float f = d.kn * dl - gam * vn;
+    if (d.clamp_tensile && f < 0.0f) f = 0.0f;
+    return f;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_integrate(DemDev d)
+{
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
+    if (i >= d.n) return;
+    float4 x = d.pos[i];
+    float4 v = d.vel[i];
+    const float4 a = d.acc[i];
+    const float im = d.vstar[i].w;
+    x.x += v.x * d.dt + a.x * d.half_dt2;
+    x.y += v.y * d.dt + a.y * d.half_dt2;
+    x.z += v.z * d.dt + a.z * d.half_dt2;
+    float4 vs = make_float4(v.x + a.x * d.dt, v.y + a.y * d.dt, v.z + a.z * d.dt, im);
+    if (d.wall_kind == DEM_WALL_SPECULAR) {
+        const float r = x.w;
+        float *xc = &x.x, *vc = &v.x, *sc = &vs.x;
+        for (int c = 0; c < 3; ++c) {
+            const float lo = d.lo[c] + r, hi = d.hi[c] - r;
+            if (xc[c] < lo) { xc[c] = 2.0f * lo - xc[c]; vc[c] = -vc[c]; sc[c] = -sc[c]; }
+            else if (xc[c] > hi) { xc[c] = 2.0f * hi - xc[c]; vc[c] = -vc[c]; sc[c] = -sc[c]; }
+        }
+        d.vel[i] = v;
+    }
+    d.pos[i] = x;
+    d.vstar[i] = vs;
+}
+
+// Narrow phase on the rows + walls + velocity finish, one thread per particle.
+__global__ void __launch_bounds__(kThreads)
+k_forces(DemDev d)
+{
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
+    if (i >= d.n) return;
+    const float4 xi = d.pos[i];
+    const float4 vi = d.vstar[i];
+    const float im_i = vi.w;
+    float F[3] = {0.f, 0.f, 0.f};
+    if (d.contacts_on) {
+        const int off = d.rows.row_off[i];
+        const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
+        for (int e = 0; e < len; ++e) {
+            const int j = d.rows.col[off + e];
+            const float4 xj = d.pos[j];
+            float h[3], l[3];
+            two_diff(xi.x, xj.x, h[0], l[0]);
+            two_diff(xi.y, xj.y, h[1], l[1]);
+            two_diff(xi.z, xj.z, h[2], l[2]);
+            // cheap reject before the compensated distance
+            const float Rr = xi.w + xj.w;
+            const float d2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+            if (d2 > Rr * Rr * 1.0001f) continue;
+            float s0, corr;
+            norm_dd(h, l, s0, corr);
+            float Rh, Rl;
+            two_sum(xi.w, xj.w, Rh, Rl);
+            const float dl = __fsub_rn(Rh, s0) + (Rl - corr);
+            if (!(dl > 0.0f) || !(s0 > 0.0f)) continue;
+            const float inv = 1.0f / (s0 + corr);
+            const float n0 = (h[0] + l[0]) * inv, n1 = (h[1] + l[1]) * inv,
+                        n2 = (h[2] + l[2]) * inv;
+            const float4 vj = d.vstar[j];
+            const float vn = (vi.x - vj.x) * n0 + (vi.y - vj.y) * n1 + (vi.z - vj.z) * n2;
+            const float meff = 1.0f / (im_i + vj.w);
+            const float f = lsd(d, dl, vn, meff);
+            F[0] += f * n0;
+            F[1] += f * n1;
+            F[2] += f * n2;
+        }
+    }
+    const float r = xi.w;
+    if (d.wall_kind == DEM_WALL_BOX || d.wall_kind == DEM_WALL_DRUM) {
+        const float m = 1.0f / im_i;
+        const float *xc = &xi.x, *vc = &vi.x;
+        const int c0 = d.wall_kind == DEM_WALL_DRUM ? 1 : 0;
+        const int c1 = d.wall_kind == DEM_WALL_DRUM ? 1 : 2;
+        for (int c = c0; c <= c1; ++c) {
+            float hh, ll;
+            two_diff(xc[c], d.lo[c], hh, ll);           // x - lo
+            float dlo = __fsub_rn(r, hh) - ll;
+            if (dlo > 0.0f) F[c] += lsd(d, dlo, vc[c], m);
+            two_diff(d.hi[c], xc[c], hh, ll);           // hi - x
+            float dhi = __fsub_rn(r, hh) - ll;
+            if (dhi > 0.0f) F[c] -= lsd(d, dhi, -vc[c], m);
+        }
+        if (d.wall_kind == DEM_WALL_DRUM) {
+            float h[3], l[3];
+            two_diff(xi.x, d.drum_cx, h[0], l[0]);
+            h[1] = 0.0f;
+            l[1] = 0.0f;
+            two_diff(xi.z, d.drum_cz, h[2], l[2]);
+            float s0, corr;
+            norm_dd(h, l, s0, corr);
+            // delta = r + rho - R, rho = s0 + corr; (s0 - R) is exact near the wall
+            const float t = __fsub_rn(s0, d.drum_R);
+            const float dl = __fadd_rn(t, r) + corr;
+            if (dl > 0.0f && s0 > 0.0f) {
+                const float inv = 1.0f / s0;
+                const float nx = -(h[0] + l[0]) * inv, nz = -(h[2] + l[2]) * inv;
+                const float vn = vi.x * nx + vi.z * nz;
+                const float f = lsd(d, dl, vn, m);
+                F[0] += f * nx;
+                F[2] += f * nz;
+            }
+        }
+    }
+    const float4 a = d.acc[i];
+    float4 v = d.vel[i];
+    const float4 an = make_float4(F[0] * im_i + d.g[0], F[1] * im_i + d.g[1],
+                                  F[2] * im_i + d.g[2], 0.0f);
+    v.x += (a.x + an.x) * d.half_dt;
+    v.y += (a.y + an.y) * d.half_dt;
+    v.z += (a.z + an.z) * d.half_dt;
+    d.vel[i] = v;
+    d.acc[i] = an;
+}
+
+__global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                            float rho)
+{
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < d.n; i += gridDim.x * kThreads) {
+        const float4 p = pos[i];
+        const float4 v = vel[i];
+        const double r = p.w;
+        const double m = (double)rho * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
+        d.pos[i] = p;
+        d.vel[i] = make_float4(v.x, v.y, v.z, 0.0f);
+        d.vstar[i] = make_float4(v.x, v.y, v.z, (float)(1.0 / m));
+        d.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// initial a0 = F(x0, v0)/m + g: the force kernel with a = 0 and dt = 0
+// leaves v unchanged and writes a0.
+}  // namespace
+
+struct dem_ctx {
+    DemDev d{};
+    dem_params prm{};
+    lvb_ctx *bp = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_steps = 0;
+};
+
+namespace {
+
+int from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return LVB_OK;
+    if (e == cudaErrorMemoryAllocation) return LVB_ENOMEM;
+    return LVB_EDEVICE;
+}
+
+int grid_n(int n) { return (n + kThreads - 1) / kThreads; }
+
+void dem_free(dem_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->bp) lvb_destroy(c->bp);
+    float4 *ptrs[] = {c->d.pos, c->d.vel, c->d.acc, c->d.vstar};
+    for (float4 *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int launch_phase(dem_ctx *c, int phase)
+{
+    if (phase == DEM_PHASE_INTEGRATE) {
+        k_integrate<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d);
+    } else if (phase == DEM_PHASE_BROAD) {
+        int rc = lvb_step(c->bp, (const float *)c->d.pos, (const float *)c->d.vstar, nullptr);
+        if (rc) return rc;
+    } else if (phase == DEM_PHASE_FORCES) {
+        k_forces<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d);
+    } else {
+        return LVB_EINVAL;
+    }
+    return from_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
+             const dem_params *prm, float dt, const lvb_box *box, const lvb_skin_policy *skin,
+             int32_t trigger, float cell_factor, void *stream)
+{
+    if (!out) return LVB_EINVAL;
+    *out = nullptr;
+    if (!pos_r || !vel || !prm || !box || !skin || n < 1 || n > INT32_MAX - 64) return LVB_EINVAL;
+    if (!(dt > 0.0f) || !(prm->kn >= 0.0f) || !(prm->rho > 0.0f) ||
+        !(prm->restitution > 0.0f && prm->restitution <= 1.0f))
+        return LVB_EINVAL;
+    if (prm->wall_kind < DEM_WALL_NONE || prm->wall_kind > DEM_WALL_SPECULAR) return LVB_EINVAL;
+    if (((uintptr_t)pos_r & 15u) || ((uintptr_t)vel & 15u)) return LVB_EINVAL;
+    cudaGetLastError();   // clear a stale error of an unrelated earlier call
+    dem_ctx *c = new (std::nothrow) dem_ctx();
+    if (!c) return LVB_ENOMEM;
+    c->prm = *prm;
+    c->stream = (cudaStream_t)stream;
+    DemDev &d = c->d;
+    d.n = (int)n;
+    d.dt = dt;
+    d.half_dt = 0.5f * dt;
+    d.half_dt2 = (float)(0.5 * (double)dt * (double)dt);
+    d.kn = prm->kn;
+    const double le = std::log((double)prm->restitution);
+    d.two_zeta = (float)(2.0 * (-le / std::sqrt(M_PI * M_PI + le * le)));
+    for (int k = 0; k < 3; ++k) {
+        d.g[k] = prm->g[k];
+        d.lo[k] = box->lo[k];
+        d.hi[k] = box->hi[k];
+    }
+    d.wall_kind = prm->wall_kind;
+    d.clamp_tensile = prm->clamp_tensile;
+    d.contacts_on = prm->contacts_on;
+    d.drum_cx = prm->drum_cx;
+    d.drum_cz = prm->drum_cz;
+    d.drum_R = prm->drum_R;
+    cudaError_t e = cudaMalloc((void **)&d.pos, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.vel, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.acc, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.vstar, sizeof(float4) * n);
+    if (e != cudaSuccess) {
+        dem_free(c);
+        delete c;
+        return from_cuda(e);
+    }
+    k_dem_setup<<<std::min(grid_n((int)n), 4 * kNumSMs), kThreads, 0, c->stream>>>(
+        d, (const float4 *)pos_r, (const float4 *)vel, prm->rho);
+    int rc = lvb_init(&c->bp, n, (const float *)d.pos, box, skin, trigger, cell_factor,
+                      (const float *)d.vstar, nullptr, stream);
+    if (rc) {
+        c->bp = nullptr;
+        dem_free(c);
+        delete c;
+        return rc;
+    }
+    d.rows = rows_view(c->bp);
+    // a0 from the forces at (x0, v0): one force pass with a = 0, dt = 0
+    DemDev d0 = d;
+    d0.half_dt = 0.0f;
+    k_forces<<<grid_n(d.n), kThreads, 0, c->stream>>>(d0);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        dem_free(c);
+        delete c;
+        return from_cuda(e);
+    }
+    *out = c;
+    return LVB_OK;
+}
+
+int dem_phase(dem_ctx *c, int32_t phase)
+{
+    if (!c) return LVB_EINVAL;
+    cudaGetLastError();
+    // the row store may have been re-laid out; pointers stay the same
+    return launch_phase(c, phase);
+}
+
+int dem_advance(dem_ctx *c, int64_t steps)
+{
+    if (!c || steps < 0) return LVB_EINVAL;
+    cudaGetLastError();   // clear a stale error of an unrelated earlier call
+    const int64_t chunk = 50;
+    if (steps >= chunk && !c->graph) {
+        // one graph of `chunk` steps, built node by node (no stream capture,
+        // so it works on any stream, the legacy default one included)
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaGraphCreate(&g, 0);
+        cudaGraphNode_t dep = nullptr;
+        const dim3 grid(grid_n(c->d.n)), block(kThreads);
+        int rc = LVB_OK;
+        for (int64_t s = 0; s < chunk && e == cudaSuccess && rc == LVB_OK; ++s) {
+            e = add_kernel(&dep, g, &dep, k_integrate, grid, block, c->d);
+            if (e != cudaSuccess) break;
+            rc = append_step_nodes(c->bp, g, &dep, (const float *)c->d.pos,
+                                   (const float *)c->d.vstar);
+            if (rc != LVB_OK) break;
+            e = add_kernel(&dep, g, &dep, k_forces, grid, block, c->d);
+        }
+        if (e == cudaSuccess && rc == LVB_OK) e = cudaGraphInstantiate(&c->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (rc != LVB_OK) return rc;
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return from_cuda(e);
+        }
+        c->graph_steps = chunk;
+    }
+    int64_t done = 0;
+    if (c->graph) {
+        for (; done + c->graph_steps <= steps; done += c->graph_steps) {
+            cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    }
+    for (; done < steps; ++done)
+        for (int ph = 0; ph < 3; ++ph) {
+            int rc = launch_phase(c, ph);
+            if (rc) return rc;
+        }
+    return LVB_OK;
+}
+
+int dem_get_state(dem_ctx *c, float *pos_r, float *vel, float *acc, float *vstar)
+{
+    if (!c) return LVB_EINVAL;
+    const size_t b = sizeof(float4) * (size_t)c->d.n;
+    cudaError_t e = cudaSuccess;
+    if (pos_r) e = cudaMemcpyAsync(pos_r, c->d.pos, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && vel) e = cudaMemcpyAsync(vel, c->d.vel, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && acc) e = cudaMemcpyAsync(acc, c->d.acc, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && vstar)
+        e = cudaMemcpyAsync(vstar, c->d.vstar, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return from_cuda(e);
+}
+
+int dem_set_state(dem_ctx *c, const float *pos_r, const float *vel, const float *acc)
+{
+    if (!c) return LVB_EINVAL;
+    const size_t b = sizeof(float4) * (size_t)c->d.n;
+    cudaError_t e = cudaSuccess;
+    if (pos_r) e = cudaMemcpyAsync(c->d.pos, pos_r, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && vel) e = cudaMemcpyAsync(c->d.vel, vel, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && acc) e = cudaMemcpyAsync(c->d.acc, acc, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return from_cuda(e);
+}
+
+int dem_lvb(dem_ctx *c, lvb_ctx **out)
+{
+    if (!c || !out) return LVB_EINVAL;
+    *out = c->bp;
+    return LVB_OK;
+}
+
+int dem_device_state(dem_ctx *c, float **pos_r, float **vel, float **acc, float **vstar)
+{
+    if (!c) return LVB_EINVAL;
+    if (pos_r) *pos_r = (float *)c->d.pos;
+    if (vel) *vel = (float *)c->d.vel;
+    if (acc) *acc = (float *)c->d.acc;
+    if (vstar) *vstar = (float *)c->d.vstar;
+    return LVB_OK;
+}
+
+int dem_sync(dem_ctx *c)
+{
+    if (!c) return LVB_EINVAL;
+    return lvb_sync(c->bp);
+}
+
+int dem_destroy(dem_ctx *c)
+{
+    if (!c) return LVB_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    dem_free(c);
+    delete c;
+    return LVB_OK;
+}
+
+}  // extern "C"

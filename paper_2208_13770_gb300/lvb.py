@@ -1,0 +1,426 @@
+"""ctypes binding of liblvb (include/lvb.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+device pointers (``tensor.data_ptr()``), sizes and the CUDA stream handle
+straight through; every step of the broad phase runs in the library's CUDA
+kernels.  Importing this module loads ``liblvb.so`` and raises ImportError
+if it has not been built -- there is no fallback.
+
+``LVB`` is a small convenience wrapper over one context that allocates the
+host output arrays of the lvb_get_* calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblvb.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("liblvb.so is not built; run `python -m paper_2208_13770_gb300.build` "
+                      "(needs nvcc) -- the broad phase has no CPU fallback")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+LVB_OK, LVB_EINVAL, LVB_ENOMEM, LVB_ECAPACITY, LVB_EDEVICE, LVB_ENAN, LVB_EOVERFLOW, \
+    LVB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+LVB_SKIN_GLOBAL, LVB_SKIN_DIAMETER_FACTOR, LVB_SKIN_PAPER_KVDT, LVB_SKIN_LEARNED = 0, 1, 2, 3
+LVB_TRIGGER_PARTIAL, LVB_TRIGGER_GLOBAL, LVB_TRIGGER_ALWAYS = 0, 1, 2
+
+
+class lvb_skin_policy(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_float), ("dt", ctypes.c_float),
+                ("mlp", ctypes.c_void_p)]
+
+
+class lvb_box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
+
+
+class lvb_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in
+                ("n", "steps", "rebuild_steps", "flagged_total", "updated_total", "last_flagged",
+                 "entries", "pairs", "relayouts", "cell_capacity", "row_store_capacity",
+                 "kernels_executed", "small_path_steps", "small_max", "graphs")] + \
+               [("cell_edge", ctypes.c_float), ("rnl_max", ctypes.c_float),
+                ("grid", ctypes.c_int32 * 3), ("pad", ctypes.c_int32)]
+
+
+class dem_params(ctypes.Structure):
+    _fields_ = [("kn", ctypes.c_float), ("restitution", ctypes.c_float), ("rho", ctypes.c_float),
+                ("g", ctypes.c_float * 3), ("wall_kind", ctypes.c_int32),
+                ("clamp_tensile", ctypes.c_int32), ("drum_cx", ctypes.c_float),
+                ("drum_cz", ctypes.c_float), ("drum_R", ctypes.c_float),
+                ("drum_omega", ctypes.c_float), ("contacts_on", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+DEM_WALL_NONE, DEM_WALL_BOX, DEM_WALL_DRUM, DEM_WALL_SPECULAR = 0, 1, 2, 3
+DEM_PHASE_INTEGRATE, DEM_PHASE_BROAD, DEM_PHASE_FORCES = 0, 1, 2
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_SIGS = {
+    "lvb_init": ([ctypes.POINTER(_p), _i64, _p, ctypes.POINTER(lvb_box),
+                  ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p, _p],
+                 ctypes.c_int),
+    "lvb_init_resume": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(lvb_box),
+                         ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p,
+                         _p], ctypes.c_int),
+    "lvb_step": ([_p, _p, _p, _p], ctypes.c_int),
+    "lvb_sync": ([_p], ctypes.c_int),
+    "lvb_set_option": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
+    "lvb_get_pairs": ([_p, _p, _p, _i64, _pi64], ctypes.c_int),
+    "lvb_get_pairs_ij": ([_p, _p, _p, _i64, _pi64], ctypes.c_int),
+    "lvb_get_contacts": ([_p, _p, _p, _p, _p, _i64, _pi64], ctypes.c_int),
+    "lvb_get_flags": ([_p, _p, _pi64], ctypes.c_int),
+    "lvb_get_ref": ([_p, _p], ctypes.c_int),
+    "lvb_stats": ([_p, ctypes.POINTER(lvb_stats_t)], ctypes.c_int),
+    "lvb_set_stream": ([_p, _p], ctypes.c_int),
+    "lvb_destroy": ([_p], ctypes.c_int),
+    "lvb_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "dem_init": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(dem_params), ctypes.c_float,
+                  ctypes.POINTER(lvb_box), ctypes.POINTER(lvb_skin_policy), ctypes.c_int32,
+                  ctypes.c_float, _p], ctypes.c_int),
+    "dem_advance": ([_p, _i64], ctypes.c_int),
+    "dem_phase": ([_p, ctypes.c_int32], ctypes.c_int),
+    "dem_get_state": ([_p, _p, _p, _p, _p], ctypes.c_int),
+    "dem_set_state": ([_p, _p, _p, _p], ctypes.c_int),
+    "dem_lvb": ([_p, ctypes.POINTER(_p)], ctypes.c_int),
+    "dem_device_state": ([_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p),
+                          ctypes.POINTER(_p)], ctypes.c_int),
+    "dem_sync": ([_p], ctypes.c_int),
+    "dem_destroy": ([_p], ctypes.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = sorted(k for k in _SIGS if k.startswith("lvb_"))
+EXPORTED_DEM = sorted(k for k in _SIGS if k.startswith("dem_"))
+
+
+class LVBError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, lvb_strerror(code), code))
+
+
+def _check(rc, what):
+    if rc != LVB_OK:
+        raise LVBError(rc, what)
+    return rc
+
+
+def lvb_strerror(code: int) -> str:
+    return _lib.lvb_strerror(int(code)).decode()
+
+
+def lvb_init(n, pos_r, box, skin, trigger, cell_factor, vel=None, acc=None, stream=None):
+    ctx = _p()
+    rc = _lib.lvb_init(ctypes.byref(ctx), int(n), pos_r, ctypes.byref(box), ctypes.byref(skin),
+                       int(trigger), float(cell_factor), vel, acc, stream)
+    _check(rc, "lvb_init")
+    return ctx
+
+
+def lvb_init_resume(n, pos_r, ref4, box, skin, trigger, cell_factor, vel=None, acc=None,
+                    stream=None):
+    ctx = _p()
+    rc = _lib.lvb_init_resume(ctypes.byref(ctx), int(n), pos_r, ref4, ctypes.byref(box),
+                              ctypes.byref(skin), int(trigger), float(cell_factor), vel, acc,
+                              stream)
+    _check(rc, "lvb_init_resume")
+    return ctx
+
+
+def lvb_step(ctx, pos_r, vel=None, acc=None):
+    return _lib.lvb_step(ctx, pos_r, vel, acc)
+
+
+LVB_OPT_GRAPH, LVB_OPT_SMALL_MAX = 0, 1
+
+
+def lvb_set_option(ctx, option, value):
+    return _lib.lvb_set_option(ctx, int(option), int(value))
+
+
+def lvb_sync(ctx):
+    return _lib.lvb_sync(ctx)
+
+
+def lvb_get_pairs(ctx, row_ptr, col, cap, n_entries):
+    return _lib.lvb_get_pairs(ctx, row_ptr, col, cap, n_entries)
+
+
+def lvb_get_pairs_ij(ctx, pi, pj, cap, n_pairs):
+    return _lib.lvb_get_pairs_ij(ctx, pi, pj, cap, n_pairs)
+
+
+def lvb_get_contacts(ctx, pos_r, ci, cj, delta, cap, n_contacts):
+    return _lib.lvb_get_contacts(ctx, pos_r, ci, cj, delta, cap, n_contacts)
+
+
+def lvb_get_flags(ctx, bits, n_flagged):
+    return _lib.lvb_get_flags(ctx, bits, n_flagged)
+
+
+def lvb_get_ref(ctx, ref4):
+    return _lib.lvb_get_ref(ctx, ref4)
+
+
+def lvb_stats(ctx, out):
+    return _lib.lvb_stats(ctx, out)
+
+
+def lvb_set_stream(ctx, stream):
+    return _lib.lvb_set_stream(ctx, stream)
+
+
+def lvb_destroy(ctx):
+    return _lib.lvb_destroy(ctx)
+
+
+def dem_init(n, pos_r, vel, prm, dt, box, skin, trigger, cell_factor, stream=None):
+    ctx = _p()
+    rc = _lib.dem_init(ctypes.byref(ctx), int(n), pos_r, vel, ctypes.byref(prm), float(dt),
+                       ctypes.byref(box), ctypes.byref(skin), int(trigger), float(cell_factor),
+                       stream)
+    _check(rc, "dem_init")
+    return ctx
+
+
+def dem_advance(ctx, steps):
+    return _lib.dem_advance(ctx, int(steps))
+
+
+def dem_phase(ctx, phase):
+    return _lib.dem_phase(ctx, int(phase))
+
+
+def dem_get_state(ctx, pos_r, vel, acc, vstar):
+    return _lib.dem_get_state(ctx, pos_r, vel, acc, vstar)
+
+
+def dem_set_state(ctx, pos_r, vel, acc):
+    return _lib.dem_set_state(ctx, pos_r, vel, acc)
+
+
+def dem_lvb(ctx):
+    out = _p()
+    _check(_lib.dem_lvb(ctx, ctypes.byref(out)), "dem_lvb")
+    return out
+
+
+def dem_device_state(ctx):
+    ptrs = [_p() for _ in range(4)]
+    _check(_lib.dem_device_state(ctx, *[ctypes.byref(q) for q in ptrs]), "dem_device_state")
+    return [q.value for q in ptrs]
+
+
+def dem_sync(ctx):
+    return _lib.dem_sync(ctx)
+
+
+def dem_destroy(ctx):
+    return _lib.dem_destroy(ctx)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(_p)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or an int/None passed through)."""
+    if t is None or isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+class LVB:
+    """One broad-phase context over device tensors of float4 records."""
+
+    def __init__(self, pos, box_lo, box_hi, skin_kind=LVB_SKIN_DIAMETER_FACTOR, skin_value=0.1,
+                 dt=0.0, trigger=LVB_TRIGGER_PARTIAL, cell_factor=1.25, vel=None, acc=None,
+                 stream=None, ref=None):
+        import torch
+        self.n = int(pos.shape[0])
+        box = lvb_box()
+        for k in range(3):
+            box.lo[k], box.hi[k] = float(box_lo[k]), float(box_hi[k])
+        skin = lvb_skin_policy(int(skin_kind), float(skin_value), float(dt), None)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        if ref is None:
+            self.ctx = lvb_init(self.n, _dptr(pos), box, skin, trigger, cell_factor, _dptr(vel),
+                                _dptr(acc), stream)
+        else:
+            self.ctx = lvb_init_resume(self.n, _dptr(pos), _dptr(ref), box, skin, trigger,
+                                       cell_factor, _dptr(vel), _dptr(acc), stream)
+
+    def step(self, pos, vel=None, acc=None):
+        _check(lvb_step(self.ctx, _dptr(pos), _dptr(vel), _dptr(acc)), "lvb_step")
+
+    def sync(self):
+        return lvb_sync(self.ctx)
+
+    def set_option(self, option, value):
+        _check(lvb_set_option(self.ctx, option, value), "lvb_set_option")
+
+    def pairs_ij(self):
+        n = ctypes.c_int64(0)
+        rc = lvb_get_pairs_ij(self.ctx, None, None, 0, ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_get_pairs_ij")
+        cap = n.value
+        pi = np.empty(max(cap, 1), dtype=np.int32)
+        pj = np.empty(max(cap, 1), dtype=np.int32)
+        _check(lvb_get_pairs_ij(self.ctx, _np_ptr(pi), _np_ptr(pj), cap, ctypes.byref(n)),
+               "lvb_get_pairs_ij")
+        return pi[:n.value], pj[:n.value]
+
+    def pairs_csr(self):
+        n = ctypes.c_int64(0)
+        row_ptr = np.empty(self.n + 1, dtype=np.int32)
+        rc = lvb_get_pairs(self.ctx, _np_ptr(row_ptr), None, 0, ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_get_pairs")
+        col = np.empty(max(n.value, 1), dtype=np.int32)
+        _check(lvb_get_pairs(self.ctx, _np_ptr(row_ptr), _np_ptr(col), n.value, ctypes.byref(n)),
+               "lvb_get_pairs")
+        return row_ptr, col[:n.value]
+
+    def contacts(self, pos):
+        n = ctypes.c_int64(0)
+        rc = lvb_get_contacts(self.ctx, _dptr(pos), None, None, None, 0, ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_get_contacts")
+        cap = n.value
+        ci = np.empty(max(cap, 1), dtype=np.int32)
+        cj = np.empty(max(cap, 1), dtype=np.int32)
+        dl = np.empty(max(cap, 1), dtype=np.float32)
+        _check(lvb_get_contacts(self.ctx, _dptr(pos), _np_ptr(ci), _np_ptr(cj), _np_ptr(dl), cap,
+                                ctypes.byref(n)), "lvb_get_contacts")
+        return ci[:n.value], cj[:n.value], dl[:n.value]
+
+    def flags(self):
+        words = np.zeros((self.n + 31) // 32, dtype=np.uint32)
+        nf = ctypes.c_int64(0)
+        _check(lvb_get_flags(self.ctx, _np_ptr(words), ctypes.byref(nf)), "lvb_get_flags")
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little")[:self.n].astype(bool)
+        return bits
+
+    def ref(self):
+        out = np.empty((self.n, 4), dtype=np.float32)
+        _check(lvb_get_ref(self.ctx, _np_ptr(out)), "lvb_get_ref")
+        return out
+
+    def stats(self):
+        st = lvb_stats_t()
+        _check(lvb_stats(self.ctx, ctypes.byref(st)), "lvb_stats")
+        return {k: (list(getattr(st, k)) if k == "grid" else getattr(st, k))
+                for k, _ in lvb_stats_t._fields_ if k != "pad"}
+
+    def close(self):
+        if self.ctx:
+            lvb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+WALLS = {"none": DEM_WALL_NONE, "box": DEM_WALL_BOX, "drum": DEM_WALL_DRUM,
+         "specular": DEM_WALL_SPECULAR}
+
+
+class _BorrowedLVB(LVB):
+    """The broad-phase context owned by a DEM context (not destroyed here)."""
+
+    def __init__(self, ctx, n):
+        self.ctx = ctx
+        self.n = n
+
+    def close(self):
+        self.ctx = None
+
+
+class DEM:
+    """A DEM driver context over a scene (``scenes.Scene``-like object)."""
+
+    def __init__(self, scene, trigger=LVB_TRIGGER_PARTIAL, skin_kind=None, skin_value=None,
+                 cell_factor=None, stream=None):
+        import torch
+        self.n = int(scene.n)
+        prm = dem_params()
+        prm.kn, prm.restitution, prm.rho = scene.kn, scene.restitution, scene.rho
+        for k in range(3):
+            prm.g[k] = scene.gravity[k]
+        prm.wall_kind = WALLS[scene.wall]
+        prm.clamp_tensile = 0
+        if scene.drum is not None:
+            prm.drum_cx, prm.drum_cz, prm.drum_R, prm.drum_omega = scene.drum
+        prm.contacts_on = int(bool(scene.contacts))
+        self.prm = prm
+        box = lvb_box()
+        for k in range(3):
+            box.lo[k], box.hi[k] = scene.lo[k], scene.hi[k]
+        kind = scene.skin_kind if skin_kind is None else skin_kind
+        value = scene.skin_value if skin_value is None else skin_value
+        skin = lvb_skin_policy(int(kind), float(value), float(scene.dt), None)
+        cf = scene.cell_factor if cell_factor is None else cell_factor
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        pos = torch.from_numpy(np.ascontiguousarray(scene.pos, dtype=np.float32)).cuda()
+        vel = torch.from_numpy(np.ascontiguousarray(scene.vel, dtype=np.float32)).cuda()
+        self.ctx = dem_init(self.n, pos.data_ptr(), vel.data_ptr(), prm, scene.dt, box, skin,
+                            trigger, cf, stream)
+        torch.cuda.synchronize()
+        self.lvb = _BorrowedLVB(dem_lvb(self.ctx), self.n)
+
+    def advance(self, steps):
+        _check(dem_advance(self.ctx, steps), "dem_advance")
+
+    def phase(self, ph):
+        _check(dem_phase(self.ctx, ph), "dem_phase")
+
+    def step(self):
+        for ph in (DEM_PHASE_INTEGRATE, DEM_PHASE_BROAD, DEM_PHASE_FORCES):
+            self.phase(ph)
+
+    def state(self):
+        outs = [np.empty((self.n, 4), dtype=np.float32) for _ in range(4)]
+        _check(dem_get_state(self.ctx, *[_np_ptr(o) for o in outs]), "dem_get_state")
+        return tuple(outs)   # pos, vel, acc, vstar
+
+    def device_pos_tensor(self, torch):
+        """A torch view (no copy) of the context's device positions."""
+        ptr = dem_device_state(self.ctx)[0]
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (self.n, 4), "typestr": "<f4",
+                                        "data": (ptr, False), "version": 2}
+        return torch.as_tensor(_View(), device="cuda")
+
+    def set_state(self, pos, vel, acc):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (pos, vel, acc)]
+        _check(dem_set_state(self.ctx, *[_np_ptr(a) for a in arrs]), "dem_set_state")
+
+    def sync(self):
+        return dem_sync(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            dem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

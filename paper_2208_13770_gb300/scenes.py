@@ -210,6 +210,31 @@ def batch(n_scenes=512, seed=SEED_BASE + 3, nmin=1000, nmax=50_000, steps=2000):
     return scenes
 
 
+def packed(n=8000, seed=SEED_BASE + 5, r=1e-3, spread=0.004, vsigma=0.05, dt=1e-6,
+           steps=1000, skin_kind=1, skin_value=0.1, cell_factor=1.25) -> Scene:
+    """A dense simple-cubic pack of near-monodisperse spheres resting on the
+    floor of a box under gravity: lattice spacing 2r, radii r * U[1 - spread,
+    1 + spread], so that about half of the neighbour pairs start in contact
+    with overlaps of a few micrometres."""
+    rng = _rng(seed)
+    a = 2.0 * r
+    m = int(math.ceil(n ** (1.0 / 3.0)))
+    side = m * a
+    radii = r * rng.uniform(1.0 - spread, 1.0 + spread, size=n)
+    sites = rng.choice(m ** 3, size=n, replace=False)
+    ix, iy, iz = sites % m, (sites // m) % m, sites // (m * m)
+    pos = np.zeros((n, 4), dtype=np.float32)
+    pos[:, 0] = (ix + 0.5) * a
+    pos[:, 1] = (iy + 0.5) * a
+    pos[:, 2] = (iz + 0.5) * a
+    pos[:, 3] = radii
+    vel = np.zeros((n, 4), dtype=np.float32)
+    vel[:, :3] = rng.normal(0.0, vsigma, size=(n, 3))
+    return Scene("packed", pos, vel, (0.0, 0.0, 0.0), (side, side, 2.0 * side), dt, steps, "box",
+                 gravity=(0.0, 0.0, -9.81), skin_kind=skin_kind, skin_value=skin_value,
+                 cell_factor=cell_factor)
+
+
 def ballistic_trajectory(scene: Scene, steps: int):
     """Positions of a ballistic scene at steps 1..steps (free flight with
     specular walls, binary32 x <- x + v dt), for feeding a broad phase with
@@ -230,4 +255,4 @@ def ballistic_trajectory(scene: Scene, steps: int):
         yield pos.copy(), vel.copy()
 
 
-SCENES = {"ballistic": ballistic, "settling": settling, "drum": drum}
+SCENES = {"ballistic": ballistic, "settling": settling, "drum": drum, "packed": packed}

@@ -1,0 +1,201 @@
+"""GPU parity of the broad phase (through the C-ABI) against the oracle.
+
+On identical position snapshots the flags, the reference state, the pair set
+and the contact set must match the oracle exactly (binary32 fixed formula),
+at every checked step.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_13770_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_13770_gb300 import lvb
+    return lvb
+
+
+def _H(scene_pos, cell_factor):
+    rmax = np.float32(scene_pos[:, 3].max())
+    L = cell_factor * 2.0 * float(rmax) * (1 + 2 ** -7)
+    return np.float32(0.5 * L * (1 - 2 ** -8))
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _csr_from_pairs(n, pi, pj):
+    """Symmetric CSR (rows ascending) of an unordered pair list."""
+    a = np.concatenate([pi, pj]).astype(np.int64)
+    b = np.concatenate([pj, pi]).astype(np.int64)
+    order = np.lexsort((b, a))
+    a, b = a[order], b[order]
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(ptr, a + 1, 1)
+    return np.cumsum(ptr), b
+
+
+def _compare(ctx, sm, pos_h, step, check_contacts=True):
+    pi, pj = ctx.pairs_ij()
+    assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj), \
+        "pair set differs at step %d: gpu %d oracle %d" % (step, len(pi), len(sm.pi))
+    # every row, seen from both ends: symmetric, no duplicates, same set
+    ptr, col = ctx.pairs_csr()
+    optr, ocol = _csr_from_pairs(len(pos_h), sm.pi, sm.pj)
+    assert np.array_equal(ptr, optr) and np.array_equal(col, ocol), \
+        "symmetric rows differ at step %d" % step
+    ref = ctx.ref()
+    assert np.array_equal(ref, sm.ref), "reference state differs at step %d" % step
+    if check_contacts:
+        ci, cj, dl = ctx.contacts(_dev(pos_h))
+        oi, oj, od = sm.contacts(pos_h)
+        assert np.array_equal(ci, oi) and np.array_equal(cj, oj)
+        assert np.array_equal(dl, od)
+
+
+def _run_trajectory(orc, scene, snaps, trigger, skin_kind, skin_value, every=1, cell_factor=1.25):
+    lvb = _cuda()
+    from oracle.statemachine import OracleLVB
+    H = _H(scene.pos, cell_factor)
+    pos0 = scene.pos
+    vel0 = scene.vel
+    ctx = lvb.LVB(_dev(pos0), scene.lo, scene.hi, skin_kind, skin_value, scene.dt, trigger,
+                  cell_factor, vel=_dev(vel0))
+    assert ctx.stats()["rnl_max"] == H
+    sm = OracleLVB(pos0, skin_kind, skin_value, scene.dt, H, trigger, vel4=vel0)
+    _compare(ctx, sm, pos0, 0)
+    nflag = 0
+    for k, (pos, vel) in enumerate(snaps, start=1):
+        ctx.step(_dev(pos), _dev(vel))
+        f, _ = sm.step(pos, vel4=vel)
+        nflag += int(f.sum())
+        if k % every == 0:
+            assert ctx.sync() == 0
+            assert np.array_equal(ctx.flags(), f), "flags differ at step %d" % k
+            _compare(ctx, sm, pos, k)
+    st = ctx.stats()
+    assert st["flagged_total"] == nflag
+    assert st["pairs"] == len(sm.pi)
+    ctx.close()
+    return st, sm
+
+
+@pytest.mark.parametrize("trigger", [0, 1, 2], ids=["partial", "global", "always"])
+def test_ballistic_parity(orc, trigger):
+    s = scenes.ballistic()
+    steps = 1000 if trigger == 0 else 300
+    every = 1 if trigger == 0 else 3
+    st, sm = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, steps), trigger, 1, 0.1,
+                             every=every)
+    assert st["steps"] == steps
+    if trigger == 0:
+        assert 0 < st["updated_total"] < s.n * steps
+
+
+def test_ballistic_paper_rule_parity(orc):
+    # skin = K |v| dt (Eq. skin_formulus1) with K = 200, the paper's default
+    s = scenes.ballistic(n=2000, seed=21)
+    _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 600), 0, 2, 200.0, every=2)
+
+
+def test_hot_gas_many_rebuilds_parity(orc):
+    # fast particles: many flags, cell moves and row changes per step
+    s = scenes.ballistic(n=3000, seed=5, phi=0.3, vsigma=3.0)
+    st, _ = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 150), 0, 1, 0.1)
+    assert st["updated_total"] > s.n
+
+
+def _random_walk(scene, steps, sigma, seed=0):
+    rng = np.random.default_rng(seed)
+    pos = scene.pos.copy()
+    vel = scene.vel.copy()
+    for _ in range(steps):
+        pos[:, :3] += rng.normal(0.0, sigma, size=(len(pos), 3)).astype(np.float32)
+        yield pos.copy(), vel
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 1027])
+def test_small_and_ragged_sizes(orc, n):
+    s = scenes.ballistic(n=n, seed=40 + n, phi=0.2 if n > 8 else 0.05)
+    s.vel[:, :3] *= 50.0
+    _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 40), 0, 1, 0.1)
+
+
+def test_all_in_one_cell_and_outside_box(orc):
+    # a dense clump (many same-cell pairs) and particles outside the box
+    lvb = _cuda()
+    rng = np.random.default_rng(3)
+    n = 300
+    pos = np.zeros((n, 4), dtype=np.float32)
+    pos[:, :3] = rng.uniform(0.0, 2e-3, size=(n, 3))
+    pos[:, 3] = 1e-3
+    pos[:50, 0] -= 0.02            # left of the box
+    pos[50:100, 2] += 0.05         # above the box
+    s = scenes.Scene("clump", pos, np.zeros_like(pos), (0, 0, 0), (0.01, 0.01, 0.01), 1e-5, 10,
+                     "box")
+    st, sm = _run_trajectory(orc, s, _random_walk(s, 20, 5e-5), 0, 1, 0.1)
+    assert st["pairs"] > 10000
+
+
+def test_exact_cutoff_pair_on_gpu(orc):
+    lvb = _cuda()
+    # r = 0.5, skin = 0.125 (global), pair exactly at the cutoff 1.25 and one
+    # ulp beyond; box large enough
+    pos = np.array([[10, 10, 10, 0.5], [10.75, 11, 10, 0.5],
+                    [20, 20, 20, 0.5], [20, 20, np.nextafter(np.float32(21.25), 99), 0.5]],
+                   dtype=np.float32)
+    ctx = lvb.LVB(_dev(pos), (0, 0, 0), (40, 40, 40), lvb.LVB_SKIN_GLOBAL, 0.125, 0.0,
+                  lvb.LVB_TRIGGER_PARTIAL, 1.25)
+    pi, pj = ctx.pairs_ij()
+    assert list(zip(pi, pj)) == [(0, 1)]
+    ctx.close()
+
+
+def test_static_particles_never_flag(orc):
+    lvb = _cuda()
+    s = scenes.ballistic(n=500, seed=2)
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, 1, 0.1, s.dt, 0, 1.25)
+    d = _dev(s.pos)
+    for _ in range(20):
+        ctx.step(d)
+    st = ctx.stats()
+    assert st["flagged_total"] == 0 and st["rebuild_steps"] == 0
+    ctx.close()
+
+
+def test_relayout_when_rows_grow(orc):
+    # contract the cloud towards its centre: rows grow past their slack and
+    # the row store is re-laid out on the device; parity must hold throughout
+    s = scenes.ballistic(n=2000, seed=8, phi=0.25)
+
+    def shrink(steps):
+        pos = s.pos.copy()
+        c = pos[:, :3].mean(axis=0)
+        for _ in range(steps):
+            pos[:, :3] = c + (pos[:, :3] - c) * np.float32(0.997)
+            yield pos.copy(), s.vel
+
+    st, _ = _run_trajectory(orc, s, shrink(60), 0, 1, 0.1)
+    assert st["relayouts"] > 0
+
+
+def test_polydisperse_settling_subset_parity(orc):
+    # polydisperse radii U[0.5, 2] mm, random displacements of mixed size
+    s = scenes.settling(n=20_000, seed=77, footprint=0.06, height=0.6)
+    st, _ = _run_trajectory(orc, s, _random_walk(s, 25, 1e-4, seed=1), 0, 1, 0.1, every=5)
+    assert st["updated_total"] > 0
+
+
+def test_settling_full_size_parity(orc):
+    # the 200,000-particle settling box at full size: complete pair-set parity
+    # after init and after steps with many flags
+    s = scenes.settling()
+    st, _ = _run_trajectory(orc, s, _random_walk(s, 6, 6e-5, seed=2), 0, 1, 0.1, every=3)
+    assert st["n"] == 200_000

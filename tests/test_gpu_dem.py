@@ -1,0 +1,181 @@
+"""GPU DEM driver against the binary64 oracle, one step at a time.
+
+The oracle is fed the GPU's binary32 state (x, v, a) before each checked step
+and, for the force evaluation, the GPU's own x' and v*, so the trajectories
+cannot drift apart; it also gets the physical constants as the GPU holds
+them (rounded to binary32).  Tolerances are relative 1e-5 of the terms that
+are summed, because a sum that cancels cannot be held to a relative bound
+of its own (possibly tiny) size:
+  x'       : |gpu - oracle| <= 1e-5 (|x| + |v| dt + |a| dt^2)
+  v*       : |gpu - oracle| <= 1e-5 (|v| + |a| dt)
+  a'       : |gpu - oracle| <= 1e-5 (S/m + |g|), S = sum over the particle's
+             contacts of |k_n delta| + |damping term|
+  v'       : |gpu - oracle| <= 1e-5 (|v| + dt (|a| + S/m + |g|))
+A contact missing from the list would show as a force error of the size of
+that contact's force.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_13770_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+RTOL = 1e-5
+
+
+def _lvb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_13770_gb300 import lvb
+    return lvb
+
+
+def _f32(v):
+    return float(np.float32(v))
+
+
+def _params(orc, s):
+    kind = {"box": orc.WALL_BOX, "drum": orc.WALL_DRUM, "specular": orc.WALL_SPECULAR,
+            "none": orc.WALL_NONE}[s.wall]
+    dc, dr = ((_f32(s.drum[0]), _f32(s.drum[1])), _f32(s.drum[2])) if s.drum else ((0.0, 0.0), 0.0)
+    return orc.dem_params(kn=_f32(s.kn), restitution=_f32(s.restitution), rho=_f32(s.rho),
+                          g=tuple(map(_f32, s.gravity)), lo=tuple(map(_f32, s.lo)),
+                          hi=tuple(map(_f32, s.hi)), wall_kind=kind, drum_center=dc,
+                          drum_radius=dr, contacts_on=s.contacts)
+
+
+def _check_step(orc, dem, s, P, idx=None):
+    """One GPU step checked against the oracle; returns (#particles in contact)."""
+    x, v, a, _ = dem.state()
+    dem.step()
+    x1, v1, a1, vs1 = dem.state()
+    xo, vso, ao, vo, fmag = orc.dem_step(x, v, a, s.dt, P, x_in=x1, vstar_in=vs1,
+                                         with_fmag=True)
+    sel = slice(None) if idx is None else idx
+    dt = s.dt
+    x64, v64, a64 = (q[sel, :3].astype(np.float64) for q in (x, v, a))
+    m = s.rho * 4.0 / 3.0 * np.pi * x[sel, 3].astype(np.float64) ** 3
+    fs = (fmag[sel] / m)[:, None] + np.linalg.norm(s.gravity)
+    checks = [
+        ("x'", x1[sel, :3], xo[sel], np.abs(x64) + np.abs(v64) * dt + np.abs(a64) * dt * dt),
+        ("v*", vs1[sel, :3], vso[sel], np.abs(v64) + np.abs(a64) * dt),
+        ("a'", a1[sel, :3], ao[sel], np.broadcast_to(fs, ao[sel].shape)),
+        ("v'", v1[sel, :3], vo[sel], np.abs(v64) + dt * (np.abs(a64) + fs)),
+    ]
+    for name, g, o, terms in checks:
+        ex = np.abs(g - o) - RTOL * terms
+        k = np.unravel_index(np.argmax(ex), ex.shape)
+        assert ex.max() <= 1e-30, "%s off at %s: gpu %r oracle %r terms %r (%d bad)" % (
+            name, k, g[k], o[k], terms[k], int((ex > 1e-30).sum()))
+    return int((fmag > 0).sum())
+
+
+def test_packed_box_per_step_parity(orc):
+    lvb = _lvb()
+    s = scenes.packed(n=8000, vsigma=1.0)     # fast enough to flag within the run
+    P = _params(orc, s)
+    dem = lvb.DEM(s)
+    touching = 0
+    for k in range(300):
+        if k % 25 == 0:
+            touching = max(touching, _check_step(orc, dem, s, P))
+        else:
+            dem.step()
+    assert dem.sync() == 0
+    assert touching > 1000
+    st = dem.lvb.stats()
+    assert st["rebuild_steps"] > 0
+    dem.close()
+
+
+def test_packed_box_no_contact_missed(orc):
+    # every overlapping pair at the checked steps is in the list (Theorem 1)
+    lvb = _lvb()
+    s = scenes.packed(n=4000, seed=99, vsigma=0.3)
+    dem = lvb.DEM(s)
+    for k in range(200):
+        dem.step()
+        if k % 20 == 19:
+            x = dem.state()[0]
+            ci, cj, _ = orc.contacts_all(x)
+            pi, pj = dem.lvb.pairs_ij()
+            lst = set(zip(pi.tolist(), pj.tolist()))
+            assert set(zip(ci.tolist(), cj.tolist())) <= lst
+            assert len(ci) > 100
+    dem.close()
+
+
+def test_drum_wall_parity(orc):
+    lvb = _lvb()
+    s = scenes.drum(n=20_000, length=0.02, seed=7)
+    # push the outermost particles into the drum wall by 1 micrometre
+    rho = np.hypot(s.pos[:, 0], s.pos[:, 2])
+    out = rho > np.quantile(rho, 0.97)
+    target = np.float32(0.3) - s.pos[out, 3] + np.float32(1e-6)
+    s.pos[out, 0] *= target / rho[out]
+    s.pos[out, 2] *= target / rho[out]
+    P = _params(orc, s)
+    dem = lvb.DEM(s)
+    for k in range(120):
+        if k % 30 == 0:
+            _check_step(orc, dem, s, P)
+        else:
+            dem.step()
+    assert dem.sync() == 0
+    dem.close()
+
+
+def test_ballistic_driver_matches_oracle_and_broad_phase(orc):
+    lvb = _lvb()
+    from oracle.statemachine import OracleLVB
+    s = scenes.ballistic()
+    s.vel[:, :3] *= 10.0
+    P = _params(orc, s)
+    dem = lvb.DEM(s)
+    H = dem.lvb.stats()["rnl_max"]
+    sm = OracleLVB(s.pos, 1, 0.1, s.dt, H, 0)
+    for k in range(200):
+        if k % 50 == 0:
+            _check_step(orc, dem, s, P)
+        else:
+            dem.step()
+        x = dem.state()[0]
+        f, _ = sm.step(x)
+        assert np.array_equal(dem.lvb.flags(), f)
+    pi, pj = dem.lvb.pairs_ij()
+    assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj)
+    dem.close()
+
+
+def test_advance_graph_matches_phase_launches(orc):
+    lvb = _lvb()
+    s = scenes.packed(n=3000, seed=4)
+    a = lvb.DEM(s)
+    b = lvb.DEM(s)
+    a.advance(120)          # two graph replays of 50 + 20 direct steps
+    for _ in range(120):
+        b.step()
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.allclose(xa, xb, rtol=0, atol=1e-9)
+    assert np.allclose(va, vb, rtol=1e-4, atol=1e-6)
+    assert a.lvb.stats()["steps"] == b.lvb.stats()["steps"] == 120
+    a.close()
+    b.close()
+
+
+def test_settling_full_size_step_parity(orc):
+    # 200,000 polydisperse particles, graph-replayed steps, then one checked
+    # step over every particle
+    lvb = _lvb()
+    s = scenes.settling()
+    P = _params(orc, s)
+    dem = lvb.DEM(s)
+    dem.advance(200)
+    _check_step(orc, dem, s, P)
+    assert dem.sync() == 0
+    st = dem.lvb.stats()
+    assert st["steps"] == 201
+    dem.close()

@@ -37,7 +37,7 @@ def _accel(orc, x, v, r, P):
     vv = np.ascontiguousarray(v, dtype=np.float64)
     rr = np.ascontiguousarray(r, dtype=np.float64)
     rc = orc.lib().orc_dem_forces64(n, xx.ctypes.data, rr.ctypes.data, vv.ctypes.data,
-                                    ctypes.byref(P), F.ctypes.data)
+                                    ctypes.byref(P), F.ctypes.data, None)
     assert rc == 0
     m = P.rho * 4.0 / 3.0 * math.pi * rr ** 3
     return F / m[:, None] + np.array(P.g[:])
