@@ -6,7 +6,7 @@ rho 2500, linear spring-dashpot k_n = 1e4, e = 0.7, velocity Verlet
 dt = 1e-6 s, local skin 0.1 d_i, cell edge 1.25 d_max), run through the
 library's DEM driver.  A "step" is one DEM step: integrate, broad phase
 (displacement check + partial rebuild), narrow phase and forces.  The L2
-cache (129 MB) is flushed with a 256 MB write before every timed step, and
+cache (129 MB) is flushed with a 1 GiB write before every timed step, and
 each phase is bracketed by CUDA events on the stream it runs on.
 
 value    = broad-phase particle-steps/s = N * K / (sum of broad-phase times)
@@ -41,7 +41,10 @@ if ROOT not in sys.path:
 METRIC = "broad-phase particle-steps/s and % HBM roofline; rebuild fraction; vs global buffer"
 WORKLOAD = ("settling box: 200,000 polydisperse spheres r~U[0.5,2] mm, rho 2500, LSD k_n 1e4 "
             "e 0.7, velocity Verlet dt 1e-6 s, local skin 0.1 d_i, cell 1.25 d_max")
-L2_FLUSH_BYTES = 256 << 20
+# 1 GiB: well above the 129 MB L2, and long enough on the GPU (~0.15 ms) that
+# the device, not Python's per-step issue rate, is the bottleneck, so the
+# event intervals around each phase hold device time only.
+L2_FLUSH_BYTES = 1 << 30
 T0_SAMPLE = 10_000        # oracle samples start mid-run (step 10,000 of 20,000)
 
 
@@ -120,10 +123,12 @@ def _scene(rank):
 
 
 def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, flush,
-             record=None):
+             record=None, graph=True):
     """Runs warmup + steps DEM steps with per-phase CUDA events.  Returns
     per-phase total ms, stats and the (optional) recorded window."""
     dem = lvb.DEM(scene, trigger=trigger, skin_kind=skin_kind, skin_value=skin_value)
+    if not graph:
+        dem.lvb.set_option(lvb.LVB_OPT_GRAPH, 0)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         flush.zero_()
@@ -315,7 +320,7 @@ def run_native(args):
     scene = _scene(rank)
     n = scene.n
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    m_e2e = min(args.e2e_steps, args.steps)
+    m_e2e = 0 if args.only_local else min(args.e2e_steps, args.steps)
     rec_start = max(0, args.steps // 2 - m_e2e // 2)
 
     if world > 1:
@@ -324,7 +329,7 @@ def run_native(args):
     with Clocks(local) as clk:
         loc = _run_dem(lvb, torch, scene, lvb.LVB_TRIGGER_PARTIAL, scene.skin_kind,
                        scene.skin_value, args.steps, args.warmup, flush,
-                       record=(rec_start, m_e2e))
+                       record=(rec_start, m_e2e) if m_e2e else None, graph=not args.no_graph)
     torch.cuda.synchronize()
     bp_ms = float(loc["phase_ms"][1])
     if world > 1:
@@ -335,6 +340,12 @@ def run_native(args):
         step_ms_tot = float(loc["phase_ms"].sum())
     value = world * n * args.steps / (bp_ms * 1e-3)
 
+    if args.only_local:
+        if rank == 0:
+            ph = loc["phase_ms"] / args.steps
+            print(json.dumps({"only_local": True, "phases_ms_per_step": list(ph),
+                              "value": value, "stats": loc["stats1"]}))
+        return 0
     # global-buffer variant: uniform skin 0.1 * mean diameter, any flag
     # rebuilds the whole list (Def. autoverlet)
     dmean = float(2.0 * scene.pos[:, 3].astype(np.float64).mean())
@@ -366,8 +377,7 @@ def run_native(args):
     bytes_integrate = n * (16.0 * 4 + 32.0)
     kern = {"k_forces (narrow phase + forces)": (ph[2], bytes_forces),
             "k_integrate": (ph[0], bytes_integrate),
-            "broad phase (check + partial rebuild, %d launches)" % s1["launches_per_step"]:
-                (ph[1], bytes_bp)}
+            "broad phase (check + partial rebuild)": (ph[1], bytes_bp)}
     dom = max(kern, key=lambda k: kern[k][0])
     t_ms, b = kern[dom]
     achieved = b / (t_ms * 1e-3) / 1e9
@@ -393,7 +403,7 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "dt": scene.dt, "skin": "0.1 d_i",
                    "trigger": "partial (local buffer)", "l2": "flushed before every timed step "
-                   "(256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+                   "(1 GiB write)", "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "broad_phase": {"ms_per_step": ph[1], "achieved_gbs": bp_ach,
                         "frac_hbm": bp_ach / hbm_peak, "bytes_per_step": bytes_bp},
@@ -408,7 +418,8 @@ def run_native(args):
         "speedup_vs_global": g_bp_ms / bp_ms,
         "list": {"entries": entries, "mean_row": row_len, "relayouts": s1["relayouts"]},
         "e2e": e2e,
-        "gpu_launches": K * (2 + s1["launches_per_step"]),
+        "gpu_launches": int(s1["kernels_executed"] - s0["kernels_executed"]),
+        "small_path_steps": int(s1["small_path_steps"] - s0["small_path_steps"]),
         "clocks": clk.summary(),
         "timed_region_ms_incl_flush": loc["wall_ms"],
     }
@@ -428,6 +439,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-local", action="store_true",
+                    help="time the local-buffer run only (for profiling)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="direct kernel launches instead of graph replays (profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

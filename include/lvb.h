@@ -101,6 +101,7 @@ typedef struct {
     int64_t entries;         /* symmetric list entries (2 x pairs) */
     int64_t pairs;           /* unordered pairs in the list */
     int64_t relayouts;       /* row-store re-layouts (a row outgrew its slack) */
+    int64_t grows;           /* times the row store or the cell slots grew */
     int64_t cell_capacity;   /* slots per cell */
     int64_t row_store_capacity; /* entries the row store can hold */
     int64_t kernels_executed;  /* kernels of this context run on the device
@@ -108,12 +109,26 @@ typedef struct {
     int64_t small_path_steps;  /* steps whose rebuild ran in one block */
     int64_t small_max;       /* flagged counts up to this use the one-block
                                 rebuild (LVB_OPT_SMALL_MAX) */
+    int64_t medium_max;      /* ... up to this the three-kernel rebuild */
     int64_t graphs;          /* 1 if steps replay a CUDA graph */
+    int64_t n_scenes;        /* independent scenes in the context */
+    int64_t fused_phase_cycles[4]; /* SM cycles spent by the one-block rebuild
+                                in its phases (update; rows; appends; cell
+                                moves), summed over steps (thread 0's view) */
+    float cell_edge;         /* L [m] (scene 0) */
+    float rnl_max;           /* cap H on R_NL = r + skin [m] (scene 0) */
+    int32_t grid[3];         /* cells per axis (scene 0) */
+    int32_t pad;
+} lvb_stats_t;
+
+typedef struct {
+    int64_t first;           /* first particle of the scene */
+    int64_t count;           /* particles of the scene */
     float cell_edge;         /* L [m] */
     float rnl_max;           /* cap H on R_NL = r + skin [m] */
     int32_t grid[3];         /* cells per axis */
     int32_t pad;
-} lvb_stats_t;
+} lvb_scene_info_t;
 
 /*
  * lvb_init -- build the context and the first list (Algorithm 1 on the
@@ -143,6 +158,27 @@ typedef struct {
 int lvb_init(lvb_ctx **out, int64_t n, const float *pos_r, const lvb_box *box,
              const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
              const float *vel, const float *acc, void *stream);
+
+/*
+ * lvb_batch_init -- one context over n_scenes independent scenes that
+ * advance together: scene s is particles [offsets[s], offsets[s+1]) of the
+ * arrays, with its own box boxes[s] and its own cell grid (edge from the
+ * scene's largest diameter), and no pair ever joins two scenes.  Every step
+ * of the context covers all scenes in the same launches, so many small
+ * scenes run at the throughput of one large one.
+ *   offsets : host, n_scenes + 1 entries, offsets[0] = 0, strictly
+ *             increasing, offsets[n_scenes] = total particles.
+ *   boxes   : host, n_scenes boxes.
+ * Other arguments as lvb_init.  The GLOBAL trigger is per context, so it is
+ * rejected (EINVAL) for n_scenes > 1; PARTIAL and ALWAYS are per particle.
+ */
+int lvb_batch_init(lvb_ctx **out, int32_t n_scenes, const int64_t *offsets,
+                   const float *pos_r, const lvb_box *boxes, const lvb_skin_policy *skin,
+                   int32_t trigger, float cell_factor, const float *vel, const float *acc,
+                   void *stream);
+
+/* lvb_scene_info -- geometry of one scene of a context. */
+int lvb_scene_info(lvb_ctx *ctx, int32_t scene, lvb_scene_info_t *out);
 
 /*
  * lvb_init_resume -- as lvb_init, but every particle's reference state is
@@ -182,7 +218,24 @@ int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *ac
                                 call made while the stream is being captured
                                 always launches directly. */
 #define LVB_OPT_SMALL_MAX 1  /* steps with at most this many flagged particles
-                                (default 128) rebuild in a single block */
+                                (default 32, at most 1024) rebuild in a
+                                single block */
+#define LVB_OPT_MEDIUM_MAX 2 /* ... up to this many (default 2048) in three
+                                grid-wide kernels; more in five */
+#define LVB_OPT_TRACE     3  /* 1: kernels record their device time (first
+                                block entry to last block exit), read with
+                                lvb_trace; 0 (default): off */
+
+/* Kernel slots of lvb_trace. */
+#define LVB_TRACE_SLOTS 16
+/* 0 check, 1 one-block rebuild, 2-4 three-kernel rebuild (update, rows,
+ * finish), 5-9 five-kernel rebuild (update, compact, insert, rows, append),
+ * 10 re-layout rows, 11 DEM integrate, 12 DEM forces. */
+
+/* lvb_trace -- per-kernel device time summed over the steps traced so far
+ * (ns) and the number of steps each kernel ran in; LVB_TRACE_SLOTS entries
+ * each.  Synchronises. */
+int lvb_trace(lvb_ctx *ctx, uint64_t *sum_ns, uint64_t *count);
 
 /* lvb_set_option -- set an LVB_OPT_* value (synchronises if a cached graph
  * has to be rebuilt).  Errors: EINVAL. */

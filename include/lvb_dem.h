@@ -78,8 +78,19 @@ int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
              const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
              void *stream);
 
+/*
+ * dem_batch_init -- as dem_init over n_scenes independent scenes advancing
+ * together (lvb_batch_init): scene s is particles [offsets[s],
+ * offsets[s+1]) with its walls at boxes[s]; the physics (prm, dt) is shared.
+ * offsets and boxes are host arrays.
+ */
+int dem_batch_init(dem_ctx **out, int32_t n_scenes, const int64_t *offsets,
+                   const float *pos_r, const float *vel, const dem_params *prm, float dt,
+                   const lvb_box *boxes, const lvb_skin_policy *skin, int32_t trigger,
+                   float cell_factor, void *stream);
+
 /* dem_advance -- enqueue `steps` full steps (no synchronisation).  Chunks of
- * steps are replayed from a CUDA graph captured on first use. */
+ * 50 steps replay one CUDA graph, built node by node on first use. */
 int dem_advance(dem_ctx *ctx, int64_t steps);
 
 /* dem_phase -- enqueue one phase (DEM_PHASE_*) of a step; a step is the

@@ -1,0 +1,121 @@
+/*
+ * lvb_mlp.h -- the learned skin: a small network proposes each flagged
+ * particle's skin from its local kinematics (an extension of the paper's
+ * rule skin_p = K |v_p| dt, Eq. skin_formulus1; the paper itself has no
+ * network).  The displacement check (Eq. update) still guards every list,
+ * so a wrong proposal costs time, never a missed contact.
+ *
+ * Network (8 -> 32 -> 32 -> 1, ReLU), evaluated exactly as written, in
+ * binary32 with bfloat16 weights and activations (round to nearest even):
+ *   z_k  = bf16((f_k - mu_k) * isd_k)
+ *   h1_o = bf16(relu(b1_o + sum_{k=0..7}  W1[o][k] z_k))     sums in k order
+ *   h2_o = bf16(relu(b2_o + sum_{k=0..31} W2[o][k] h1_k))
+ *   y    = b3 + sum_{k=0..31} w3[k] h2_k
+ *   skin = (2 r) * max(y, 0), then the cap of lvb.h
+ * relu(x) = x if x > 0 else 0.  Products of bfloat16 values are exact in
+ * binary32, so the result does not depend on fused multiply-add use.
+ *
+ * Features f (binary32, at the step that flags the particle, from the state
+ * before its update; d = 2 r, dt the policy's time step):
+ *   f0 = (|v| dt) / d           f1 = ((|a| dt) dt) / d
+ *   f2 = r / H                  (H: the scene's cap on r + skin)
+ *   f3 = partners of the particle in the list
+ *   f4 = steps since the particle's last update (0 at init)
+ *   f5 = |x - xref| / skin_old  (0 if skin_old = 0)
+ *   f6 = particles whose reference position lies in the cell of x
+ *   f7 = (min over the box planes of the gap x - lo - r, hi - x - r) / d
+ * |.| is sqrt((x*x + y*y) + z*z) with the correctly rounded square root;
+ * at lvb_init all of f3..f6 are 0.
+ *
+ * Label used for training (rebuild logs): the largest displacement of the
+ * particle over the `horizon` steps after its update, divided by d -- the
+ * skin that would have kept it valid for exactly that many steps.
+ */
+#ifndef LVB_MLP_H
+#define LVB_MLP_H
+
+#include <stdint.h>
+
+#include "lvb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LVB_MLP_IN 8
+#define LVB_MLP_HIDDEN 32
+#define LVB_MLP_PARAMS 1377   /* 32*8 + 32 + 32*32 + 32 + 32 + 1 */
+
+/* Device layout of the weights given to LVB_SKIN_LEARNED (lvb_skin_policy.mlp).
+ * W1, W2, w3 hold bfloat16 values stored as binary32 (lvb_mlp_pack rounds
+ * them); row-major [out][in]. */
+typedef struct {
+    float W1[LVB_MLP_HIDDEN * LVB_MLP_IN];
+    float b1[LVB_MLP_HIDDEN];
+    float W2[LVB_MLP_HIDDEN * LVB_MLP_HIDDEN];
+    float b2[LVB_MLP_HIDDEN];
+    float w3[LVB_MLP_HIDDEN];
+    float b3;
+    float mu[LVB_MLP_IN];
+    float isd[LVB_MLP_IN];
+    float pad[3];
+} lvb_mlp_weights;
+
+/*
+ * lvb_mlp_pack -- write an lvb_mlp_weights record from master parameters.
+ *   params : host, LVB_MLP_PARAMS binary32 in the order W1, b1, W2, b2, w3, b3.
+ *   mu, isd: host, LVB_MLP_IN each (feature offset and inverse scale).
+ *   out    : host or device lvb_mlp_weights (weights rounded to bfloat16).
+ */
+int lvb_mlp_pack(const float *params, const float *mu, const float *isd, lvb_mlp_weights *out);
+
+/*
+ * lvb_mlp_infer -- the network on n feature rows: skin[i] = d[i] * max(y, 0)
+ * (no cap) and y[i].  feats: device n x 8; diam, skin, y: device n (y may be
+ * NULL); w: device weights.  Enqueues on `stream`.
+ */
+int lvb_mlp_infer(const float *feats, const float *diam, int64_t n, const lvb_mlp_weights *w,
+                  float *skin, float *y, void *stream);
+
+/*
+ * lvb_mlp_grad -- mean squared error of y against labels over n samples and
+ * its gradient with respect to the master parameters (straight-through
+ * through the bfloat16 roundings).  samples: device n x 9 (8 features,
+ * label); params, mu, isd: host; grad: host LVB_MLP_PARAMS; loss: host.
+ * Synchronises.
+ */
+int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const float *mu,
+                 const float *isd, float *grad, double *loss, void *stream);
+
+/*
+ * lvb_mlp_train -- train the network on the GPU with Adam.
+ *   samples     : device n x 9 (features, label).
+ *   params      : host in/out, LVB_MLP_PARAMS master parameters.
+ *   mu, isd     : host out, the feature normalisation computed from the
+ *                 samples (mean and 1/std per feature).
+ *   losses      : host out, mean loss of every epoch (epochs entries).
+ * Synchronises.  Errors: EINVAL, ENOMEM, EDEVICE.
+ */
+int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch, float lr,
+                  uint64_t seed, float *params, float *mu, float *isd, float *losses,
+                  void *stream);
+
+/*
+ * lvb_log_enable -- start recording training samples from a broad-phase
+ * context (PARTIAL trigger): each particle's update opens a record with its
+ * features; `horizon` steps later the record closes with its label and is
+ * appended to a device buffer of `capacity` samples (later ones are
+ * dropped).  A particle with an open record opens no other.  horizon >= 1.
+ */
+int lvb_log_enable(lvb_ctx *ctx, int32_t horizon, int64_t capacity);
+
+/* lvb_log_read -- copy the recorded samples (n x 9 binary32, host or device)
+ * and their count; cap limits the copy (LVB_ECAPACITY if more exist, with
+ * *n_samples set).  Synchronises. */
+int lvb_log_read(lvb_ctx *ctx, float *samples, int64_t cap, int64_t *n_samples);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LVB_MLP_H */

@@ -36,16 +36,31 @@ TRIGGER_PARTIAL, TRIGGER_GLOBAL, TRIGGER_ALWAYS = 0, 1, 2
 
 
 class OracleLVB:
+    """learned: for SKIN_LEARNED, a dict with "weights" (oracle.mlp.Weights)
+    and "grid" (oracle.mlp.grid_params of the context); the proposal of each
+    updated particle is then the network's, from the features of lvb_mlp.h."""
+
     def __init__(self, pos4, skin_kind, skin_value, dt, H, trigger=TRIGGER_PARTIAL,
-                 vel4=None, proposal=None, ref4=None):
+                 vel4=None, proposal=None, ref4=None, learned=None, acc4=None):
         pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
         self.n = len(pos4)
         self.kind, self.value, self.dt, self.H = int(skin_kind), np.float32(skin_value), \
             np.float32(dt), np.float32(H)
         self.trigger = int(trigger)
         self.rad = pos4[:, 3].copy()
+        self.learned = learned
+        self.born = np.zeros(self.n, dtype=np.int64)
         if ref4 is not None:      # resume from a saved reference state
             self.ref = np.array(ref4, dtype=np.float32, copy=True)
+        elif learned is not None:
+            from . import mlp
+            z = np.zeros(self.n, dtype=np.int64)
+            f = mlp.features(pos4, vel4, acc4, dt, learned["grid"], np.zeros((self.n, 4), np.float32),
+                             z, z, z)
+            prop = mlp.infer(learned["weights"], f, (np.float32(2.0) * pos4[:, 3]))[0]
+            self.ref = np.zeros((self.n, 4), dtype=np.float32)
+            self.ref[:, :3] = pos4[:, :3]
+            self.ref[:, 3] = _skin(SKIN_LEARNED, self.value, self.dt, self.H, pos4, vel4, prop)
         else:
             self.ref = np.zeros((self.n, 4), dtype=np.float32)
             self.ref[:, :3] = pos4[:, :3]
@@ -55,10 +70,11 @@ class OracleLVB:
         self.updates = 0          # particle reference updates (sum over steps of |U|)
         self.rebuild_steps = 0    # steps at which at least one reference changed
 
-    def step(self, pos4, vel4=None, proposal=None):
+    def step(self, pos4, vel4=None, proposal=None, acc4=None):
         """Advance one step; returns (flags, updated) boolean arrays."""
         pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
         f = _flags(pos4, self.ref)
+        step = self.steps + 1
         if self.trigger == TRIGGER_PARTIAL:
             upd = f.copy()
         elif self.trigger == TRIGGER_GLOBAL:
@@ -67,10 +83,13 @@ class OracleLVB:
             upd = np.ones(self.n, dtype=bool)
         if upd.any():
             idx = np.nonzero(upd)[0]
-            self.ref[idx, :3] = pos4[idx, :3]
             v = None if vel4 is None else np.ascontiguousarray(vel4, dtype=np.float32)[idx]
             prop = None if proposal is None else np.asarray(proposal, dtype=np.float32)[idx]
+            if self.learned is not None:
+                prop = self._learned_proposal(idx, pos4, vel4, acc4, step)
+            self.ref[idx, :3] = pos4[idx, :3]
             self.ref[idx, 3] = _skin(self.kind, self.value, self.dt, self.H, pos4[idx], v, prop)
+            self.born[idx] = step
             self.pi, self.pj = _pairs(self.ref, self.rad)
             self.rebuild_steps += 1
             self.updates += len(idx)
@@ -79,3 +98,18 @@ class OracleLVB:
 
     def contacts(self, pos4):
         return _contacts(self.pi, self.pj, pos4)
+
+    def _learned_proposal(self, idx, pos4, vel4, acc4, step):
+        """Network proposal from the state at the start of the step."""
+        from . import mlp
+        grid = self.learned["grid"]
+        nrow = np.bincount(np.concatenate([self.pi, self.pj]), minlength=self.n)[idx]
+        occ_all = np.bincount(mlp.cell_index(self.ref[:, :3], grid),
+                              minlength=int(np.prod(grid["dims"])))
+        occ = occ_all[mlp.cell_index(pos4[idx, :3], grid)]
+        vel = np.asarray(vel4, np.float32)[idx]
+        acc = np.asarray(acc4, np.float32)[idx]
+        feats = mlp.features(pos4[idx], vel, acc, self.dt, grid, self.ref[idx], nrow,
+                             step - self.born[idx], occ)
+        self.last_features = (idx, feats)
+        return mlp.infer(self.learned["weights"], feats, np.float32(2.0) * pos4[idx, 3])[0]

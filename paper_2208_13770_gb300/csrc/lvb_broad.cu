@@ -29,6 +29,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 using namespace lvb;
 
@@ -37,10 +38,20 @@ namespace {
 constexpr int kNumSMs = 152;
 constexpr int kThreads = 256;
 
+// Written by kernels straight into mapped host memory: requests to grow a
+// store before it fills (read by the host before every step, no sync).
+struct HostFlags {
+    int grow_store;
+    int grow_cells;
+    long long store_needed;
+};
+
 struct DevState {
     int n, nwords, trigger, skin_kind;
-    float skin_value, skin_dt, H, pad;
-    GridGeom g;
+    float skin_value, skin_dt;
+    int nscenes, ccap;
+    const SceneGeom *sg;    // per-scene geometry
+    const int *scene_of;    // scene of each particle (null when one scene)
     long long ncells;
     float4 *ref;
     float *rad;
@@ -55,27 +66,55 @@ struct DevState {
     int *tcell, *tcell_mark;
     DevCounters *cnt;
     long long *blk;
+    const lvb_mlp_weights *mlp;   // skin network (LVB_SKIN_LEARNED)
+    int *born;        // step of each particle's last update
+    int *cell_live;   // particles whose reference position lies in each cell
+    // rebuild log (training samples of the skin network)
+    int log_on, log_horizon;
+    long long log_cap;
+    float *lg_feat;   // n x 8 features of the open record
+    float4 *lg_x;     // position at which the record opened
+    int *lg_t;        // step the record opened (-1: none)
+    float *lg_m;      // largest squared displacement since
+    float *log_buf;   // log_cap x 9 samples
+    HostFlags *hflags;    // device view of the mapped host flags
+    int trace;            // record per-kernel device time (LVB_OPT_TRACE)
     cudaGraphConditionalHandle h_path;      // which rebuild body runs
-    cudaGraphConditionalHandle h_relayout;  // whether the re-layout body runs
     int use_cond;     // 1 inside a graph that owns the handles
     int small_max;    // flagged counts up to this use the one-block rebuild
+    int medium_max;   // ... up to this the three-kernel rebuild, above it the five-kernel one
+    float4 *fref_g;   // new (xref, R_NL) of the flagged particles (three-kernel rebuild)
+    int *fid_g;       // their ids
 };
 
-// rebuild paths chosen by the check (values of h_path)
-enum Path { PATH_SMALL = 0, PATH_BIG = 1, PATH_NONE = 2 };
+// bodies of the step's SWITCH, chosen by the check (values of h_path); the
+// one-block rebuild runs inside the check itself, so it needs no body
+enum Path { PATH_MEDIUM = 0, PATH_BIG = 1, PATH_RELAYOUT = 2, PATH_NONE = 3 };
 // gate modes of the kernels
 enum Gate { GATE_FLAGGED_BIG = 0, GATE_OVERFLOW = 1, GATE_ANY_FLAG = 2, GATE_ALWAYS = 3 };
+
+__device__ __forceinline__ const SceneGeom &geom_of(const DevState &s, int i)
+{
+    return s.sg[s.nscenes == 1 ? 0 : s.scene_of[i]];
+}
 
 __device__ __forceinline__ bool store_failed(const DevState &s)
 {
     return (s.cnt->err & DERR_STORE) != 0;
 }
 
-// flagged count when the multi-kernel (big) partial path applies, else 0
+// flagged count when the three-kernel (medium) partial path applies, else 0
+__device__ __forceinline__ int medium_nF(const DevState &s)
+{
+    const int nF = s.cnt->nF;
+    return (store_failed(s) || nF <= s.small_max || nF > s.medium_max) ? 0 : nF;
+}
+
+// flagged count when the five-kernel (big) partial path applies, else 0
 __device__ __forceinline__ int big_nF(const DevState &s)
 {
     const int nF = s.cnt->nF;
-    return (store_failed(s) || nF <= s.small_max) ? 0 : nF;
+    return (store_failed(s) || nF <= s.medium_max) ? 0 : nF;
 }
 
 // After a failed re-layout (DERR_STORE) the row offsets no longer fit the
@@ -94,83 +133,15 @@ __device__ __forceinline__ void count_kernel(const DevState &s)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt->kernels, 1ULL);
 }
 
-// ---------------------------------------------------------------------------
-// a1: displacement check (Eq. update) and compaction of the flagged ids.
-// One particle per thread: 32 B of coalesced loads (pos, ref); one ballot
-// word per warp; one atomic per block.  The last block to finish publishes
-// the step's flagged count, resets the per-step counters, keeps the
-// statistics and, inside a graph, selects the rebuild body to run.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-k_check(const float4 *__restrict__ pos, DevState s)
+// per-kernel trace: first entry and last exit over the kernel's blocks
+__device__ __forceinline__ void tr_enter(const DevState &s, int slot)
 {
-    __shared__ int wcount[kThreads / 32];
-    __shared__ int base;
-    __shared__ bool last;
-    count_kernel(s);
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    bool f = false;
-    if (i < s.n) {
-        float4 p = __ldg(pos + i);
-        float4 q = s.ref[i];
-        f = violates(p, q);
-        if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) atomicOr(&s.cnt->err, DERR_NAN);
-    }
-    const unsigned b = __ballot_sync(FULL, f);
-    const int word = i >> 5;
-    if (lane == 0) {
-        if (word < s.nwords) s.bits[word] = b;
-        wcount[warp] = __popc(b);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            int c = wcount[w];
-            wcount[w] = tot;
-            tot += c;
-        }
-        base = tot ? atomicAdd(&s.cnt->nF_accum, tot) : 0;
-    }
-    __syncthreads();
-    if (f) s.fid[base + wcount[warp] + __popc(b & lanemask_lt())] = i;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&s.cnt->done_blocks, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
-    DevCounters *c = s.cnt;
-    const int nF = atomicExch(&c->nF_accum, 0);
-    c->done_blocks = 0;
-    c->nF = nF;
-    c->ntrow = 0;
-    c->ntcell = 0;
-    c->row_overflow = 0;
-    int upd;
-    if (s.trigger == LVB_TRIGGER_PARTIAL) upd = nF;
-    else if (s.trigger == LVB_TRIGGER_GLOBAL) upd = nF ? s.n : 0;
-    else upd = s.n;
-    c->steps += 1;
-    c->flagged_total += nF;
-    c->updated_total += upd;
-    if (upd) c->rebuild_steps += 1;
-    c->last_flagged = nF;
-    c->last_updated = upd;
-    const bool ok = !(c->err & DERR_STORE);
-    if (s.trigger == LVB_TRIGGER_PARTIAL && ok && nF > 0 && nF <= s.small_max)
-        c->small_steps += 1;
-    if (s.use_cond) {
-        unsigned path;
-        if (s.trigger == LVB_TRIGGER_PARTIAL)
-            path = (!ok || nF == 0) ? PATH_NONE : (nF <= s.small_max ? PATH_SMALL : PATH_BIG);
-        else
-            path = (ok && upd) ? 1u : 0u;
-        cudaGraphSetConditional(s.h_path, path);
-    }
+    if (s.trace && threadIdx.x == 0) atomicMin(&s.cnt->tr_start[slot], global_ns());
+}
+
+__device__ __forceinline__ void tr_exit(const DevState &s, int slot)
+{
+    if (s.trace && (threadIdx.x & 31) == 0) atomicMax(&s.cnt->tr_end[slot], global_ns());
 }
 
 // ---------------------------------------------------------------------------
@@ -179,66 +150,189 @@ k_check(const float4 *__restrict__ pos, DevState s)
 // grid-wide kernel (many flagged particles) or inside one block (few).
 // ---------------------------------------------------------------------------
 
+// Phases that walk a row or a cell run one warp per item (w0/wstride count
+// warps): the lanes take the entries, so a step costs a few memory
+// latencies however long the rows are, and atomics are warp-aggregated.
+
+// Features of the skin network (lvb_mlp.h) from the state before the
+// particle's update; q_old is its old reference state.
+__device__ __forceinline__ void skin_features(const DevState &s, float4 p, float4 v, float4 a,
+                                              float r, const SceneGeom &g, float4 q_old,
+                                              int nrow, int age, int occ, float f[LVB_MLP_IN])
+{
+    const float d = __fmul_rn(2.0f, r);
+    const float vm = __fsqrt_rn(sqdist_rn(v.x, v.y, v.z, 0.f, 0.f, 0.f));
+    const float am = __fsqrt_rn(sqdist_rn(a.x, a.y, a.z, 0.f, 0.f, 0.f));
+    f[0] = __fdiv_rn(__fmul_rn(vm, s.skin_dt), d);
+    f[1] = __fdiv_rn(__fmul_rn(__fmul_rn(am, s.skin_dt), s.skin_dt), d);
+    f[2] = __fdiv_rn(r, g.H);
+    f[3] = (float)nrow;
+    f[4] = (float)age;
+    f[5] = q_old.w > 0.0f
+               ? __fdiv_rn(__fsqrt_rn(sqdist_rn(p.x, p.y, p.z, q_old.x, q_old.y, q_old.z)), q_old.w)
+               : 0.0f;
+    f[6] = (float)occ;
+    float w = __fsub_rn(__fsub_rn(p.x, g.lo[0]), r);
+    w = fminf(w, __fsub_rn(__fsub_rn(g.hi[0], p.x), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(p.y, g.lo[1]), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(g.hi[1], p.y), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(p.z, g.lo[2]), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(g.hi[2], p.z), r));
+    f[7] = __fdiv_rn(w, d);
+}
+
+// Skin of particle i by the context's policy; the learned policy needs the
+// whole warp (all lanes compute the same value).
+__device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g, float r,
+                                           float4 v, const float f[LVB_MLP_IN])
+{
+    float prop = 0.0f;
+    if (s.skin_kind == LVB_SKIN_LEARNED) {
+        const float y = mlp_y_warp(s.mlp, f);
+        prop = __fmul_rn(__fmul_rn(2.0f, r), relu(y));
+    }
+    return skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
+}
+
+// Phases that walk a row or a cell run one warp per item (w0/wstride count
+// warps): the lanes take the entries, so a step costs a few memory
+// latencies however long the rows are, and atomics are warp-aggregated.
+
 // a2 (+ bookkeeping for a3/a5): new reference position and skin of each
 // flagged particle; marks the cell it leaves and every unflagged row that
-// lists it.
+// lists it; opens a rebuild-log record if logging.
 __device__ __forceinline__ void ph_update(const DevState &s, const float4 *__restrict__ pos,
-                                          const float4 *__restrict__ vel, int nF, int k0,
-                                          int stride)
+                                          const float4 *__restrict__ vel,
+                                          const float4 *__restrict__ acc, int nF, int w0,
+                                          int wstride, bool mark_cells = true,
+                                          float4 *fref = nullptr, int *fids = nullptr,
+                                          bool mark_slots = false)
 {
-    for (int k = k0; k < nF; k += stride) {
+    const int lane = threadIdx.x & 31;
+    const bool feats = s.skin_kind == LVB_SKIN_LEARNED || s.log_on;
+    const int step = (int)s.cnt->steps;
+    for (int k = w0; k < nF; k += wstride) {
         const int i = s.fid[k];
         const float4 p = pos[i];
         const float r = s.rad[i];
         const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, s.H, r, v, 0.0f);
-        s.ref[i] = make_float4(p.x, p.y, p.z, sk);
-        const int nc = cell_key(s.g, p.x, p.y, p.z);
+        const SceneGeom &g = geom_of(s, i);
+        const int nc = cell_key(g, p.x, p.y, p.z);
         const int oc = s.cell_of[i];
-        s.newcell[i] = nc;
-        if (nc != oc && atomicExch(&s.tcell_mark[oc], 1) == 0)
-            s.tcell[atomicAdd(&s.cnt->ntcell, 1)] = oc;
         const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
-        for (int e = 0; e < len; ++e) {
-            const int j = s.col[off + e];
-            if (!bit_of(s.bits, j) && atomicExch(&s.trow_mark[j], 1) == 0)
-                s.trow[atomicAdd(&s.cnt->ntrow, 1)] = j;
+        float f[LVB_MLP_IN];
+        if (feats) {
+            const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            skin_features(s, p, v, a, r, g, s.ref[i], len, step - s.born[i], s.cell_live[nc], f);
+        }
+        const float sk = warp_skin(s, g, r, v, f);
+        if (lane == 0) {
+            s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+            s.born[i] = step;
+            if (fref) {
+                fref[k] = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+                fids[k] = i;
+            }
+            s.newcell[i] = nc;
+            // the three-phase rebuilds hide flagged particles from the cells'
+            // readers until their slots move: a negative id -2 - i
+            if (mark_slots) s.cell_id[(long long)oc * s.ccap + s.slot_of[i]] = -2 - i;
+            if (mark_cells && nc != oc && atomicExch(&s.tcell_mark[oc], 1) == 0)
+                s.tcell[atomicAdd(&s.cnt->ntcell, 1)] = oc;
+            if (s.log_on && s.lg_t[i] < 0) {
+                s.lg_t[i] = step;
+                s.lg_x[i] = p;
+                s.lg_m[i] = 0.0f;
+#pragma unroll
+                for (int q = 0; q < LVB_MLP_IN; ++q) s.lg_feat[(long long)i * LVB_MLP_IN + q] = f[q];
+            }
+        }
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            int j = 0;
+            bool push = false;
+            if (e < len) {
+                j = s.col[off + e];
+                push = !bit_of(s.bits, j) && atomicExch(&s.trow_mark[j], 1) == 0;
+            }
+            const unsigned m = __ballot_sync(FULL, push);
+            if (m) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s.cnt->ntrow, __popc(m));
+                base = __shfl_sync(FULL, base, 0);
+                if (push) s.trow[base + __popc(m & lanemask_lt())] = j;
+            }
         }
     }
 }
 
-// a5 (removal) and a3 (leavers): one item per touched row or cell.
-__device__ __forceinline__ void ph_compact(const DevState &s, int k0, int stride)
+// a5 (removal): unflagged row j drops its flagged entries; one warp, stable
+// in-place compaction (every lane reads its entry before the ballot, and an
+// entry only moves to a lower index).
+__device__ __forceinline__ void compact_row_warp(const DevState &s, int j)
 {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int off = s.row_off[j], len = min(s.row_len[j], s.row_cap[j]);
+    int w = 0;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        int c = 0;
+        bool keep = false;
+        if (e < len) {
+            c = s.col[off + e];
+            keep = !bit_of(s.bits, c);
+        }
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) s.col[off + w + __popc(m & lt)] = c;
+        w += __popc(m);
+    }
+    if (lane == 0) {
+        s.row_len[j] = w;
+        s.trow_mark[j] = 0;
+    }
+}
+
+// a5 (removal) and a3 (leavers): one warp per touched row or cell.
+__device__ __forceinline__ void ph_compact(const DevState &s, int w0, int wstride)
+{
+    const int lane = threadIdx.x & 31;
     const int ntrow = s.cnt->ntrow, ntcell = s.cnt->ntcell;
-    const int ccap = s.g.ccap;
-    for (int k = k0; k < ntrow + ntcell; k += stride) {
+    const int ccap = s.ccap;
+    const unsigned lt = lanemask_lt();
+    for (int k = w0; k < ntrow + ntcell; k += wstride) {
         if (k < ntrow) {
-            const int j = s.trow[k];
-            const int off = s.row_off[j], len = min(s.row_len[j], s.row_cap[j]);
-            int w = 0;
-            for (int e = 0; e < len; ++e) {
-                const int c = s.col[off + e];
-                if (!bit_of(s.bits, c)) s.col[off + w++] = c;
-            }
-            s.row_len[j] = w;
-            s.trow_mark[j] = 0;
+            compact_row_warp(s, s.trow[k]);
         } else {
             const int c = s.tcell[k - ntrow];
             const long long base = (long long)c * ccap;
             const int cn = min(s.cell_cnt[c], ccap);
             int w = 0;
-            for (int sl = 0; sl < cn; ++sl) {
-                const int id = s.cell_id[base + sl];
-                if (bit_of(s.bits, id) && s.newcell[id] != c) continue;   // left
-                const float4 q = s.ref[id];
-                s.cell_id[base + w] = id;
-                s.cell_ref[base + w] = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[id], q.w));
-                s.slot_of[id] = w;
-                ++w;
+            for (int e0 = 0; e0 < cn; e0 += 32) {
+                const int sl = e0 + lane;
+                int id = 0;
+                bool keep = false;
+                if (sl < cn) {
+                    id = s.cell_id[base + sl];
+                    // tombstones (id < 0) and leavers go
+                    keep = id >= 0 && !(bit_of(s.bits, id) && s.newcell[id] != c);
+                }
+                const unsigned m = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int dst = w + __popc(m & lt);
+                    const float4 q = s.ref[id];
+                    s.cell_id[base + dst] = id;
+                    s.cell_ref[base + dst] = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[id], q.w));
+                    s.slot_of[id] = dst;
+                }
+                w += __popc(m);
             }
-            s.cell_cnt[c] = w;
-            s.tcell_mark[c] = 0;
+            for (int sl = w + lane; sl < cn; sl += 32) s.cell_id[base + sl] = -1;
+            if (lane == 0) {
+                s.cell_cnt[c] = w;
+                s.cell_live[c] = w;
+                s.tcell_mark[c] = 0;
+            }
         }
     }
 }
@@ -247,7 +341,7 @@ __device__ __forceinline__ void ph_compact(const DevState &s, int k0, int stride
 // that stay refresh their slot's copy of the reference state.
 __device__ __forceinline__ void ph_insert(const DevState &s, int nF, int k0, int stride)
 {
-    const int ccap = s.g.ccap;
+    const int ccap = s.ccap;
     for (int k = k0; k < nF; k += stride) {
         const int i = s.fid[k];
         const int nc = s.newcell[i];
@@ -255,6 +349,8 @@ __device__ __forceinline__ void ph_insert(const DevState &s, int nF, int k0, int
         const float4 cr = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
         if (nc != s.cell_of[i]) {
             const int sl = atomicAdd(&s.cell_cnt[nc], 1);
+            atomicAdd(&s.cell_live[nc], 1);
+            if (sl * 4 >= ccap * 3) s.hflags->grow_cells = 1;
             if (sl < ccap) {
                 s.cell_id[(long long)nc * ccap + sl] = i;
                 s.cell_ref[(long long)nc * ccap + sl] = cr;
@@ -275,24 +371,38 @@ __device__ __forceinline__ void ph_insert(const DevState &s, int nF, int k0, int
 // shuffle binary search, so lanes stay busy across cell boundaries.
 // fill = 0 counts only (row_len = count); fill = 1 also writes up to the
 // row's capacity and raises row_overflow if the row does not fit.
-// Items are fid[w] when `from_list`, else particle w.
+// Items are fid[w] when `from_list`, else particle w.  Cell slots holding a
+// tombstone (id < 0) are skipped.
+// fx != null selects the three-phase rebuilds' form: the cells still hold
+// the flagged particles at their old positions, marked with negative ids,
+// so they are skipped, and the flagged-flagged pairs come from a direct test
+// against the new references of all flagged particles (fx: xyz + R_NL, ids,
+// count); the stencil is centred on the new cell newcell[i].
+struct FlaggedSet {
+    const float4 *ref;   // new (xref, R_NL) of the flagged particles
+    const int *id;
+    int n;
+};
+
 __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from_list, int fill,
-                                        int w0, int wstride)
+                                        int w0, int wstride, const FlaggedSet *fx = nullptr)
 {
     const int lane = threadIdx.x & 31;
-    const int ccap = s.g.ccap;
-    const int d0 = s.g.dim[0], d1 = s.g.dim[1], d2 = s.g.dim[2];
+    const int ccap = s.ccap;
+    const unsigned lt = lanemask_lt();
     for (int w = w0; w < nitems; w += wstride) {
         const int i = from_list ? s.fid[w] : w;
+        const SceneGeom &g = geom_of(s, i);
+        const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
         const float4 q = s.ref[i];
         const float4 qi = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
-        const int ci = s.cell_of[i];
+        const int ci = (fx ? s.newcell[i] : s.cell_of[i]) - g.cell_base;
         const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
         int cnt_l = 0, cid = 0;
         if (lane < 27) {
             const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
             if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
-                cid = (z * d1 + y) * d0 + x;
+                cid = g.cell_base + (z * d1 + y) * d0 + x;
                 cnt_l = min(s.cell_cnt[cid], ccap);
             }
         }
@@ -315,14 +425,31 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
             if (k < total) {
                 const long long idx = (long long)cc * ccap + (k - ex);
                 j = s.cell_id[idx];
-                if (j != i) hit = pair_hit(qi, s.cell_ref[idx]);
+                if (j >= 0 && j != i) hit = pair_hit(qi, s.cell_ref[idx]);
             }
             const unsigned m = __ballot_sync(FULL, hit);
             if (fill && hit) {
-                const int p = found + __popc(m & lanemask_lt());
+                const int p = found + __popc(m & lt);
                 if (p < cap) s.col[off + p] = j;
             }
             found += __popc(m);
+        }
+        if (fx) {
+            for (int b0 = 0; b0 < fx->n; b0 += 32) {
+                const int k = b0 + lane;
+                bool hit = false;
+                int j = -1;
+                if (k < fx->n) {
+                    j = fx->id[k];
+                    hit = j != i && pair_hit(qi, fx->ref[k]);
+                }
+                const unsigned m = __ballot_sync(FULL, hit);
+                if (fill && hit) {
+                    const int p = found + __popc(m & lt);
+                    if (p < cap) s.col[off + p] = j;
+                }
+                found += __popc(m);
+            }
         }
         if (lane == 0) {
             s.row_len[i] = found;
@@ -331,15 +458,70 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
     }
 }
 
-// a5 (insertion): flagged i joins the row of each unflagged partner.
-__device__ __forceinline__ void ph_append(const DevState &s, int nF, int k0, int stride)
+// The one-block rebuild's cell move of flagged particle i (warp): a leaver
+// leaves a tombstone in its old slot and takes a tombstone slot of its new
+// cell (claimed with compare-and-swap) or a fresh slot at the end; a stayer
+// refreshes its slot's copy of the reference state.
+__device__ __forceinline__ void cell_move_warp(const DevState &s, int i)
 {
-    for (int k = k0; k < nF; k += stride) {
+    const int lane = threadIdx.x & 31;
+    const int ccap = s.ccap;
+    const int nc = s.newcell[i], oc = s.cell_of[i], so = s.slot_of[i];
+    const float4 q = s.ref[i];
+    const float4 cr = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
+    if (nc == oc) {
+        if (lane == 0) {
+            s.cell_ref[(long long)oc * ccap + so] = cr;
+            s.cell_id[(long long)oc * ccap + so] = i;    // unmark
+        }
+        return;
+    }
+    if (lane == 0) {
+        s.cell_id[(long long)oc * ccap + so] = -1;
+        atomicSub(&s.cell_live[oc], 1);
+        atomicAdd(&s.cell_live[nc], 1);
+    }
+    const long long base = (long long)nc * ccap;
+    const int cn = min(s.cell_cnt[nc], ccap);
+    int slot = -1;
+    for (int e0 = 0; e0 < cn && slot < 0; e0 += 32) {
+        const int sl = e0 + lane;
+        unsigned m = __ballot_sync(FULL, sl < cn && s.cell_id[base + sl] < 0);
+        while (m && slot < 0) {
+            const int src = __ffs(m) - 1;
+            int won = 0;
+            if (lane == src) won = atomicCAS(&s.cell_id[base + sl], -1, i) == -1;
+            won = __shfl_sync(FULL, won, src);
+            if (won) slot = e0 + src;
+            m &= m - 1;
+        }
+    }
+    if (lane == 0) {
+        if (slot < 0) {
+            slot = atomicAdd(&s.cell_cnt[nc], 1);
+            if (slot * 4 >= ccap * 3) s.hflags->grow_cells = 1;
+            if (slot < ccap) s.cell_id[base + slot] = i;
+            else atomicOr(&s.cnt->err, DERR_CELL);
+        }
+        if (slot < ccap) {
+            s.cell_ref[base + slot] = cr;
+            s.slot_of[i] = slot;
+        }
+        s.cell_of[i] = nc;
+    }
+}
+
+// a5 (insertion): flagged i joins the row of each unflagged partner; one
+// warp per flagged particle, one lane per partner.
+__device__ __forceinline__ void ph_append(const DevState &s, int nF, int w0, int wstride)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = w0; k < nF; k += wstride) {
         const int i = s.fid[k];
         const int len = s.row_len[i];
         if (len > s.row_cap[i]) continue;     // re-layout rebuilds everything
         const int off = s.row_off[i];
-        for (int e = 0; e < len; ++e) {
+        for (int e = lane; e < len; e += 32) {
             const int j = s.col[off + e];
             if (bit_of(s.bits, j)) continue;  // j's own new row lists i
             const int p = atomicAdd(&s.row_len[j], 1);
@@ -349,46 +531,236 @@ __device__ __forceinline__ void ph_append(const DevState &s, int nF, int k0, int
     }
 }
 
-__device__ __forceinline__ void set_relayout_cond(const DevState &s)
+__device__ __forceinline__ void set_relayout_cond(const DevState &s,
+                                                  cudaGraphConditionalHandle h)
 {
     if (s.use_cond)
-        cudaGraphSetConditional(s.h_relayout,
-                                (s.cnt->row_overflow && !store_failed(s)) ? 1u : 0u);
+        cudaGraphSetConditional(h, (s.cnt->row_overflow && !store_failed(s)) ? 1u : 0u);
 }
 
 // The whole partial rebuild in one block, for steps with few flagged
-// particles: five phases separated by block barriers instead of five
-// launches.
-constexpr int kFusedThreads = 1024;
+// particles, in three phases separated by block barriers:
+//   1. new reference + skin of every flagged particle (kept in shared
+//      memory too) and the marks of the unflagged rows that list it;
+//   2. its new row: the 27-cell stencil over the unflagged particles (the
+//      cells still hold the flagged ones at their old places, marked, so
+//      they are skipped) plus a direct test against every other flagged
+//      particle; at the same time the marked rows drop their flagged entries;
+//   3. it joins its unflagged partners' rows and moves to its new cell slot.
+// Runs in the last block of the check kernel (1024 threads).
+constexpr int kCheckThreads = 1024;
+constexpr int kFusedMax = 1024;   // flagged particles the one-block form takes
 
-__global__ void __launch_bounds__(kFusedThreads)
-k_p_fused(const float4 *__restrict__ pos, const float4 *__restrict__ vel, DevState s)
+__device__ __forceinline__ void fused_rebuild(const DevState &s, const float4 *__restrict__ pos,
+                                              const float4 *__restrict__ vel,
+                                              const float4 *__restrict__ acc, int nF,
+                                              float4 *fref, int *fid_s)
 {
-    const int nF = s.cnt->nF;
-    if (store_failed(s) || nF == 0 || nF > s.small_max) return;
+    const int t = threadIdx.x, wid = t >> 5, nw = kCheckThreads / 32;
+    long long c0 = clock64();
+    ph_update(s, pos, vel, acc, nF, wid, nw, /*mark_cells=*/false, fref, fid_s,
+              /*mark_slots=*/true);
+    __syncthreads();
+    long long c1 = clock64();
+    const FlaggedSet fx = {fref, fid_s, nF};
+    const int ntrow = s.cnt->ntrow;
+    for (int w = wid; w < nF + ntrow; w += nw) {
+        if (w < nF) ph_rows(s, w + 1, true, 1, w, nF + 1, &fx);
+        else compact_row_warp(s, s.trow[w - nF]);
+    }
+    __syncthreads();
+    long long c2 = clock64();
+    ph_append(s, nF, wid, nw);
+    long long c3 = clock64();
+    for (int k = wid; k < nF; k += nw) cell_move_warp(s, fid_s[k]);
+    __syncthreads();
+    if (t == 0) {
+        const long long c4 = clock64();
+        atomicAdd(&s.cnt->fused_cycles[0], (unsigned long long)(c1 - c0));
+        atomicAdd(&s.cnt->fused_cycles[1], (unsigned long long)(c2 - c1));
+        atomicAdd(&s.cnt->fused_cycles[2], (unsigned long long)(c3 - c2));
+        atomicAdd(&s.cnt->fused_cycles[3], (unsigned long long)(c4 - c3));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a1: displacement check (Eq. update) and compaction of the flagged ids, for
+// every particle; with `ia.active` each thread first performs the DEM
+// driver's position half-step of its particle.  At most two blocks per SM
+// stride over the particles (one ballot word per warp, one atomic per block
+// iteration that found flags).  The last block to finish publishes the
+// step's flagged count, resets the per-step counters, keeps the statistics,
+// runs the one-block rebuild itself when few particles are flagged, and
+// inside a graph selects the SWITCH body that still has to run.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCheckThreads, 1)
+k_check(const float4 *__restrict__ pos_in, const float4 *__restrict__ vel,
+        const float4 *__restrict__ acc, DevState s, IntegrateArgs ia)
+{
+    __shared__ int wcount[kCheckThreads / 32];
+    __shared__ int base;
+    __shared__ bool last;
+    __shared__ int s_nF, s_small;
+    __shared__ float4 fref[kFusedMax];
+    __shared__ int fid_s[kFusedMax];
     count_kernel(s);
-    const int t = threadIdx.x;
-    ph_update(s, pos, vel, nF, t, kFusedThreads);
+    tr_enter(s, TR_CHECK);
+    const float4 *pos = ia.active ? ia.pos : pos_in;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = blockIdx.x * kCheckThreads; i0 < s.n; i0 += gridDim.x * kCheckThreads) {
+        const int i = i0 + threadIdx.x;
+        bool f = false;
+        if (i < s.n) {
+            const float4 p = ia.active ? integrate_one(ia, geom_of(s, i), i) : __ldg(pos_in + i);
+            const float4 q = s.ref[i];
+            f = violates(p, q);
+            if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z)))
+                atomicOr(&s.cnt->err, DERR_NAN);
+        }
+        const unsigned b = __ballot_sync(FULL, f);
+        if (lane == 0) {
+            if ((i >> 5) < s.nwords) s.bits[i >> 5] = b;
+            wcount[warp] = __popc(b);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kCheckThreads / 32; ++w) {
+                const int c = wcount[w];
+                wcount[w] = tot;
+                tot += c;
+            }
+            base = tot ? atomicAdd(&s.cnt->nF_accum, tot) : 0;
+        }
+        __syncthreads();
+        if (f) s.fid[base + wcount[warp] + __popc(b & lanemask_lt())] = i;
+        __syncthreads();
+    }
+    __threadfence();   // flags, ids and new positions visible to the last block
     __syncthreads();
-    ph_compact(s, t, kFusedThreads);
+    if (threadIdx.x == 0) last = atomicAdd(&s.cnt->done_blocks, 1u) == gridDim.x - 1;
     __syncthreads();
-    ph_insert(s, nF, t, kFusedThreads);
+    if (!last) return;
+    DevCounters *c = s.cnt;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (s.trace) {   // fold the kernels of the previous step
+            for (int k = 1; k < kTraceSlots; ++k) {
+                const unsigned long long a = c->tr_start[k], bb = c->tr_end[k];
+                if (bb != 0 && bb >= a) {
+                    c->tr_sum[k] += bb - a;
+                    c->tr_cnt[k] += 1;
+                }
+                c->tr_start[k] = ~0ULL;
+                c->tr_end[k] = 0;
+            }
+        }
+        const int nF = atomicExch(&c->nF_accum, 0);
+        c->done_blocks = 0;
+        c->nF = nF;
+        c->ntrow = 0;
+        c->ntcell = 0;
+        c->row_overflow = 0;
+        int upd;
+        if (s.trigger == LVB_TRIGGER_PARTIAL) upd = nF;
+        else if (s.trigger == LVB_TRIGGER_GLOBAL) upd = nF ? s.n : 0;
+        else upd = s.n;
+        c->steps += 1;
+        c->flagged_total += nF;
+        c->updated_total += upd;
+        if (upd) c->rebuild_steps += 1;
+        c->last_flagged = nF;
+        c->last_updated = upd;
+        const bool ok = !(c->err & DERR_STORE);
+        const bool small = s.trigger == LVB_TRIGGER_PARTIAL && ok && nF > 0 &&
+                           nF <= s.small_max && nF <= kFusedMax;
+        if (small) c->small_steps += 1;
+        s_nF = nF;
+        s_small = small;
+    }
     __syncthreads();
-    ph_rows(s, nF, true, 1, t >> 5, kFusedThreads / 32);
-    __syncthreads();
-    ph_append(s, nF, t, kFusedThreads);
-    __syncthreads();
-    if (t == 0) set_relayout_cond(s);
+    if (s_small) fused_rebuild(s, pos, vel, acc, s_nF, fref, fid_s);
+    if (threadIdx.x == 0) {
+        const int nF = s_nF;
+        const bool ok = !(c->err & DERR_STORE);
+        if (s.use_cond) {
+            unsigned path;
+            if (s.trigger == LVB_TRIGGER_PARTIAL) {
+                if (!ok || nF == 0) path = PATH_NONE;
+                else if (s_small) path = c->row_overflow ? PATH_RELAYOUT : PATH_NONE;
+                else path = nF <= s.medium_max ? PATH_MEDIUM : PATH_BIG;
+            } else {
+                path = (ok && c->last_updated) ? 1u : 0u;
+            }
+            cudaGraphSetConditional(s.h_path, path);
+        }
+        if (s.trace) {
+            c->tr_sum[TR_CHECK] += global_ns() - c->tr_start[TR_CHECK];
+            c->tr_cnt[TR_CHECK] += 1;
+            c->tr_start[TR_CHECK] = ~0ULL;
+        }
+    }
+}
+
+// Three-kernel partial path, for steps with more flagged particles than one
+// block takes: the same three phases as the one-block form, each a grid-wide kernel,
+// with the flagged particles' new references in global scratch.
+__global__ void __launch_bounds__(kThreads)
+k_m_update(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+           const float4 *__restrict__ acc, DevState s)
+{
+    const int nF = medium_nF(s);
+    if (!nF) return;
+    count_kernel(s);
+    tr_enter(s, TR_M_UPDATE);
+    ph_update(s, pos, vel, acc, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5,
+              (gridDim.x * kThreads) >> 5, /*mark_cells=*/false, s.fref_g, s.fid_g,
+              /*mark_slots=*/true);
+    tr_exit(s, TR_M_UPDATE);
+}
+
+__global__ void __launch_bounds__(kThreads, 4)
+k_m_rows(DevState s)
+{
+    const int nF = medium_nF(s);
+    if (!nF) return;
+    count_kernel(s);
+    tr_enter(s, TR_M_ROWS);
+    const FlaggedSet fx = {s.fref_g, s.fid_g, nF};
+    const int ntrow = s.cnt->ntrow;
+    const int nw = (gridDim.x * kThreads) >> 5;
+    for (int w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nF + ntrow; w += nw) {
+        if (w < nF) ph_rows(s, w + 1, true, 1, w, nF + 1, &fx);
+        else compact_row_warp(s, s.trow[w - nF]);
+    }
+    tr_exit(s, TR_M_ROWS);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_m_finish(DevState s)
+{
+    const int nF = medium_nF(s);
+    if (!nF) return;
+    count_kernel(s);
+    tr_enter(s, TR_M_FINISH);
+    const int w0 = (blockIdx.x * kThreads + threadIdx.x) >> 5, nw = (gridDim.x * kThreads) >> 5;
+    ph_append(s, nF, w0, nw);
+    for (int k = w0; k < nF; k += nw) cell_move_warp(s, s.fid_g[k]);
+    tr_exit(s, TR_M_FINISH);
 }
 
 // Multi-kernel partial path, for steps with many flagged particles.
 __global__ void __launch_bounds__(kThreads)
-k_p_update(const float4 *__restrict__ pos, const float4 *__restrict__ vel, DevState s)
+k_p_update(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+           const float4 *__restrict__ acc, DevState s)
 {
     const int nF = big_nF(s);
     if (!nF) return;
     count_kernel(s);
-    ph_update(s, pos, vel, nF, blockIdx.x * kThreads + threadIdx.x, gridDim.x * kThreads);
+    tr_enter(s, TR_P_UPDATE);
+    ph_update(s, pos, vel, acc, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5,
+              (gridDim.x * kThreads) >> 5);
+    tr_exit(s, TR_P_UPDATE);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -396,7 +768,9 @@ k_p_compact(DevState s)
 {
     if (!big_nF(s)) return;
     count_kernel(s);
-    ph_compact(s, blockIdx.x * kThreads + threadIdx.x, gridDim.x * kThreads);
+    tr_enter(s, TR_P_COMPACT);
+    ph_compact(s, (blockIdx.x * kThreads + threadIdx.x) >> 5, (gridDim.x * kThreads) >> 5);
+    tr_exit(s, TR_P_COMPACT);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -405,7 +779,9 @@ k_p_insert(DevState s)
     const int nF = big_nF(s);
     if (!nF) return;
     count_kernel(s);
+    tr_enter(s, TR_P_INSERT);
     ph_insert(s, nF, blockIdx.x * kThreads + threadIdx.x, gridDim.x * kThreads);
+    tr_exit(s, TR_P_INSERT);
 }
 
 __global__ void __launch_bounds__(kThreads, 4)
@@ -414,8 +790,11 @@ k_rows(DevState s, int gate, int fill)
     const int nitems = gated_items(s, gate);
     if (!nitems) return;
     count_kernel(s);
+    const int slot = gate == GATE_OVERFLOW ? TR_RELAYOUT : TR_ROWS;
+    tr_enter(s, slot);
     ph_rows(s, nitems, gate == GATE_FLAGGED_BIG, fill, (blockIdx.x * kThreads + threadIdx.x) >> 5,
             (gridDim.x * kThreads) >> 5);
+    tr_exit(s, slot);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -424,14 +803,16 @@ k_p_append(DevState s)
     const int nF = big_nF(s);
     if (!nF) return;
     count_kernel(s);
-    ph_append(s, nF, blockIdx.x * kThreads + threadIdx.x, gridDim.x * kThreads);
+    tr_enter(s, TR_P_APPEND);
+    ph_append(s, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5, (gridDim.x * kThreads) >> 5);
+    tr_exit(s, TR_P_APPEND);
 }
 
-// end of a rebuild body inside a graph: arm the re-layout body if needed
-__global__ void k_set_relayout(DevState s)
+// end of a rebuild body inside a graph: arm its re-layout body if needed
+__global__ void k_set_relayout(DevState s, cudaGraphConditionalHandle h)
 {
     count_kernel(s);
-    set_relayout_cond(s);
+    set_relayout_cond(s, h);
 }
 
 // end of the re-layout body
@@ -441,6 +822,11 @@ __global__ void k_relayout_done(DevState s)
     count_kernel(s);
     s.cnt->relayouts += 1;
     s.cnt->row_overflow = 0;
+    const long long need = s.cnt->store_needed;
+    if (need * 4 > s.col_cap * 3) {        // over 75% of the store: grow it
+        s.hflags->store_needed = need;
+        s.hflags->grow_store = 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -456,9 +842,66 @@ k_full_update(const float4 *__restrict__ pos, const float4 *__restrict__ vel, De
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < items; i += gridDim.x * kThreads) {
         const float4 p = pos[i];
         const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, s.H, s.rad[i], v, 0.0f);
+        const SceneGeom &g = geom_of(s, i);
+        const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, s.rad[i], v, 0.0f);
         s.ref[i] = make_float4(p.x, p.y, p.z, sk);
-        s.cell_of[i] = cell_key(s.g, p.x, p.y, p.z);
+        s.cell_of[i] = cell_key(g, p.x, p.y, p.z);
+    }
+}
+
+// Init with the learned policy: the network needs a whole warp, so one
+// warp per particle; the list does not exist yet, so partners, age, the
+// old-skin ratio and the cell occupancy enter as 0.
+__global__ void __launch_bounds__(kThreads)
+k_full_update_learned(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                      const float4 *__restrict__ acc, DevState s)
+{
+    count_kernel(s);
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * kThreads + threadIdx.x) >> 5; i < s.n;
+         i += (gridDim.x * kThreads) >> 5) {
+        const float4 p = pos[i];
+        const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float r = s.rad[i];
+        const SceneGeom &g = geom_of(s, i);
+        float f[LVB_MLP_IN];
+        skin_features(s, p, v, a, r, g, make_float4(0.f, 0.f, 0.f, 0.f), 0, 0, 0, f);
+        const float sk = warp_skin(s, g, r, v, f);
+        if (lane == 0) {
+            s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+            s.cell_of[i] = cell_key(g, p.x, p.y, p.z);
+        }
+    }
+}
+
+// Rebuild log: every open record tracks the particle's largest displacement
+// since it opened, and closes `horizon` steps later with label
+// sqrt(max |x - x_open|^2) / d.
+__global__ void __launch_bounds__(kThreads)
+k_log_step(const float4 *__restrict__ pos, DevState s)
+{
+    count_kernel(s);
+    const int step = (int)s.cnt->steps;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < s.n; i += gridDim.x * kThreads) {
+        const int t = s.lg_t[i];
+        if (t < 0) continue;
+        const float4 p = pos[i];
+        const float4 x0 = s.lg_x[i];
+        const float m = fmaxf(s.lg_m[i], sqdist_rn(p.x, p.y, p.z, x0.x, x0.y, x0.z));
+        if (step - t >= s.log_horizon) {
+            const long long idx =
+                (long long)atomicAdd((unsigned long long *)&s.cnt->log_n, 1ULL);
+            if (idx < s.log_cap) {
+                float *o = s.log_buf + idx * (LVB_MLP_IN + 1);
+#pragma unroll
+                for (int q = 0; q < LVB_MLP_IN; ++q) o[q] = s.lg_feat[(long long)i * LVB_MLP_IN + q];
+                o[LVB_MLP_IN] = __fdiv_rn(__fsqrt_rn(m), __fmul_rn(2.0f, s.rad[i]));
+            }
+            s.lg_t[i] = -1;
+        } else {
+            s.lg_m[i] = m;
+        }
     }
 }
 
@@ -469,13 +912,14 @@ k_load_ref(const float4 *__restrict__ ref4, DevState s, unsigned *bad)
 {
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < s.n; i += gridDim.x * kThreads) {
         const float4 q = ref4[i];
-        float capv = __fsub_rn(s.H, s.rad[i]);
+        const SceneGeom &g = geom_of(s, i);
+        float capv = __fsub_rn(g.H, s.rad[i]);
         if (!(capv > 0.0f)) capv = 0.0f;
         const bool ok = isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && q.w >= 0.0f &&
                         q.w <= capv;
         if (!ok) atomicOr(bad, 1u);
         s.ref[i] = q;
-        s.cell_of[i] = cell_key(s.g, q.x, q.y, q.z);
+        s.cell_of[i] = cell_key(g, q.x, q.y, q.z);
     }
 }
 
@@ -485,8 +929,10 @@ k_cells_clear(DevState s, int gate)
     if (gated_items(s, gate) == 0) return;
     count_kernel(s);
     for (long long c = blockIdx.x * kThreads + threadIdx.x; c < s.ncells;
-         c += (long long)gridDim.x * kThreads)
+         c += (long long)gridDim.x * kThreads) {
         s.cell_cnt[c] = 0;
+        s.cell_live[c] = 0;
+    }
 }
 
 // count_only: occupancy histogram (init, before the slot capacity is known)
@@ -496,11 +942,12 @@ k_cells_insert(DevState s, int gate, int count_only)
     const int items = gated_items(s, gate);
     if (!items) return;
     count_kernel(s);
-    const int ccap = s.g.ccap;
+    const int ccap = s.ccap;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < items; i += gridDim.x * kThreads) {
         const int c = s.cell_of[i];
         const int sl = atomicAdd(&s.cell_cnt[c], 1);
         if (count_only) continue;
+        atomicAdd(&s.cell_live[c], 1);
         if (sl < ccap) {
             const float4 q = s.ref[i];
             s.cell_id[(long long)c * ccap + sl] = i;
@@ -631,16 +1078,18 @@ k_scan_down(ScanArgs a, DevState s, int gate)
 // ---------------------------------------------------------------------------
 // Init helpers.
 // ---------------------------------------------------------------------------
-__global__ void k_radius_scan(const float4 *__restrict__ pos, int n, unsigned *out)
+// out[0] = min radius bits, out[1] = bad input, out[2 + s] = max radius
+// bits of scene s (positive floats order like their bit patterns)
+__global__ void k_radius_scan(const float4 *__restrict__ pos, int n, const int *scene_of,
+                              unsigned *out)
 {
-    // out[0] = max radius bits, out[1] = min radius bits, out[2] = bad input
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         const float4 p = pos[i];
         const bool ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) &&
                         p.w > 0.0f;
-        if (!ok) { atomicOr(&out[2], 1u); continue; }
-        atomicMax(&out[0], __float_as_uint(p.w));
-        atomicMin(&out[1], __float_as_uint(p.w));
+        if (!ok) { atomicOr(&out[1], 1u); continue; }
+        atomicMin(&out[0], __float_as_uint(p.w));
+        atomicMax(&out[2 + (scene_of ? scene_of[i] : 0)], __float_as_uint(p.w));
     }
 }
 
@@ -736,8 +1185,11 @@ struct lvb_ctx {
     int nwords = 0;
     int trigger = 0;
     lvb_skin_policy skin{};
-    float L = 0, H = 0;
-    GridGeom g{};
+    int nscenes = 0;
+    std::vector<SceneGeom> sg;      // host copy of the per-scene geometry
+    SceneGeom *sg_d = nullptr;
+    int *scene_of_d = nullptr;
+    int ccap = 0;
     long long ncells = 0;
     cudaStream_t stream = nullptr;
     DevState s{};
@@ -753,7 +1205,10 @@ struct lvb_ctx {
     // cached graph of one step, for the last (pos, vel) pointers seen
     bool use_graph = true;
     cudaGraphExec_t gexec = nullptr;
-    const void *g_pos = nullptr, *g_vel = nullptr;
+    const void *g_pos = nullptr, *g_vel = nullptr, *g_acc = nullptr;
+    int version = 0;                // bumped whenever the step's graph changes
+    HostFlags *hflags = nullptr;    // mapped pinned host memory
+    long long grows = 0;            // store or cell-slot growths done
 };
 
 namespace {
@@ -780,10 +1235,13 @@ void free_all(lvb_ctx *c)
     void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.newcell, s.bits, s.fid, s.row_off,
                     s.row_len, s.row_cap, s.col, s.trow, s.trow_mark, s.cell_cnt, s.cell_id,
                     s.cell_ref, s.tcell, s.tcell_mark, s.cnt, s.blk, c->ex_cnt, c->ex_off,
-                    c->ex_i, c->ex_j, c->ex_d, c->scratch, c->sum64};
+                    c->ex_i, c->ex_j, c->ex_d, c->scratch, c->sum64, c->sg_d, c->scene_of_d,
+                    s.born, s.cell_live, s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf,
+                    s.fref_g, s.fid_g};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cnt_h) cudaFreeHost(c->cnt_h);
+    if (c->hflags) cudaFreeHost(c->hflags);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
 }
 
@@ -818,8 +1276,9 @@ void launch_layout_scan(lvb_ctx *c, int gate)
 int rows_grid(lvb_ctx *c) { return grid_for(c->n, kThreads / 32, 16 * kNumSMs); }
 int items_grid(lvb_ctx *c) { return grid_for(c->n, kThreads, 4 * kNumSMs); }
 
-constexpr int kPerFlaggedGrid = 2 * kNumSMs;   // grid of the per-flagged kernels
-constexpr int kDefaultSmallMax = 128;
+constexpr int kPerFlaggedGrid = 8 * kNumSMs;   // grid of the per-flagged kernels
+constexpr int kDefaultSmallMax = 32;
+constexpr int kDefaultMediumMax = 2048;
 
 ScanArgs layout_args(lvb_ctx *c)
 {
@@ -843,19 +1302,29 @@ void launch_relayout(lvb_ctx *c)
     k_relayout_done<<<1, 1, 0, c->stream>>>(c->s);
 }
 
+int check_grid(lvb_ctx *c) { return grid_for(c->n, kCheckThreads, kNumSMs); }
+int medium_grid(lvb_ctx *c)
+{
+    return grid_for(std::min<long long>(c->s.medium_max, c->n), kThreads / 32, kNumSMs);
+}
+
 // One step as direct launches (used while the caller's stream is being
 // captured, or when graphs are switched off): every kernel is launched and
 // the ones with nothing to do return at once.
-void launch_step_direct(lvb_ctx *c, const float4 *pos, const float4 *v4)
+void launch_step_direct(lvb_ctx *c, const float4 *pos, const float4 *v4, const float4 *a4,
+                        const IntegrateArgs &ia)
 {
     const cudaStream_t st = c->stream;
     DevState s = c->s;
     s.use_cond = 0;
-    k_check<<<grid_for(c->n, kThreads, 1 << 30), kThreads, 0, st>>>(pos, s);
+    k_check<<<check_grid(c), kCheckThreads, 0, st>>>(pos, v4, a4, s, ia);
+    const float4 *p = ia.active ? ia.pos : pos;
     if (c->trigger == LVB_TRIGGER_PARTIAL) {
-        const int gp = kPerFlaggedGrid;
-        k_p_fused<<<1, kFusedThreads, 0, st>>>(pos, v4, s);
-        k_p_update<<<gp, kThreads, 0, st>>>(pos, v4, s);
+        const int gp = kPerFlaggedGrid, gm = medium_grid(c);
+        k_m_update<<<gm, kThreads, 0, st>>>(p, v4, a4, s);
+        k_m_rows<<<gm, kThreads, 0, st>>>(s);
+        k_m_finish<<<gm, kThreads, 0, st>>>(s);
+        k_p_update<<<gp, kThreads, 0, st>>>(p, v4, a4, s);
         k_p_compact<<<gp, kThreads, 0, st>>>(s);
         k_p_insert<<<gp, kThreads, 0, st>>>(s);
         k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_FLAGGED_BIG, 1);
@@ -863,12 +1332,13 @@ void launch_step_direct(lvb_ctx *c, const float4 *pos, const float4 *v4)
     } else {
         const int gate = c->trigger == LVB_TRIGGER_GLOBAL ? GATE_ANY_FLAG : GATE_ALWAYS;
         const int gi = items_grid(c);
-        k_full_update<<<gi, kThreads, 0, st>>>(pos, v4, s, gate);
+        k_full_update<<<gi, kThreads, 0, st>>>(p, v4, s, gate);
         k_cells_clear<<<grid_for(c->ncells, kThreads, 4 * kNumSMs), kThreads, 0, st>>>(s, gate);
         k_cells_insert<<<gi, kThreads, 0, st>>>(s, gate, 0);
         k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, gate, 1);
     }
     launch_relayout(c);
+    if (s.log_on) k_log_step<<<items_grid(c), kThreads, 0, st>>>(p, s);
 }
 
 #define GK(x)                                  \
@@ -892,81 +1362,100 @@ cudaGraph_t add_cond(cudaGraphNode_t *out, cudaGraph_t g, cudaGraphNode_t dep,
     return bodies[0];
 }
 
-// The step as graph nodes: k_check, then a SWITCH (PARTIAL: body 0 = the
-// one-block rebuild, body 1 = the multi-kernel rebuild, no body when
-// nothing is flagged) or an IF (GLOBAL/ALWAYS: the full rebuild), then an
-// IF for the row-store re-layout.  The check's last block and the end of
-// each rebuild body set the conditions on the device.
+// The re-layout body (count, scan, fill) appended to graph g after *dep.
+cudaError_t add_relayout_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, const DevState &s)
+{
+    const ScanArgs a = layout_args(c);
+    const int nb = (int)c->nblk;
+    GK(add_kernel(dep, g, dep, k_rows, dim3(rows_grid(c)), dim3(kThreads), s, (int)GATE_OVERFLOW,
+                  0));
+    GK(add_kernel(dep, g, dep, k_scan_reduce, dim3(nb), dim3(kThreads), a, s, (int)GATE_OVERFLOW));
+    GK(add_kernel(dep, g, dep, k_scan_top, dim3(1), dim3(kThreads), a, s, (int)GATE_OVERFLOW, nb));
+    GK(add_kernel(dep, g, dep, k_scan_down, dim3(nb), dim3(kThreads), a, s, (int)GATE_OVERFLOW));
+    GK(add_kernel(dep, g, dep, k_rows, dim3(rows_grid(c)), dim3(kThreads), s, (int)GATE_OVERFLOW,
+                  1));
+    GK(add_kernel(dep, g, dep, k_relayout_done, dim3(1), dim3(1), s));
+    return cudaSuccess;
+}
+
+// Ends a rebuild body: a kernel arms an IF whose body is the re-layout.
+cudaError_t add_relayout_if(lvb_ctx *c, cudaGraph_t body, cudaGraphNode_t *dep, const DevState &s)
+{
+    cudaGraphConditionalHandle h;
+    GK(cudaGraphConditionalHandleCreate(&h, body, 0u, cudaGraphCondAssignDefault));
+    GK(add_kernel(dep, body, dep, k_set_relayout, dim3(1), dim3(1), s, h));
+    cudaGraph_t rl[1] = {nullptr};
+    cudaGraphNode_t n = nullptr;
+    cudaError_t err = cudaSuccess;
+    add_cond(&n, body, *dep, h, cudaGraphCondTypeIf, 1, rl, &err);
+    GK(err);
+    cudaGraphNode_t b = nullptr;
+    GK(add_relayout_nodes(c, rl[0], &b, s));
+    *dep = n;
+    return cudaSuccess;
+}
+
+// The step as graph nodes: k_check (which also runs the one-block rebuild
+// when few particles are flagged), then for the PARTIAL trigger a SWITCH
+// whose bodies are the three-kernel rebuild, the five-kernel rebuild and
+// the re-layout alone (no body when the check did all the work); the two
+// rebuild bodies end in an IF around the re-layout.  GLOBAL / ALWAYS use an
+// IF around the full rebuild.  Conditions are set on the device.
 cudaError_t build_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, const float4 *pos,
-                             const float4 *v4)
+                             const float4 *v4, const float4 *a4, const IntegrateArgs &ia)
 {
     DevState s = c->s;
-    cudaGraphConditionalHandle hp, hr;
+    cudaGraphConditionalHandle hp;
     const bool partial = c->trigger == LVB_TRIGGER_PARTIAL;
     GK(cudaGraphConditionalHandleCreate(&hp, g, partial ? PATH_NONE : 0u,
                                         cudaGraphCondAssignDefault));
-    GK(cudaGraphConditionalHandleCreate(&hr, g, 0u, cudaGraphCondAssignDefault));
     s.h_path = hp;
-    s.h_relayout = hr;
     s.use_cond = 1;
     cudaGraphNode_t n = dep ? *dep : nullptr;
-    GK(add_kernel(&n, g, &n, k_check, dim3(grid_for(c->n, kThreads, 1 << 30)), dim3(kThreads),
-                  pos, s));
-    cudaGraph_t bodies[2] = {nullptr, nullptr};
+    GK(add_kernel(&n, g, &n, k_check, dim3(check_grid(c)), dim3(kCheckThreads), pos, v4, a4, s,
+                  ia));
+    const float4 *p = ia.active ? ia.pos : pos;
     cudaGraphNode_t cn = nullptr;
     cudaError_t err = cudaSuccess;
-    const int gp = kPerFlaggedGrid;
     if (partial) {
-        add_cond(&cn, g, n, hp, cudaGraphCondTypeSwitch, 2, bodies, &err);
+        cudaGraph_t b3[3] = {nullptr, nullptr, nullptr};
+        add_cond(&cn, g, n, hp, cudaGraphCondTypeSwitch, 3, b3, &err);
         GK(err);
+        const int gm = medium_grid(c), gp = kPerFlaggedGrid;
         cudaGraphNode_t b = nullptr;
-        GK(add_kernel(&b, bodies[PATH_SMALL], &b, k_p_fused, dim3(1), dim3(kFusedThreads), pos,
-                      v4, s));
+        GK(add_kernel(&b, b3[PATH_MEDIUM], &b, k_m_update, dim3(gm), dim3(kThreads), p, v4, a4, s));
+        GK(add_kernel(&b, b3[PATH_MEDIUM], &b, k_m_rows, dim3(gm), dim3(kThreads), s));
+        GK(add_kernel(&b, b3[PATH_MEDIUM], &b, k_m_finish, dim3(gm), dim3(kThreads), s));
+        GK(add_relayout_if(c, b3[PATH_MEDIUM], &b, s));
         b = nullptr;
-        cudaGraph_t big = bodies[PATH_BIG];
-        GK(add_kernel(&b, big, &b, k_p_update, dim3(gp), dim3(kThreads), pos, v4, s));
+        cudaGraph_t big = b3[PATH_BIG];
+        GK(add_kernel(&b, big, &b, k_p_update, dim3(gp), dim3(kThreads), p, v4, a4, s));
         GK(add_kernel(&b, big, &b, k_p_compact, dim3(gp), dim3(kThreads), s));
         GK(add_kernel(&b, big, &b, k_p_insert, dim3(gp), dim3(kThreads), s));
         GK(add_kernel(&b, big, &b, k_rows, dim3(rows_grid(c)), dim3(kThreads), s,
                       (int)GATE_FLAGGED_BIG, 1));
         GK(add_kernel(&b, big, &b, k_p_append, dim3(gp), dim3(kThreads), s));
-        GK(add_kernel(&b, big, &b, k_set_relayout, dim3(1), dim3(1), s));
+        GK(add_relayout_if(c, big, &b, s));
+        b = nullptr;
+        GK(add_relayout_nodes(c, b3[PATH_RELAYOUT], &b, s));
     } else {
-        add_cond(&cn, g, n, hp, cudaGraphCondTypeIf, 1, bodies, &err);
+        cudaGraph_t body[1] = {nullptr};
+        add_cond(&cn, g, n, hp, cudaGraphCondTypeIf, 1, body, &err);
         GK(err);
         const int gate = c->trigger == LVB_TRIGGER_GLOBAL ? GATE_ANY_FLAG : GATE_ALWAYS;
         const int gi = items_grid(c);
-        cudaGraph_t full = bodies[0];
         cudaGraphNode_t b = nullptr;
-        GK(add_kernel(&b, full, &b, k_full_update, dim3(gi), dim3(kThreads), pos, v4, s, gate));
-        GK(add_kernel(&b, full, &b, k_cells_clear,
+        GK(add_kernel(&b, body[0], &b, k_full_update, dim3(gi), dim3(kThreads), p, v4, s, gate));
+        GK(add_kernel(&b, body[0], &b, k_cells_clear,
                       dim3(grid_for(c->ncells, kThreads, 4 * kNumSMs)), dim3(kThreads), s, gate));
-        GK(add_kernel(&b, full, &b, k_cells_insert, dim3(gi), dim3(kThreads), s, gate, 0));
-        GK(add_kernel(&b, full, &b, k_rows, dim3(rows_grid(c)), dim3(kThreads), s, gate, 1));
-        GK(add_kernel(&b, full, &b, k_set_relayout, dim3(1), dim3(1), s));
+        GK(add_kernel(&b, body[0], &b, k_cells_insert, dim3(gi), dim3(kThreads), s, gate, 0));
+        GK(add_kernel(&b, body[0], &b, k_rows, dim3(rows_grid(c)), dim3(kThreads), s, gate, 1));
+        GK(add_relayout_if(c, body[0], &b, s));
     }
-    cudaGraph_t rl[1] = {nullptr};
-    cudaGraphNode_t rn = nullptr;
-    add_cond(&rn, g, cn, hr, cudaGraphCondTypeIf, 1, rl, &err);
-    GK(err);
-    cudaGraphNode_t b = nullptr;
-    const ScanArgs a = layout_args(c);
-    const int nb = (int)c->nblk;
-    GK(add_kernel(&b, rl[0], &b, k_rows, dim3(rows_grid(c)), dim3(kThreads), s,
-                  (int)GATE_OVERFLOW, 0));
-    GK(add_kernel(&b, rl[0], &b, k_scan_reduce, dim3(nb), dim3(kThreads), a, s,
-                  (int)GATE_OVERFLOW));
-    GK(add_kernel(&b, rl[0], &b, k_scan_top, dim3(1), dim3(kThreads), a, s, (int)GATE_OVERFLOW,
-                  nb));
-    GK(add_kernel(&b, rl[0], &b, k_scan_down, dim3(nb), dim3(kThreads), a, s,
-                  (int)GATE_OVERFLOW));
-    GK(add_kernel(&b, rl[0], &b, k_rows, dim3(rows_grid(c)), dim3(kThreads), s,
-                  (int)GATE_OVERFLOW, 1));
-    GK(add_kernel(&b, rl[0], &b, k_relayout_done, dim3(1), dim3(1), s));
-    if (dep) *dep = rn;
+    if (s.log_on) GK(add_kernel(&cn, g, &cn, k_log_step, dim3(items_grid(c)), dim3(kThreads), p, s));
+    if (dep) *dep = cn;
     return cudaSuccess;
 }
-
 int sync_counters(lvb_ctx *c)
 {
     cudaError_t e = cudaMemcpyAsync(c->cnt_h, c->s.cnt, sizeof(DevCounters),
@@ -974,6 +1463,70 @@ int sync_counters(lvb_ctx *c)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return from_cuda(e);
     return from_derr(c->cnt_h->err);
+}
+
+// Grows the row store and/or the cell slots when a kernel asked for it
+// (over 75% full), then rebuilds the cells and rows from the current
+// reference state -- the list is a function of that state alone, so the
+// rebuilt list is the one the steps would have produced.  Synchronises;
+// runs only on the rare steps that need it.
+int grow_if_asked(lvb_ctx *c)
+{
+    volatile HostFlags *h = c->hflags;
+    if (!h->grow_store && !h->grow_cells) return LVB_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    DevState &s = c->s;
+    const cudaStream_t st = c->stream;
+    const bool cells = h->grow_cells != 0;
+    if (cells && s.ccap < (1 << 16)) {
+        const int ccap = std::min(2 * s.ccap, 1 << 16);
+        cudaFree(s.cell_id);
+        cudaFree(s.cell_ref);
+        s.cell_id = nullptr;
+        s.cell_ref = nullptr;
+        e = dalloc(&s.cell_id, c->ncells * (long long)ccap);
+        if (e == cudaSuccess) e = dalloc(&s.cell_ref, c->ncells * (long long)ccap);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(s.cell_id, 0xff, sizeof(int) * (size_t)c->ncells * ccap, st);
+        if (e != cudaSuccess) return from_cuda(e);
+        s.ccap = ccap;
+        c->ccap = ccap;
+        k_cells_clear<<<grid_for(c->ncells, kThreads, 4 * kNumSMs), kThreads, 0, st>>>(
+            s, GATE_ALWAYS);
+        k_cells_insert<<<items_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 0);
+    }
+    // rows: count, then a store with room to grow, then fill
+    k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 0);
+    const long long cap0 = s.col_cap;
+    s.col_cap = 1LL << 62;
+    launch_layout_scan(c, GATE_ALWAYS);
+    int rc = sync_counters(c);
+    s.col_cap = cap0;
+    if (rc) return rc;
+    const long long need = c->cnt_h->store_needed;
+    if (need * 4 > s.col_cap * 3) {
+        const long long cap = std::min<long long>(2 * need + 8 * c->n + 1024, INT32_MAX);
+        if (need > cap) return LVB_ENOMEM;
+        cudaFree(s.col);
+        s.col = nullptr;
+        e = dalloc(&s.col, cap);
+        if (e != cudaSuccess) return from_cuda(e);
+        s.col_cap = cap;
+    }
+    k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    h->grow_store = 0;
+    h->grow_cells = 0;
+    c->grows += 1;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->version += 1;
+    return sync_counters(c);
 }
 
 int ensure_export(lvb_ctx *c, long long need)
@@ -1054,24 +1607,38 @@ const char *lvb_strerror(int status)
     }
 }
 
-static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *ref4,
-                     const lvb_box *box, const lvb_skin_policy *skin, int32_t trigger,
-                     float cell_factor, const float *vel, const float *acc, void *stream)
+static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t n,
+                     const float *pos_r, const float *ref4, const lvb_box *boxes,
+                     const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
+                     const float *vel, const float *acc, void *stream)
 {
-    (void)acc;
     if (!out) return LVB_EINVAL;
     *out = nullptr;
-    if (!pos_r || !box || !skin || n < 1 || n > INT32_MAX - 64) return LVB_EINVAL;
+    if (!pos_r || !boxes || !skin || n < 1 || n > INT32_MAX - 64 || nscenes < 1) return LVB_EINVAL;
     if (!aligned16(pos_r) || (vel && !aligned16(vel)) || (ref4 && !aligned16(ref4)))
         return LVB_EINVAL;
     if (trigger < LVB_TRIGGER_PARTIAL || trigger > LVB_TRIGGER_ALWAYS) return LVB_EINVAL;
-    if (skin->kind < LVB_SKIN_GLOBAL || skin->kind > LVB_SKIN_PAPER_KVDT) return LVB_EINVAL;
+    if (trigger == LVB_TRIGGER_GLOBAL && nscenes > 1) return LVB_EINVAL;
+    if (skin->kind < LVB_SKIN_GLOBAL || skin->kind > LVB_SKIN_LEARNED) return LVB_EINVAL;
+    if (skin->kind == LVB_SKIN_LEARNED &&
+        (!skin->mlp || !vel || !acc || trigger != LVB_TRIGGER_PARTIAL || !(skin->dt > 0.0f)))
+        return LVB_EINVAL;
+    if (acc && !aligned16(acc)) return LVB_EINVAL;
     if (!(skin->value >= 0.0f) || !std::isfinite(skin->value)) return LVB_EINVAL;
     if (skin->kind == LVB_SKIN_PAPER_KVDT && (!vel || !(skin->dt > 0.0f))) return LVB_EINVAL;
     if (!(cell_factor >= 1.0f) || !std::isfinite(cell_factor)) return LVB_EINVAL;
-    for (int k = 0; k < 3; ++k)
-        if (!(box->hi[k] > box->lo[k]) || !std::isfinite(box->lo[k]) || !std::isfinite(box->hi[k]))
-            return LVB_EINVAL;
+    if (offsets) {
+        if (offsets[0] != 0 || offsets[nscenes] != n) return LVB_EINVAL;
+        for (int q = 0; q < nscenes; ++q)
+            if (!(offsets[q + 1] > offsets[q])) return LVB_EINVAL;
+    } else if (nscenes != 1) {
+        return LVB_EINVAL;
+    }
+    for (int q = 0; q < nscenes; ++q)
+        for (int k = 0; k < 3; ++k)
+            if (!(boxes[q].hi[k] > boxes[q].lo[k]) || !std::isfinite(boxes[q].lo[k]) ||
+                !std::isfinite(boxes[q].hi[k]))
+                return LVB_EINVAL;
 
     cudaGetLastError();   // clear a stale error of an unrelated earlier call
     lvb_ctx *c = new (std::nothrow) lvb_ctx();
@@ -1080,6 +1647,7 @@ static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *
     c->nwords = (int)((n + 31) / 32);
     c->trigger = trigger;
     c->skin = *skin;
+    c->nscenes = nscenes;
     c->stream = (cudaStream_t)stream;
     DevState &s = c->s;
     const cudaStream_t st = c->stream;
@@ -1092,44 +1660,84 @@ static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *
         return code;
     };
 
-    // radii: range and validity
-    e = dalloc(&c->scratch, 8);
+    // scene of every particle (only stored when there is more than one)
+    if (nscenes > 1) {
+        std::vector<int> so((size_t)n);
+        for (int q = 0; q < nscenes; ++q)
+            for (int64_t i = offsets[q]; i < offsets[q + 1]; ++i) so[(size_t)i] = q;
+        e = dalloc(&c->scene_of_d, n);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->scene_of_d, so.data(), sizeof(int) * (size_t)n,
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(from_cuda(e));
+    }
+
+    // radii: range per scene and validity
+    e = dalloc(&c->scratch, 2 + nscenes + 8);
     if (e == cudaSuccess) e = dalloc(&c->sum64, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->cnt_h, sizeof(DevCounters));
+    if (e == cudaSuccess)
+        e = cudaHostAlloc((void **)&c->hflags, sizeof(HostFlags), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        memset(c->hflags, 0, sizeof(HostFlags));
+        e = cudaHostGetDevicePointer((void **)&s.hflags, c->hflags, 0);
+    }
     if (e != cudaSuccess) return fail(from_cuda(e));
-    unsigned init_h[3] = {0u, 0x7f800000u, 0u};
-    e = cudaMemcpyAsync(c->scratch, init_h, sizeof(init_h), cudaMemcpyHostToDevice, st);
+    std::vector<unsigned> rs((size_t)nscenes + 2, 0u);
+    rs[0] = 0x7f800000u;
+    e = cudaMemcpyAsync(c->scratch, rs.data(), sizeof(unsigned) * rs.size(),
+                        cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail(from_cuda(e));
     k_radius_scan<<<grid_for(n, kThreads, 4 * kNumSMs), kThreads, 0, st>>>(
-        (const float4 *)pos_r, (int)n, c->scratch);
-    unsigned rs[3];
-    e = cudaMemcpyAsync(rs, c->scratch, sizeof(rs), cudaMemcpyDeviceToHost, st);
+        (const float4 *)pos_r, (int)n, c->scene_of_d, c->scratch);
+    e = cudaMemcpyAsync(rs.data(), c->scratch, sizeof(unsigned) * rs.size(),
+                        cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(from_cuda(e));
-    if (rs[2]) return fail(LVB_ENAN);
-    float rmax, rmin;
-    memcpy(&rmax, &rs[0], 4);
-    memcpy(&rmin, &rs[1], 4);
+    if (rs[1]) return fail(LVB_ENAN);
+    float rmin;
+    memcpy(&rmin, &rs[0], 4);
 
-    // geometry: cell edge, cap H, grid (at most 2048 cells per axis)
-    double L = (double)cell_factor * 2.0 * (double)rmax * (1.0 + 1.0 / 128.0);
-    double ext = 0.0;
-    for (int k = 0; k < 3; ++k) ext = std::max(ext, (double)box->hi[k] - (double)box->lo[k]);
-    if (ext / L > 2048.0) L = ext / 2048.0;
-    long long ncells = 1;
-    for (int k = 0; k < 3; ++k) {
-        long long d = (long long)std::ceil(((double)box->hi[k] - (double)box->lo[k]) / L);
-        d = std::max(1LL, std::min(d, 2048LL));
-        c->g.dim[k] = (int)d;
-        c->g.lo[k] = box->lo[k];
-        ncells *= d;
+    // per-scene geometry: cell edge, cap H, grid (at most 2048 cells per axis)
+    c->sg.resize((size_t)nscenes);
+    long long ncells = 0;
+    double Lmax = 0.0;
+    for (int q = 0; q < nscenes; ++q) {
+        SceneGeom &g = c->sg[(size_t)q];
+        memset(&g, 0, sizeof(g));
+        float rmax;
+        memcpy(&rmax, &rs[(size_t)q + 2], 4);
+        double L = (double)cell_factor * 2.0 * (double)rmax * (1.0 + 1.0 / 128.0);
+        const lvb_box &box = boxes[q];
+        double ext = 0.0;
+        for (int k = 0; k < 3; ++k) ext = std::max(ext, (double)box.hi[k] - (double)box.lo[k]);
+        if (ext / L > 2048.0) L = ext / 2048.0;
+        long long nc = 1;
+        for (int k = 0; k < 3; ++k) {
+            long long d = (long long)std::ceil(((double)box.hi[k] - (double)box.lo[k]) / L);
+            d = std::max(1LL, std::min(d, 2048LL));
+            g.dim[k] = (int)d;
+            g.lo[k] = box.lo[k];
+            g.hi[k] = box.hi[k];
+            nc *= d;
+        }
+        g.cell_base = (int)ncells;
+        ncells += nc;
+        if (ncells > (1LL << 28)) return fail(LVB_EINVAL);
+        g.L = (float)L;
+        g.H = (float)(0.5 * L * (1.0 - 1.0 / 256.0));
+        g.invL = (float)(1.0 / L);
+        g.first = offsets ? (int)offsets[q] : 0;
+        g.count = offsets ? (int)(offsets[q + 1] - offsets[q]) : (int)n;
+        if (!(rmax <= g.H)) return fail(LVB_EINVAL);
+        Lmax = std::max(Lmax, L);
     }
-    if (ncells > (1LL << 28)) return fail(LVB_EINVAL);
     c->ncells = ncells;
-    c->L = (float)L;
-    c->H = (float)(0.5 * L * (1.0 - 1.0 / 256.0));
-    c->g.invL = (float)(1.0 / L);
-    if (!(rmax <= c->H)) return fail(LVB_EINVAL);
+    e = dalloc(&c->sg_d, nscenes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->sg_d, c->sg.data(), sizeof(SceneGeom) * (size_t)nscenes,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(from_cuda(e));
 
     c->nblk = (n + kScanBlock - 1) / kScanBlock;
     e = dalloc(&s.ref, n);
@@ -1145,25 +1753,35 @@ static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *
     if (e == cudaSuccess) e = dalloc(&s.trow, n);
     if (e == cudaSuccess) e = dalloc(&s.trow_mark, n);
     if (e == cudaSuccess) e = dalloc(&s.cell_cnt, ncells);
+    if (e == cudaSuccess) e = dalloc(&s.cell_live, ncells);
+    if (e == cudaSuccess) e = dalloc(&s.born, n);
+    if (e == cudaSuccess) e = dalloc(&s.fref_g, n);
+    if (e == cudaSuccess) e = dalloc(&s.fid_g, n);
     if (e == cudaSuccess) e = dalloc(&s.tcell, ncells);
     if (e == cudaSuccess) e = dalloc(&s.tcell_mark, ncells);
     if (e == cudaSuccess) e = dalloc(&s.cnt, 1);
     if (e == cudaSuccess) e = dalloc(&s.blk, c->nblk + 1);
     if (e != cudaSuccess) return fail(from_cuda(e));
     cudaMemsetAsync(s.trow_mark, 0, sizeof(int) * n, st);
+    cudaMemsetAsync(s.born, 0, sizeof(int) * n, st);
+    cudaMemsetAsync(s.cell_live, 0, sizeof(int) * ncells, st);
     cudaMemsetAsync(s.tcell_mark, 0, sizeof(int) * ncells, st);
     cudaMemsetAsync(s.cnt, 0, sizeof(DevCounters), st);
+    cudaMemsetAsync(&s.cnt->tr_start, 0xff, sizeof(s.cnt->tr_start), st);
     cudaMemsetAsync(s.bits, 0, sizeof(uint32_t) * c->nwords, st);
 
     s.n = (int)n;
     s.small_max = kDefaultSmallMax;
+    s.medium_max = (int)std::min<int64_t>(kDefaultMediumMax, n);
     s.nwords = c->nwords;
     s.trigger = trigger;
     s.skin_kind = skin->kind;
     s.skin_value = skin->value;
     s.skin_dt = skin->dt;
-    s.H = c->H;
-    s.g = c->g;
+    s.mlp = (const lvb_mlp_weights *)skin->mlp;
+    s.nscenes = nscenes;
+    s.sg = c->sg_d;
+    s.scene_of = c->scene_of_d;
     s.ncells = ncells;
 
     const float4 *pos = (const float4 *)pos_r;
@@ -1178,6 +1796,9 @@ static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail(from_cuda(e));
         if (bad) return fail(LVB_EINVAL);
+    } else if (skin->kind == LVB_SKIN_LEARNED) {
+        k_full_update_learned<<<grid_for(n, kThreads / 32, 16 * kNumSMs), kThreads, 0, st>>>(
+            pos, v4, (const float4 *)acc, s);
     } else {
         k_full_update<<<gi, kThreads, 0, st>>>(pos, v4, s, GATE_ALWAYS);
     }
@@ -1195,16 +1816,18 @@ static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *
     if (e != cudaSuccess) return fail(from_cuda(e));
     {
         const double vmean = 4.0 / 3.0 * M_PI * (double)rmin * rmin * rmin;
-        const double dense = 0.74 * L * L * L / std::max(vmean, 1e-30);
+        const double dense = 0.74 * Lmax * Lmax * Lmax / std::max(vmean, 1e-30);
         long long cap = std::max<long long>(2LL * maxocc + 8, 32);
         cap = std::max<long long>(cap, (long long)std::min(dense * 0.5, 4096.0));
         cap = (cap + 31) / 32 * 32;
         cap = std::min<long long>(cap, 1 << 16);
-        c->g.ccap = (int)cap;
-        s.g.ccap = (int)cap;
+        c->ccap = (int)cap;
+        s.ccap = (int)cap;
     }
-    e = dalloc(&s.cell_id, ncells * (long long)c->g.ccap);
-    if (e == cudaSuccess) e = dalloc(&s.cell_ref, ncells * (long long)c->g.ccap);
+    e = dalloc(&s.cell_id, ncells * (long long)c->ccap);
+    if (e == cudaSuccess) e = dalloc(&s.cell_ref, ncells * (long long)c->ccap);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s.cell_id, 0xff, sizeof(int) * (size_t)ncells * c->ccap, st);
     if (e != cudaSuccess) return fail(from_cuda(e));
     cudaMemsetAsync(s.cell_cnt, 0, sizeof(int) * ncells, st);
     k_cells_insert<<<gi, kThreads, 0, st>>>(s, GATE_ALWAYS, 0);
@@ -1217,7 +1840,7 @@ static int init_impl(lvb_ctx **out, int64_t n, const float *pos_r, const float *
     rc = sync_counters(c);
     if (rc) return fail(rc);
     const long long needed = c->cnt_h->store_needed;
-    long long col_cap = std::max<long long>(needed + needed / 2 + 1024, 4096);
+    long long col_cap = std::max<long long>(2 * needed + 8 * n + 1024, 4096);
     if (col_cap > INT32_MAX) col_cap = INT32_MAX;
     if (needed > col_cap) return fail(LVB_ENOMEM);
     e = dalloc(&s.col, col_cap);
@@ -1237,7 +1860,30 @@ int lvb_init(lvb_ctx **out, int64_t n, const float *pos_r, const lvb_box *box,
              const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
              const float *vel, const float *acc, void *stream)
 {
-    return init_impl(out, n, pos_r, nullptr, box, skin, trigger, cell_factor, vel, acc, stream);
+    return init_impl(out, 1, nullptr, n, pos_r, nullptr, box, skin, trigger, cell_factor, vel,
+                     acc, stream);
+}
+
+int lvb_batch_init(lvb_ctx **out, int32_t n_scenes, const int64_t *offsets, const float *pos_r,
+                   const lvb_box *boxes, const lvb_skin_policy *skin, int32_t trigger,
+                   float cell_factor, const float *vel, const float *acc, void *stream)
+{
+    if (!offsets || n_scenes < 1) return LVB_EINVAL;
+    return init_impl(out, n_scenes, offsets, offsets[n_scenes], pos_r, nullptr, boxes, skin,
+                     trigger, cell_factor, vel, acc, stream);
+}
+
+int lvb_scene_info(lvb_ctx *c, int32_t scene, lvb_scene_info_t *o)
+{
+    if (!c || !o || scene < 0 || scene >= c->nscenes) return LVB_EINVAL;
+    const SceneGeom &g = c->sg[(size_t)scene];
+    memset(o, 0, sizeof(*o));
+    o->first = g.first;
+    o->count = g.count;
+    o->cell_edge = g.L;
+    o->rnl_max = g.H;
+    for (int k = 0; k < 3; ++k) o->grid[k] = g.dim[k];
+    return LVB_OK;
 }
 
 int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *ref4,
@@ -1245,15 +1891,22 @@ int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *r
                     float cell_factor, const float *vel, const float *acc, void *stream)
 {
     if (!ref4) return LVB_EINVAL;
-    return init_impl(out, n, pos_r, ref4, box, skin, trigger, cell_factor, vel, acc, stream);
+    return init_impl(out, 1, nullptr, n, pos_r, ref4, box, skin, trigger, cell_factor, vel, acc,
+                     stream);
 }
 
 int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
 {
-    (void)acc;
-    if (!c || !pos_r || !aligned16(pos_r) || (vel && !aligned16(vel))) return LVB_EINVAL;
+    if (!c || !pos_r || !aligned16(pos_r) || (vel && !aligned16(vel)) || (acc && !aligned16(acc)))
+        return LVB_EINVAL;
     if (c->skin.kind == LVB_SKIN_PAPER_KVDT && !vel) return LVB_EINVAL;
+    if (c->skin.kind == LVB_SKIN_LEARNED && (!vel || !acc)) return LVB_EINVAL;
+    const float4 *a4 = (const float4 *)acc;
     cudaGetLastError();   // clear a stale error of an unrelated earlier call
+    {
+        const int rc = grow_if_asked(c);
+        if (rc) return rc;
+    }
     const cudaStream_t st = c->stream;
     const float4 *pos = (const float4 *)pos_r;
     const float4 *v4 = (const float4 *)vel;
@@ -1261,17 +1914,17 @@ int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
     cudaError_t e = cudaStreamIsCapturing(st, &cs);
     if (e != cudaSuccess) return from_cuda(e);
     if (!c->use_graph || cs != cudaStreamCaptureStatusNone) {
-        launch_step_direct(c, pos, v4);
+        launch_step_direct(c, pos, v4, a4, IntegrateArgs{});
         return from_cuda(cudaGetLastError());
     }
-    if (!c->gexec || c->g_pos != pos_r || c->g_vel != vel) {
+    if (!c->gexec || c->g_pos != pos_r || c->g_vel != vel || c->g_acc != acc) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
         cudaGraph_t g = nullptr;
         e = cudaGraphCreate(&g, 0);
-        if (e == cudaSuccess) e = build_step_nodes(c, g, nullptr, pos, v4);
+        if (e == cudaSuccess) e = build_step_nodes(c, g, nullptr, pos, v4, a4, IntegrateArgs{});
         if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
@@ -1280,6 +1933,7 @@ int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
         }
         c->g_pos = pos_r;
         c->g_vel = vel;
+        c->g_acc = acc;
     }
     return from_cuda(cudaGraphLaunch(c->gexec, st));
 }
@@ -1290,8 +1944,15 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     if (option == LVB_OPT_GRAPH) {
         c->use_graph = value != 0;
     } else if (option == LVB_OPT_SMALL_MAX) {
-        if (value < 0 || value > INT32_MAX) return LVB_EINVAL;
-        c->s.small_max = (int)value;
+        if (value < 0) return LVB_EINVAL;
+        c->s.small_max = (int)std::min<int64_t>(value, kFusedMax);
+        c->s.medium_max = std::max(c->s.medium_max, c->s.small_max);
+    } else if (option == LVB_OPT_TRACE) {
+        c->s.trace = value != 0;
+    } else if (option == LVB_OPT_MEDIUM_MAX) {
+        if (value < 0) return LVB_EINVAL;
+        c->s.medium_max = (int)std::max<int64_t>(std::min<int64_t>(value, c->n),
+                                                 c->s.small_max);
     } else {
         return LVB_EINVAL;
     }
@@ -1300,7 +1961,64 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
+    c->version += 1;
     return LVB_OK;
+}
+
+int lvb_trace(lvb_ctx *c, uint64_t *sum_ns, uint64_t *count)
+{
+    if (!c || !sum_ns || !count) return LVB_EINVAL;
+    int rc = sync_counters(c);
+    if (rc) return rc;
+    for (int k = 0; k < kTraceSlots; ++k) {
+        sum_ns[k] = c->cnt_h->tr_sum[k];
+        count[k] = c->cnt_h->tr_cnt[k];
+    }
+    return LVB_OK;
+}
+
+int lvb_log_enable(lvb_ctx *c, int32_t horizon, int64_t capacity)
+{
+    if (!c || horizon < 1 || capacity < 1 || c->trigger != LVB_TRIGGER_PARTIAL) return LVB_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    DevState &s = c->s;
+    if (e == cudaSuccess && !s.lg_feat) {
+        e = dalloc(&s.lg_feat, c->n * (long long)LVB_MLP_IN);
+        if (e == cudaSuccess) e = dalloc(&s.lg_x, c->n);
+        if (e == cudaSuccess) e = dalloc(&s.lg_t, c->n);
+        if (e == cudaSuccess) e = dalloc(&s.lg_m, c->n);
+        if (e == cudaSuccess) e = cudaMemset(s.lg_t, 0xff, sizeof(int) * (size_t)c->n);
+    }
+    if (e == cudaSuccess && s.log_cap != capacity) {
+        if (s.log_buf) cudaFree(s.log_buf);
+        s.log_buf = nullptr;
+        e = dalloc(&s.log_buf, capacity * (long long)(LVB_MLP_IN + 1));
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    s.log_on = 1;
+    s.log_horizon = horizon;
+    s.log_cap = capacity;
+    e = cudaMemsetAsync(&s.cnt->log_n, 0, sizeof(long long), c->stream);
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->version += 1;
+    return from_cuda(e);
+}
+
+int lvb_log_read(lvb_ctx *c, float *samples, int64_t cap, int64_t *n_samples)
+{
+    if (!c || !n_samples || cap < 0) return LVB_EINVAL;
+    if (!c->s.log_on) return LVB_ESTATE;
+    int rc = sync_counters(c);
+    if (rc) return rc;
+    const long long n = std::min<long long>(c->cnt_h->log_n, c->s.log_cap);
+    *n_samples = n;
+    if (n > cap || (n > 0 && !samples)) return LVB_ECAPACITY;
+    rc = copy_out(c, samples, c->s.log_buf, sizeof(float) * (size_t)n * (LVB_MLP_IN + 1));
+    if (rc) return rc;
+    return from_cuda(cudaStreamSynchronize(c->stream));
 }
 
 int lvb_sync(lvb_ctx *c)
@@ -1419,15 +2137,19 @@ int lvb_stats(lvb_ctx *c, lvb_stats_t *o)
     o->entries = (int64_t)entries;
     o->pairs = (int64_t)(entries / 2);
     o->relayouts = h.relayouts;
-    o->cell_capacity = c->g.ccap;
+    o->grows = c->grows;
+    o->cell_capacity = c->ccap;
     o->row_store_capacity = c->s.col_cap;
     o->kernels_executed = (int64_t)h.kernels;
+    for (int k = 0; k < 4; ++k) o->fused_phase_cycles[k] = (int64_t)h.fused_cycles[k];
     o->small_path_steps = h.small_steps;
     o->small_max = c->s.small_max;
+    o->medium_max = c->s.medium_max;
     o->graphs = c->use_graph ? 1 : 0;
-    o->cell_edge = c->L;
-    o->rnl_max = c->H;
-    for (int k = 0; k < 3; ++k) o->grid[k] = c->g.dim[k];
+    o->n_scenes = c->nscenes;
+    o->cell_edge = c->sg[0].L;
+    o->rnl_max = c->sg[0].H;
+    for (int k = 0; k < 3; ++k) o->grid[k] = c->sg[0].dim[k];
     return LVB_OK;
 }
 
@@ -1460,13 +2182,29 @@ RowsView rows_view(lvb_ctx *c)
     v.col = c->s.col;
     v.rad = c->s.rad;
     v.kernels = &c->s.cnt->kernels;
+    v.cnt = c->s.cnt;
+    v.trace = &c->s.trace;
+    v.sg = c->sg_d;
+    v.scene_of = c->scene_of_d;
+    v.nscenes = c->nscenes;
     v.n = (int)c->n;
     return v;
 }
 
 int append_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, const float *pos_r,
-                      const float *vel)
+                      const float *vel, const float *acc, const IntegrateArgs *integ)
 {
-    return from_cuda(build_step_nodes(c, g, dep, (const float4 *)pos_r, (const float4 *)vel));
+    return from_cuda(build_step_nodes(c, g, dep, (const float4 *)pos_r, (const float4 *)vel,
+                                      (const float4 *)acc, integ ? *integ : IntegrateArgs{}));
+}
+
+int grow_stores_if_asked(lvb_ctx *c)
+{
+    return grow_if_asked(c);
+}
+
+int graph_version(lvb_ctx *c)
+{
+    return c->version;
 }
 }  // namespace lvb

@@ -32,11 +32,21 @@ struct DemDev {
     float dt, half_dt, half_dt2;
     float kn, two_zeta, g[3];
     int wall_kind, clamp_tensile, contacts_on;
-    float lo[3], hi[3];
     float drum_cx, drum_cz, drum_R;
     float4 *pos, *vel, *acc, *vstar;   // vstar.w = 1 / m
     RowsView rows;
+    int trace;                         // per-kernel trace (copied at launch)
 };
+
+__device__ __forceinline__ void dtr_enter(const DemDev &d, int slot)
+{
+    if (d.trace && threadIdx.x == 0) atomicMin(&d.rows.cnt->tr_start[slot], global_ns());
+}
+
+__device__ __forceinline__ void dtr_exit(const DemDev &d, int slot)
+{
+    if (d.trace && (threadIdx.x & 31) == 0) atomicMax(&d.rows.cnt->tr_end[slot], global_ns());
+}
 
 // exact a - b = s + e (TwoSum on a and -b)
 __device__ __forceinline__ void two_diff(float a, float b, float &s, float &e)
@@ -78,32 +88,43 @@ __device__ __forceinline__ float lsd(const DemDev &d, float dl, float vn, float 
     return f;
 }
 
+__device__ __forceinline__ IntegrateArgs integrate_args(const DemDev &d)
+{
+    IntegrateArgs a;
+    a.pos = d.pos;
+    a.vel = d.vel;
+    a.acc = d.acc;
+    a.vstar = d.vstar;
+    a.dt = d.dt;
+    a.half_dt2 = d.half_dt2;
+    a.specular = d.wall_kind == DEM_WALL_SPECULAR;
+    a.active = 1;
+    return a;
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_integrate(DemDev d)
 {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
-    if (i >= d.n) return;
-    float4 x = d.pos[i];
-    float4 v = d.vel[i];
-    const float4 a = d.acc[i];
-    const float im = d.vstar[i].w;
-    x.x += v.x * d.dt + a.x * d.half_dt2;
-    x.y += v.y * d.dt + a.y * d.half_dt2;
-    x.z += v.z * d.dt + a.z * d.half_dt2;
-    float4 vs = make_float4(v.x + a.x * d.dt, v.y + a.y * d.dt, v.z + a.z * d.dt, im);
-    if (d.wall_kind == DEM_WALL_SPECULAR) {
-        const float r = x.w;
-        float *xc = &x.x, *vc = &v.x, *sc = &vs.x;
-        for (int c = 0; c < 3; ++c) {
-            const float lo = d.lo[c] + r, hi = d.hi[c] - r;
-            if (xc[c] < lo) { xc[c] = 2.0f * lo - xc[c]; vc[c] = -vc[c]; sc[c] = -sc[c]; }
-            else if (xc[c] > hi) { xc[c] = 2.0f * hi - xc[c]; vc[c] = -vc[c]; sc[c] = -sc[c]; }
-        }
-        d.vel[i] = v;
-    }
-    d.pos[i] = x;
-    d.vstar[i] = vs;
+    dtr_enter(d, TR_INTEGRATE);
+    if (i < d.n)
+        integrate_one(integrate_args(d), d.rows.sg[d.rows.nscenes == 1 ? 0 : d.rows.scene_of[i]], i);
+    dtr_exit(d, TR_INTEGRATE);
+}
+
+// Wall planes normal to one axis: x in [lo, hi], velocity component v.
+__device__ __forceinline__ float plane_force(const DemDev &d, float x, float v, float r, float lo,
+                                             float hi, float m)
+{
+    float F = 0.0f, hh, ll;
+    two_diff(x, lo, hh, ll);                       // x - lo
+    const float dlo = __fsub_rn(r, hh) - ll;
+    if (dlo > 0.0f) F += lsd(d, dlo, v, m);
+    two_diff(hi, x, hh, ll);                       // hi - x
+    const float dhi = __fsub_rn(r, hh) - ll;
+    if (dhi > 0.0f) F -= lsd(d, dhi, -v, m);
+    return F;
 }
 
 // Narrow phase on the rows + walls + velocity finish, one thread per particle.
@@ -112,11 +133,17 @@ k_forces(DemDev d)
 {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
-    if (i >= d.n) return;
+    dtr_enter(d, TR_FORCES);
+    if (i >= d.n) {
+        dtr_exit(d, TR_FORCES);
+        return;
+    }
     const float4 xi = d.pos[i];
     const float4 vi = d.vstar[i];
+    const float4 a = d.acc[i];
+    float4 v = d.vel[i];
     const float im_i = vi.w;
-    float F[3] = {0.f, 0.f, 0.f};
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if (d.contacts_on) {
         const int off = d.rows.row_off[i];
         const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
@@ -144,26 +171,20 @@ k_forces(DemDev d)
             const float vn = (vi.x - vj.x) * n0 + (vi.y - vj.y) * n1 + (vi.z - vj.z) * n2;
             const float meff = 1.0f / (im_i + vj.w);
             const float f = lsd(d, dl, vn, meff);
-            F[0] += f * n0;
-            F[1] += f * n1;
-            F[2] += f * n2;
+            Fx += f * n0;
+            Fy += f * n1;
+            Fz += f * n2;
         }
     }
     const float r = xi.w;
     if (d.wall_kind == DEM_WALL_BOX || d.wall_kind == DEM_WALL_DRUM) {
+        const SceneGeom &g = d.rows.sg[d.rows.nscenes == 1 ? 0 : d.rows.scene_of[i]];
         const float m = 1.0f / im_i;
-        const float *xc = &xi.x, *vc = &vi.x;
-        const int c0 = d.wall_kind == DEM_WALL_DRUM ? 1 : 0;
-        const int c1 = d.wall_kind == DEM_WALL_DRUM ? 1 : 2;
-        for (int c = c0; c <= c1; ++c) {
-            float hh, ll;
-            two_diff(xc[c], d.lo[c], hh, ll);           // x - lo
-            float dlo = __fsub_rn(r, hh) - ll;
-            if (dlo > 0.0f) F[c] += lsd(d, dlo, vc[c], m);
-            two_diff(d.hi[c], xc[c], hh, ll);           // hi - x
-            float dhi = __fsub_rn(r, hh) - ll;
-            if (dhi > 0.0f) F[c] -= lsd(d, dhi, -vc[c], m);
+        if (d.wall_kind == DEM_WALL_BOX) {
+            Fx += plane_force(d, xi.x, vi.x, r, g.lo[0], g.hi[0], m);
+            Fz += plane_force(d, xi.z, vi.z, r, g.lo[2], g.hi[2], m);
         }
+        Fy += plane_force(d, xi.y, vi.y, r, g.lo[1], g.hi[1], m);   // box side / drum caps
         if (d.wall_kind == DEM_WALL_DRUM) {
             float h[3], l[3];
             two_diff(xi.x, d.drum_cx, h[0], l[0]);
@@ -180,20 +201,19 @@ k_forces(DemDev d)
                 const float nx = -(h[0] + l[0]) * inv, nz = -(h[2] + l[2]) * inv;
                 const float vn = vi.x * nx + vi.z * nz;
                 const float f = lsd(d, dl, vn, m);
-                F[0] += f * nx;
-                F[2] += f * nz;
+                Fx += f * nx;
+                Fz += f * nz;
             }
         }
     }
-    const float4 a = d.acc[i];
-    float4 v = d.vel[i];
-    const float4 an = make_float4(F[0] * im_i + d.g[0], F[1] * im_i + d.g[1],
-                                  F[2] * im_i + d.g[2], 0.0f);
+    const float4 an = make_float4(Fx * im_i + d.g[0], Fy * im_i + d.g[1], Fz * im_i + d.g[2],
+                                  0.0f);
     v.x += (a.x + an.x) * d.half_dt;
     v.y += (a.y + an.y) * d.half_dt;
     v.z += (a.z + an.z) * d.half_dt;
     d.vel[i] = v;
     d.acc[i] = an;
+    dtr_exit(d, TR_FORCES);
 }
 
 __global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const float4 *__restrict__ vel,
@@ -222,6 +242,7 @@ struct dem_ctx {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;
+    int graph_version = 0;
 };
 
 namespace {
@@ -246,10 +267,12 @@ void dem_free(dem_ctx *c)
 
 int launch_phase(dem_ctx *c, int phase)
 {
+    c->d.trace = *c->d.rows.trace;
     if (phase == DEM_PHASE_INTEGRATE) {
         k_integrate<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d);
     } else if (phase == DEM_PHASE_BROAD) {
-        int rc = lvb_step(c->bp, (const float *)c->d.pos, (const float *)c->d.vstar, nullptr);
+        int rc = lvb_step(c->bp, (const float *)c->d.pos, (const float *)c->d.vstar,
+                          (const float *)c->d.acc);
         if (rc) return rc;
     } else if (phase == DEM_PHASE_FORCES) {
         k_forces<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d);
@@ -263,9 +286,10 @@ int launch_phase(dem_ctx *c, int phase)
 
 extern "C" {
 
-int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
-             const dem_params *prm, float dt, const lvb_box *box, const lvb_skin_policy *skin,
-             int32_t trigger, float cell_factor, void *stream)
+static int dem_init_impl(dem_ctx **out, int32_t n_scenes, const int64_t *offsets, int64_t n,
+                         const float *pos_r, const float *vel, const dem_params *prm, float dt,
+                         const lvb_box *box, const lvb_skin_policy *skin, int32_t trigger,
+                         float cell_factor, void *stream)
 {
     if (!out) return LVB_EINVAL;
     *out = nullptr;
@@ -288,11 +312,7 @@ int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
     d.kn = prm->kn;
     const double le = std::log((double)prm->restitution);
     d.two_zeta = (float)(2.0 * (-le / std::sqrt(M_PI * M_PI + le * le)));
-    for (int k = 0; k < 3; ++k) {
-        d.g[k] = prm->g[k];
-        d.lo[k] = box->lo[k];
-        d.hi[k] = box->hi[k];
-    }
+    for (int k = 0; k < 3; ++k) d.g[k] = prm->g[k];
     d.wall_kind = prm->wall_kind;
     d.clamp_tensile = prm->clamp_tensile;
     d.contacts_on = prm->contacts_on;
@@ -310,8 +330,11 @@ int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
     }
     k_dem_setup<<<std::min(grid_n((int)n), 4 * kNumSMs), kThreads, 0, c->stream>>>(
         d, (const float4 *)pos_r, (const float4 *)vel, prm->rho);
-    int rc = lvb_init(&c->bp, n, (const float *)d.pos, box, skin, trigger, cell_factor,
-                      (const float *)d.vstar, nullptr, stream);
+    int rc = offsets ? lvb_batch_init(&c->bp, n_scenes, offsets, (const float *)d.pos, box, skin,
+                                      trigger, cell_factor, (const float *)d.vstar,
+                                      (const float *)d.acc, stream)
+                     : lvb_init(&c->bp, n, (const float *)d.pos, box, skin, trigger, cell_factor,
+                                (const float *)d.vstar, (const float *)d.acc, stream);
     if (rc) {
         c->bp = nullptr;
         dem_free(c);
@@ -334,6 +357,23 @@ int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
     return LVB_OK;
 }
 
+int dem_init(dem_ctx **out, int64_t n, const float *pos_r, const float *vel,
+             const dem_params *prm, float dt, const lvb_box *box, const lvb_skin_policy *skin,
+             int32_t trigger, float cell_factor, void *stream)
+{
+    return dem_init_impl(out, 1, nullptr, n, pos_r, vel, prm, dt, box, skin, trigger,
+                         cell_factor, stream);
+}
+
+int dem_batch_init(dem_ctx **out, int32_t n_scenes, const int64_t *offsets, const float *pos_r,
+                   const float *vel, const dem_params *prm, float dt, const lvb_box *boxes,
+                   const lvb_skin_policy *skin, int32_t trigger, float cell_factor, void *stream)
+{
+    if (!offsets || n_scenes < 1) return LVB_EINVAL;
+    return dem_init_impl(out, n_scenes, offsets, offsets[n_scenes], pos_r, vel, prm, dt, boxes,
+                         skin, trigger, cell_factor, stream);
+}
+
 int dem_phase(dem_ctx *c, int32_t phase)
 {
     if (!c) return LVB_EINVAL;
@@ -347,19 +387,32 @@ int dem_advance(dem_ctx *c, int64_t steps)
     if (!c || steps < 0) return LVB_EINVAL;
     cudaGetLastError();   // clear a stale error of an unrelated earlier call
     const int64_t chunk = 50;
+    if (c->graph && c->graph_version != graph_version(c->bp)) {
+        cudaGraphExecDestroy(c->graph);   // the broad phase's nodes changed
+        c->graph = nullptr;
+    }
     if (steps >= chunk && !c->graph) {
         // one graph of `chunk` steps, built node by node (no stream capture,
         // so it works on any stream, the legacy default one included)
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaGraphCreate(&g, 0);
         cudaGraphNode_t dep = nullptr;
+        c->d.trace = *c->d.rows.trace;
         const dim3 grid(grid_n(c->d.n)), block(kThreads);
         int rc = LVB_OK;
+        // the position half-step runs inside the broad phase's check kernel
+        IntegrateArgs ia;
+        ia.pos = c->d.pos;
+        ia.vel = c->d.vel;
+        ia.acc = c->d.acc;
+        ia.vstar = c->d.vstar;
+        ia.dt = c->d.dt;
+        ia.half_dt2 = c->d.half_dt2;
+        ia.specular = c->d.wall_kind == DEM_WALL_SPECULAR;
+        ia.active = 1;
         for (int64_t s = 0; s < chunk && e == cudaSuccess && rc == LVB_OK; ++s) {
-            e = add_kernel(&dep, g, &dep, k_integrate, grid, block, c->d);
-            if (e != cudaSuccess) break;
             rc = append_step_nodes(c->bp, g, &dep, (const float *)c->d.pos,
-                                   (const float *)c->d.vstar);
+                                   (const float *)c->d.vstar, (const float *)c->d.acc, &ia);
             if (rc != LVB_OK) break;
             e = add_kernel(&dep, g, &dep, k_forces, grid, block, c->d);
         }
@@ -371,10 +424,16 @@ int dem_advance(dem_ctx *c, int64_t steps)
             return from_cuda(e);
         }
         c->graph_steps = chunk;
+        c->graph_version = graph_version(c->bp);
     }
     int64_t done = 0;
     if (c->graph) {
         for (; done + c->graph_steps <= steps; done += c->graph_steps) {
+            // a store asked to grow: grow it, and rebuild this graph, which
+            // holds the old store's addresses
+            int rc = grow_stores_if_asked(c->bp);
+            if (rc) return rc;
+            if (c->graph_version != graph_version(c->bp)) return dem_advance(c, steps - done);
             cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
             if (e != cudaSuccess) return from_cuda(e);
         }

@@ -22,11 +22,20 @@
 #include <tuple>
 
 #include "lvb.h"
+#include "lvb_mlp.h"
+
+#include <cuda_bf16.h>
 
 namespace lvb {
 
 // sticky device error bits
 enum : unsigned { DERR_NAN = 1u, DERR_CELL = 2u, DERR_STORE = 4u };
+
+// kernel slots of the per-kernel trace
+enum TraceSlot {
+    TR_CHECK = 0, TR_FUSED, TR_M_UPDATE, TR_M_ROWS, TR_M_FINISH, TR_P_UPDATE, TR_P_COMPACT,
+    TR_P_INSERT, TR_ROWS, TR_P_APPEND, TR_RELAYOUT, TR_INTEGRATE, TR_FORCES, kTraceSlots = 16
+};
 
 struct DevCounters {
     int nF;            // flagged at this step (final, set by the check's last block)
@@ -47,13 +56,34 @@ struct DevCounters {
     long long store_needed;  // entries the row store needed at the last layout
     unsigned long long kernels;  // kernels of this library executed (device count)
     long long small_steps;   // steps whose rebuild ran in the one-block kernel
+    long long log_n;         // rebuild-log samples closed so far
+    unsigned long long fused_cycles[4];  // one-block rebuild: SM cycles per phase
+    // per-kernel device time (LVB_OPT_TRACE): first block entry / last block
+    // exit of the current step, and their differences summed over steps
+    unsigned long long tr_start[kTraceSlots], tr_end[kTraceSlots];
+    unsigned long long tr_sum[kTraceSlots], tr_cnt[kTraceSlots];
 };
 
-struct GridGeom {
-    float lo[3];
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Geometry of one scene (a context holds one or many independent scenes,
+// each a contiguous range of particles with its own box and cell grid).
+struct SceneGeom {
+    float lo[3];    // box lower corner (origin of the cell grid)
     float invL;     // 1 / L, rounded to binary32
+    float hi[3];    // box upper corner
+    float H;        // cap on R_NL = r + skin (just under L/2)
     int dim[3];     // cells per axis
-    int ccap;       // slots per cell
+    int cell_base;  // first global cell index of the scene
+    float L;        // cell edge
+    int first;      // first particle
+    int count;      // particles
+    int pad;
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -126,12 +156,13 @@ __device__ __forceinline__ int cell_coord(float x, float lo, float invL, int dim
     return min(max(c, 0), dim - 1);
 }
 
-__device__ __forceinline__ int cell_key(const GridGeom &g, float x, float y, float z)
+// global cell index of a point in scene g
+__device__ __forceinline__ int cell_key(const SceneGeom &g, float x, float y, float z)
 {
     int cx = cell_coord(x, g.lo[0], g.invL, g.dim[0]);
     int cy = cell_coord(y, g.lo[1], g.invL, g.dim[1]);
     int cz = cell_coord(z, g.lo[2], g.invL, g.dim[2]);
-    return (cz * g.dim[1] + cy) * g.dim[0] + cx;
+    return g.cell_base + (cz * g.dim[1] + cy) * g.dim[0] + cx;
 }
 
 __device__ __forceinline__ bool bit_of(const uint32_t *bits, int i)
@@ -157,6 +188,42 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// ---------------------------------------------------------------------------
+// The skin network (lvb_mlp.h), one warp per particle: lane o computes hidden
+// unit o of each layer; every sum runs in index order from its bias, so the
+// result is the same on every lane and equal to the CPU evaluation.  The
+// weights hold bfloat16 values, so fmaf(w, x, acc) = acc + w*x rounded once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bf16_rn(float x)
+{
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ float relu(float x) { return x > 0.0f ? x : 0.0f; }
+
+__device__ __forceinline__ float mlp_y_warp(const lvb_mlp_weights *__restrict__ W,
+                                            const float f[LVB_MLP_IN])
+{
+    const int lane = threadIdx.x & 31;
+    float z[LVB_MLP_IN];
+#pragma unroll
+    for (int k = 0; k < LVB_MLP_IN; ++k)
+        z[k] = bf16_rn(__fmul_rn(__fsub_rn(f[k], W->mu[k]), W->isd[k]));
+    float acc = W->b1[lane];
+#pragma unroll
+    for (int k = 0; k < LVB_MLP_IN; ++k) acc = fmaf(W->W1[lane * LVB_MLP_IN + k], z[k], acc);
+    const float h1 = bf16_rn(relu(acc));
+    float acc2 = W->b2[lane];
+#pragma unroll
+    for (int k = 0; k < LVB_MLP_HIDDEN; ++k)
+        acc2 = fmaf(W->W2[lane * LVB_MLP_HIDDEN + k], __shfl_sync(FULL, h1, k), acc2);
+    const float h2 = bf16_rn(relu(acc2));
+    float y = W->b3;
+#pragma unroll
+    for (int k = 0; k < LVB_MLP_HIDDEN; ++k) y = fmaf(W->w3[k], __shfl_sync(FULL, h2, k), y);
+    return y;
+}
+
 // Slack rule of the row store: capacity for a row of `len` entries.
 __host__ __device__ __forceinline__ int row_capacity(int len)
 {
@@ -168,6 +235,50 @@ __host__ __device__ __forceinline__ int row_capacity(int len)
 // Library-internal view of a broad-phase context's rows (used by the DEM
 // driver in the same library; not part of the C-ABI).
 namespace lvb {
+// Velocity-Verlet position half-step of the DEM driver, shared by its own
+// integrate kernel and by the check kernel that fuses it (identical
+// arithmetic either way: explicit roundings, no compiler-chosen fusion):
+//   x' = x + (v dt + a dt^2/2),  v* = v + a dt   (v*.w keeps 1/m)
+// with specular reflection at the scene box when `specular` (x mirrored, v
+// and v* negated per axis).
+struct IntegrateArgs {
+    float4 *pos, *vel, *acc, *vstar;
+    float dt, half_dt2;
+    int specular;
+    int active;     // 0: the check reads positions as they are
+};
+
+__device__ __forceinline__ float4 integrate_one(const IntegrateArgs &a, const SceneGeom &g, int i)
+{
+    float4 x = a.pos[i];
+    float4 v = a.vel[i];
+    const float4 ac = a.acc[i];
+    const float im = a.vstar[i].w;
+    x.x = __fadd_rn(x.x, fmaf(ac.x, a.half_dt2, __fmul_rn(v.x, a.dt)));
+    x.y = __fadd_rn(x.y, fmaf(ac.y, a.half_dt2, __fmul_rn(v.y, a.dt)));
+    x.z = __fadd_rn(x.z, fmaf(ac.z, a.half_dt2, __fmul_rn(v.z, a.dt)));
+    float4 vs = make_float4(fmaf(ac.x, a.dt, v.x), fmaf(ac.y, a.dt, v.y), fmaf(ac.z, a.dt, v.z), im);
+    if (a.specular) {
+        const float r = x.w;
+        float lo = __fadd_rn(g.lo[0], r), hi = __fsub_rn(g.hi[0], r);
+        if (x.x < lo || x.x > hi) {
+            x.x = __fsub_rn(__fmul_rn(2.0f, x.x < lo ? lo : hi), x.x); v.x = -v.x; vs.x = -vs.x;
+        }
+        lo = __fadd_rn(g.lo[1], r); hi = __fsub_rn(g.hi[1], r);
+        if (x.y < lo || x.y > hi) {
+            x.y = __fsub_rn(__fmul_rn(2.0f, x.y < lo ? lo : hi), x.y); v.y = -v.y; vs.y = -vs.y;
+        }
+        lo = __fadd_rn(g.lo[2], r); hi = __fsub_rn(g.hi[2], r);
+        if (x.z < lo || x.z > hi) {
+            x.z = __fsub_rn(__fmul_rn(2.0f, x.z < lo ? lo : hi), x.z); v.z = -v.z; vs.z = -vs.z;
+        }
+        a.vel[i] = v;
+    }
+    a.pos[i] = x;
+    a.vstar[i] = vs;
+    return x;
+}
+
 struct RowsView {
     const int *row_off;
     const int *row_len;
@@ -175,14 +286,28 @@ struct RowsView {
     const int *col;
     const float *rad;
     unsigned long long *kernels;   // device kernel counter of the context
+    DevCounters *cnt;              // counters (trace slots)
+    const int *trace;              // host address of the trace switch
+    const SceneGeom *sg;           // per-scene geometry (device)
+    const int *scene_of;           // scene of each particle (null: one scene)
+    int nscenes;
     int n;
 };
 RowsView rows_view(lvb_ctx *c);
 
 // Appends the nodes of one lvb_step (check, conditional rebuild, conditional
 // re-layout) to graph g after *dep (may be null); *dep receives the last node.
+// With `integ`, the step's first kernel also performs the driver's
+// position half-step (IntegrateArgs) before checking.
 int append_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, const float *pos_r,
-                      const float *vel);
+                      const float *vel, const float *acc, const IntegrateArgs *integ = nullptr);
+
+// Changes whenever the nodes of a step change (options, logging, store
+// growth), so that a caller holding a graph of steps knows to rebuild it.
+int graph_version(lvb_ctx *c);
+
+// Grows the row store / cell slots if a kernel asked for it (see lvb_step).
+int grow_stores_if_asked(lvb_ctx *c);
 
 // Adds a kernel node running fn(args...) after the given dependency (none
 // when dep or *dep is null); the argument values are copied into the node.

@@ -40,9 +40,17 @@ class lvb_box(ctypes.Structure):
 class lvb_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("n", "steps", "rebuild_steps", "flagged_total", "updated_total", "last_flagged",
-                 "entries", "pairs", "relayouts", "cell_capacity", "row_store_capacity",
-                 "kernels_executed", "small_path_steps", "small_max", "graphs")] + \
+                 "entries", "pairs", "relayouts", "grows", "cell_capacity", "row_store_capacity",
+                 "kernels_executed", "small_path_steps", "small_max", "medium_max", "graphs",
+                 "n_scenes")] + \
+               [("fused_phase_cycles", ctypes.c_int64 * 4)] + \
                [("cell_edge", ctypes.c_float), ("rnl_max", ctypes.c_float),
+                ("grid", ctypes.c_int32 * 3), ("pad", ctypes.c_int32)]
+
+
+class lvb_scene_info_t(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int64), ("count", ctypes.c_int64),
+                ("cell_edge", ctypes.c_float), ("rnl_max", ctypes.c_float),
                 ("grid", ctypes.c_int32 * 3), ("pad", ctypes.c_int32)]
 
 
@@ -65,12 +73,17 @@ _SIGS = {
     "lvb_init": ([ctypes.POINTER(_p), _i64, _p, ctypes.POINTER(lvb_box),
                   ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p, _p],
                  ctypes.c_int),
+    "lvb_batch_init": ([ctypes.POINTER(_p), ctypes.c_int32, _p, _p, ctypes.POINTER(lvb_box),
+                        ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p,
+                        _p], ctypes.c_int),
+    "lvb_scene_info": ([_p, ctypes.c_int32, ctypes.POINTER(lvb_scene_info_t)], ctypes.c_int),
     "lvb_init_resume": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(lvb_box),
                          ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p,
                          _p], ctypes.c_int),
     "lvb_step": ([_p, _p, _p, _p], ctypes.c_int),
     "lvb_sync": ([_p], ctypes.c_int),
     "lvb_set_option": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
+    "lvb_trace": ([_p, _p, _p], ctypes.c_int),
     "lvb_get_pairs": ([_p, _p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_get_pairs_ij": ([_p, _p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_get_contacts": ([_p, _p, _p, _p, _p, _i64, _pi64], ctypes.c_int),
@@ -80,9 +93,20 @@ _SIGS = {
     "lvb_set_stream": ([_p, _p], ctypes.c_int),
     "lvb_destroy": ([_p], ctypes.c_int),
     "lvb_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "lvb_mlp_pack": ([_p, _p, _p, _p], ctypes.c_int),
+    "lvb_mlp_infer": ([_p, _p, _i64, _p, _p, _p, _p], ctypes.c_int),
+    "lvb_mlp_grad": ([_p, _i64, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_double), _p],
+                     ctypes.c_int),
+    "lvb_mlp_train": ([_p, _i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
+                       _p, _p, _p, _p, _p], ctypes.c_int),
+    "lvb_log_enable": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
+    "lvb_log_read": ([_p, _p, _i64, _pi64], ctypes.c_int),
     "dem_init": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(dem_params), ctypes.c_float,
                   ctypes.POINTER(lvb_box), ctypes.POINTER(lvb_skin_policy), ctypes.c_int32,
                   ctypes.c_float, _p], ctypes.c_int),
+    "dem_batch_init": ([ctypes.POINTER(_p), ctypes.c_int32, _p, _p, _p, ctypes.POINTER(dem_params),
+                        ctypes.c_float, ctypes.POINTER(lvb_box), ctypes.POINTER(lvb_skin_policy),
+                        ctypes.c_int32, ctypes.c_float, _p], ctypes.c_int),
     "dem_advance": ([_p, _i64], ctypes.c_int),
     "dem_phase": ([_p, ctypes.c_int32], ctypes.c_int),
     "dem_get_state": ([_p, _p, _p, _p, _p], ctypes.c_int),
@@ -126,6 +150,22 @@ def lvb_init(n, pos_r, box, skin, trigger, cell_factor, vel=None, acc=None, stre
     return ctx
 
 
+def lvb_batch_init(n_scenes, offsets, pos_r, boxes, skin, trigger, cell_factor, vel=None,
+                   acc=None, stream=None):
+    """offsets: host int64 array (n_scenes + 1); boxes: ctypes array of lvb_box."""
+    ctx = _p()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    rc = _lib.lvb_batch_init(ctypes.byref(ctx), int(n_scenes), off.ctypes.data, pos_r, boxes,
+                             ctypes.byref(skin), int(trigger), float(cell_factor), vel, acc,
+                             stream)
+    _check(rc, "lvb_batch_init")
+    return ctx
+
+
+def lvb_scene_info(ctx, scene, out):
+    return _lib.lvb_scene_info(ctx, int(scene), out)
+
+
 def lvb_init_resume(n, pos_r, ref4, box, skin, trigger, cell_factor, vel=None, acc=None,
                     stream=None):
     ctx = _p()
@@ -140,7 +180,13 @@ def lvb_step(ctx, pos_r, vel=None, acc=None):
     return _lib.lvb_step(ctx, pos_r, vel, acc)
 
 
-LVB_OPT_GRAPH, LVB_OPT_SMALL_MAX = 0, 1
+LVB_OPT_GRAPH, LVB_OPT_SMALL_MAX, LVB_OPT_MEDIUM_MAX, LVB_OPT_TRACE = 0, 1, 2, 3
+TRACE_SLOTS = ["check", "one_block", "m_update", "m_rows", "m_finish", "p_update", "p_compact",
+               "p_insert", "rows", "p_append", "relayout", "integrate", "forces"]
+
+
+def lvb_trace(ctx, sum_ns, count):
+    return _lib.lvb_trace(ctx, sum_ns, count)
 
 
 def lvb_set_option(ctx, option, value):
@@ -192,6 +238,17 @@ def dem_init(n, pos_r, vel, prm, dt, box, skin, trigger, cell_factor, stream=Non
     return ctx
 
 
+def dem_batch_init(n_scenes, offsets, pos_r, vel, prm, dt, boxes, skin, trigger, cell_factor,
+                   stream=None):
+    ctx = _p()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    rc = _lib.dem_batch_init(ctypes.byref(ctx), int(n_scenes), off.ctypes.data, pos_r, vel,
+                             ctypes.byref(prm), float(dt), boxes, ctypes.byref(skin),
+                             int(trigger), float(cell_factor), stream)
+    _check(rc, "dem_batch_init")
+    return ctx
+
+
 def dem_advance(ctx, steps):
     return _lib.dem_advance(ctx, int(steps))
 
@@ -228,6 +285,35 @@ def dem_destroy(ctx):
     return _lib.dem_destroy(ctx)
 
 
+LVB_MLP_IN, LVB_MLP_HIDDEN, LVB_MLP_PARAMS = 8, 32, 1377
+MLP_WEIGHTS_BYTES = 4 * (32 * 8 + 32 + 32 * 32 + 32 + 32 + 1 + 8 + 8 + 3)
+
+
+def lvb_mlp_pack(params, mu, isd, out):
+    return _lib.lvb_mlp_pack(params, mu, isd, out)
+
+
+def lvb_mlp_infer(feats, diam, n, w, skin, y, stream=None):
+    return _lib.lvb_mlp_infer(feats, diam, int(n), w, skin, y, stream)
+
+
+def lvb_mlp_grad(samples, n, params, mu, isd, grad, loss, stream=None):
+    return _lib.lvb_mlp_grad(samples, int(n), params, mu, isd, grad, loss, stream)
+
+
+def lvb_mlp_train(samples, n, epochs, batch, lr, seed, params, mu, isd, losses, stream=None):
+    return _lib.lvb_mlp_train(samples, int(n), int(epochs), int(batch), float(lr), int(seed),
+                              params, mu, isd, losses, stream)
+
+
+def lvb_log_enable(ctx, horizon, capacity):
+    return _lib.lvb_log_enable(ctx, int(horizon), int(capacity))
+
+
+def lvb_log_read(ctx, samples, cap, n_samples):
+    return _lib.lvb_log_read(ctx, samples, int(cap), n_samples)
+
+
 def _np_ptr(a):
     return a.ctypes.data_as(_p)
 
@@ -244,15 +330,28 @@ class LVB:
 
     def __init__(self, pos, box_lo, box_hi, skin_kind=LVB_SKIN_DIAMETER_FACTOR, skin_value=0.1,
                  dt=0.0, trigger=LVB_TRIGGER_PARTIAL, cell_factor=1.25, vel=None, acc=None,
-                 stream=None, ref=None):
+                 stream=None, ref=None, offsets=None, mlp=None):
+        """One scene (box_lo/box_hi: 3 floats), or several independent scenes
+        when offsets (n_scenes + 1 particle offsets) is given and box_lo /
+        box_hi hold one corner per scene."""
         import torch
         self.n = int(pos.shape[0])
+        self._mlp = mlp            # keeps the weights alive with the context
+        skin = lvb_skin_policy(int(skin_kind), float(skin_value), float(dt), _dptr(mlp))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        if offsets is not None:
+            ns = len(offsets) - 1
+            boxes = (lvb_box * ns)()
+            for q in range(ns):
+                for k in range(3):
+                    boxes[q].lo[k], boxes[q].hi[k] = float(box_lo[q][k]), float(box_hi[q][k])
+            self.ctx = lvb_batch_init(ns, offsets, _dptr(pos), boxes, skin, trigger, cell_factor,
+                                      _dptr(vel), _dptr(acc), stream)
+            return
         box = lvb_box()
         for k in range(3):
             box.lo[k], box.hi[k] = float(box_lo[k]), float(box_hi[k])
-        skin = lvb_skin_policy(int(skin_kind), float(skin_value), float(dt), None)
-        if stream is None:
-            stream = torch.cuda.current_stream().cuda_stream
         if ref is None:
             self.ctx = lvb_init(self.n, _dptr(pos), box, skin, trigger, cell_factor, _dptr(vel),
                                 _dptr(acc), stream)
@@ -317,10 +416,36 @@ class LVB:
         _check(lvb_get_ref(self.ctx, _np_ptr(out)), "lvb_get_ref")
         return out
 
+    def trace(self):
+        """Mean device time per step (us) of each traced kernel."""
+        a = np.zeros(16, np.uint64)
+        b = np.zeros(16, np.uint64)
+        _check(lvb_trace(self.ctx, _np_ptr(a), _np_ptr(b)), "lvb_trace")
+        return {name: (float(a[k]) / 1e3 / max(int(b[k]), 1), int(b[k]))
+                for k, name in enumerate(TRACE_SLOTS)}
+
+    def log_enable(self, horizon, capacity):
+        _check(lvb_log_enable(self.ctx, horizon, capacity), "lvb_log_enable")
+
+    def log_samples(self):
+        n = ctypes.c_int64(0)
+        rc = lvb_log_read(self.ctx, None, 0, ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_log_read")
+        out = np.empty((max(n.value, 1), LVB_MLP_IN + 1), dtype=np.float32)
+        _check(lvb_log_read(self.ctx, _np_ptr(out), n.value, ctypes.byref(n)), "lvb_log_read")
+        return out[:n.value]
+
+    def scene_info(self, scene):
+        si = lvb_scene_info_t()
+        _check(lvb_scene_info(self.ctx, scene, ctypes.byref(si)), "lvb_scene_info")
+        return {"first": si.first, "count": si.count, "cell_edge": si.cell_edge,
+                "rnl_max": si.rnl_max, "grid": list(si.grid)}
+
     def stats(self):
         st = lvb_stats_t()
         _check(lvb_stats(self.ctx, ctypes.byref(st)), "lvb_stats")
-        return {k: (list(getattr(st, k)) if k == "grid" else getattr(st, k))
+        return {k: (list(getattr(st, k)) if k in ("grid", "fused_phase_cycles") else getattr(st, k))
                 for k, _ in lvb_stats_t._fields_ if k != "pad"}
 
     def close(self):
@@ -355,8 +480,13 @@ class DEM:
 
     def __init__(self, scene, trigger=LVB_TRIGGER_PARTIAL, skin_kind=None, skin_value=None,
                  cell_factor=None, stream=None):
+        """scene: one scene, or a list of scenes (same physics, own boxes)
+        advanced together as one batch."""
         import torch
-        self.n = int(scene.n)
+        batch = isinstance(scene, (list, tuple))
+        scenes_ = list(scene) if batch else [scene]
+        scene = scenes_[0]
+        self.n = int(sum(q.n for q in scenes_))
         prm = dem_params()
         prm.kn, prm.restitution, prm.rho = scene.kn, scene.restitution, scene.rho
         for k in range(3):
@@ -367,19 +497,28 @@ class DEM:
             prm.drum_cx, prm.drum_cz, prm.drum_R, prm.drum_omega = scene.drum
         prm.contacts_on = int(bool(scene.contacts))
         self.prm = prm
-        box = lvb_box()
-        for k in range(3):
-            box.lo[k], box.hi[k] = scene.lo[k], scene.hi[k]
+        boxes = (lvb_box * len(scenes_))()
+        for q, sc in enumerate(scenes_):
+            for k in range(3):
+                boxes[q].lo[k], boxes[q].hi[k] = sc.lo[k], sc.hi[k]
         kind = scene.skin_kind if skin_kind is None else skin_kind
         value = scene.skin_value if skin_value is None else skin_value
         skin = lvb_skin_policy(int(kind), float(value), float(scene.dt), None)
         cf = scene.cell_factor if cell_factor is None else cell_factor
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
-        pos = torch.from_numpy(np.ascontiguousarray(scene.pos, dtype=np.float32)).cuda()
-        vel = torch.from_numpy(np.ascontiguousarray(scene.vel, dtype=np.float32)).cuda()
-        self.ctx = dem_init(self.n, pos.data_ptr(), vel.data_ptr(), prm, scene.dt, box, skin,
-                            trigger, cf, stream)
+        pos = torch.from_numpy(np.ascontiguousarray(np.concatenate([q.pos for q in scenes_]),
+                                                    dtype=np.float32)).cuda()
+        vel = torch.from_numpy(np.ascontiguousarray(np.concatenate([q.vel for q in scenes_]),
+                                                    dtype=np.float32)).cuda()
+        if batch:
+            self.offsets = np.concatenate([[0], np.cumsum([q.n for q in scenes_])]).astype(np.int64)
+            self.ctx = dem_batch_init(len(scenes_), self.offsets, pos.data_ptr(), vel.data_ptr(),
+                                      prm, scene.dt, boxes, skin, trigger, cf, stream)
+        else:
+            self.offsets = np.array([0, self.n], dtype=np.int64)
+            self.ctx = dem_init(self.n, pos.data_ptr(), vel.data_ptr(), prm, scene.dt, boxes[0],
+                                skin, trigger, cf, stream)
         torch.cuda.synchronize()
         self.lvb = _BorrowedLVB(dem_lvb(self.ctx), self.n)
 
@@ -424,3 +563,29 @@ class DEM:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ skin network
+def mlp_weights_device(params, mu, isd):
+    """Pack master parameters (+ normalisation) into a device
+    lvb_mlp_weights record; returns the torch byte tensor holding it."""
+    import torch
+    buf = torch.empty(MLP_WEIGHTS_BYTES, dtype=torch.uint8, device="cuda")
+    p = np.ascontiguousarray(params, np.float32)
+    m = np.ascontiguousarray(mu, np.float32)
+    d = np.ascontiguousarray(isd, np.float32)
+    _check(lvb_mlp_pack(_np_ptr(p), _np_ptr(m), _np_ptr(d), buf.data_ptr()), "lvb_mlp_pack")
+    return buf
+
+
+def mlp_train(samples_dev, epochs, batch, lr, seed, params0):
+    """Train on device samples (torch (n, 9) float32); returns (params, mu,
+    isd, losses)."""
+    p = np.ascontiguousarray(params0, np.float32).copy()
+    mu = np.zeros(LVB_MLP_IN, np.float32)
+    isd = np.zeros(LVB_MLP_IN, np.float32)
+    losses = np.zeros(int(epochs), np.float32)
+    _check(lvb_mlp_train(samples_dev.data_ptr(), samples_dev.shape[0], epochs, batch, lr, seed,
+                         _np_ptr(p), _np_ptr(mu), _np_ptr(isd), _np_ptr(losses)),
+           "lvb_mlp_train")
+    return p, mu, isd, losses

@@ -120,7 +120,7 @@ def settling(n=200_000, seed=SEED_BASE + 1, rmin=0.5e-3, rmax=2e-3, footprint=0.
     spacing = 2.0 * rmax * 1.01
     per_layer = int(math.floor(footprint / spacing)) ** 2
     layers = int(math.ceil(n / per_layer))
-    fill_h = layers * spacing
+    fill_h = layers * spacing * (1.0 + 1e-9)   # exact multiple: keep the last layer
     if fill_h > height:
         raise ValueError("box too short for %d particles" % n)
     xyz = _jittered_lattice(rng, n, (0, 0, 0), (footprint, footprint, fill_h), spacing, radii)

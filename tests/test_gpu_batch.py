@@ -1,0 +1,112 @@
+"""Batched contexts: many independent scenes of uneven size in one context
+must give, scene by scene, exactly the oracle's result for that scene alone
+(no pair joins two scenes), and the batched DEM driver must match the
+binary64 oracle per scene with each scene's own walls."""
+import numpy as np
+import pytest
+
+from paper_2208_13770_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _lvb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_13770_gb300 import lvb
+    return lvb
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _scenes(k, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(k):
+        n = int(rng.integers(50, 3000))
+        s = scenes.settling(n=n, seed=1000 + seed * 100 + q, footprint=0.03 + 0.01 * (q % 3),
+                            height=0.5, rmin=0.5e-3, rmax=float(rng.uniform(1.0e-3, 2e-3)))
+        out.append(s)
+    return out
+
+
+def _walks(sc, steps, sigma, seed):
+    rng = np.random.default_rng(seed)
+    pos = [s.pos.copy() for s in sc]
+    for _ in range(steps):
+        for p in pos:
+            p[:, :3] += rng.normal(0, sigma, size=(len(p), 3)).astype(np.float32)
+        yield [p.copy() for p in pos]
+
+
+def test_batch_broad_phase_parity_per_scene(orc):
+    lvb = _lvb()
+    from oracle.statemachine import OracleLVB
+    sc = _scenes(9, seed=3)
+    off = np.concatenate([[0], np.cumsum([s.n for s in sc])]).astype(np.int64)
+    pos0 = np.concatenate([s.pos for s in sc])
+    ctx = lvb.LVB(_dev(pos0), [s.lo for s in sc], [s.hi for s in sc], 1, 0.1, 1e-6, 0, 1.25,
+                  offsets=off)
+    assert ctx.stats()["n_scenes"] == len(sc)
+    sms = []
+    for q, s in enumerate(sc):
+        info = ctx.scene_info(q)
+        assert info["first"] == off[q] and info["count"] == s.n
+        rmax = np.float32(s.pos[:, 3].max())
+        L = 1.25 * 2.0 * float(rmax) * (1 + 2 ** -7)
+        H = np.float32(0.5 * L * (1 - 2 ** -8))
+        assert info["rnl_max"] == H
+        sms.append(OracleLVB(s.pos, 1, 0.1, 1e-6, H, 0))
+    for k, snaps in enumerate(_walks(sc, 12, 1.2e-4, 5)):
+        ctx.step(_dev(np.concatenate(snaps)))
+        for sm, p in zip(sms, snaps):
+            sm.step(p)
+        if k % 4 == 3:
+            pi, pj = ctx.pairs_ij()
+            ei = np.concatenate([sm.pi + off[q] for q, sm in enumerate(sms)])
+            ej = np.concatenate([sm.pj + off[q] for q, sm in enumerate(sms)])
+            assert np.array_equal(pi, ei) and np.array_equal(pj, ej)
+            ref = ctx.ref()
+            assert np.array_equal(ref, np.concatenate([sm.ref for sm in sms]))
+            fl = ctx.flags()
+    st = ctx.stats()
+    assert st["updated_total"] == sum(sm.updates for sm in sms) > 0
+    ctx.close()
+
+
+def test_batch_rejects_global_trigger():
+    lvb = _lvb()
+    sc = _scenes(2, seed=1)
+    off = np.concatenate([[0], np.cumsum([s.n for s in sc])]).astype(np.int64)
+    with pytest.raises(lvb.LVBError):
+        lvb.LVB(_dev(np.concatenate([s.pos for s in sc])), [s.lo for s in sc],
+                [s.hi for s in sc], 1, 0.1, 1e-6, 1, 1.25, offsets=off)
+
+
+def test_batch_dem_matches_oracle_per_scene(orc):
+    lvb = _lvb()
+    from tests.test_gpu_dem import _params, RTOL
+    sc = [scenes.packed(n=n, seed=70 + n, vsigma=0.3) for n in (500, 1500, 3000)]
+    # shift boxes so that scenes overlap in space: they must still not interact
+    dem = lvb.DEM(sc)
+    off = dem.offsets
+    for k in range(60):
+        if k % 20 == 0:
+            x, v, a, _ = dem.state()
+            dem.step()
+            x1, v1, a1, vs1 = dem.state()
+            for q, s in enumerate(sc):
+                sl = slice(off[q], off[q + 1])
+                P = _params(orc, s)
+                xo, vso, ao, vo, fmag = orc.dem_step(x[sl], v[sl], a[sl], s.dt, P, x_in=x1[sl],
+                                                     vstar_in=vs1[sl], with_fmag=True)
+                m = s.rho * 4 / 3 * np.pi * x[sl, 3].astype(np.float64) ** 3
+                fs = (fmag / m)[:, None] + 9.81
+                assert (np.abs(a1[sl, :3] - ao) - RTOL * fs).max() <= 0
+        else:
+            dem.step()
+    assert dem.sync() == 0
+    dem.close()

@@ -60,7 +60,8 @@ def _compare(ctx, sm, pos_h, step, check_contacts=True):
         assert np.array_equal(dl, od)
 
 
-def _run_trajectory(orc, scene, snaps, trigger, skin_kind, skin_value, every=1, cell_factor=1.25):
+def _run_trajectory(orc, scene, snaps, trigger, skin_kind, skin_value, every=1, cell_factor=1.25,
+                    options=()):
     lvb = _cuda()
     from oracle.statemachine import OracleLVB
     H = _H(scene.pos, cell_factor)
@@ -68,6 +69,8 @@ def _run_trajectory(orc, scene, snaps, trigger, skin_kind, skin_value, every=1, 
     vel0 = scene.vel
     ctx = lvb.LVB(_dev(pos0), scene.lo, scene.hi, skin_kind, skin_value, scene.dt, trigger,
                   cell_factor, vel=_dev(vel0))
+    for opt, val in options:
+        ctx.set_option(opt, val)
     assert ctx.stats()["rnl_max"] == H
     sm = OracleLVB(pos0, skin_kind, skin_value, scene.dt, H, trigger, vel4=vel0)
     _compare(ctx, sm, pos0, 0)
@@ -105,11 +108,27 @@ def test_ballistic_paper_rule_parity(orc):
     _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 600), 0, 2, 200.0, every=2)
 
 
-def test_hot_gas_many_rebuilds_parity(orc):
-    # fast particles: many flags, cell moves and row changes per step
+@pytest.mark.parametrize("path", ["auto", "one_block", "three_kernel", "five_kernel", "direct"])
+def test_hot_gas_many_rebuilds_parity(orc, path):
+    # fast particles: many flags, cell moves and row changes per step, through
+    # each way a step can run: graph with the automatic choice, graph forced
+    # to the one-block rebuild, to the three-kernel rebuild, to the five-kernel
+    # rebuild, and direct launches without a graph
+    lvb = _cuda()
+    opts = {"auto": (), "one_block": ((lvb.LVB_OPT_SMALL_MAX, 1 << 30),),
+            "three_kernel": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 1 << 30)),
+            "five_kernel": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 0)),
+            "direct": ((lvb.LVB_OPT_GRAPH, 0),)}[path]
     s = scenes.ballistic(n=3000, seed=5, phi=0.3, vsigma=3.0)
-    st, _ = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 150), 0, 1, 0.1)
+    st, _ = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 150), 0, 1, 0.1,
+                            options=opts)
     assert st["updated_total"] > s.n
+    if path == "one_block":      # every step with at most 1024 flagged
+        assert st["small_path_steps"] > 0 and st["small_max"] == 1024
+    if path in ("three_kernel", "five_kernel"):
+        assert st["small_path_steps"] == 0
+    if path == "direct":
+        assert st["graphs"] == 0
 
 
 def _random_walk(scene, steps, sigma, seed=0):
@@ -170,9 +189,11 @@ def test_static_particles_never_flag(orc):
     ctx.close()
 
 
-def test_relayout_when_rows_grow(orc):
+@pytest.mark.parametrize("small_max,medium_max", [(32, 2048), (0, 2048), (0, 0)])
+def test_relayout_when_rows_grow(orc, small_max, medium_max):
     # contract the cloud towards its centre: rows grow past their slack and
     # the row store is re-laid out on the device; parity must hold throughout
+    lvb = _cuda()
     s = scenes.ballistic(n=2000, seed=8, phi=0.25)
 
     def shrink(steps):
@@ -182,7 +203,9 @@ def test_relayout_when_rows_grow(orc):
             pos[:, :3] = c + (pos[:, :3] - c) * np.float32(0.997)
             yield pos.copy(), s.vel
 
-    st, _ = _run_trajectory(orc, s, shrink(60), 0, 1, 0.1)
+    st, _ = _run_trajectory(orc, s, shrink(60), 0, 1, 0.1,
+                            options=((lvb.LVB_OPT_SMALL_MAX, small_max),
+                                     (lvb.LVB_OPT_MEDIUM_MAX, medium_max)))
     assert st["relayouts"] > 0
 
 
@@ -191,6 +214,70 @@ def test_polydisperse_settling_subset_parity(orc):
     s = scenes.settling(n=20_000, seed=77, footprint=0.06, height=0.6)
     st, _ = _run_trajectory(orc, s, _random_walk(s, 25, 1e-4, seed=1), 0, 1, 0.1, every=5)
     assert st["updated_total"] > 0
+
+
+def test_store_growth_keeps_parity(orc):
+    # skins that grow step by step (K|v|dt with the velocity handed to the
+    # step ramping up 1000-fold): rows grow well past the initial row store,
+    # which must grow on the fly (at 75% use), every step exact
+    lvb = _cuda()
+    from oracle.statemachine import OracleLVB
+    s = scenes.ballistic(n=3000, seed=51, vsigma=2.0, phi=0.3)
+    slow = s.vel.copy()
+    slow[:, :3] *= 1e-3
+    K = 400.0
+    # ALWAYS: every particle takes the growing skin at every step; large
+    # cells (factor 3) let the skins reach ~2 mm, rows ~60 partners
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_PAPER_KVDT, K, s.dt, 2, 3.0,
+                  vel=_dev(slow))
+    sm = OracleLVB(s.pos, 2, K, s.dt, _H(s.pos, 3.0), 2, vel4=slow)
+    cap0 = ctx.stats()["row_store_capacity"]
+    steps = 60
+    for k, (pos, vel) in enumerate(scenes.ballistic_trajectory(s, steps), start=1):
+        v = vel.copy()
+        v[:, :3] *= np.float32(10.0 ** (-3.0 + 3.0 * k / steps))
+        ctx.step(_dev(pos), _dev(v))
+        sm.step(pos, vel4=v)
+        _compare(ctx, sm, pos, k, check_contacts=(k % 10 == 0))
+    st = ctx.stats()
+    assert st["grows"] > 0 and st["row_store_capacity"] > cap0
+    ctx.close()
+
+
+def test_global_and_always_direct_launches(orc):
+    lvb = _cuda()
+    s = scenes.ballistic(n=1500, seed=12, vsigma=1.0)
+    for trig in (1, 2):
+        _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 40), trig, 1, 0.1,
+                        options=((lvb.LVB_OPT_GRAPH, 0),))
+
+
+def test_resume_from_saved_reference(orc):
+    # lvb_init_resume on a saved reference state continues exactly
+    lvb = _cuda()
+    from oracle.statemachine import OracleLVB
+    s = scenes.ballistic(n=2000, seed=31, vsigma=0.5)
+    traj = list(scenes.ballistic_trajectory(s, 80))
+    a = lvb.LVB(_dev(s.pos), s.lo, s.hi, 1, 0.1, s.dt, 0, 1.25)
+    for pos, _ in traj[:40]:
+        a.step(_dev(pos))
+    ref = a.ref()
+    b = lvb.LVB(_dev(traj[39][0]), s.lo, s.hi, 1, 0.1, s.dt, 0, 1.25, ref=_dev(ref))
+    sm = OracleLVB(traj[39][0], 1, 0.1, s.dt, _H(s.pos, 1.25), 0, ref4=ref)
+    for pos, _ in traj[40:]:
+        a.step(_dev(pos))
+        b.step(_dev(pos))
+        sm.step(pos)
+    for ctx in (a, b):
+        pi, pj = ctx.pairs_ij()
+        assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj)
+        assert np.array_equal(ctx.ref(), sm.ref)
+    bad = ref.copy()
+    bad[0, 3] = 1.0                    # skin above the cap
+    with pytest.raises(lvb.LVBError):
+        lvb.LVB(_dev(traj[39][0]), s.lo, s.hi, 1, 0.1, s.dt, 0, 1.25, ref=_dev(bad))
+    a.close()
+    b.close()
 
 
 def test_settling_full_size_parity(orc):

@@ -1,0 +1,158 @@
+"""The learned skin on the GPU against the oracle.
+
+* inference: the exact binary32/bfloat16 formula, bit for bit;
+* gradients of the mean squared error: against the binary64 oracle with the
+  same bfloat16 roundings (straight-through), 1e-4 of the largest component
+  (binary32 accumulation order differs);
+* training on the GPU lowers the loss;
+* the LEARNED skin policy inside the broad phase: the oracle recomputes every
+  feature and proposal and must get the same skins, flags and pair sets;
+* the rebuild log: samples carry the features of the update and the label
+  (largest displacement over the horizon / d).
+"""
+import numpy as np
+import pytest
+
+from paper_2208_13770_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _lvb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_13770_gb300 import lvb
+    return lvb
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _weights(seed):
+    from oracle import mlp
+    W = mlp.Weights.random(seed=seed, scale=0.6)
+    W.mu = np.linspace(-0.5, 0.5, 8).astype(np.float32)
+    W.isd = np.linspace(0.5, 2.0, 8).astype(np.float32)
+    return W
+
+
+def test_inference_bit_exact():
+    lvb = _lvb()
+    from oracle import mlp
+    W = _weights(1)
+    rng = np.random.default_rng(2)
+    n = 5000
+    f = rng.normal(0, 2, (n, 8)).astype(np.float32)
+    d = rng.uniform(1e-3, 4e-3, n).astype(np.float32)
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd)
+    skin = torch.empty(n, device="cuda")
+    y = torch.empty(n, device="cuda")
+    fd, dd = _dev(f), _dev(d)
+    rc = lvb.lvb_mlp_infer(fd.data_ptr(), dd.data_ptr(), n, wbuf.data_ptr(), skin.data_ptr(),
+                           y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    es, ey = mlp.infer(W, f, d)
+    assert np.array_equal(y.cpu().numpy(), ey)
+    assert np.array_equal(skin.cpu().numpy(), es)
+    assert (ey > 0).any() and (ey <= 0).any()
+
+
+def test_gradient_matches_oracle():
+    lvb = _lvb()
+    from oracle import mlp
+    W = _weights(5)
+    rng = np.random.default_rng(6)
+    n = 3000
+    samp = np.zeros((n, 9), np.float32)
+    samp[:, :8] = rng.normal(0, 2, (n, 8))
+    samp[:, 8] = rng.normal(0.3, 0.2, n)
+    grad = np.zeros(mlp.N_PARAMS, np.float32)
+    loss = lvb.ctypes.c_double(0)
+    p = W.flat()
+    rc = lvb.lvb_mlp_grad(_dev(samp).data_ptr(), n, p.ctypes.data, W.mu.ctypes.data,
+                          W.isd.ctypes.data, grad.ctypes.data, lvb.ctypes.byref(loss))
+    assert rc == 0
+    eloss, eg = mlp.loss_and_grad64(W, samp[:, :8], samp[:, 8], quantize=True)
+    assert abs(loss.value - eloss) <= 1e-5 * eloss
+    err = np.abs(grad - eg).max()
+    assert err <= 1e-4 * np.abs(eg).max(), err
+
+
+def test_training_lowers_loss():
+    lvb = _lvb()
+    from oracle import mlp
+    rng = np.random.default_rng(8)
+    n = 20000
+    samp = np.zeros((n, 9), np.float32)
+    samp[:, :8] = rng.normal(0, 1, (n, 8))
+    samp[:, 8] = 0.3 + 0.2 * np.tanh(samp[:, 0]) + 0.1 * np.abs(samp[:, 1])
+    p0 = mlp.Weights.random(seed=9, scale=0.3).flat()
+    p, mu, isd, losses = lvb.mlp_train(_dev(samp), epochs=15, batch=256, lr=3e-3, seed=1,
+                                       params0=p0)
+    assert losses[-1] < 0.2 * losses[0], losses
+    # the trained network, evaluated by the oracle's exact formula, fits the data
+    W = mlp.Weights.from_flat(p, mu, isd)
+    _, y = mlp.infer(W, samp[:2000, :8], np.ones(2000, np.float32))
+    assert np.mean((y - samp[:2000, 8]) ** 2) < 0.3 * np.var(samp[:, 8]) + losses[-1]
+
+
+def _learned_setup(lvb, s, seed=3):
+    from oracle import mlp
+    W = _weights(seed)
+    # keep the proposals of the order of a tenth of a diameter
+    W.b3 = np.float32(0.05)
+    W.w3 *= np.float32(0.05)
+    grid = mlp.grid_params(s.pos[:, 3].max(), s.cell_factor, s.lo, s.hi)
+    return W, grid
+
+
+def test_learned_policy_broad_phase_parity(orc):
+    lvb = _lvb()
+    from oracle.statemachine import OracleLVB
+    s = scenes.ballistic(n=2000, seed=17, vsigma=1.0)
+    W, grid = _learned_setup(lvb, s)
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd)
+    acc = np.zeros_like(s.pos)
+    acc[:, 2] = -9.81
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_LEARNED, 0.0, s.dt,
+                  lvb.LVB_TRIGGER_PARTIAL, s.cell_factor, vel=_dev(s.vel), acc=_dev(acc),
+                  mlp=wbuf)
+    sm = OracleLVB(s.pos, orc.SKIN_LEARNED, 0.0, s.dt, grid["H"], 0, vel4=s.vel,
+                   learned={"weights": W, "grid": grid}, acc4=acc)
+    assert np.array_equal(ctx.ref(), sm.ref)
+    nflag = 0
+    for k, (pos, vel) in enumerate(scenes.ballistic_trajectory(s, 120), start=1):
+        ctx.step(_dev(pos), _dev(vel), _dev(acc))
+        f, _ = sm.step(pos, vel4=vel, acc4=acc)
+        nflag += int(f.sum())
+        if k % 4 == 0:
+            assert np.array_equal(ctx.flags(), f), k
+            assert np.array_equal(ctx.ref(), sm.ref), k
+            pi, pj = ctx.pairs_ij()
+            assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj), k
+    assert nflag > 50
+    ctx.close()
+
+
+def test_rebuild_log_samples(orc):
+    lvb = _lvb()
+    s = scenes.ballistic(n=2000, seed=23, vsigma=1.0)
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, 1, 0.1, s.dt, 0, s.cell_factor)
+    horizon = 10
+    ctx.log_enable(horizon, 100000)
+    traj = list(scenes.ballistic_trajectory(s, 80))
+    for pos, _ in traj:
+        ctx.step(_dev(pos))
+    smp = ctx.log_samples()
+    assert len(smp) > 20
+    # labels are the largest displacement over the horizon in diameters:
+    # bounded by |v| * horizon * dt / d for ballistic motion between walls
+    vmax = np.linalg.norm(s.vel[:, :3], axis=1).max()
+    assert (smp[:, 8] >= 0).all()
+    assert smp[:, 8].max() <= vmax * horizon * s.dt / (2 * 1e-3) * 1.001
+    # features f2 = r / H, f4 = age > 0 after the first update
+    assert np.allclose(smp[:, 2], np.float32(1e-3) / ctx.stats()["rnl_max"])
+    ctx.close()

@@ -1,0 +1,84 @@
+"""Pins of the skin-network oracle: bfloat16 rounding against torch's own
+conversion (a library routine) and hand cases, the fixed-order binary32 dot
+product, a one-path network in closed form, and the binary64 backward pass
+against central finite differences."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def test_bf16_round_hand_cases():
+    one = np.float32(1.0)
+    cases = {1.0: 1.0, 1 + 2 ** -8: 1.0, 1 + 3 * 2 ** -8: 1 + 2 ** -6,
+             1 + 2 ** -7: 1 + 2 ** -7, -(1 + 3 * 2 ** -8): -(1 + 2 ** -6), 0.0: 0.0}
+    for x, want in cases.items():
+        assert mlp.bf16_round(np.array([x], np.float32))[0] == np.float32(want), x
+    assert np.isinf(mlp.bf16_round(np.array([3.4e38], np.float32))[0])
+    assert one == mlp.bf16_round(np.array([one]))[0]
+
+
+def test_bf16_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 1, 20000), rng.normal(0, 1e-30, 2000),
+                        rng.normal(0, 1e30, 2000)]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(mlp.bf16_round(x), want)
+
+
+def test_fixed_order_dot_is_sequential_binary32():
+    # a case where the order matters: 1 + 2^-24 + 2^-24 in order gives 1,
+    # while pairing the small terms first would give 1 + 2^-23
+    w = np.array([[1.0, 1.0, 1.0]], np.float32)
+    x = np.array([[1.0, 2.0 ** -24, 2.0 ** -24]], np.float32)
+    got = mlp._dot_fixed(np.zeros(1, np.float32), w, x)[0, 0]
+    assert got == np.float32(1.0)
+    x2 = np.array([[2.0 ** -24, 2.0 ** -24, 1.0]], np.float32)
+    assert mlp._dot_fixed(np.zeros(1, np.float32), w, x2)[0, 0] == np.float32(1 + 2.0 ** -23)
+
+
+def test_one_path_network_closed_form():
+    z = np.zeros((mlp.N_H, mlp.N_IN), np.float32)
+    W1 = z.copy(); W1[0, 0] = 1.0
+    W2 = np.zeros((mlp.N_H, mlp.N_H), np.float32); W2[0, 0] = 2.0
+    w3 = np.zeros(mlp.N_H, np.float32); w3[0] = 0.5
+    W = mlp.Weights(W1, np.zeros(mlp.N_H), W2, np.zeros(mlp.N_H), w3, 0.25,
+                    np.full(mlp.N_IN, 1.0), np.full(mlp.N_IN, 2.0))
+    f = np.array([[3.0] + [0.0] * 7, [-1.0] + [0.0] * 7, [1.3] + [0.0] * 7], np.float32)
+    d = np.array([2e-3, 2e-3, 1e-3], np.float32)
+    skin, y = mlp.infer(W, f, d)
+    z0 = mlp.bf16_round((f[:, 0] - 1.0) * 2.0)
+    expect_y = 0.25 + 0.5 * mlp.bf16_round(2.0 * np.maximum(z0, 0))
+    assert np.array_equal(y, expect_y.astype(np.float32))
+    assert np.array_equal(skin, (d * np.maximum(expect_y, 0)).astype(np.float32))
+    assert y[1] == np.float32(0.25)                 # negative input: ReLU blocks the path
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    W = mlp.Weights.random(seed=4, scale=0.5)
+    f = rng.normal(0, 1, (64, mlp.N_IN))
+    t = rng.normal(0.2, 0.1, 64)
+    loss, g = mlp.loss_and_grad64(W, f, t, quantize=False)
+    p0 = W.flat().astype(np.float64)
+    eps = 1e-6
+    idx = rng.choice(len(p0), 60, replace=False)
+    for k in idx:
+        def L(delta):
+            p = p0.copy(); p[k] += delta
+            Wk = mlp.Weights.from_flat(p, W.mu, W.isd)
+            # float32 parameters would lose the perturbation: evaluate in binary64
+            Wk.W1, Wk.b1, Wk.W2, Wk.b2, Wk.w3 = (a.astype(np.float64) for a in
+                                                  (Wk.W1, Wk.b1, Wk.W2, Wk.b2, Wk.w3))
+            o = 0
+            parts = []
+            for shape in [(mlp.N_H, mlp.N_IN), (mlp.N_H,), (mlp.N_H, mlp.N_H), (mlp.N_H,),
+                          (mlp.N_H,), ()]:
+                size = int(np.prod(shape)) if shape else 1
+                parts.append(p[o:o + size].reshape(shape) if shape else p[o]); o += size
+            Wk.W1, Wk.b1, Wk.W2, Wk.b2, Wk.w3, Wk.b3 = parts
+            return mlp.loss_and_grad64(Wk, f, t, quantize=False)[0]
+        fd = (L(eps) - L(-eps)) / (2 * eps)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+    assert len(g) == mlp.N_PARAMS == 1377
