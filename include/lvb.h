@@ -57,6 +57,8 @@ extern "C" {
 #define LVB_EOVERFLOW  (-6)  /* an internal fixed-capacity store overflowed
                                 (cell slots or pair store); list invalid */
 #define LVB_ESTATE     (-7)  /* call not valid in the context's state */
+#define LVB_ELIMIT     (-8)  /* input larger than a fixed-size entry point's
+                                stated maximum (lvb_noalloc.h) */
 
 /* Skin policies (Sec. "The local skin parameter" and Sec. Results). */
 #define LVB_SKIN_GLOBAL           0  /* skin = value (uniform; the paper's

@@ -1603,6 +1603,7 @@ const char *lvb_strerror(int status)
     case LVB_ENAN: return "non-finite position or radius";
     case LVB_EOVERFLOW: return "internal store overflow (cell slots or pair store)";
     case LVB_ESTATE: return "invalid call for the context state";
+    case LVB_ELIMIT: return "input exceeds the entry point's fixed maximum size";
     default: return "unknown status";
     }
 }

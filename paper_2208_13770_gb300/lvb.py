@@ -23,7 +23,8 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 LVB_OK, LVB_EINVAL, LVB_ENOMEM, LVB_ECAPACITY, LVB_EDEVICE, LVB_ENAN, LVB_EOVERFLOW, \
-    LVB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+    LVB_ESTATE, LVB_ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7, -8
+LVB_NOALLOC_MAX_N = 65536
 LVB_SKIN_GLOBAL, LVB_SKIN_DIAMETER_FACTOR, LVB_SKIN_PAPER_KVDT, LVB_SKIN_LEARNED = 0, 1, 2, 3
 LVB_TRIGGER_PARTIAL, LVB_TRIGGER_GLOBAL, LVB_TRIGGER_ALWAYS = 0, 1, 2
 
@@ -101,6 +102,8 @@ _SIGS = {
                        _p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_log_enable": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
     "lvb_log_read": ([_p, _p, _i64, _pi64], ctypes.c_int),
+    "lvb_pairs_noalloc": ([_i64, _p, _p, ctypes.POINTER(lvb_box), _p, _p, _i64, _pi64, _p],
+                          ctypes.c_int),
     "dem_init": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(dem_params), ctypes.c_float,
                   ctypes.POINTER(lvb_box), ctypes.POINTER(lvb_skin_policy), ctypes.c_int32,
                   ctypes.c_float, _p], ctypes.c_int),
@@ -312,6 +315,10 @@ def lvb_log_enable(ctx, horizon, capacity):
 
 def lvb_log_read(ctx, samples, cap, n_samples):
     return _lib.lvb_log_read(ctx, samples, int(cap), n_samples)
+
+
+def lvb_pairs_noalloc(n, pos4, ref4, box, pi, pj, cap, n_pairs, stream=None):
+    return _lib.lvb_pairs_noalloc(int(n), pos4, ref4, box, pi, pj, int(cap), n_pairs, stream)
 
 
 def _np_ptr(a):
