@@ -123,15 +123,22 @@ def _scene(rank):
 
 
 def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, flush,
-             record=None, graph=True):
+             record=None, graph=True, choice=None):
     """Runs warmup + steps DEM steps with per-phase CUDA events.  Returns
-    per-phase total ms, stats and the (optional) recorded window."""
-    dem = lvb.DEM(scene, trigger=trigger, skin_kind=skin_kind, skin_value=skin_value)
+    per-phase total ms, stats and the (optional) recorded window.  flush:
+    a buffer larger than L2 written before every step, or None when the
+    inputs themselves are larger than L2.  choice: an autotuned launch
+    choice (cell factor, check block shape, last-block threshold)."""
+    dem = lvb.DEM(scene, trigger=trigger, skin_kind=skin_kind, skin_value=skin_value,
+                  cell_factor=None if choice is None else choice.cell_factor)
+    if choice is not None:
+        choice.apply(dem, lvb)
     if not graph:
         dem.lvb.set_option(lvb.LVB_OPT_GRAPH, 0)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         dem.step()
     torch.cuda.synchronize()
     st0 = dem.lvb.stats()
@@ -156,7 +163,8 @@ def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, f
                 torch.cuda.synchronize()
                 rec["ref"] = dem.lvb.ref()
                 rec["pos0"] = dem.state()[0]
-            flush.zero_()
+            if flush is not None:
+                flush.zero_()
             e = evs[b]
             e[0].record(stream)
             dem.phase(lvb.DEM_PHASE_INTEGRATE)
@@ -182,6 +190,69 @@ def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, f
     out = {"phase_ms": tot, "wall_ms": wall_ms, "stats0": st0, "stats1": st1, "rec": rec}
     dem.close()
     return out
+
+
+BATCH_STEPS = 2000
+
+
+def _batched(lvb, torch, hbm_peak, warmup):
+    """512 independent settling scenes (6.2M particles) advanced together:
+    autotuned launch choice, then the 2,000-step workload through graphs of
+    DEM_GRAPH_STEPS steps (full steps), and once more phase by phase with
+    CUDA events for the broad phase's share.  The inputs exceed L2, so no
+    flush is needed."""
+    from paper_2208_13770_gb300 import autotune, scenes
+    sc = scenes.batch()
+    n = int(sum(q.n for q in sc))
+    best, trials = autotune.tune(sc)
+    dem = lvb.DEM(sc, cell_factor=best.cell_factor)
+    best.apply(dem, lvb)
+    dem.advance(warmup)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    k0 = dem.lvb.stats()["kernels_executed"]
+    e0.record(stream)
+    dem.advance(BATCH_STEPS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rc = dem.sync()
+    if rc != 0:
+        raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
+    graph_ms = e0.elapsed_time(e1)
+    k1 = dem.lvb.stats()["kernels_executed"]
+    dem.close()
+    ph = _run_dem(lvb, torch, sc, lvb.LVB_TRIGGER_PARTIAL, sc[0].skin_kind, sc[0].skin_value,
+                  BATCH_STEPS, warmup, None, choice=best)
+    bp_ms = float(ph["phase_ms"][1])
+    s0, s1 = ph["stats0"], ph["stats1"]
+    F = (s1["flagged_total"] - s0["flagged_total"]) / BATCH_STEPS
+    row_len = s1["entries"] / n
+    bytes_bp = 32.0 * n + n / 8.0 + F * (64.0 + 8.0 * row_len)
+    t_ms = bp_ms / BATCH_STEPS
+    ach = bytes_bp / (t_ms * 1e-3) / 1e9
+    return {
+        "workload": "512 settling boxes, N log-uniform in [1000, 50000] (seeded), %d particles, "
+                    "r~U[0.5,2] mm, skin 0.1 d_i, %d steps" % (n, BATCH_STEPS),
+        "n_scenes": len(sc), "n": n, "steps": BATCH_STEPS,
+        "value": n * BATCH_STEPS / (bp_ms * 1e-3), "unit": "particle-steps/s",
+        "full_step_graph_value": n * BATCH_STEPS / (graph_ms * 1e-3),
+        "graph_steps": 100, "graph_ms_per_step": graph_ms / BATCH_STEPS,
+        "gpu_launches_graph_run": int(k1 - k0),
+        "phases_ms_per_step": {"integrate": float(ph["phase_ms"][0]) / BATCH_STEPS,
+                               "broad": t_ms, "forces": float(ph["phase_ms"][2]) / BATCH_STEPS},
+        "roofline": {"bound": "hbm", "kernel": "broad phase (check + partial rebuild)",
+                     "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "bytes_per_launch": bytes_bp, "ms_per_launch": t_ms},
+        "flagged_per_step": F,
+        "rebuild_fraction": (s1["updated_total"] - s0["updated_total"]) / (n * BATCH_STEPS),
+        "autotune": {"choice": {"cell_factor": best.cell_factor,
+                                "check_threads": best.check_threads,
+                                "small_max": best.small_max},
+                     "trials": trials},
+        "l2": "inputs (%.0f MB of particle state) exceed L2; no flush" % (n * 96 / 1e6),
+    }
 
 
 def _e2e(lvb, torch, scene, rec):
@@ -360,6 +431,7 @@ def run_native(args):
 
     e2e = _e2e(lvb, torch, scene, loc["rec"])
     e2e["value"] *= world
+    batched = None if args.no_batched else _batched(lvb, torch, hbm_peak, args.warmup)
 
     s0, s1 = loc["stats0"], loc["stats1"]
     flagged = s1["flagged_total"] - s0["flagged_total"]
@@ -423,6 +495,9 @@ def run_native(args):
         "clocks": clk.summary(),
         "timed_region_ms_incl_flush": loc["wall_ms"],
     }
+    if batched is not None:
+        batched["vs_single_scene"] = batched["value"] / value
+        line["batched"] = batched
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -443,6 +518,8 @@ def main():
                     help="time the local-buffer run only (for profiling)")
     ap.add_argument("--no-graph", action="store_true",
                     help="direct kernel launches instead of graph replays (profilers)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched (512-scene) run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

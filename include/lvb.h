@@ -111,12 +111,14 @@ typedef struct {
     int64_t small_path_steps;  /* steps whose rebuild ran in one block */
     int64_t small_max;       /* flagged counts up to this use the one-block
                                 rebuild (LVB_OPT_SMALL_MAX) */
-    int64_t medium_max;      /* ... up to this the three-kernel rebuild */
+    int64_t medium_max;      /* ... up to this the grid-wide passes on the
+                                medium grid, above it on the big grid */
     int64_t graphs;          /* 1 if steps replay a CUDA graph */
     int64_t n_scenes;        /* independent scenes in the context */
     int64_t fused_phase_cycles[4]; /* SM cycles spent by the one-block rebuild
-                                in its phases (update; rows; appends; cell
-                                moves), summed over steps (thread 0's view) */
+                                in its phases (rows and removals; appends;
+                                unused; unused), summed over steps (thread
+                                0's view) */
     float cell_edge;         /* L [m] (scene 0) */
     float rnl_max;           /* cap H on R_NL = r + skin [m] (scene 0) */
     int32_t grid[3];         /* cells per axis (scene 0) */
@@ -220,19 +222,25 @@ int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *ac
                                 call made while the stream is being captured
                                 always launches directly. */
 #define LVB_OPT_SMALL_MAX 1  /* steps with at most this many flagged particles
-                                (default 32, at most 1024) rebuild in a
-                                single block */
-#define LVB_OPT_MEDIUM_MAX 2 /* ... up to this many (default 2048) in three
-                                grid-wide kernels; more in five */
+                                (default 32, at most 1024) finish their
+                                rebuild in the check kernel's last block */
+#define LVB_OPT_MEDIUM_MAX 2 /* ... up to this many (default 2048) in two
+                                grid-wide kernels on a grid sized for this
+                                count; more on a grid of 4 blocks per SM */
 #define LVB_OPT_TRACE     3  /* 1: kernels record their device time (first
                                 block entry to last block exit), read with
                                 lvb_trace; 0 (default): off */
+#define LVB_OPT_CHECK_THREADS 4 /* block size of the check kernel: 1024
+                                (default, one block per SM), 512 or 256
+                                (two or four per SM); a launch shape only,
+                                the results do not change */
 
 /* Kernel slots of lvb_trace. */
 #define LVB_TRACE_SLOTS 16
-/* 0 check, 1 one-block rebuild, 2-4 three-kernel rebuild (update, rows,
- * finish), 5-9 five-kernel rebuild (update, compact, insert, rows, append),
- * 10 re-layout rows, 11 DEM integrate, 12 DEM forces. */
+/* 0 check (with the flagged particles' updates and, for few flagged, the
+ * one-block rest of the rebuild), 1 unused, 2-3 grid-wide rebuild passes
+ * (rows and removals, appends), 4 full-build rows, 5 re-layout rows,
+ * 6 DEM integrate, 7 DEM forces. */
 
 /* lvb_trace -- per-kernel device time summed over the steps traced so far
  * (ns) and the number of steps each kernel ran in; LVB_TRACE_SLOTS entries

@@ -89,8 +89,13 @@ int dem_batch_init(dem_ctx **out, int32_t n_scenes, const int64_t *offsets,
                    const lvb_box *boxes, const lvb_skin_policy *skin, int32_t trigger,
                    float cell_factor, void *stream);
 
+/* Steps captured in one CUDA graph by dem_advance. */
+#define DEM_GRAPH_STEPS 100
+
 /* dem_advance -- enqueue `steps` full steps (no synchronisation).  Chunks of
- * 50 steps replay one CUDA graph, built node by node on first use. */
+ * DEM_GRAPH_STEPS steps replay one CUDA graph, built node by node on first
+ * use (and again after a store grew); the remainder runs as direct
+ * launches.  Between chunks the host grows a store that asked to grow. */
 int dem_advance(dem_ctx *ctx, int64_t steps);
 
 /* dem_phase -- enqueue one phase (DEM_PHASE_*) of a step; a step is the

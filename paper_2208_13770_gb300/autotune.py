@@ -1,0 +1,92 @@
+"""Autotuner for the batched DEM step: cell-size factor, block shape of the
+check kernel, and the flagged count up to which the check's last block
+finishes a rebuild itself (beyond it, the grid-wide passes run).
+
+Each candidate is a fresh context on the same batch from the same initial
+state; it runs ``warm`` steps, then ``steps`` steps timed with CUDA events
+on the context's stream (graph replays of DEM_GRAPH_STEPS steps).  The
+search is coordinate-wise: the cell factor first (it changes the grid, so a
+new context), then the block shape, then the last-block threshold, each on
+the best of the previous ones.  The block shape and the threshold are
+launch choices only: the lists do not change.  The cell factor also sets
+the cap on every skin (R_NL <= half a cell edge, Eq.
+skin_formulus_mincell), so at 1.0 the largest particles get smaller skins
+and update more often; the lists change with the skins, but no contact is
+ever missed (Theorem 1 holds for any skin).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+CELL_FACTORS = (1.0, 1.25, 1.5)
+CHECK_THREADS = (1024, 512, 256)
+SMALL_MAX = (32, 128, 512)
+
+
+@dataclasses.dataclass
+class Choice:
+    cell_factor: float = 1.25
+    check_threads: int = 1024
+    small_max: int = 32
+
+    def apply(self, dem, lvb):
+        dem.lvb.set_option(lvb.LVB_OPT_CHECK_THREADS, self.check_threads)
+        dem.lvb.set_option(lvb.LVB_OPT_SMALL_MAX, self.small_max)
+
+
+def _trial(torch, lvb, scene_list, choice, warm, steps):
+    dem = lvb.DEM(scene_list, cell_factor=choice.cell_factor)
+    try:
+        choice.apply(dem, lvb)
+        dem.advance(warm)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dem.advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rc = dem.sync()
+        if rc != 0:
+            raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
+        return e0.elapsed_time(e1) / steps
+    finally:
+        dem.close()
+
+
+def tune(scene_list, warm=200, steps=400):
+    """Returns (best Choice, list of trials {choice fields, ms_per_step})."""
+    import torch
+    from . import lvb
+    trials = []
+
+    def run(choice):
+        ms = _trial(torch, lvb, scene_list, choice, warm, steps)
+        trials.append(dict(dataclasses.asdict(choice), ms_per_step=ms))
+        return ms
+
+    best = Choice()
+    best_ms = None
+    for cf in CELL_FACTORS:
+        c = dataclasses.replace(best, cell_factor=cf)
+        ms = run(c)
+        if best_ms is None or ms < best_ms:
+            best, best_ms = c, ms
+    base = best
+    for ct in CHECK_THREADS:
+        if ct == base.check_threads:
+            continue
+        c = dataclasses.replace(base, check_threads=ct)
+        ms = run(c)
+        if ms < best_ms:
+            best, best_ms = c, ms
+    base = best
+    for sm in SMALL_MAX:
+        if sm == base.small_max:
+            continue
+        c = dataclasses.replace(base, small_max=sm)
+        ms = run(c)
+        if ms < best_ms:
+            best, best_ms = c, ms
+    return best, trials

@@ -2,25 +2,24 @@
 //
 // One step (lvb_step) is, in launch order:
 //   k_check        displacement check of every particle (Eq. update), ballot
-//                  + block-scan compaction of the flagged ids
-//   PARTIAL trigger (local buffer, only flagged particles change):
-//   k_p_update     new reference position and skin of each flagged particle
-//                  (Eq. skin_formulus1 or another policy, capped per Eq.
-//                  skin_formulus_mincell); marks the cells it leaves and the
-//                  unflagged rows that list it
-//   k_p_compact    drops flagged entries from those rows and the leavers
-//                  from those cells
-//   k_p_insert     moves the leavers into their new cells
-//   k_rows         27-cell stencil search (Algorithm 1 on the extended
-//                  spheres of Eq. bounding_sphere) for each flagged row
-//   k_p_append     adds each flagged particle to its unflagged partners' rows
+//                  + block-scan compaction of the flagged ids; with the
+//                  PARTIAL trigger (local buffer) each block then gives the
+//                  particles it flagged their new reference position and
+//                  skin (Eq. skin_formulus1 or another policy, capped per
+//                  Eq. skin_formulus_mincell), moves them to their new cell
+//                  slots and queues the rows that listed them.  Its last
+//                  block finishes small rebuilds itself:
+//   k_inc_rows     27-cell stencil search (Algorithm 1 on the extended
+//                  spheres of Eq. bounding_sphere) for each flagged row, and
+//                  removal of the flagged entries from the queued rows
+//   k_inc_append   adds each flagged particle to its unflagged partners' rows
 //   GLOBAL / ALWAYS trigger (Def. autoverlet / no buffer):
 //   k_full_update, k_cells_clear, k_cells_insert, k_rows over all particles
 //   then, only if a row outgrew its slack: k_rows (count), scan, k_rows (fill)
-//   k_step_end     counters
-// Every kernel after k_check is launched unconditionally and returns at once
-// when the device-side counts say it has nothing to do, so a step needs no
-// host round trip.
+// Inside a graph the check selects, on the device, which of these run
+// (conditional nodes); launched directly, every kernel after k_check runs
+// and returns at once when the device-side counts say it has nothing to do,
+// so a step needs no host round trip either way.
 #include "lvb_internal.cuh"
 
 #include <algorithm>
@@ -55,7 +54,8 @@ struct DevState {
     long long ncells;
     float4 *ref;
     float *rad;
-    int *cell_of, *slot_of, *newcell;
+    int *cell_of, *slot_of;
+    int *prevcell;    // cell of each flagged particle before its update
     uint32_t *bits;
     int *fid;
     int *row_off, *row_len, *row_cap, *col;
@@ -63,7 +63,6 @@ struct DevState {
     int *trow, *trow_mark;
     int *cell_cnt, *cell_id;
     float4 *cell_ref;
-    int *tcell, *tcell_mark;
     DevCounters *cnt;
     long long *blk;
     const lvb_mlp_weights *mlp;   // skin network (LVB_SKIN_LEARNED)
@@ -82,16 +81,14 @@ struct DevState {
     cudaGraphConditionalHandle h_path;      // which rebuild body runs
     int use_cond;     // 1 inside a graph that owns the handles
     int small_max;    // flagged counts up to this use the one-block rebuild
-    int medium_max;   // ... up to this the three-kernel rebuild, above it the five-kernel one
-    float4 *fref_g;   // new (xref, R_NL) of the flagged particles (three-kernel rebuild)
-    int *fid_g;       // their ids
+    int medium_max;   // ... above it the grid-wide passes with the medium grid, then the big one
 };
 
-// bodies of the step's SWITCH, chosen by the check (values of h_path); the
-// one-block rebuild runs inside the check itself, so it needs no body
+// bodies of the step's SWITCH, chosen by the check (values of h_path); when
+// the check's last block finishes the rebuild itself no body runs
 enum Path { PATH_MEDIUM = 0, PATH_BIG = 1, PATH_RELAYOUT = 2, PATH_NONE = 3 };
 // gate modes of the kernels
-enum Gate { GATE_FLAGGED_BIG = 0, GATE_OVERFLOW = 1, GATE_ANY_FLAG = 2, GATE_ALWAYS = 3 };
+enum Gate { GATE_OVERFLOW = 1, GATE_ANY_FLAG = 2, GATE_ALWAYS = 3 };
 
 __device__ __forceinline__ const SceneGeom &geom_of(const DevState &s, int i)
 {
@@ -103,18 +100,12 @@ __device__ __forceinline__ bool store_failed(const DevState &s)
     return (s.cnt->err & DERR_STORE) != 0;
 }
 
-// flagged count when the three-kernel (medium) partial path applies, else 0
-__device__ __forceinline__ int medium_nF(const DevState &s)
+// flagged count when the grid-wide passes of a partial rebuild run (more
+// flagged than the check's last block takes), else 0
+__device__ __forceinline__ int grid_nF(const DevState &s)
 {
     const int nF = s.cnt->nF;
-    return (store_failed(s) || nF <= s.small_max || nF > s.medium_max) ? 0 : nF;
-}
-
-// flagged count when the five-kernel (big) partial path applies, else 0
-__device__ __forceinline__ int big_nF(const DevState &s)
-{
-    const int nF = s.cnt->nF;
-    return (store_failed(s) || nF <= s.medium_max) ? 0 : nF;
+    return (s.trigger != LVB_TRIGGER_PARTIAL || store_failed(s) || nF <= s.small_max) ? 0 : nF;
 }
 
 // After a failed re-layout (DERR_STORE) the row offsets no longer fit the
@@ -122,7 +113,6 @@ __device__ __forceinline__ int big_nF(const DevState &s)
 __device__ __forceinline__ int gated_items(const DevState &s, int gate)
 {
     if (store_failed(s)) return 0;
-    if (gate == GATE_FLAGGED_BIG) return big_nF(s);
     if (gate == GATE_OVERFLOW) return s.cnt->row_overflow ? s.n : 0;
     if (gate == GATE_ANY_FLAG) return s.cnt->nF ? s.n : 0;
     return s.n;
@@ -194,173 +184,164 @@ __device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g
     return skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
 }
 
-// Phases that walk a row or a cell run one warp per item (w0/wstride count
-// warps): the lanes take the entries, so a step costs a few memory
-// latencies however long the rows are, and atomics are warp-aggregated.
-
-// a2 (+ bookkeeping for a3/a5): new reference position and skin of each
-// flagged particle; marks the cell it leaves and every unflagged row that
-// lists it; opens a rebuild-log record if logging.
-__device__ __forceinline__ void ph_update(const DevState &s, const float4 *__restrict__ pos,
-                                          const float4 *__restrict__ vel,
-                                          const float4 *__restrict__ acc, int nF, int w0,
-                                          int wstride, bool mark_cells = true,
-                                          float4 *fref = nullptr, int *fids = nullptr,
-                                          bool mark_slots = false)
+// a2 + a3 for one flagged particle i, run by one warp inside the check
+// kernel (PARTIAL trigger), right after the block that checked i found it
+// flagged:
+//   * new reference position and skin (the policy's features come from the
+//     state before the update; `step` is the number of the step being taken);
+//   * its cell slot: a stayer refreshes the slot's copy of the reference
+//     state; a leaver leaves a tombstone (-1) in its old slot and takes a
+//     tombstone slot of its new cell (claimed with compare-and-swap) or a
+//     fresh one at the end.  Slots of unflagged particles never change, so
+//     after the check every cell holds the step's final reference states;
+//   * every partner j of its old row is queued (once) for the removal of
+//     the flagged entries; whether j is flagged itself is only known after
+//     the check, so the removal pass skips flagged rows;
+//   * the occupancy counts of the cells (a feature of the skin network) are
+//     left as they were before the step: the rows pass moves the counts
+//     after the check, from the old cell kept in prevcell[i].
+// (pos and vel may have been written earlier in the same kernel by the DEM
+// position half-step, so they are read through plain coherent loads.)
+// Not inlined: it runs only for flagged particles, and as a call it keeps
+// the check loop's registers free of its working set.
+__device__ __noinline__ void update_move_warp(const DevState &s, int i, const float4 *pos,
+                                                 const float4 *vel, const float4 *acc, int step)
 {
     const int lane = threadIdx.x & 31;
-    const bool feats = s.skin_kind == LVB_SKIN_LEARNED || s.log_on;
-    const int step = (int)s.cnt->steps;
-    for (int k = w0; k < nF; k += wstride) {
-        const int i = s.fid[k];
-        const float4 p = pos[i];
-        const float r = s.rad[i];
-        const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const SceneGeom &g = geom_of(s, i);
-        const int nc = cell_key(g, p.x, p.y, p.z);
-        const int oc = s.cell_of[i];
-        const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
-        float f[LVB_MLP_IN];
-        if (feats) {
-            const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            skin_features(s, p, v, a, r, g, s.ref[i], len, step - s.born[i], s.cell_live[nc], f);
-        }
-        const float sk = warp_skin(s, g, r, v, f);
-        if (lane == 0) {
-            s.ref[i] = make_float4(p.x, p.y, p.z, sk);
-            s.born[i] = step;
-            if (fref) {
-                fref[k] = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
-                fids[k] = i;
-            }
-            s.newcell[i] = nc;
-            // the three-phase rebuilds hide flagged particles from the cells'
-            // readers until their slots move: a negative id -2 - i
-            if (mark_slots) s.cell_id[(long long)oc * s.ccap + s.slot_of[i]] = -2 - i;
-            if (mark_cells && nc != oc && atomicExch(&s.tcell_mark[oc], 1) == 0)
-                s.tcell[atomicAdd(&s.cnt->ntcell, 1)] = oc;
-            if (s.log_on && s.lg_t[i] < 0) {
-                s.lg_t[i] = step;
-                s.lg_x[i] = p;
-                s.lg_m[i] = 0.0f;
+    const int ccap = s.ccap;
+    const float4 p = pos[i];
+    const float r = s.rad[i];
+    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const SceneGeom &g = geom_of(s, i);
+    const int nc = cell_key(g, p.x, p.y, p.z);
+    const int oc = s.cell_of[i], so = s.slot_of[i];
+    const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
+    float f[LVB_MLP_IN];
+    if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
+        const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        skin_features(s, p, v, a, r, g, s.ref[i], len, step - s.born[i], s.cell_live[nc], f);
+    }
+    const float sk = warp_skin(s, g, r, v, f);
+    const float4 cr = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+    if (lane == 0) {
+        s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+        s.born[i] = step;
+        s.prevcell[i] = oc;
+        if (s.log_on && s.lg_t[i] < 0) {
+            s.lg_t[i] = step;
+            s.lg_x[i] = p;
+            s.lg_m[i] = 0.0f;
 #pragma unroll
-                for (int q = 0; q < LVB_MLP_IN; ++q) s.lg_feat[(long long)i * LVB_MLP_IN + q] = f[q];
-            }
-        }
-        for (int e0 = 0; e0 < len; e0 += 32) {
-            const int e = e0 + lane;
-            int j = 0;
-            bool push = false;
-            if (e < len) {
-                j = s.col[off + e];
-                push = !bit_of(s.bits, j) && atomicExch(&s.trow_mark[j], 1) == 0;
-            }
-            const unsigned m = __ballot_sync(FULL, push);
-            if (m) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&s.cnt->ntrow, __popc(m));
-                base = __shfl_sync(FULL, base, 0);
-                if (push) s.trow[base + __popc(m & lanemask_lt())] = j;
-            }
+            for (int q = 0; q < LVB_MLP_IN; ++q) s.lg_feat[(long long)i * LVB_MLP_IN + q] = f[q];
         }
     }
-}
-
-// a5 (removal): unflagged row j drops its flagged entries; one warp, stable
-// in-place compaction (every lane reads its entry before the ballot, and an
-// entry only moves to a lower index).
-__device__ __forceinline__ void compact_row_warp(const DevState &s, int j)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = lanemask_lt();
-    const int off = s.row_off[j], len = min(s.row_len[j], s.row_cap[j]);
-    int w = 0;
+    // old partners: queue their rows for the removal pass
     for (int e0 = 0; e0 < len; e0 += 32) {
         const int e = e0 + lane;
-        int c = 0;
-        bool keep = false;
+        int j = 0;
+        bool push = false;
         if (e < len) {
-            c = s.col[off + e];
-            keep = !bit_of(s.bits, c);
+            j = s.col[off + e];
+            push = atomicExch(&s.trow_mark[j], 1) == 0;
         }
-        const unsigned m = __ballot_sync(FULL, keep);
-        if (keep) s.col[off + w + __popc(m & lt)] = c;
-        w += __popc(m);
+        const unsigned m = __ballot_sync(FULL, push);
+        if (m) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&s.cnt->ntrow, __popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (push) s.trow[base + __popc(m & lanemask_lt())] = j;
+        }
+    }
+    // cell slot
+    if (nc == oc) {
+        if (lane == 0) s.cell_ref[(long long)oc * ccap + so] = cr;
+        return;
+    }
+    if (lane == 0) s.cell_id[(long long)oc * ccap + so] = -1;
+    const long long base = (long long)nc * ccap;
+    const int cn = min(s.cell_cnt[nc], ccap);
+    int slot = -1;
+    for (int e0 = 0; e0 < cn && slot < 0; e0 += 32) {
+        const int sl = e0 + lane;
+        unsigned m = __ballot_sync(FULL, sl < cn && s.cell_id[base + sl] < 0);
+        while (m && slot < 0) {
+            const int src = __ffs(m) - 1;
+            int won = 0;
+            if (lane == src) won = atomicCAS(&s.cell_id[base + sl], -1, i) == -1;
+            won = __shfl_sync(FULL, won, src);
+            if (won) slot = e0 + src;
+            m &= m - 1;
+        }
     }
     if (lane == 0) {
-        s.row_len[j] = w;
-        s.trow_mark[j] = 0;
+        if (slot < 0) {
+            slot = atomicAdd(&s.cell_cnt[nc], 1);
+            if (slot * 4 >= ccap * 3) s.hflags->grow_cells = 1;
+            if (slot < ccap) s.cell_id[base + slot] = i;
+            else atomicOr(&s.cnt->err, DERR_CELL);
+        }
+        if (slot < ccap) {
+            s.cell_ref[base + slot] = cr;
+            s.slot_of[i] = slot;
+        }
+        s.cell_of[i] = nc;
     }
 }
 
-// a5 (removal) and a3 (leavers): one warp per touched row or cell.
-__device__ __forceinline__ void ph_compact(const DevState &s, int w0, int wstride)
+// Occupancy counts of the cells a flagged particle left and entered.
+__device__ __forceinline__ void move_live_count(const DevState &s, int i)
 {
-    const int lane = threadIdx.x & 31;
-    const int ntrow = s.cnt->ntrow, ntcell = s.cnt->ntcell;
-    const int ccap = s.ccap;
-    const unsigned lt = lanemask_lt();
-    for (int k = w0; k < ntrow + ntcell; k += wstride) {
-        if (k < ntrow) {
-            compact_row_warp(s, s.trow[k]);
-        } else {
-            const int c = s.tcell[k - ntrow];
-            const long long base = (long long)c * ccap;
-            const int cn = min(s.cell_cnt[c], ccap);
-            int w = 0;
-            for (int e0 = 0; e0 < cn; e0 += 32) {
-                const int sl = e0 + lane;
-                int id = 0;
-                bool keep = false;
-                if (sl < cn) {
-                    id = s.cell_id[base + sl];
-                    // tombstones (id < 0) and leavers go
-                    keep = id >= 0 && !(bit_of(s.bits, id) && s.newcell[id] != c);
-                }
-                const unsigned m = __ballot_sync(FULL, keep);
-                if (keep) {
-                    const int dst = w + __popc(m & lt);
-                    const float4 q = s.ref[id];
-                    s.cell_id[base + dst] = id;
-                    s.cell_ref[base + dst] = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[id], q.w));
-                    s.slot_of[id] = dst;
-                }
-                w += __popc(m);
-            }
-            for (int sl = w + lane; sl < cn; sl += 32) s.cell_id[base + sl] = -1;
-            if (lane == 0) {
-                s.cell_cnt[c] = w;
-                s.cell_live[c] = w;
-                s.tcell_mark[c] = 0;
+    const int oc = s.prevcell[i], nc = s.cell_of[i];
+    if (oc != nc) {
+        atomicSub(&s.cell_live[oc], 1);
+        atomicAdd(&s.cell_live[nc], 1);
+    }
+}
+
+// a5 (removal): each queued unflagged row drops its flagged entries.  Rows
+// are short, so a warp takes four rows at a time, eight lanes each (stable
+// in-place compaction: every lane reads its entry before the ballot, and an
+// entry only moves to a lower index).  A queued row that is flagged itself
+// is rebuilt by the rows pass and only loses its queue mark here.  `w0` and
+// `wstride` count warps.
+__device__ __forceinline__ void compact_rows(const DevState &s, int w0, int wstride)
+{
+    const int lane = threadIdx.x & 31, sub = lane >> 3, l8 = lane & 7;
+    const unsigned below = lanemask_lt() & (0xFFu << (sub * 8));
+    const int ntrow = s.cnt->ntrow;
+    for (int k0 = w0 * 4; k0 < ntrow; k0 += wstride * 4) {
+        const int k = k0 + sub;
+        int j = -1, off = 0, len = 0;
+        bool act = k < ntrow;
+        if (act) {
+            j = s.trow[k];
+            if (bit_of(s.bits, j)) {
+                act = false;
+                if (l8 == 0) s.trow_mark[j] = 0;
+            } else {
+                off = s.row_off[j];
+                len = min(s.row_len[j], s.row_cap[j]);
             }
         }
-    }
-}
-
-// a3 (arrivals): leavers take a slot in their new cell; flagged particles
-// that stay refresh their slot's copy of the reference state.
-__device__ __forceinline__ void ph_insert(const DevState &s, int nF, int k0, int stride)
-{
-    const int ccap = s.ccap;
-    for (int k = k0; k < nF; k += stride) {
-        const int i = s.fid[k];
-        const int nc = s.newcell[i];
-        const float4 q = s.ref[i];
-        const float4 cr = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
-        if (nc != s.cell_of[i]) {
-            const int sl = atomicAdd(&s.cell_cnt[nc], 1);
-            atomicAdd(&s.cell_live[nc], 1);
-            if (sl * 4 >= ccap * 3) s.hflags->grow_cells = 1;
-            if (sl < ccap) {
-                s.cell_id[(long long)nc * ccap + sl] = i;
-                s.cell_ref[(long long)nc * ccap + sl] = cr;
-                s.slot_of[i] = sl;
-            } else {
-                atomicOr(&s.cnt->err, DERR_CELL);
+        int mx = len;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+        int w = 0;
+        for (int e0 = 0; e0 < mx; e0 += 8) {
+            const int e = e0 + l8;
+            int c = 0;
+            bool keep = false;
+            if (act && e < len) {
+                c = s.col[off + e];
+                keep = !bit_of(s.bits, c);
             }
-            s.cell_of[i] = nc;
-        } else {
-            s.cell_ref[(long long)nc * ccap + s.slot_of[i]] = cr;
+            const unsigned m = __ballot_sync(FULL, keep);
+            if (keep) s.col[off + w + __popc(m & below)] = c;
+            w += __popc((m >> (sub * 8)) & 0xFFu);
+        }
+        if (act && l8 == 0) {
+            s.row_len[j] = w;
+            s.trow_mark[j] = 0;
         }
     }
 }
@@ -372,20 +353,10 @@ __device__ __forceinline__ void ph_insert(const DevState &s, int nF, int k0, int
 // fill = 0 counts only (row_len = count); fill = 1 also writes up to the
 // row's capacity and raises row_overflow if the row does not fit.
 // Items are fid[w] when `from_list`, else particle w.  Cell slots holding a
-// tombstone (id < 0) are skipped.
-// fx != null selects the three-phase rebuilds' form: the cells still hold
-// the flagged particles at their old positions, marked with negative ids,
-// so they are skipped, and the flagged-flagged pairs come from a direct test
-// against the new references of all flagged particles (fx: xyz + R_NL, ids,
-// count); the stencil is centred on the new cell newcell[i].
-struct FlaggedSet {
-    const float4 *ref;   // new (xref, R_NL) of the flagged particles
-    const int *id;
-    int n;
-};
-
+// tombstone (id < 0) are skipped.  The cells must hold the step's final
+// reference states (after the check kernel's moves, or a full re-bin).
 __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from_list, int fill,
-                                        int w0, int wstride, const FlaggedSet *fx = nullptr)
+                                        int w0, int wstride)
 {
     const int lane = threadIdx.x & 31;
     const int ccap = s.ccap;
@@ -396,7 +367,7 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
         const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
         const float4 q = s.ref[i];
         const float4 qi = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
-        const int ci = (fx ? s.newcell[i] : s.cell_of[i]) - g.cell_base;
+        const int ci = s.cell_of[i] - g.cell_base;
         const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
         int cnt_l = 0, cid = 0;
         if (lane < 27) {
@@ -434,23 +405,6 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
             }
             found += __popc(m);
         }
-        if (fx) {
-            for (int b0 = 0; b0 < fx->n; b0 += 32) {
-                const int k = b0 + lane;
-                bool hit = false;
-                int j = -1;
-                if (k < fx->n) {
-                    j = fx->id[k];
-                    hit = j != i && pair_hit(qi, fx->ref[k]);
-                }
-                const unsigned m = __ballot_sync(FULL, hit);
-                if (fill && hit) {
-                    const int p = found + __popc(m & lt);
-                    if (p < cap) s.col[off + p] = j;
-                }
-                found += __popc(m);
-            }
-        }
         if (lane == 0) {
             s.row_len[i] = found;
             if (fill && found > cap) atomicExch(&s.cnt->row_overflow, 1);
@@ -458,61 +412,9 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
     }
 }
 
-// The one-block rebuild's cell move of flagged particle i (warp): a leaver
-// leaves a tombstone in its old slot and takes a tombstone slot of its new
-// cell (claimed with compare-and-swap) or a fresh slot at the end; a stayer
-// refreshes its slot's copy of the reference state.
-__device__ __forceinline__ void cell_move_warp(const DevState &s, int i)
-{
-    const int lane = threadIdx.x & 31;
-    const int ccap = s.ccap;
-    const int nc = s.newcell[i], oc = s.cell_of[i], so = s.slot_of[i];
-    const float4 q = s.ref[i];
-    const float4 cr = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
-    if (nc == oc) {
-        if (lane == 0) {
-            s.cell_ref[(long long)oc * ccap + so] = cr;
-            s.cell_id[(long long)oc * ccap + so] = i;    // unmark
-        }
-        return;
-    }
-    if (lane == 0) {
-        s.cell_id[(long long)oc * ccap + so] = -1;
-        atomicSub(&s.cell_live[oc], 1);
-        atomicAdd(&s.cell_live[nc], 1);
-    }
-    const long long base = (long long)nc * ccap;
-    const int cn = min(s.cell_cnt[nc], ccap);
-    int slot = -1;
-    for (int e0 = 0; e0 < cn && slot < 0; e0 += 32) {
-        const int sl = e0 + lane;
-        unsigned m = __ballot_sync(FULL, sl < cn && s.cell_id[base + sl] < 0);
-        while (m && slot < 0) {
-            const int src = __ffs(m) - 1;
-            int won = 0;
-            if (lane == src) won = atomicCAS(&s.cell_id[base + sl], -1, i) == -1;
-            won = __shfl_sync(FULL, won, src);
-            if (won) slot = e0 + src;
-            m &= m - 1;
-        }
-    }
-    if (lane == 0) {
-        if (slot < 0) {
-            slot = atomicAdd(&s.cell_cnt[nc], 1);
-            if (slot * 4 >= ccap * 3) s.hflags->grow_cells = 1;
-            if (slot < ccap) s.cell_id[base + slot] = i;
-            else atomicOr(&s.cnt->err, DERR_CELL);
-        }
-        if (slot < ccap) {
-            s.cell_ref[base + slot] = cr;
-            s.slot_of[i] = slot;
-        }
-        s.cell_of[i] = nc;
-    }
-}
-
 // a5 (insertion): flagged i joins the row of each unflagged partner; one
-// warp per flagged particle, one lane per partner.
+// warp per flagged particle, one lane per partner.  Runs after the removal
+// pass, so a pair that survives the update is removed and re-added once.
 __device__ __forceinline__ void ph_append(const DevState &s, int nF, int w0, int wstride)
 {
     const int lane = threadIdx.x & 31;
@@ -538,105 +440,111 @@ __device__ __forceinline__ void set_relayout_cond(const DevState &s,
         cudaGraphSetConditional(h, (s.cnt->row_overflow && !store_failed(s)) ? 1u : 0u);
 }
 
-// The whole partial rebuild in one block, for steps with few flagged
-// particles, in three phases separated by block barriers:
-//   1. new reference + skin of every flagged particle (kept in shared
-//      memory too) and the marks of the unflagged rows that list it;
-//   2. its new row: the 27-cell stencil over the unflagged particles (the
-//      cells still hold the flagged ones at their old places, marked, so
-//      they are skipped) plus a direct test against every other flagged
-//      particle; at the same time the marked rows drop their flagged entries;
-//   3. it joins its unflagged partners' rows and moves to its new cell slot.
-// Runs in the last block of the check kernel (1024 threads).
-constexpr int kCheckThreads = 1024;
-constexpr int kFusedMax = 1024;   // flagged particles the one-block form takes
+constexpr int kCheckMaxThreads = 1024;   // largest check block (LVB_OPT_CHECK_THREADS)
+constexpr int kCheckUnroll = 2;          // 32-particle chunks a warp has in flight
+constexpr int kFusedMax = 1024;          // flagged particles the one-block form takes
 
-__device__ __forceinline__ void fused_rebuild(const DevState &s, const float4 *__restrict__ pos,
-                                              const float4 *__restrict__ vel,
-                                              const float4 *__restrict__ acc, int nF,
-                                              float4 *fref, int *fid_s)
+// The rest of a partial rebuild, for steps with few flagged particles, in
+// the last block of the check kernel: the flagged rows by the stencil and
+// the removal pass together (they touch different rows), then, after a
+// block barrier, the insertion pass.
+__device__ __forceinline__ void last_block_rebuild(const DevState &s, int nF)
 {
-    const int t = threadIdx.x, wid = t >> 5, nw = kCheckThreads / 32;
-    long long c0 = clock64();
-    ph_update(s, pos, vel, acc, nF, wid, nw, /*mark_cells=*/false, fref, fid_s,
-              /*mark_slots=*/true);
+    const int t = threadIdx.x, nt = blockDim.x, wid = t >> 5, nw = nt >> 5;
+    const long long c0 = clock64();
+    ph_rows(s, nF, true, 1, wid, nw);
+    compact_rows(s, wid, nw);
+    for (int k = t; k < nF; k += nt) move_live_count(s, s.fid[k]);
     __syncthreads();
-    long long c1 = clock64();
-    const FlaggedSet fx = {fref, fid_s, nF};
-    const int ntrow = s.cnt->ntrow;
-    for (int w = wid; w < nF + ntrow; w += nw) {
-        if (w < nF) ph_rows(s, w + 1, true, 1, w, nF + 1, &fx);
-        else compact_row_warp(s, s.trow[w - nF]);
-    }
-    __syncthreads();
-    long long c2 = clock64();
+    const long long c1 = clock64();
     ph_append(s, nF, wid, nw);
-    long long c3 = clock64();
-    for (int k = wid; k < nF; k += nw) cell_move_warp(s, fid_s[k]);
     __syncthreads();
     if (t == 0) {
-        const long long c4 = clock64();
+        s.cnt->ntrow = 0;   // the queue was filled by the check, used above
         atomicAdd(&s.cnt->fused_cycles[0], (unsigned long long)(c1 - c0));
-        atomicAdd(&s.cnt->fused_cycles[1], (unsigned long long)(c2 - c1));
-        atomicAdd(&s.cnt->fused_cycles[2], (unsigned long long)(c3 - c2));
-        atomicAdd(&s.cnt->fused_cycles[3], (unsigned long long)(c4 - c3));
+        atomicAdd(&s.cnt->fused_cycles[1], (unsigned long long)(clock64() - c1));
     }
 }
 
 // ---------------------------------------------------------------------------
 // a1: displacement check (Eq. update) and compaction of the flagged ids, for
 // every particle; with `ia.active` each thread first performs the DEM
-// driver's position half-step of its particle.  At most two blocks per SM
-// stride over the particles (one ballot word per warp, one atomic per block
-// iteration that found flags).  The last block to finish publishes the
-// step's flagged count, resets the per-step counters, keeps the statistics,
-// runs the one-block rebuild itself when few particles are flagged, and
-// inside a graph selects the SWITCH body that still has to run.
+// driver's position half-step of its particle.  Each warp takes chunks of 32
+// consecutive particles (kCheckUnroll of them in flight), writes one ballot
+// word per chunk, and a chunk with flags costs the warp one atomic on the
+// flagged count (warp-level compaction: no block barrier in the loop).  With
+// the PARTIAL trigger the warp then updates the particles it flagged (a2,
+// a3: update_move_warp), one after the other.  The grid holds one block per
+// SM at 1024 threads (more, smaller blocks at 512 or 256).  The last block to
+// finish publishes the step's flagged count, resets the per-step counters,
+// keeps the statistics, runs the rest of the rebuild itself when few
+// particles are flagged, and inside a graph selects the SWITCH body that
+// still has to run.  kFused selects the form with the DEM half-step
+// (ia.active), compiled apart so the plain form keeps its registers.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCheckThreads, 1)
-k_check(const float4 *__restrict__ pos_in, const float4 *__restrict__ vel,
-        const float4 *__restrict__ acc, DevState s, IntegrateArgs ia)
+template <bool kFused>
+__global__ void __launch_bounds__(kCheckMaxThreads, 1)
+k_check(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, DevState s,
+        IntegrateArgs ia)
 {
-    __shared__ int wcount[kCheckThreads / 32];
-    __shared__ int base;
-    __shared__ bool last;
-    __shared__ int s_nF, s_small;
-    __shared__ float4 fref[kFusedMax];
-    __shared__ int fid_s[kFusedMax];
+    __shared__ bool last, s_inc;
+    __shared__ int s_nF, s_small, s_step;
     count_kernel(s);
     tr_enter(s, TR_CHECK);
-    const float4 *pos = ia.active ? ia.pos : pos_in;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i0 = blockIdx.x * kCheckThreads; i0 < s.n; i0 += gridDim.x * kCheckThreads) {
-        const int i = i0 + threadIdx.x;
-        bool f = false;
-        if (i < s.n) {
-            const float4 p = ia.active ? integrate_one(ia, geom_of(s, i), i) : __ldg(pos_in + i);
-            const float4 q = s.ref[i];
-            f = violates(p, q);
-            if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z)))
-                atomicOr(&s.cnt->err, DERR_NAN);
-        }
-        const unsigned b = __ballot_sync(FULL, f);
-        if (lane == 0) {
-            if ((i >> 5) < s.nwords) s.bits[i >> 5] = b;
-            wcount[warp] = __popc(b);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < kCheckThreads / 32; ++w) {
-                const int c = wcount[w];
-                wcount[w] = tot;
-                tot += c;
-            }
-            base = tot ? atomicAdd(&s.cnt->nF_accum, tot) : 0;
-        }
-        __syncthreads();
-        if (f) s.fid[base + wcount[warp] + __popc(b & lanemask_lt())] = i;
-        __syncthreads();
+    const float4 *pos = kFused ? ia.pos : pos_in;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    if (threadIdx.x == 0) {
+        // updates in the check: PARTIAL trigger, row store intact (after a
+        // failed re-layout the list stays invalid and nothing is touched)
+        s_inc = s.trigger == LVB_TRIGGER_PARTIAL && !store_failed(s);
+        s_step = (int)s.cnt->steps + 1;
     }
-    __threadfence();   // flags, ids and new positions visible to the last block
+    __syncthreads();
+    const bool inc = s_inc;
+    const int step = s_step;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int stride = nwarps * 32;
+    for (int c0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; c0 < s.n;
+         c0 += stride * kCheckUnroll) {
+        float4 p[kCheckUnroll], q[kCheckUnroll];
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            const int i = c0 + u * stride + lane;
+            if (i < s.n) {
+                p[u] = kFused ? integrate_one(ia, geom_of(s, i), i) : __ldg(pos_in + i);
+                q[u] = s.ref[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            const int cu = c0 + u * stride;   // chunk start, a multiple of 32
+            if (cu >= s.n) break;             // uniform over the warp
+            const int i = cu + lane;
+            bool f = false;
+            if (i < s.n) {
+                f = violates(p[u], q[u]);
+                if (!(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(p[u].z)))
+                    atomicOr(&s.cnt->err, DERR_NAN);
+            }
+            const unsigned b = __ballot_sync(FULL, f);
+            if (lane == 0) s.bits[cu >> 5] = b;
+            if (b) {
+                int k0 = 0;
+                if (lane == 0) k0 = atomicAdd(&s.cnt->nF_accum, __popc(b));
+                k0 = __shfl_sync(FULL, k0, 0);
+                if (f) s.fid[k0 + __popc(b & lt)] = i;
+                if (inc) {
+                    // the new positions of this chunk were written by the
+                    // warp's own lanes (DEM form): make them visible to all
+                    __syncwarp();
+                    for (unsigned m = b; m; m &= m - 1)
+                        update_move_warp(s, cu + __ffs(m) - 1, pos, vel, acc, step);
+                }
+            }
+        }
+    }
+    __threadfence();   // flags, ids, updates and new positions visible to the last block
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&s.cnt->done_blocks, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -658,8 +566,6 @@ k_check(const float4 *__restrict__ pos_in, const float4 *__restrict__ vel,
         const int nF = atomicExch(&c->nF_accum, 0);
         c->done_blocks = 0;
         c->nF = nF;
-        c->ntrow = 0;
-        c->ntcell = 0;
         c->row_overflow = 0;
         int upd;
         if (s.trigger == LVB_TRIGGER_PARTIAL) upd = nF;
@@ -671,26 +577,23 @@ k_check(const float4 *__restrict__ pos_in, const float4 *__restrict__ vel,
         if (upd) c->rebuild_steps += 1;
         c->last_flagged = nF;
         c->last_updated = upd;
-        const bool ok = !(c->err & DERR_STORE);
-        const bool small = s.trigger == LVB_TRIGGER_PARTIAL && ok && nF > 0 &&
-                           nF <= s.small_max && nF <= kFusedMax;
+        const bool small = inc && nF > 0 && nF <= s.small_max && nF <= kFusedMax;
         if (small) c->small_steps += 1;
         s_nF = nF;
         s_small = small;
     }
     __syncthreads();
-    if (s_small) fused_rebuild(s, pos, vel, acc, s_nF, fref, fid_s);
+    if (s_small) last_block_rebuild(s, s_nF);
     if (threadIdx.x == 0) {
         const int nF = s_nF;
-        const bool ok = !(c->err & DERR_STORE);
         if (s.use_cond) {
             unsigned path;
             if (s.trigger == LVB_TRIGGER_PARTIAL) {
-                if (!ok || nF == 0) path = PATH_NONE;
+                if (!inc || nF == 0) path = PATH_NONE;
                 else if (s_small) path = c->row_overflow ? PATH_RELAYOUT : PATH_NONE;
                 else path = nF <= s.medium_max ? PATH_MEDIUM : PATH_BIG;
             } else {
-                path = (ok && c->last_updated) ? 1u : 0u;
+                path = (!store_failed(s) && c->last_updated) ? 1u : 0u;
             }
             cudaGraphSetConditional(s.h_path, path);
         }
@@ -702,86 +605,34 @@ k_check(const float4 *__restrict__ pos_in, const float4 *__restrict__ vel,
     }
 }
 
-// Three-kernel partial path, for steps with more flagged particles than one
-// block takes: the same three phases as the one-block form, each a grid-wide kernel,
-// with the flagged particles' new references in global scratch.
-__global__ void __launch_bounds__(kThreads)
-k_m_update(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
-           const float4 *__restrict__ acc, DevState s)
-{
-    const int nF = medium_nF(s);
-    if (!nF) return;
-    count_kernel(s);
-    tr_enter(s, TR_M_UPDATE);
-    ph_update(s, pos, vel, acc, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5,
-              (gridDim.x * kThreads) >> 5, /*mark_cells=*/false, s.fref_g, s.fid_g,
-              /*mark_slots=*/true);
-    tr_exit(s, TR_M_UPDATE);
-}
-
+// The rest of a partial rebuild when more particles are flagged than the
+// check's last block takes: the same two passes as grid-wide kernels (the
+// SWITCH bodies PATH_MEDIUM and PATH_BIG differ only in grid size).
 __global__ void __launch_bounds__(kThreads, 4)
-k_m_rows(DevState s)
+k_inc_rows(DevState s)
 {
-    const int nF = medium_nF(s);
+    const int nF = grid_nF(s);
     if (!nF) return;
     count_kernel(s);
-    tr_enter(s, TR_M_ROWS);
-    const FlaggedSet fx = {s.fref_g, s.fid_g, nF};
-    const int ntrow = s.cnt->ntrow;
-    const int nw = (gridDim.x * kThreads) >> 5;
-    for (int w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nF + ntrow; w += nw) {
-        if (w < nF) ph_rows(s, w + 1, true, 1, w, nF + 1, &fx);
-        else compact_row_warp(s, s.trow[w - nF]);
-    }
-    tr_exit(s, TR_M_ROWS);
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_m_finish(DevState s)
-{
-    const int nF = medium_nF(s);
-    if (!nF) return;
-    count_kernel(s);
-    tr_enter(s, TR_M_FINISH);
+    tr_enter(s, TR_INC_ROWS);
     const int w0 = (blockIdx.x * kThreads + threadIdx.x) >> 5, nw = (gridDim.x * kThreads) >> 5;
-    ph_append(s, nF, w0, nw);
-    for (int k = w0; k < nF; k += nw) cell_move_warp(s, s.fid_g[k]);
-    tr_exit(s, TR_M_FINISH);
+    ph_rows(s, nF, true, 1, w0, nw);
+    compact_rows(s, w0, nw);
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < nF; k += gridDim.x * kThreads)
+        move_live_count(s, s.fid[k]);
+    tr_exit(s, TR_INC_ROWS);
 }
 
-// Multi-kernel partial path, for steps with many flagged particles.
 __global__ void __launch_bounds__(kThreads)
-k_p_update(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
-           const float4 *__restrict__ acc, DevState s)
+k_inc_append(DevState s)
 {
-    const int nF = big_nF(s);
+    const int nF = grid_nF(s);
     if (!nF) return;
     count_kernel(s);
-    tr_enter(s, TR_P_UPDATE);
-    ph_update(s, pos, vel, acc, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5,
-              (gridDim.x * kThreads) >> 5);
-    tr_exit(s, TR_P_UPDATE);
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_p_compact(DevState s)
-{
-    if (!big_nF(s)) return;
-    count_kernel(s);
-    tr_enter(s, TR_P_COMPACT);
-    ph_compact(s, (blockIdx.x * kThreads + threadIdx.x) >> 5, (gridDim.x * kThreads) >> 5);
-    tr_exit(s, TR_P_COMPACT);
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_p_insert(DevState s)
-{
-    const int nF = big_nF(s);
-    if (!nF) return;
-    count_kernel(s);
-    tr_enter(s, TR_P_INSERT);
-    ph_insert(s, nF, blockIdx.x * kThreads + threadIdx.x, gridDim.x * kThreads);
-    tr_exit(s, TR_P_INSERT);
+    tr_enter(s, TR_INC_APPEND);
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.cnt->ntrow = 0;   // used by k_inc_rows
+    ph_append(s, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5, (gridDim.x * kThreads) >> 5);
+    tr_exit(s, TR_INC_APPEND);
 }
 
 __global__ void __launch_bounds__(kThreads, 4)
@@ -792,20 +643,9 @@ k_rows(DevState s, int gate, int fill)
     count_kernel(s);
     const int slot = gate == GATE_OVERFLOW ? TR_RELAYOUT : TR_ROWS;
     tr_enter(s, slot);
-    ph_rows(s, nitems, gate == GATE_FLAGGED_BIG, fill, (blockIdx.x * kThreads + threadIdx.x) >> 5,
+    ph_rows(s, nitems, false, fill, (blockIdx.x * kThreads + threadIdx.x) >> 5,
             (gridDim.x * kThreads) >> 5);
     tr_exit(s, slot);
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_p_append(DevState s)
-{
-    const int nF = big_nF(s);
-    if (!nF) return;
-    count_kernel(s);
-    tr_enter(s, TR_P_APPEND);
-    ph_append(s, nF, (blockIdx.x * kThreads + threadIdx.x) >> 5, (gridDim.x * kThreads) >> 5);
-    tr_exit(s, TR_P_APPEND);
 }
 
 // end of a rebuild body inside a graph: arm its re-layout body if needed
@@ -1204,6 +1044,7 @@ struct lvb_ctx {
     unsigned long long *sum64 = nullptr;
     // cached graph of one step, for the last (pos, vel) pointers seen
     bool use_graph = true;
+    int check_threads = kCheckMaxThreads;   // block size of the check kernel
     cudaGraphExec_t gexec = nullptr;
     const void *g_pos = nullptr, *g_vel = nullptr, *g_acc = nullptr;
     int version = 0;                // bumped whenever the step's graph changes
@@ -1232,12 +1073,11 @@ cudaError_t dalloc(T **p, long long count)
 void free_all(lvb_ctx *c)
 {
     DevState &s = c->s;
-    void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.newcell, s.bits, s.fid, s.row_off,
+    void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.prevcell, s.bits, s.fid, s.row_off,
                     s.row_len, s.row_cap, s.col, s.trow, s.trow_mark, s.cell_cnt, s.cell_id,
-                    s.cell_ref, s.tcell, s.tcell_mark, s.cnt, s.blk, c->ex_cnt, c->ex_off,
-                    c->ex_i, c->ex_j, c->ex_d, c->scratch, c->sum64, c->sg_d, c->scene_of_d,
-                    s.born, s.cell_live, s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf,
-                    s.fref_g, s.fid_g};
+                    s.cell_ref, s.cnt, s.blk, c->ex_cnt, c->ex_off, c->ex_i, c->ex_j, c->ex_d,
+                    c->scratch, c->sum64, c->sg_d, c->scene_of_d, s.born, s.cell_live,
+                    s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cnt_h) cudaFreeHost(c->cnt_h);
@@ -1276,7 +1116,7 @@ void launch_layout_scan(lvb_ctx *c, int gate)
 int rows_grid(lvb_ctx *c) { return grid_for(c->n, kThreads / 32, 16 * kNumSMs); }
 int items_grid(lvb_ctx *c) { return grid_for(c->n, kThreads, 4 * kNumSMs); }
 
-constexpr int kPerFlaggedGrid = 8 * kNumSMs;   // grid of the per-flagged kernels
+constexpr int kBigGrid = 4 * kNumSMs;   // grid of the partial passes above medium_max flagged
 constexpr int kDefaultSmallMax = 32;
 constexpr int kDefaultMediumMax = 2048;
 
@@ -1302,7 +1142,13 @@ void launch_relayout(lvb_ctx *c)
     k_relayout_done<<<1, 1, 0, c->stream>>>(c->s);
 }
 
-int check_grid(lvb_ctx *c) { return grid_for(c->n, kCheckThreads, kNumSMs); }
+// 1024 check threads per SM (the kernel's register budget), in blocks of
+// check_threads; each thread takes kCheckUnroll particles per pass
+int check_grid(lvb_ctx *c)
+{
+    return grid_for((c->n + kCheckUnroll - 1) / kCheckUnroll, c->check_threads,
+                    kNumSMs * (kCheckMaxThreads / c->check_threads));
+}
 int medium_grid(lvb_ctx *c)
 {
     return grid_for(std::min<long long>(c->s.medium_max, c->n), kThreads / 32, kNumSMs);
@@ -1317,18 +1163,15 @@ void launch_step_direct(lvb_ctx *c, const float4 *pos, const float4 *v4, const f
     const cudaStream_t st = c->stream;
     DevState s = c->s;
     s.use_cond = 0;
-    k_check<<<check_grid(c), kCheckThreads, 0, st>>>(pos, v4, a4, s, ia);
+    if (ia.active)
+        k_check<true><<<check_grid(c), c->check_threads, 0, st>>>(pos, v4, a4, s, ia);
+    else
+        k_check<false><<<check_grid(c), c->check_threads, 0, st>>>(pos, v4, a4, s, ia);
     const float4 *p = ia.active ? ia.pos : pos;
     if (c->trigger == LVB_TRIGGER_PARTIAL) {
-        const int gp = kPerFlaggedGrid, gm = medium_grid(c);
-        k_m_update<<<gm, kThreads, 0, st>>>(p, v4, a4, s);
-        k_m_rows<<<gm, kThreads, 0, st>>>(s);
-        k_m_finish<<<gm, kThreads, 0, st>>>(s);
-        k_p_update<<<gp, kThreads, 0, st>>>(p, v4, a4, s);
-        k_p_compact<<<gp, kThreads, 0, st>>>(s);
-        k_p_insert<<<gp, kThreads, 0, st>>>(s);
-        k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_FLAGGED_BIG, 1);
-        k_p_append<<<gp, kThreads, 0, st>>>(s);
+        const int gm = medium_grid(c);
+        k_inc_rows<<<gm, kThreads, 0, st>>>(s);
+        k_inc_append<<<gm, kThreads, 0, st>>>(s);
     } else {
         const int gate = c->trigger == LVB_TRIGGER_GLOBAL ? GATE_ANY_FLAG : GATE_ALWAYS;
         const int gi = items_grid(c);
@@ -1395,10 +1238,11 @@ cudaError_t add_relayout_if(lvb_ctx *c, cudaGraph_t body, cudaGraphNode_t *dep, 
     return cudaSuccess;
 }
 
-// The step as graph nodes: k_check (which also runs the one-block rebuild
-// when few particles are flagged), then for the PARTIAL trigger a SWITCH
-// whose bodies are the three-kernel rebuild, the five-kernel rebuild and
-// the re-layout alone (no body when the check did all the work); the two
+// The step as graph nodes: k_check (which also updates the flagged
+// particles and, when few are flagged, finishes the rebuild in its last
+// block), then for the PARTIAL trigger a SWITCH whose bodies are the two
+// grid-wide passes on a medium grid, the same on a big grid, and the
+// re-layout alone (no body when the check did all the work); the two
 // rebuild bodies end in an IF around the re-layout.  GLOBAL / ALWAYS use an
 // IF around the full rebuild.  Conditions are set on the device.
 cudaError_t build_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, const float4 *pos,
@@ -1412,7 +1256,8 @@ cudaError_t build_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, co
     s.h_path = hp;
     s.use_cond = 1;
     cudaGraphNode_t n = dep ? *dep : nullptr;
-    GK(add_kernel(&n, g, &n, k_check, dim3(check_grid(c)), dim3(kCheckThreads), pos, v4, a4, s,
+    GK(add_kernel(&n, g, &n, ia.active ? k_check<true> : k_check<false>, dim3(check_grid(c)),
+                  dim3(c->check_threads), pos, v4, a4, s,
                   ia));
     const float4 *p = ia.active ? ia.pos : pos;
     cudaGraphNode_t cn = nullptr;
@@ -1421,22 +1266,15 @@ cudaError_t build_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, co
         cudaGraph_t b3[3] = {nullptr, nullptr, nullptr};
         add_cond(&cn, g, n, hp, cudaGraphCondTypeSwitch, 3, b3, &err);
         GK(err);
-        const int gm = medium_grid(c), gp = kPerFlaggedGrid;
+        const int grids[2] = {medium_grid(c), kBigGrid};
+        for (int q = PATH_MEDIUM; q <= PATH_BIG; ++q) {
+            cudaGraphNode_t b = nullptr;
+            const dim3 gq(grids[q]);
+            GK(add_kernel(&b, b3[q], &b, k_inc_rows, gq, dim3(kThreads), s));
+            GK(add_kernel(&b, b3[q], &b, k_inc_append, gq, dim3(kThreads), s));
+            GK(add_relayout_if(c, b3[q], &b, s));
+        }
         cudaGraphNode_t b = nullptr;
-        GK(add_kernel(&b, b3[PATH_MEDIUM], &b, k_m_update, dim3(gm), dim3(kThreads), p, v4, a4, s));
-        GK(add_kernel(&b, b3[PATH_MEDIUM], &b, k_m_rows, dim3(gm), dim3(kThreads), s));
-        GK(add_kernel(&b, b3[PATH_MEDIUM], &b, k_m_finish, dim3(gm), dim3(kThreads), s));
-        GK(add_relayout_if(c, b3[PATH_MEDIUM], &b, s));
-        b = nullptr;
-        cudaGraph_t big = b3[PATH_BIG];
-        GK(add_kernel(&b, big, &b, k_p_update, dim3(gp), dim3(kThreads), p, v4, a4, s));
-        GK(add_kernel(&b, big, &b, k_p_compact, dim3(gp), dim3(kThreads), s));
-        GK(add_kernel(&b, big, &b, k_p_insert, dim3(gp), dim3(kThreads), s));
-        GK(add_kernel(&b, big, &b, k_rows, dim3(rows_grid(c)), dim3(kThreads), s,
-                      (int)GATE_FLAGGED_BIG, 1));
-        GK(add_kernel(&b, big, &b, k_p_append, dim3(gp), dim3(kThreads), s));
-        GK(add_relayout_if(c, big, &b, s));
-        b = nullptr;
         GK(add_relayout_nodes(c, b3[PATH_RELAYOUT], &b, s));
     } else {
         cudaGraph_t body[1] = {nullptr};
@@ -1745,7 +1583,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (e == cudaSuccess) e = dalloc(&s.rad, n);
     if (e == cudaSuccess) e = dalloc(&s.cell_of, n);
     if (e == cudaSuccess) e = dalloc(&s.slot_of, n);
-    if (e == cudaSuccess) e = dalloc(&s.newcell, n);
+    if (e == cudaSuccess) e = dalloc(&s.prevcell, n);
     if (e == cudaSuccess) e = dalloc(&s.bits, c->nwords);
     if (e == cudaSuccess) e = dalloc(&s.fid, n);
     if (e == cudaSuccess) e = dalloc(&s.row_off, n);
@@ -1756,17 +1594,12 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (e == cudaSuccess) e = dalloc(&s.cell_cnt, ncells);
     if (e == cudaSuccess) e = dalloc(&s.cell_live, ncells);
     if (e == cudaSuccess) e = dalloc(&s.born, n);
-    if (e == cudaSuccess) e = dalloc(&s.fref_g, n);
-    if (e == cudaSuccess) e = dalloc(&s.fid_g, n);
-    if (e == cudaSuccess) e = dalloc(&s.tcell, ncells);
-    if (e == cudaSuccess) e = dalloc(&s.tcell_mark, ncells);
     if (e == cudaSuccess) e = dalloc(&s.cnt, 1);
     if (e == cudaSuccess) e = dalloc(&s.blk, c->nblk + 1);
     if (e != cudaSuccess) return fail(from_cuda(e));
     cudaMemsetAsync(s.trow_mark, 0, sizeof(int) * n, st);
     cudaMemsetAsync(s.born, 0, sizeof(int) * n, st);
     cudaMemsetAsync(s.cell_live, 0, sizeof(int) * ncells, st);
-    cudaMemsetAsync(s.tcell_mark, 0, sizeof(int) * ncells, st);
     cudaMemsetAsync(s.cnt, 0, sizeof(DevCounters), st);
     cudaMemsetAsync(&s.cnt->tr_start, 0xff, sizeof(s.cnt->tr_start), st);
     cudaMemsetAsync(s.bits, 0, sizeof(uint32_t) * c->nwords, st);
@@ -1954,6 +1787,9 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
         if (value < 0) return LVB_EINVAL;
         c->s.medium_max = (int)std::max<int64_t>(std::min<int64_t>(value, c->n),
                                                  c->s.small_max);
+    } else if (option == LVB_OPT_CHECK_THREADS) {
+        if (value != 256 && value != 512 && value != 1024) return LVB_EINVAL;
+        c->check_threads = (int)value;
     } else {
         return LVB_EINVAL;
     }

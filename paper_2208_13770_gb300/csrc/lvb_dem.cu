@@ -386,7 +386,7 @@ int dem_advance(dem_ctx *c, int64_t steps)
 {
     if (!c || steps < 0) return LVB_EINVAL;
     cudaGetLastError();   // clear a stale error of an unrelated earlier call
-    const int64_t chunk = 50;
+    const int64_t chunk = DEM_GRAPH_STEPS;
     if (c->graph && c->graph_version != graph_version(c->bp)) {
         cudaGraphExecDestroy(c->graph);   // the broad phase's nodes changed
         c->graph = nullptr;

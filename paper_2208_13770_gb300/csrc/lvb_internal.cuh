@@ -33,14 +33,14 @@ enum : unsigned { DERR_NAN = 1u, DERR_CELL = 2u, DERR_STORE = 4u };
 
 // kernel slots of the per-kernel trace
 enum TraceSlot {
-    TR_CHECK = 0, TR_FUSED, TR_M_UPDATE, TR_M_ROWS, TR_M_FINISH, TR_P_UPDATE, TR_P_COMPACT,
-    TR_P_INSERT, TR_ROWS, TR_P_APPEND, TR_RELAYOUT, TR_INTEGRATE, TR_FORCES, kTraceSlots = 16
+    TR_CHECK = 0, TR_FUSED, TR_INC_ROWS, TR_INC_APPEND, TR_ROWS, TR_RELAYOUT, TR_INTEGRATE,
+    TR_FORCES, kTraceSlots = 16
 };
 
 struct DevCounters {
     int nF;            // flagged at this step (final, set by the check's last block)
     int ntrow;         // rows touched by removals this step
-    int ntcell;        // cells touched by removals this step
+    int pad1;
     int row_overflow;  // some row exceeded its capacity this step
     unsigned err;      // sticky DERR_* bits
     int last_flagged;

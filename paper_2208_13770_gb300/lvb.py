@@ -183,9 +183,10 @@ def lvb_step(ctx, pos_r, vel=None, acc=None):
     return _lib.lvb_step(ctx, pos_r, vel, acc)
 
 
-LVB_OPT_GRAPH, LVB_OPT_SMALL_MAX, LVB_OPT_MEDIUM_MAX, LVB_OPT_TRACE = 0, 1, 2, 3
-TRACE_SLOTS = ["check", "one_block", "m_update", "m_rows", "m_finish", "p_update", "p_compact",
-               "p_insert", "rows", "p_append", "relayout", "integrate", "forces"]
+LVB_OPT_GRAPH, LVB_OPT_SMALL_MAX, LVB_OPT_MEDIUM_MAX, LVB_OPT_TRACE, LVB_OPT_CHECK_THREADS = \
+    0, 1, 2, 3, 4
+TRACE_SLOTS = ["check", "one_block", "inc_rows", "inc_append", "rows", "relayout", "integrate",
+               "forces"]
 
 
 def lvb_trace(ctx, sum_ns, count):
@@ -486,9 +487,10 @@ class DEM:
     """A DEM driver context over a scene (``scenes.Scene``-like object)."""
 
     def __init__(self, scene, trigger=LVB_TRIGGER_PARTIAL, skin_kind=None, skin_value=None,
-                 cell_factor=None, stream=None):
+                 cell_factor=None, stream=None, mlp=None):
         """scene: one scene, or a list of scenes (same physics, own boxes)
-        advanced together as one batch."""
+        advanced together as one batch.  mlp: device weights of the skin
+        network (mlp_weights_device) for LVB_SKIN_LEARNED."""
         import torch
         batch = isinstance(scene, (list, tuple))
         scenes_ = list(scene) if batch else [scene]
@@ -510,7 +512,8 @@ class DEM:
                 boxes[q].lo[k], boxes[q].hi[k] = sc.lo[k], sc.hi[k]
         kind = scene.skin_kind if skin_kind is None else skin_kind
         value = scene.skin_value if skin_value is None else skin_value
-        skin = lvb_skin_policy(int(kind), float(value), float(scene.dt), None)
+        self._mlp = mlp            # keeps the weights alive with the context
+        skin = lvb_skin_policy(int(kind), float(value), float(scene.dt), _dptr(mlp))
         cf = scene.cell_factor if cell_factor is None else cell_factor
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

@@ -108,16 +108,16 @@ def test_ballistic_paper_rule_parity(orc):
     _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 600), 0, 2, 200.0, every=2)
 
 
-@pytest.mark.parametrize("path", ["auto", "one_block", "three_kernel", "five_kernel", "direct"])
+@pytest.mark.parametrize("path", ["auto", "one_block", "medium_grid", "big_grid", "direct"])
 def test_hot_gas_many_rebuilds_parity(orc, path):
     # fast particles: many flags, cell moves and row changes per step, through
     # each way a step can run: graph with the automatic choice, graph forced
-    # to the one-block rebuild, to the three-kernel rebuild, to the five-kernel
-    # rebuild, and direct launches without a graph
+    # to the one-block rest of the rebuild, to the grid-wide passes on the
+    # medium grid, on the big grid, and direct launches without a graph
     lvb = _cuda()
     opts = {"auto": (), "one_block": ((lvb.LVB_OPT_SMALL_MAX, 1 << 30),),
-            "three_kernel": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 1 << 30)),
-            "five_kernel": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 0)),
+            "medium_grid": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 1 << 30)),
+            "big_grid": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 0)),
             "direct": ((lvb.LVB_OPT_GRAPH, 0),)}[path]
     s = scenes.ballistic(n=3000, seed=5, phi=0.3, vsigma=3.0)
     st, _ = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 150), 0, 1, 0.1,
@@ -125,7 +125,7 @@ def test_hot_gas_many_rebuilds_parity(orc, path):
     assert st["updated_total"] > s.n
     if path == "one_block":      # every step with at most 1024 flagged
         assert st["small_path_steps"] > 0 and st["small_max"] == 1024
-    if path in ("three_kernel", "five_kernel"):
+    if path in ("medium_grid", "big_grid"):
         assert st["small_path_steps"] == 0
     if path == "direct":
         assert st["graphs"] == 0

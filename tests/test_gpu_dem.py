@@ -154,14 +154,14 @@ def test_advance_graph_matches_phase_launches(orc):
     s = scenes.packed(n=3000, seed=4)
     a = lvb.DEM(s)
     b = lvb.DEM(s)
-    a.advance(120)          # two graph replays of 50 + 20 direct steps
-    for _ in range(120):
+    a.advance(250)          # two graph replays of 100 steps + 50 direct steps
+    for _ in range(250):
         b.step()
     xa, va, _, _ = a.state()
     xb, vb, _, _ = b.state()
     assert np.allclose(xa, xb, rtol=0, atol=1e-9)
     assert np.allclose(va, vb, rtol=1e-4, atol=1e-6)
-    assert a.lvb.stats()["steps"] == b.lvb.stats()["steps"] == 120
+    assert a.lvb.stats()["steps"] == b.lvb.stats()["steps"] == 250
     a.close()
     b.close()
 
