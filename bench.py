@@ -123,19 +123,22 @@ def _scene(rank):
 
 
 def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, flush,
-             record=None, graph=True, choice=None):
+             record=None, choice=None, profile_from=0):
     """Runs warmup + steps DEM steps with per-phase CUDA events.  Returns
     per-phase total ms, stats and the (optional) recorded window.  flush:
     a buffer larger than L2 written before every step, or None when the
     inputs themselves are larger than L2.  choice: an autotuned launch
-    choice (cell factor, check block shape, last-block threshold)."""
+    choice (cell factor, step-kernel block size, flag compaction).
+    profile_from: advance this many steps first (100-step graphs), and
+    bracket the timed steps with cudaProfilerStart/Stop, so that a profiler
+    started with profiling off sees only them."""
     dem = lvb.DEM(scene, trigger=trigger, skin_kind=skin_kind, skin_value=skin_value,
                   cell_factor=None if choice is None else choice.cell_factor)
     if choice is not None:
         choice.apply(dem, lvb)
-    if not graph:
-        dem.lvb.set_option(lvb.LVB_OPT_GRAPH, 0)
     stream = torch.cuda.current_stream()
+    if profile_from:
+        dem.advance(profile_from)
     for _ in range(warmup):
         if flush is not None:
             flush.zero_()
@@ -153,6 +156,9 @@ def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, f
         rec = {"pos": torch.empty((m, scene.n, 4), dtype=torch.float32, pin_memory=True),
                "start": start, "m": m}
         dpos = dem.device_pos_tensor(torch)
+    if profile_from:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
     t_all0.record(stream)
     done = 0
     while done < steps:
@@ -182,6 +188,8 @@ def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, f
         done += nb
     t_all1.record(stream)
     torch.cuda.synchronize()
+    if profile_from:
+        torch.cuda.profiler.stop()
     wall_ms = t_all0.elapsed_time(t_all1)
     rc = dem.sync()
     if rc != 0:
@@ -248,8 +256,8 @@ def _batched(lvb, torch, hbm_peak, warmup):
         "flagged_per_step": F,
         "rebuild_fraction": (s1["updated_total"] - s0["updated_total"]) / (n * BATCH_STEPS),
         "autotune": {"choice": {"cell_factor": best.cell_factor,
-                                "check_threads": best.check_threads,
-                                "small_max": best.small_max},
+                                "block_threads": best.block_threads,
+                                "compaction": best.compaction},
                      "trials": trials},
         "l2": "inputs (%.0f MB of particle state) exceed L2; no flush" % (n * 96 / 1e6),
     }
@@ -400,7 +408,8 @@ def run_native(args):
     with Clocks(local) as clk:
         loc = _run_dem(lvb, torch, scene, lvb.LVB_TRIGGER_PARTIAL, scene.skin_kind,
                        scene.skin_value, args.steps, args.warmup, flush,
-                       record=(rec_start, m_e2e) if m_e2e else None, graph=not args.no_graph)
+                       record=(rec_start, m_e2e) if m_e2e else None,
+                       profile_from=args.profile_from)
     torch.cuda.synchronize()
     bp_ms = float(loc["phase_ms"][1])
     if world > 1:
@@ -491,7 +500,9 @@ def run_native(args):
         "list": {"entries": entries, "mean_row": row_len, "relayouts": s1["relayouts"]},
         "e2e": e2e,
         "gpu_launches": int(s1["kernels_executed"] - s0["kernels_executed"]),
-        "small_path_steps": int(s1["small_path_steps"] - s0["small_path_steps"]),
+        "grid_barriers": int(s1["barriers"] - s0["barriers"]),
+        "step_kernel": {"blocks": s1["step_blocks"], "threads": s1["block_threads"],
+                        "launch": "cooperative, one per broad-phase step"},
         "clocks": clk.summary(),
         "timed_region_ms_incl_flush": loc["wall_ms"],
     }
@@ -516,8 +527,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-local", action="store_true",
                     help="time the local-buffer run only (for profiling)")
-    ap.add_argument("--no-graph", action="store_true",
-                    help="direct kernel launches instead of graph replays (profilers)")
+    ap.add_argument("--profile-from", type=int, default=0,
+                    help="with --only-local: advance this many steps first and bracket the "
+                         "timed steps with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (512-scene) run")
     args = ap.parse_args()

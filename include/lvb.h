@@ -59,6 +59,9 @@ extern "C" {
 #define LVB_ESTATE     (-7)  /* call not valid in the context's state */
 #define LVB_ELIMIT     (-8)  /* input larger than a fixed-size entry point's
                                 stated maximum (lvb_noalloc.h) */
+#define LVB_ETIMEOUT   (-9)  /* a grid-wide barrier of the step kernel waited
+                                past its limit (about a second); the step was
+                                abandoned and the context is unusable */
 
 /* Skin policies (Sec. "The local skin parameter" and Sec. Results). */
 #define LVB_SKIN_GLOBAL           0  /* skin = value (uniform; the paper's
@@ -108,17 +111,12 @@ typedef struct {
     int64_t row_store_capacity; /* entries the row store can hold */
     int64_t kernels_executed;  /* kernels of this context run on the device
                                   (including the DEM driver's, if any) */
-    int64_t small_path_steps;  /* steps whose rebuild ran in one block */
-    int64_t small_max;       /* flagged counts up to this use the one-block
-                                rebuild (LVB_OPT_SMALL_MAX) */
-    int64_t medium_max;      /* ... up to this the grid-wide passes on the
-                                medium grid, above it on the big grid */
-    int64_t graphs;          /* 1 if steps replay a CUDA graph */
+    int64_t barriers;        /* grid-wide barriers passed by step kernels */
+    int64_t step_blocks;     /* blocks of the step kernel (all resident) */
+    int64_t block_threads;   /* threads per block of the step kernel */
+    int64_t compaction;      /* LVB_COMPACT_* in use */
     int64_t n_scenes;        /* independent scenes in the context */
-    int64_t fused_phase_cycles[4]; /* SM cycles spent by the one-block rebuild
-                                in its phases (rows and removals; appends;
-                                unused; unused), summed over steps (thread
-                                0's view) */
+    int64_t reserved[4];
     float cell_edge;         /* L [m] (scene 0) */
     float rnl_max;           /* cap H on R_NL = r + skin [m] (scene 0) */
     int32_t grid[3];         /* cells per axis (scene 0) */
@@ -200,7 +198,7 @@ int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *r
 
 /*
  * lvb_step -- one step of the automatic Verlet update at the positions
- * pos_r (same n and radii as at init):
+ * pos_r (same n and radii as at init), as one cooperative kernel launch:
  *   1. flag every particle whose displacement since its reference position
  *      exceeds its skin (Eq. update);
  *   2. update reference position and skin of the flagged particles
@@ -215,32 +213,28 @@ int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *r
  */
 int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *acc);
 
-/* Options of lvb_set_option. */
-#define LVB_OPT_GRAPH     0  /* 1 (default): each lvb_step replays a CUDA graph
-                                whose conditional nodes skip the rebuild work
-                                a step does not need; 0: direct launches.  A
-                                call made while the stream is being captured
-                                always launches directly. */
-#define LVB_OPT_SMALL_MAX 1  /* steps with at most this many flagged particles
-                                (default 32, at most 1024) finish their
-                                rebuild in the check kernel's last block */
-#define LVB_OPT_MEDIUM_MAX 2 /* ... up to this many (default 2048) in two
-                                grid-wide kernels on a grid sized for this
-                                count; more on a grid of 4 blocks per SM */
-#define LVB_OPT_TRACE     3  /* 1: kernels record their device time (first
-                                block entry to last block exit), read with
-                                lvb_trace; 0 (default): off */
-#define LVB_OPT_CHECK_THREADS 4 /* block size of the check kernel: 1024
+/* Options of lvb_set_option.  None of them changes a result. */
+#define LVB_OPT_TRACE     3  /* 1: the step kernel records the device time of
+                                its phases, the DEM driver's separate kernels
+                                theirs, read with lvb_trace; 0 (default): off */
+#define LVB_OPT_BLOCK_THREADS 4 /* block size of the step kernel: 1024
                                 (default, one block per SM), 512 or 256
-                                (two or four per SM); a launch shape only,
-                                the results do not change */
+                                (two or four per SM) */
+#define LVB_OPT_COMPACT   5  /* compaction of the flagged ids in the check:
+                                LVB_COMPACT_WARP (default) or LVB_COMPACT_BLOCK */
 
-/* Kernel slots of lvb_trace. */
+/* Values of LVB_OPT_COMPACT. */
+#define LVB_COMPACT_WARP  0  /* one atomic per 32-particle chunk with flags,
+                                no block barrier */
+#define LVB_COMPACT_BLOCK 1  /* one atomic per block tile with flags, two
+                                block barriers in such a tile */
+
+/* Slots of lvb_trace. */
 #define LVB_TRACE_SLOTS 16
-/* 0 check (with the flagged particles' updates and, for few flagged, the
- * one-block rest of the rebuild), 1 unused, 2-3 grid-wide rebuild passes
- * (rows and removals, appends), 4 full-build rows, 5 re-layout rows,
- * 6 DEM integrate, 7 DEM forces. */
+/* Phases of the step kernel: 0 check (with the flagged particles'
+ * updates), 1 rebuild passes, 2 re-layout, 3 tail (the DEM driver's
+ * forces); separate kernels: 4 DEM integrate, 5 DEM forces, 6 full-build
+ * rows (init, store growth). */
 
 /* lvb_trace -- per-kernel device time summed over the steps traced so far
  * (ns) and the number of steps each kernel ran in; LVB_TRACE_SLOTS entries
@@ -252,7 +246,7 @@ int lvb_trace(lvb_ctx *ctx, uint64_t *sum_ns, uint64_t *count);
 int lvb_set_option(lvb_ctx *ctx, int32_t option, int64_t value);
 
 /* lvb_sync -- wait for the context's stream and return the sticky device
- * error (LVB_OK, LVB_ENAN or LVB_EOVERFLOW). */
+ * error (LVB_OK, LVB_ENAN, LVB_EOVERFLOW or LVB_ETIMEOUT). */
 int lvb_sync(lvb_ctx *ctx);
 
 /*

@@ -1,14 +1,14 @@
 """Autotuner for the batched DEM step: cell-size factor, block shape of the
-check kernel, and the flagged count up to which the check's last block
-finishes a rebuild itself (beyond it, the grid-wide passes run).
+step kernel, and the compaction scheme of the flagged ids (one atomic per
+warp chunk, or one per block tile).
 
 Each candidate is a fresh context on the same batch from the same initial
 state; it runs ``warm`` steps, then ``steps`` steps timed with CUDA events
 on the context's stream (graph replays of DEM_GRAPH_STEPS steps).  The
 search is coordinate-wise: the cell factor first (it changes the grid, so a
-new context), then the block shape, then the last-block threshold, each on
-the best of the previous ones.  The block shape and the threshold are
-launch choices only: the lists do not change.  The cell factor also sets
+new context), then the block shape, then the compaction scheme, each on
+the best of the previous ones.  The block shape and the compaction scheme
+are launch choices only: the lists do not change.  The cell factor also sets
 the cap on every skin (R_NL <= half a cell edge, Eq.
 skin_formulus_mincell), so at 1.0 the largest particles get smaller skins
 and update more often; the lists change with the skins, but no contact is
@@ -19,19 +19,19 @@ from __future__ import annotations
 import dataclasses
 
 CELL_FACTORS = (1.0, 1.25, 1.5)
-CHECK_THREADS = (1024, 512, 256)
-SMALL_MAX = (32, 128, 512)
+BLOCK_THREADS = (1024, 512, 256)
+COMPACTION = (0, 1)   # LVB_COMPACT_WARP, LVB_COMPACT_BLOCK
 
 
 @dataclasses.dataclass
 class Choice:
     cell_factor: float = 1.25
-    check_threads: int = 1024
-    small_max: int = 32
+    block_threads: int = 1024
+    compaction: int = 0
 
     def apply(self, dem, lvb):
-        dem.lvb.set_option(lvb.LVB_OPT_CHECK_THREADS, self.check_threads)
-        dem.lvb.set_option(lvb.LVB_OPT_SMALL_MAX, self.small_max)
+        dem.lvb.set_option(lvb.LVB_OPT_BLOCK_THREADS, self.block_threads)
+        dem.lvb.set_option(lvb.LVB_OPT_COMPACT, self.compaction)
 
 
 def _trial(torch, lvb, scene_list, choice, warm, steps):
@@ -74,18 +74,18 @@ def tune(scene_list, warm=200, steps=400):
         if best_ms is None or ms < best_ms:
             best, best_ms = c, ms
     base = best
-    for ct in CHECK_THREADS:
-        if ct == base.check_threads:
+    for ct in BLOCK_THREADS:
+        if ct == base.block_threads:
             continue
-        c = dataclasses.replace(base, check_threads=ct)
+        c = dataclasses.replace(base, block_threads=ct)
         ms = run(c)
         if ms < best_ms:
             best, best_ms = c, ms
     base = best
-    for sm in SMALL_MAX:
-        if sm == base.small_max:
+    for cp in COMPACTION:
+        if cp == base.compaction:
             continue
-        c = dataclasses.replace(base, small_max=sm)
+        c = dataclasses.replace(base, compaction=cp)
         ms = run(c)
         if ms < best_ms:
             best, best_ms = c, ms

@@ -1,8 +1,12 @@
 // lvb_dem.cu -- DEM driver on the local Verlet buffer list (include/lvb_dem.h).
 //
-// Per step: k_integrate (x', v*), lvb_step at x' (displacement check and
-// partial rebuild), k_forces (narrow phase on the list rows, linear
-// spring-dashpot, walls, a', v').  Forces are accumulated per row of the
+// Per step: position half-step (x', v*), the broad-phase step at x'
+// (displacement check and partial rebuild), forces (narrow phase on the
+// list rows, linear spring-dashpot, walls, a', v').  dem_advance runs each
+// step as one cooperative launch of the broad phase's step kernel with the
+// half-step fused into its check pass and the forces as its tail phase;
+// dem_phase runs the three parts as separate launches (k_integrate,
+// lvb_step, k_forces), with identical results.  Forces are accumulated per row of the
 // symmetric list, so each pair is evaluated once from each side and no
 // atomics are needed; both evaluations give exactly opposite forces.
 //
@@ -13,9 +17,10 @@
 // (error-free TwoSum / TwoProduct transformations, Knuth and Dekker), which
 // brings its error to ~1e-16 m at the cost of ~30 FP32 operations per
 // contact -- far cheaper on this part than binary64.
-#include "lvb_internal.cuh"
+#include "lvb_step.cuh"
 #include "lvb_dem.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -88,7 +93,7 @@ __device__ __forceinline__ float lsd(const DemDev &d, float dl, float vn, float 
     return f;
 }
 
-__device__ __forceinline__ IntegrateArgs integrate_args(const DemDev &d)
+__host__ __device__ __forceinline__ IntegrateArgs integrate_args(const DemDev &d)
 {
     IntegrateArgs a;
     a.pos = d.pos;
@@ -127,17 +132,9 @@ __device__ __forceinline__ float plane_force(const DemDev &d, float x, float v, 
     return F;
 }
 
-// Narrow phase on the rows + walls + velocity finish, one thread per particle.
-__global__ void __launch_bounds__(kThreads)
-k_forces(DemDev d)
+// Narrow phase on the row of particle i + walls + velocity finish.
+__device__ __forceinline__ void forces_one(const DemDev &d, int i)
 {
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
-    dtr_enter(d, TR_FORCES);
-    if (i >= d.n) {
-        dtr_exit(d, TR_FORCES);
-        return;
-    }
     const float4 xi = d.pos[i];
     const float4 vi = d.vstar[i];
     const float4 a = d.acc[i];
@@ -213,8 +210,28 @@ k_forces(DemDev d)
     v.z += (a.z + an.z) * d.half_dt;
     d.vel[i] = v;
     d.acc[i] = an;
+}
+
+// Forces as a separate kernel, one thread per particle.
+__global__ void __launch_bounds__(kThreads)
+k_forces(DemDev d)
+{
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
+    dtr_enter(d, TR_FORCES);
+    if (i < d.n) forces_one(d, i);
     dtr_exit(d, TR_FORCES);
 }
+
+// Forces as the tail phase of the fused step kernel (grid-stride).
+struct DemTail {
+    static constexpr bool kActive = true;
+    DemDev d;
+    __device__ void operator()(int t, int nt) const
+    {
+        for (int i = t; i < d.n; i += nt) forces_one(d, i);
+    }
+};
 
 __global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                             float rho)
@@ -265,9 +282,17 @@ void dem_free(dem_ctx *c)
         if (p) cudaFree(p);
 }
 
+// The driver's copy of the row-store addresses follows the broad phase's
+// (a grown store moves), and the trace switch follows its option.
+void refresh(dem_ctx *c)
+{
+    c->d.rows = rows_view(c->bp);
+    c->d.trace = *c->d.rows.trace;
+}
+
 int launch_phase(dem_ctx *c, int phase)
 {
-    c->d.trace = *c->d.rows.trace;
+    refresh(c);
     if (phase == DEM_PHASE_INTEGRATE) {
         k_integrate<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d);
     } else if (phase == DEM_PHASE_BROAD) {
@@ -280,6 +305,40 @@ int launch_phase(dem_ctx *c, int phase)
         return LVB_EINVAL;
     }
     return from_cuda(cudaGetLastError());
+}
+
+// Launch shape of the fused step: the broad phase's block size, and no more
+// blocks than fit on the device at once for this kernel.
+int fused_shape(dem_ctx *c, dim3 *grid, dim3 *block)
+{
+    int blocks = 0, threads = 0, dev = 0, sms = 0, per_sm = 0;
+    step_shape(c->bp, &blocks, &threads);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<true, DemTail>, threads,
+                                                          0);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (per_sm < 1) return LVB_EDEVICE;
+    *grid = dim3(std::min(blocks, per_sm * sms));
+    *block = dim3(threads);
+    return LVB_OK;
+}
+
+// One whole step (half-step, broad phase, forces) as one cooperative launch.
+int launch_fused(dem_ctx *c)
+{
+    int rc = grow_stores_if_asked(c->bp);
+    if (rc) return rc;
+    refresh(c);
+    dim3 grid, block;
+    rc = fused_shape(c, &grid, &block);
+    if (rc) return rc;
+    const DemDev &d = c->d;
+    return from_cuda(launch_coop(k_step<true, DemTail>, grid, block, c->stream,
+                                 (const float4 *)d.pos, (const float4 *)d.vstar,
+                                 (const float4 *)d.acc, step_state(c->bp), integrate_args(d),
+                                 DemTail{d}));
 }
 
 }  // namespace
@@ -387,62 +446,51 @@ int dem_advance(dem_ctx *c, int64_t steps)
     if (!c || steps < 0) return LVB_EINVAL;
     cudaGetLastError();   // clear a stale error of an unrelated earlier call
     const int64_t chunk = DEM_GRAPH_STEPS;
-    if (c->graph && c->graph_version != graph_version(c->bp)) {
-        cudaGraphExecDestroy(c->graph);   // the broad phase's nodes changed
-        c->graph = nullptr;
-    }
-    if (steps >= chunk && !c->graph) {
-        // one graph of `chunk` steps, built node by node (no stream capture,
-        // so it works on any stream, the legacy default one included)
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaGraphCreate(&g, 0);
-        cudaGraphNode_t dep = nullptr;
-        c->d.trace = *c->d.rows.trace;
-        const dim3 grid(grid_n(c->d.n)), block(kThreads);
-        int rc = LVB_OK;
-        // the position half-step runs inside the broad phase's check kernel
-        IntegrateArgs ia;
-        ia.pos = c->d.pos;
-        ia.vel = c->d.vel;
-        ia.acc = c->d.acc;
-        ia.vstar = c->d.vstar;
-        ia.dt = c->d.dt;
-        ia.half_dt2 = c->d.half_dt2;
-        ia.specular = c->d.wall_kind == DEM_WALL_SPECULAR;
-        ia.active = 1;
-        for (int64_t s = 0; s < chunk && e == cudaSuccess && rc == LVB_OK; ++s) {
-            rc = append_step_nodes(c->bp, g, &dep, (const float *)c->d.pos,
-                                   (const float *)c->d.vstar, (const float *)c->d.acc, &ia);
-            if (rc != LVB_OK) break;
-            e = add_kernel(&dep, g, &dep, k_forces, grid, block, c->d);
-        }
-        if (e == cudaSuccess && rc == LVB_OK) e = cudaGraphInstantiate(&c->graph, g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (rc != LVB_OK) return rc;
-        if (e != cudaSuccess) {
-            c->graph = nullptr;
-            return from_cuda(e);
-        }
-        c->graph_steps = chunk;
-        c->graph_version = graph_version(c->bp);
-    }
     int64_t done = 0;
-    if (c->graph) {
-        for (; done + c->graph_steps <= steps; done += c->graph_steps) {
-            // a store asked to grow: grow it, and rebuild this graph, which
-            // holds the old store's addresses
-            int rc = grow_stores_if_asked(c->bp);
-            if (rc) return rc;
-            if (c->graph_version != graph_version(c->bp)) return dem_advance(c, steps - done);
-            cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
-            if (e != cudaSuccess) return from_cuda(e);
+    while (steps - done >= chunk) {
+        // a store asked to grow: grow it (the graph holds the old store's
+        // addresses, so it is rebuilt below)
+        int rc = grow_stores_if_asked(c->bp);
+        if (rc) return rc;
+        if (c->graph && c->graph_version != graph_version(c->bp)) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
         }
+        if (!c->graph) {
+            // one graph of `chunk` cooperative step kernels, built node by
+            // node (no stream capture, so any stream works, the legacy
+            // default one included)
+            refresh(c);
+            dim3 grid, block;
+            rc = fused_shape(c, &grid, &block);
+            if (rc) return rc;
+            const DemDev &d = c->d;
+            const DevState st = step_state(c->bp);
+            const IntegrateArgs ia = integrate_args(d);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaGraphCreate(&g, 0);
+            cudaGraphNode_t dep = nullptr;
+            for (int64_t k = 0; k < chunk && e == cudaSuccess; ++k)
+                e = add_coop_kernel(&dep, g, &dep, k_step<true, DemTail>, grid, block,
+                                    (const float4 *)d.pos, (const float4 *)d.vstar,
+                                    (const float4 *)d.acc, st, ia, DemTail{d});
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->graph = nullptr;
+                return from_cuda(e);
+            }
+            c->graph_steps = chunk;
+            c->graph_version = graph_version(c->bp);
+        }
+        const cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        done += chunk;
     }
-    for (; done < steps; ++done)
-        for (int ph = 0; ph < 3; ++ph) {
-            int rc = launch_phase(c, ph);
-            if (rc) return rc;
-        }
+    for (; done < steps; ++done) {
+        const int rc = launch_fused(c);
+        if (rc) return rc;
+    }
     return LVB_OK;
 }
 

@@ -29,25 +29,25 @@
 namespace lvb {
 
 // sticky device error bits
-enum : unsigned { DERR_NAN = 1u, DERR_CELL = 2u, DERR_STORE = 4u };
+enum : unsigned { DERR_NAN = 1u, DERR_CELL = 2u, DERR_STORE = 4u, DERR_SYNC = 8u };
 
-// kernel slots of the per-kernel trace
+// slots of the trace: phases of the step kernel, then separate kernels
 enum TraceSlot {
-    TR_CHECK = 0, TR_FUSED, TR_INC_ROWS, TR_INC_APPEND, TR_ROWS, TR_RELAYOUT, TR_INTEGRATE,
-    TR_FORCES, kTraceSlots = 16
+    TR_CHECK = 0, TR_REBUILD, TR_RELAYOUT, TR_TAIL, TR_INTEGRATE, TR_FORCES, TR_ROWS,
+    kTraceSlots = 16
 };
 
 struct DevCounters {
-    int nF;            // flagged at this step (final, set by the check's last block)
-    int ntrow;         // rows touched by removals this step
-    int pad1;
-    int row_overflow;  // some row exceeded its capacity this step
+    int nF;            // flagged at the last step (final)
+    int ntrow;         // rows queued for removals this step
+    int nF_acc[2];     // flagged count while the check runs (slot: step parity)
+    int ovf[2];        // a row outgrew its capacity (slot: step parity)
+    int row_overflow;  // same, for the separate full-build kernels
     unsigned err;      // sticky DERR_* bits
     int last_flagged;
     int last_updated;
-    int nF_accum;      // running count while the check kernel's blocks compact
-    unsigned done_blocks;  // check blocks finished (last-block detection)
-    int pad0;
+    int pad0, pad1;
+    unsigned long long bar_word;  // grid barrier: generation << 32 | arrivals
     long long steps;
     long long rebuild_steps;
     long long flagged_total;
@@ -55,11 +55,10 @@ struct DevCounters {
     long long relayouts;
     long long store_needed;  // entries the row store needed at the last layout
     unsigned long long kernels;  // kernels of this library executed (device count)
-    long long small_steps;   // steps whose rebuild ran in the one-block kernel
+    unsigned long long barriers; // grid barriers passed by step kernels
     long long log_n;         // rebuild-log samples closed so far
-    unsigned long long fused_cycles[4];  // one-block rebuild: SM cycles per phase
-    // per-kernel device time (LVB_OPT_TRACE): first block entry / last block
-    // exit of the current step, and their differences summed over steps
+    // per-phase / per-kernel device time (LVB_OPT_TRACE): sums over steps;
+    // separate kernels record first block entry / last block exit first
     unsigned long long tr_start[kTraceSlots], tr_end[kTraceSlots];
     unsigned long long tr_sum[kTraceSlots], tr_cnt[kTraceSlots];
 };
@@ -279,6 +278,8 @@ __device__ __forceinline__ float4 integrate_one(const IntegrateArgs &a, const Sc
     return x;
 }
 
+struct DevState;
+
 struct RowsView {
     const int *row_off;
     const int *row_len;
@@ -295,15 +296,15 @@ struct RowsView {
 };
 RowsView rows_view(lvb_ctx *c);
 
-// Appends the nodes of one lvb_step (check, conditional rebuild, conditional
-// re-layout) to graph g after *dep (may be null); *dep receives the last node.
-// With `integ`, the step's first kernel also performs the driver's
-// position half-step (IntegrateArgs) before checking.
-int append_step_nodes(lvb_ctx *c, cudaGraph_t g, cudaGraphNode_t *dep, const float *pos_r,
-                      const float *vel, const float *acc, const IntegrateArgs *integ = nullptr);
+// The device state a step kernel takes by value, and the launch shape of
+// the step kernel (blocks: all co-resident; threads per block).
+DevState step_state(lvb_ctx *c);
+void step_shape(lvb_ctx *c, int *blocks, int *threads);
+cudaStream_t step_stream(lvb_ctx *c);
 
-// Changes whenever the nodes of a step change (options, logging, store
-// growth), so that a caller holding a graph of steps knows to rebuild it.
+// Changes whenever the step kernel's arguments change (options, logging,
+// store growth), so that a caller holding a graph of steps knows to rebuild
+// it.
 int graph_version(lvb_ctx *c);
 
 // Grows the row store / cell slots if a kernel asked for it (see lvb_step).
@@ -311,6 +312,41 @@ int grow_stores_if_asked(lvb_ctx *c);
 
 // Adds a kernel node running fn(args...) after the given dependency (none
 // when dep or *dep is null); the argument values are copied into the node.
+// add_coop_kernel adds a cooperative one (all blocks resident at once).
+template <typename... P, typename... A>
+cudaError_t add_kernel(cudaGraphNode_t *out, cudaGraph_t g, const cudaGraphNode_t *dep,
+                       void (*fn)(P...), dim3 grid, dim3 block, A... args);
+
+template <typename... P, typename... A>
+cudaError_t add_coop_kernel(cudaGraphNode_t *out, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            void (*fn)(P...), dim3 grid, dim3 block, A... args)
+{
+    cudaError_t e = add_kernel(out, g, dep, fn, grid, block, args...);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttributeValue v = {};
+    v.cooperative = 1;
+    return cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &v);
+}
+
+// Launches fn(args...) cooperatively on `stream`.
+template <typename... P, typename... A>
+cudaError_t launch_coop(void (*fn)(P...), dim3 grid, dim3 block, cudaStream_t stream,
+                        A... args)
+{
+    static_assert(sizeof...(P) == sizeof...(A), "argument count");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, static_cast<P>(args)...);
+}
+
 template <typename... P, typename... A>
 cudaError_t add_kernel(cudaGraphNode_t *out, cudaGraph_t g, const cudaGraphNode_t *dep,
                        void (*fn)(P...), dim3 grid, dim3 block, A... args)

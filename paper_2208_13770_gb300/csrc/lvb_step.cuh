@@ -1,0 +1,867 @@
+// lvb_step.cuh -- device state of a broad-phase context and the step kernel.
+//
+// One step of the local Verlet buffer is one cooperative kernel, k_step,
+// whose phases are separated by grid-wide barriers (all its blocks are
+// co-resident: cooperative launch, grid sized by occupancy):
+//   check      every particle: displacement check (Eq. update), ballot
+//              words, compaction of the flagged ids; with the PARTIAL
+//              trigger the warp that flags a particle also gives it its new
+//              reference state and skin (Eq. skin_formulus1 or another
+//              policy, capped per Eq. skin_formulus_mincell), moves it to
+//              its new cell slot and queues the rows that listed it
+//   -- barrier --
+//   rebuild    PARTIAL: rows of the flagged particles by the 27-cell stencil
+//              (Algorithm 1 on the extended spheres, Eq. bounding_sphere)
+//              and removal of the flagged entries from the queued rows;
+//              -- barrier -- insertion of each flagged particle into its
+//              unflagged partners' rows; -- barrier --
+//              GLOBAL / ALWAYS (Def. autoverlet / no buffer): new reference
+//              states, cells and rows of every particle
+//   re-layout  only when a row outgrew its slack: count, scan, fill
+//   tail       the DEM driver's forces (k_step instantiated by lvb_dem.cu)
+// A step with nothing flagged is the check and one barrier.  The kernel is
+// included by lvb_broad.cu (the broad phase alone) and lvb_dem.cu (a whole
+// DEM step per launch).
+#pragma once
+
+#include "lvb_internal.cuh"
+
+namespace lvb {
+
+constexpr int kStepMaxThreads = 1024;     // block size limit of k_step (one block per SM)
+constexpr int kCheckUnroll = 2;           // 32-particle chunks a warp has in flight
+constexpr unsigned kBarrierSpins = 1u << 22;   // ~1-3 s of polling (L2 round trips) before a barrier gives up
+
+// Written by kernels straight into mapped host memory: requests to grow a
+// store before it fills (read by the host before every step, no sync).
+struct HostFlags {
+    int grow_store;
+    int grow_cells;
+    long long store_needed;
+};
+
+struct DevState {
+    int n, nwords, trigger, skin_kind;
+    float skin_value, skin_dt;
+    int nscenes, ccap;
+    const SceneGeom *sg;    // per-scene geometry
+    const int *scene_of;    // scene of each particle (null when one scene)
+    long long ncells;
+    float4 *ref;
+    float *rad;
+    int *cell_of, *slot_of;
+    int *prevcell;    // cell of each flagged particle before its update
+    uint32_t *bits;
+    int *fid;
+    int *row_off, *row_len, *row_cap, *col;
+    long long col_cap;
+    int *trow, *trow_mark;
+    int *cell_cnt, *cell_id;
+    float4 *cell_ref;
+    DevCounters *cnt;
+    long long *blk;   // scan partials (one per block of the widest scan)
+    const lvb_mlp_weights *mlp;   // skin network (LVB_SKIN_LEARNED)
+    int *born;        // step of each particle's last update
+    int *cell_live;   // particles whose reference position lies in each cell
+    // rebuild log (training samples of the skin network)
+    int log_on, log_horizon;
+    long long log_cap;
+    float *lg_feat;   // n x 8 features of the open record
+    float4 *lg_x;     // position at which the record opened
+    int *lg_t;        // step the record opened (-1: none)
+    float *lg_m;      // largest squared displacement since
+    float *log_buf;   // log_cap x 9 samples
+    HostFlags *hflags;    // device view of the mapped host flags
+    int trace;            // record per-phase device time (LVB_OPT_TRACE)
+    int compact_block;    // flag compaction: 0 one atomic per warp chunk,
+                          // 1 one per block tile (LVB_OPT_COMPACT)
+};
+
+// gate modes of the separate full-build kernels (init, store growth)
+enum Gate { GATE_OVERFLOW = 1, GATE_ANY_FLAG = 2, GATE_ALWAYS = 3 };
+
+__device__ __forceinline__ const SceneGeom &geom_of(const DevState &s, int i)
+{
+    return s.sg[s.nscenes == 1 ? 0 : s.scene_of[i]];
+}
+
+__device__ __forceinline__ bool store_failed(const DevState &s)
+{
+    return (s.cnt->err & DERR_STORE) != 0;
+}
+
+// After a failed re-layout (DERR_STORE) the row offsets no longer fit the
+// store, so every kernel that touches rows or cells stands down.
+__device__ __forceinline__ int gated_items(const DevState &s, int gate)
+{
+    if (store_failed(s)) return 0;
+    if (gate == GATE_OVERFLOW) return s.cnt->row_overflow ? s.n : 0;
+    if (gate == GATE_ANY_FLAG) return s.cnt->nF ? s.n : 0;
+    return s.n;
+}
+
+__device__ __forceinline__ void count_kernel(const DevState &s)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt->kernels, 1ULL);
+}
+
+// per-kernel trace of the separate kernels: first entry and last exit over
+// the kernel's blocks (folded into the sums by the next step)
+__device__ __forceinline__ void tr_enter(const DevState &s, int slot)
+{
+    if (s.trace && threadIdx.x == 0) atomicMin(&s.cnt->tr_start[slot], global_ns());
+}
+
+__device__ __forceinline__ void tr_exit(const DevState &s, int slot)
+{
+    if (s.trace && (threadIdx.x & 31) == 0) atomicMax(&s.cnt->tr_end[slot], global_ns());
+}
+
+// ---------------------------------------------------------------------------
+// Phases that walk a row or a cell run one warp per item (w0/wstride count
+// warps): the lanes take the entries, so a phase costs a few memory
+// latencies however long the rows are, and atomics are warp-aggregated.
+// ---------------------------------------------------------------------------
+
+// Features of the skin network (lvb_mlp.h) from the state before the
+// particle's update; q_old is its old reference state.
+__device__ __forceinline__ void skin_features(const DevState &s, float4 p, float4 v, float4 a,
+                                              float r, const SceneGeom &g, float4 q_old,
+                                              int nrow, int age, int occ, float f[LVB_MLP_IN])
+{
+    const float d = __fmul_rn(2.0f, r);
+    const float vm = __fsqrt_rn(sqdist_rn(v.x, v.y, v.z, 0.f, 0.f, 0.f));
+    const float am = __fsqrt_rn(sqdist_rn(a.x, a.y, a.z, 0.f, 0.f, 0.f));
+    f[0] = __fdiv_rn(__fmul_rn(vm, s.skin_dt), d);
+    f[1] = __fdiv_rn(__fmul_rn(__fmul_rn(am, s.skin_dt), s.skin_dt), d);
+    f[2] = __fdiv_rn(r, g.H);
+    f[3] = (float)nrow;
+    f[4] = (float)age;
+    f[5] = q_old.w > 0.0f
+               ? __fdiv_rn(__fsqrt_rn(sqdist_rn(p.x, p.y, p.z, q_old.x, q_old.y, q_old.z)), q_old.w)
+               : 0.0f;
+    f[6] = (float)occ;
+    float w = __fsub_rn(__fsub_rn(p.x, g.lo[0]), r);
+    w = fminf(w, __fsub_rn(__fsub_rn(g.hi[0], p.x), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(p.y, g.lo[1]), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(g.hi[1], p.y), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(p.z, g.lo[2]), r));
+    w = fminf(w, __fsub_rn(__fsub_rn(g.hi[2], p.z), r));
+    f[7] = __fdiv_rn(w, d);
+}
+
+// Skin of particle i by the context's policy; the learned policy needs the
+// whole warp (all lanes compute the same value).
+__device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g, float r,
+                                           float4 v, const float f[LVB_MLP_IN])
+{
+    float prop = 0.0f;
+    if (s.skin_kind == LVB_SKIN_LEARNED) {
+        const float y = mlp_y_warp(s.mlp, f);
+        prop = __fmul_rn(__fmul_rn(2.0f, r), relu(y));
+    }
+    return skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
+}
+
+
+// a2 + a3 for one flagged particle i, run inside the step kernel's check
+// pass by the warp that flagged it (PARTIAL trigger):
+//   * new reference position and skin (the policy's features come from the
+//     state before the update; `step` is the number of the step being taken);
+//   * its cell slot: a stayer refreshes the slot's copy of the reference
+//     state; a leaver leaves a tombstone (-1) in its old slot and takes a
+//     tombstone slot of its new cell (claimed with compare-and-swap) or a
+//     fresh one at the end.  Slots of unflagged particles never change, so
+//     after the check every cell holds the step's final reference states;
+//   * every partner j of its old row is queued (once) for the removal of
+//     the flagged entries; whether j is flagged itself is only known after
+//     the check, so the removal pass skips flagged rows;
+//   * the occupancy counts of the cells (a feature of the skin network) are
+//     left as they were before the step: the rows pass moves the counts
+//     after the check, from the old cell kept in prevcell[i].
+// (pos and vel may have been written earlier in the same kernel by the DEM
+// position half-step, so they are read through plain coherent loads.)
+// Not inlined: it runs only for flagged particles, and as a call it keeps
+// the check loop's registers free of its working set.
+static __device__ __noinline__ void update_move_warp(const DevState &s, int i, const float4 *pos,
+                                                 const float4 *vel, const float4 *acc, int step,
+                                                 int *ovf)
+{
+    const int lane = threadIdx.x & 31;
+    const int ccap = s.ccap;
+    const float4 p = pos[i];
+    const float r = s.rad[i];
+    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int oc = s.cell_of[i], so = s.slot_of[i];
+    const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
+    const SceneGeom &g = geom_of(s, i);
+    const int nc = cell_key(g, p.x, p.y, p.z);
+    // issued now, used below: the new cell's slot count and the first 32
+    // partners of the old row (their latency overlaps the skin policy)
+    const int cn0 = nc != oc ? s.cell_cnt[nc] : 0;
+    const int j0 = lane < len ? s.col[off + lane] : -1;
+    float f[LVB_MLP_IN];
+    if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
+        const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        skin_features(s, p, v, a, r, g, s.ref[i], len, step - s.born[i], s.cell_live[nc], f);
+    }
+    const float sk = warp_skin(s, g, r, v, f);
+    const float4 cr = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+    if (lane == 0) {
+        s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+        s.born[i] = step;
+        s.prevcell[i] = oc;
+        if (s.log_on && s.lg_t[i] < 0) {
+            s.lg_t[i] = step;
+            s.lg_x[i] = p;
+            s.lg_m[i] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < LVB_MLP_IN; ++q) s.lg_feat[(long long)i * LVB_MLP_IN + q] = f[q];
+        }
+    }
+    // old partners: queue their rows for the removal pass.  Queue slots are
+    // reserved for every partner at once (one atomic, issued together with
+    // the marks); a partner already queued leaves -1 in its slot.  The queue
+    // holds n slots; reservations beyond it raise the row-overflow flag, and
+    // the re-layout then rebuilds every row from the cells (and clears the
+    // marks).
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        const int j = e0 == 0 ? j0 : (e < len ? s.col[off + e] : -1);
+        const unsigned m = __ballot_sync(FULL, e < len);
+        int q = 0;
+        if (lane == 0) q = atomicAdd(&s.cnt->ntrow, __popc(m));
+        const bool push = e < len && atomicExch(&s.trow_mark[j], 1) == 0;
+        q = __shfl_sync(FULL, q, 0) + __popc(m & lanemask_lt());
+        if (e < len) {
+            if (q < s.n) s.trow[q] = push ? j : -1;
+            else atomicExch(ovf, 1);
+        }
+    }
+    // cell slot
+    if (nc == oc) {
+        if (lane == 0) s.cell_ref[(long long)oc * ccap + so] = cr;
+        return;
+    }
+    if (lane == 0) s.cell_id[(long long)oc * ccap + so] = -1;
+    const long long base = (long long)nc * ccap;
+    const int cn = min(cn0, ccap);
+    int slot = -1;
+    for (int e0 = 0; e0 < cn && slot < 0; e0 += 32) {
+        const int sl = e0 + lane;
+        unsigned m = __ballot_sync(FULL, sl < cn && s.cell_id[base + sl] < 0);
+        while (m && slot < 0) {
+            const int src = __ffs(m) - 1;
+            int won = 0;
+            if (lane == src) won = atomicCAS(&s.cell_id[base + sl], -1, i) == -1;
+            won = __shfl_sync(FULL, won, src);
+            if (won) slot = e0 + src;
+            m &= m - 1;
+        }
+    }
+    if (lane == 0) {
+        if (slot < 0) {
+            slot = atomicAdd(&s.cell_cnt[nc], 1);
+            if (slot * 4 >= ccap * 3) s.hflags->grow_cells = 1;
+            if (slot < ccap) s.cell_id[base + slot] = i;
+            else atomicOr(&s.cnt->err, DERR_CELL);
+        }
+        if (slot < ccap) {
+            s.cell_ref[base + slot] = cr;
+            s.slot_of[i] = slot;
+        }
+        s.cell_of[i] = nc;
+    }
+}
+
+// Occupancy counts of the cells a flagged particle left and entered.
+__device__ __forceinline__ void move_live_count(const DevState &s, int i)
+{
+    const int oc = s.prevcell[i], nc = s.cell_of[i];
+    if (oc != nc) {
+        atomicSub(&s.cell_live[oc], 1);
+        atomicAdd(&s.cell_live[nc], 1);
+    }
+}
+
+// a5 (removal): each queued unflagged row drops its flagged entries.  Rows
+// are short, so a warp takes four rows at a time, eight lanes each (stable
+// in-place compaction: every lane reads its entry before the ballot, and an
+// entry only moves to a lower index).  A queued row that is flagged itself
+// is rebuilt by the rows pass and only loses its queue mark here; -1
+// entries are reserved slots that a duplicate left empty.  `w0` and
+// `wstride` count warps.
+__device__ __forceinline__ void compact_rows(const DevState &s, int w0, int wstride)
+{
+    const int lane = threadIdx.x & 31, sub = lane >> 3, l8 = lane & 7;
+    const unsigned below = lanemask_lt() & (0xFFu << (sub * 8));
+    const int ntrow = min(s.cnt->ntrow, s.n);
+    for (int k0 = w0 * 4; k0 < ntrow; k0 += wstride * 4) {
+        const int k = k0 + sub;
+        int j = -1, off = 0, len = 0;
+        bool act = k < ntrow;
+        if (act) {
+            j = s.trow[k];
+            if (j < 0) {
+                act = false;            // a duplicate's reserved slot
+            } else if (bit_of(s.bits, j)) {
+                act = false;
+                if (l8 == 0) s.trow_mark[j] = 0;
+            } else {
+                off = s.row_off[j];
+                len = min(s.row_len[j], s.row_cap[j]);
+            }
+        }
+        int mx = len;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+        int w = 0;
+        for (int e0 = 0; e0 < mx; e0 += 8) {
+            const int e = e0 + l8;
+            int c = 0;
+            bool keep = false;
+            if (act && e < len) {
+                c = s.col[off + e];
+                keep = !bit_of(s.bits, c);
+            }
+            const unsigned m = __ballot_sync(FULL, keep);
+            if (keep) s.col[off + w + __popc(m & below)] = c;
+            w += __popc((m >> (sub * 8)) & 0xFFu);
+        }
+        if (act && l8 == 0) {
+            s.row_len[j] = w;
+            s.trow_mark[j] = 0;
+        }
+    }
+}
+
+// a4: rows by the 27-cell stencil, one warp per row.  Lanes 0..26 each own
+// one neighbour cell; a warp scan of their occupancies flattens the
+// candidates, and every lane finds its candidate's cell with a 5-step
+// shuffle binary search, so lanes stay busy across cell boundaries.
+// fill = 0 counts only (row_len = count); fill = 1 also writes up to the
+// row's capacity and raises *ovf if the row does not fit.
+// Items are fid[w] when `from_list`, else particle w.  Cell slots holding a
+// tombstone (id < 0) are skipped.  The cells must hold the step's final
+// reference states (after the check kernel's moves, or a full re-bin).
+__device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from_list, int fill,
+                                        int w0, int wstride, int *ovf)
+{
+    const int lane = threadIdx.x & 31;
+    const int ccap = s.ccap;
+    const unsigned lt = lanemask_lt();
+    for (int w = w0; w < nitems; w += wstride) {
+        const int i = from_list ? s.fid[w] : w;
+        const SceneGeom &g = geom_of(s, i);
+        const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
+        const float4 q = s.ref[i];
+        const float4 qi = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
+        const int ci = s.cell_of[i] - g.cell_base;
+        const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
+        int cnt_l = 0, cid = 0;
+        if (lane < 27) {
+            const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+            if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+                cid = g.cell_base + (z * d1 + y) * d0 + x;
+                cnt_l = min(s.cell_cnt[cid], ccap);
+            }
+        }
+        const int incl = warp_incl_scan(cnt_l);
+        const int excl = incl - cnt_l;
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int off = fill ? s.row_off[i] : 0;
+        const int cap = fill ? s.row_cap[i] : 0;
+        int found = 0;
+        for (int b0 = 0; b0 < total; b0 += 32) {
+            const int k = b0 + lane;
+            int c = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                c += (__shfl_sync(FULL, incl, c + step - 1) <= k) ? step : 0;
+            const int cc = __shfl_sync(FULL, cid, c);
+            const int ex = __shfl_sync(FULL, excl, c);
+            bool hit = false;
+            int j = -1;
+            if (k < total) {
+                const long long idx = (long long)cc * ccap + (k - ex);
+                j = s.cell_id[idx];
+                if (j >= 0 && j != i) hit = pair_hit(qi, s.cell_ref[idx]);
+            }
+            const unsigned m = __ballot_sync(FULL, hit);
+            if (fill && hit) {
+                const int p = found + __popc(m & lt);
+                if (p < cap) s.col[off + p] = j;
+            }
+            found += __popc(m);
+        }
+        if (lane == 0) {
+            s.row_len[i] = found;
+            if (fill && found > cap) atomicExch(ovf, 1);
+        }
+    }
+}
+
+// a5 (insertion): flagged i joins the row of each unflagged partner; one
+// warp per flagged particle, one lane per partner.  Runs after the removal
+// pass, so a pair that survives the update is removed and re-added once.
+__device__ __forceinline__ void ph_append(const DevState &s, int nF, int w0, int wstride, int *ovf)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = w0; k < nF; k += wstride) {
+        const int i = s.fid[k];
+        const int len = s.row_len[i];
+        if (len > s.row_cap[i]) continue;     // re-layout rebuilds everything
+        const int off = s.row_off[i];
+        for (int e = lane; e < len; e += 32) {
+            const int j = s.col[off + e];
+            if (bit_of(s.bits, j)) continue;  // j's own new row lists i
+            const int p = atomicAdd(&s.row_len[j], 1);
+            if (p < s.row_cap[j]) s.col[s.row_off[j] + p] = i;
+            else atomicExch(ovf, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide barrier of the step kernel (all blocks co-resident).  One 64-bit
+// word holds the generation (high half) and the arrivals (low half).  Thread
+// 0 of each block arrives with one acquire-release add; the last arrival
+// adds 2^32 - blocks (next generation, arrivals back to zero) with release
+// semantics, the others poll the generation with acquire loads.  Polling is
+// bounded: after kBarrierSpins polls the block records DERR_SYNC and
+// leaves; every block then returns, and later steps do nothing (the context
+// reports the error).  Returns false when the step must be abandoned.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long *p,
+                                                               unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                 : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(const DevState &s)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DevCounters *c = s.cnt;
+        const unsigned nb = gridDim.x;
+        const unsigned long long old = atom_add_acq_rel(&c->bar_word, 1ULL);
+        int ok = 1;
+        if ((unsigned)old == nb - 1) {
+            c->barriers += 1;
+            red_add_release(&c->bar_word, (1ULL << 32) - nb);
+        } else {
+            const unsigned gen = (unsigned)(old >> 32);
+            unsigned it = 0;
+            while ((unsigned)(ld_acquire(&c->bar_word) >> 32) == gen) {
+                if (++it > kBarrierSpins) {
+                    atomicOr(&c->err, DERR_SYNC);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Exclusive scan over the block (any block size up to 1024); *total gets
+// the block's sum.  Contains block barriers.
+__device__ __forceinline__ long long block_scan_any(long long v, long long *total)
+{
+    __shared__ long long ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long y = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane < nw) ws[lane] = y;
+    }
+    __syncthreads();
+    const long long before = warp ? ws[warp - 1] : 0;
+    *total = ws[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// a1 (+ a2, a3 with the PARTIAL trigger): the check pass.  Block b takes
+// tiles b, b + grid, ... of blockDim * kCheckUnroll particles; in a tile each
+// warp checks kCheckUnroll chunks of 32 consecutive particles (loads of all
+// chunks first, so several are in flight), writes one ballot word per chunk
+// and compacts the flagged ids, either with one atomic per chunk that has
+// flags (warp scheme) or with one per tile (block scheme, two barriers per
+// tile that has flags).  The warp then updates the particles it flagged.
+// ---------------------------------------------------------------------------
+template <bool kFused>
+__device__ __forceinline__ void check_pass(const DevState &s, const float4 *__restrict__ pos_in,
+                                           const float4 *vel, const float4 *acc,
+                                           const IntegrateArgs &ia, bool inc, int step,
+                                           int *nF_acc, int *ovf)
+{
+    __shared__ int s_cnt[32];
+    __shared__ int s_base;
+    const float4 *pos = kFused ? ia.pos : pos_in;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const int tile = blockDim.x * kCheckUnroll;
+    for (int t0 = blockIdx.x * tile; t0 < s.n; t0 += gridDim.x * tile) {
+        float4 p[kCheckUnroll], q[kCheckUnroll];
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            const int i = t0 + u * blockDim.x + warp * 32 + lane;
+            if (i < s.n) {
+                p[u] = kFused ? integrate_one(ia, geom_of(s, i), i) : __ldg(pos_in + i);
+                q[u] = s.ref[i];
+            }
+        }
+        unsigned b[kCheckUnroll];
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            const int cu = t0 + u * blockDim.x + warp * 32;   // chunk start, a multiple of 32
+            const int i = cu + lane;
+            bool f = false;
+            if (i < s.n) {
+                f = violates(p[u], q[u]);
+                if (!(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(p[u].z)))
+                    atomicOr(&s.cnt->err, DERR_NAN);
+            }
+            b[u] = __ballot_sync(FULL, f);
+            if (lane == 0 && cu < s.n) s.bits[cu >> 5] = b[u];
+            cnt += __popc(b[u]);
+        }
+        int k0 = 0;
+        if (s.compact_block) {
+            // one atomic per tile: warp counts, block scan by thread 0
+            if (!__syncthreads_or(cnt)) continue;
+            if (lane == 0) s_cnt[warp] = cnt;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int run = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    const int v = s_cnt[w];
+                    s_cnt[w] = run;
+                    run += v;
+                }
+                s_base = atomicAdd(nF_acc, run);
+            }
+            __syncthreads();
+            k0 = s_base + s_cnt[warp];
+        } else {
+            if (!cnt) continue;
+            if (lane == 0) k0 = atomicAdd(nF_acc, cnt);
+            k0 = __shfl_sync(FULL, k0, 0);
+        }
+        if (!cnt) continue;
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            if (b[u] >> lane & 1u) s.fid[k0 + __popc(b[u] & lt)] = t0 + u * blockDim.x + warp * 32 + lane;
+            k0 += __popc(b[u]);
+        }
+        if (inc) {
+            // the new positions of these chunks were written by the warp's
+            // own lanes (DEM form): make them visible to the whole warp
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < kCheckUnroll; ++u)
+                for (unsigned m = b[u]; m; m &= m - 1)
+                    update_move_warp(s, t0 + u * blockDim.x + warp * 32 + __ffs(m) - 1, pos, vel,
+                                     acc, step, ovf);
+        }
+    }
+}
+
+// a4 + a5 (removal) of a partial rebuild, then (after a barrier) a5
+// (insertion); w0 / nw count warps of the grid, t / nt threads.
+static __device__ __noinline__ void partial_rows_pass(const DevState &s, int nF, int *ovf)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    ph_rows(s, nF, true, 1, t >> 5, nt >> 5, ovf);
+    compact_rows(s, t >> 5, nt >> 5);
+    for (int k = t; k < nF; k += nt) move_live_count(s, s.fid[k]);
+}
+
+static __device__ __noinline__ void partial_append_pass(const DevState &s, int nF, int *ovf)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    ph_append(s, nF, t >> 5, nt >> 5, ovf);
+}
+
+// GLOBAL / ALWAYS: new reference state of every particle (the learned
+// policy needs the partial trigger), and cleared cells.
+static __device__ __noinline__ void full_update_pass(const DevState &s, const float4 *pos,
+                                              const float4 *vel)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int i = t; i < s.n; i += nt) {
+        const float4 p = pos[i];
+        const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const SceneGeom &g = geom_of(s, i);
+        const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, s.rad[i], v, 0.0f);
+        s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+        s.cell_of[i] = cell_key(g, p.x, p.y, p.z);
+    }
+    for (long long c = t; c < s.ncells; c += nt) {
+        s.cell_cnt[c] = 0;
+        s.cell_live[c] = 0;
+    }
+}
+
+static __device__ __noinline__ void full_insert_pass(const DevState &s)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int ccap = s.ccap;
+    for (int i = t; i < s.n; i += nt) {
+        const int c = s.cell_of[i];
+        const int sl = atomicAdd(&s.cell_cnt[c], 1);
+        atomicAdd(&s.cell_live[c], 1);
+        if (sl < ccap) {
+            const float4 q = s.ref[i];
+            s.cell_id[(long long)c * ccap + sl] = i;
+            s.cell_ref[(long long)c * ccap + sl] = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
+            s.slot_of[i] = sl;
+        } else {
+            atomicOr(&s.cnt->err, DERR_CELL);
+        }
+        if (sl * 4 >= ccap * 3) s.hflags->grow_cells = 1;
+    }
+}
+
+static __device__ __noinline__ void all_rows_pass(const DevState &s, int fill, int *ovf)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    ph_rows(s, s.n, false, fill, t >> 5, nt >> 5, ovf);
+}
+
+// Re-layout of the row store after a row outgrew its slack: rows counted
+// from the (final) cells, offsets by a grid-wide scan of row_capacity(len),
+// rows filled.  Block b owns rows [b * per, (b + 1) * per).  Returns false
+// when the step must be abandoned (a barrier gave up).
+static __device__ __noinline__ bool relayout_pass(const DevState &s)
+{
+    DevCounters *c = s.cnt;
+    all_rows_pass(s, 0, nullptr);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x)
+        s.trow_mark[i] = 0;   // queue marks left by an overflowed queue
+    if (!grid_barrier(s)) return false;
+    const long long per = ((long long)s.n + gridDim.x - 1) / gridDim.x;
+    const int lo = (int)min((long long)s.n, blockIdx.x * per);
+    const int hi = (int)min((long long)s.n, lo + per);
+    long long sum = 0, tot;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) sum += row_capacity(s.row_len[i]);
+    block_scan_any(sum, &tot);
+    if (threadIdx.x == 0) s.blk[blockIdx.x] = tot;
+    if (!grid_barrier(s)) return false;
+    if (blockIdx.x == 0) {
+        __shared__ long long carry;
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (int b0 = 0; b0 < (int)gridDim.x; b0 += blockDim.x) {
+            const int b = b0 + threadIdx.x;
+            const long long v = b < (int)gridDim.x ? s.blk[b] : 0;
+            const long long ex = block_scan_any(v, &tot);
+            if (b < (int)gridDim.x) s.blk[b] = carry + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            c->store_needed = carry;
+            if (carry > s.col_cap) atomicOr(&c->err, DERR_STORE);
+        }
+    }
+    if (!grid_barrier(s)) return false;
+    long long run = s.blk[blockIdx.x];
+    for (int i0 = lo; i0 < hi; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const int v = i < hi ? row_capacity(s.row_len[i]) : 0;
+        const long long ex = block_scan_any(v, &tot);
+        if (i < hi) {
+            s.row_off[i] = (int)min(run + ex, (long long)INT32_MAX);
+            s.row_cap[i] = v;
+        }
+        run += tot;
+    }
+    if (!grid_barrier(s)) return false;
+    if (!store_failed(s)) {
+        int unused = 0;
+        all_rows_pass(s, 1, &unused);
+    }
+    if (!grid_barrier(s)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !store_failed(s)) {
+        c->relayouts += 1;
+        const long long need = c->store_needed;
+        if (need * 4 > s.col_cap * 3) {        // over 75% of the store: grow it
+            s.hflags->store_needed = need;
+            s.hflags->grow_store = 1;
+        }
+    }
+    return true;
+}
+
+// Rebuild log: every open record tracks the particle's largest displacement
+// since it opened, and closes `horizon` steps later with label
+// sqrt(max |x - x_open|^2) / d.
+static __device__ __noinline__ void log_pass(const DevState &s, const float4 *pos, int step)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int i = t; i < s.n; i += nt) {
+        const int t0 = s.lg_t[i];
+        if (t0 < 0) continue;
+        const float4 p = pos[i];
+        const float4 x0 = s.lg_x[i];
+        const float m = fmaxf(s.lg_m[i], sqdist_rn(p.x, p.y, p.z, x0.x, x0.y, x0.z));
+        if (step - t0 >= s.log_horizon) {
+            const long long idx =
+                (long long)atomicAdd((unsigned long long *)&s.cnt->log_n, 1ULL);
+            if (idx < s.log_cap) {
+                float *o = s.log_buf + idx * (LVB_MLP_IN + 1);
+#pragma unroll
+                for (int q = 0; q < LVB_MLP_IN; ++q) o[q] = s.lg_feat[(long long)i * LVB_MLP_IN + q];
+                o[LVB_MLP_IN] = __fdiv_rn(__fsqrt_rn(m), __fmul_rn(2.0f, s.rad[i]));
+            }
+            s.lg_t[i] = -1;
+        } else {
+            s.lg_m[i] = m;
+        }
+    }
+}
+
+// Tail of a step that only does the broad phase.
+struct NoTail {
+    static constexpr bool kActive = false;
+    __device__ void operator()(int, int) const {}
+};
+
+__device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned long long a,
+                                          unsigned long long b)
+{
+    c->tr_sum[slot] += b - a;
+    c->tr_cnt[slot] += 1;
+}
+
+// ---------------------------------------------------------------------------
+// One step.  pos_in / vel / acc: the caller's positions, velocities (policy
+// input) and accelerations; with kFused the positions come from the DEM
+// half-step (ia) instead.  Launched cooperatively with every block resident.
+// Per-step counts live in two slots chosen by the step's parity, so that the
+// slots of the next step can be cleared while this one is read.
+// ---------------------------------------------------------------------------
+template <bool kFused, class Tail>
+__global__ void __launch_bounds__(kStepMaxThreads, 1)
+k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, DevState s,
+       IntegrateArgs ia, Tail tail)
+{
+    DevCounters *c = s.cnt;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const unsigned long long t0 = (s.trace && lead) ? global_ns() : 0ULL;
+    // every thread reads the counters it needs (one broadcast load each, no
+    // block barrier before the check's loads); the values are stable while
+    // the check runs
+    const unsigned err = c->err;
+    const bool inc = s.trigger == LVB_TRIGGER_PARTIAL && !(err & DERR_STORE);
+    const int step = (int)c->steps + 1, par = step & 1;
+    const float4 *pos = kFused ? ia.pos : pos_in;
+    int *ovf = &c->ovf[par];
+
+    check_pass<kFused>(s, pos_in, vel, acc, ia, inc, step, &c->nF_acc[par], ovf);
+    if (err & DERR_SYNC) return;   // a barrier failed earlier: the context is unusable
+    if (!grid_barrier(s)) return;
+    const int nF = *(volatile int *)&c->nF_acc[par];
+    int upd;
+    if (s.trigger == LVB_TRIGGER_PARTIAL) upd = nF;
+    else if (s.trigger == LVB_TRIGGER_GLOBAL) upd = nF ? s.n : 0;
+    else upd = s.n;
+    unsigned long long t1 = 0;
+    if (lead) {
+        c->nF_acc[par ^ 1] = 0;
+        c->ovf[par ^ 1] = 0;
+        c->nF = nF;
+        c->steps += 1;
+        c->flagged_total += nF;
+        c->updated_total += upd;
+        if (upd) c->rebuild_steps += 1;
+        c->last_flagged = nF;
+        c->last_updated = upd;
+        atomicAdd(&c->kernels, 1ULL);
+        if (s.trace) {
+            t1 = global_ns();
+            trace_add(c, TR_CHECK, t0, t1);
+            // separate kernels (DEM phases) since the last step
+            for (int k = TR_INTEGRATE; k <= TR_ROWS; ++k) {
+                const unsigned long long a = c->tr_start[k], b = c->tr_end[k];
+                if (b != 0 && b >= a) trace_add(c, k, a, b);
+                c->tr_start[k] = ~0ULL;
+                c->tr_end[k] = 0;
+            }
+        }
+    }
+    if (inc) {
+        if (nF > 0) {
+            partial_rows_pass(s, nF, ovf);
+            if (!grid_barrier(s)) return;
+            if (lead) c->ntrow = 0;
+            partial_append_pass(s, nF, ovf);
+            if (!grid_barrier(s)) return;
+        }
+    } else if (upd > 0 && !store_failed(s)) {
+        full_update_pass(s, pos, vel);
+        if (!grid_barrier(s)) return;
+        full_insert_pass(s);
+        if (!grid_barrier(s)) return;
+        all_rows_pass(s, 1, ovf);
+        if (!grid_barrier(s)) return;
+    }
+    unsigned long long t2 = 0;
+    if (s.trace && lead) {
+        t2 = global_ns();
+        trace_add(c, TR_REBUILD, t1, t2);
+    }
+    if (*(volatile int *)ovf && !store_failed(s)) {
+        if (!relayout_pass(s)) return;
+        if (s.trace && lead) {
+            const unsigned long long t3 = global_ns();
+            trace_add(c, TR_RELAYOUT, t2, t3);
+            t2 = t3;
+        }
+    }
+    if (s.log_on) log_pass(s, pos, step);
+    if (Tail::kActive) {
+        tail(blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+        if (s.trace) {
+            if (!grid_barrier(s)) return;
+            if (lead) trace_add(c, TR_TAIL, t2, global_ns());
+        }
+    }
+}
+
+}  // namespace lvb

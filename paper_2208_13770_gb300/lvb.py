@@ -23,7 +23,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 LVB_OK, LVB_EINVAL, LVB_ENOMEM, LVB_ECAPACITY, LVB_EDEVICE, LVB_ENAN, LVB_EOVERFLOW, \
-    LVB_ESTATE, LVB_ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7, -8
+    LVB_ESTATE, LVB_ELIMIT, LVB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 LVB_NOALLOC_MAX_N = 65536
 LVB_SKIN_GLOBAL, LVB_SKIN_DIAMETER_FACTOR, LVB_SKIN_PAPER_KVDT, LVB_SKIN_LEARNED = 0, 1, 2, 3
 LVB_TRIGGER_PARTIAL, LVB_TRIGGER_GLOBAL, LVB_TRIGGER_ALWAYS = 0, 1, 2
@@ -42,9 +42,9 @@ class lvb_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("n", "steps", "rebuild_steps", "flagged_total", "updated_total", "last_flagged",
                  "entries", "pairs", "relayouts", "grows", "cell_capacity", "row_store_capacity",
-                 "kernels_executed", "small_path_steps", "small_max", "medium_max", "graphs",
+                 "kernels_executed", "barriers", "step_blocks", "block_threads", "compaction",
                  "n_scenes")] + \
-               [("fused_phase_cycles", ctypes.c_int64 * 4)] + \
+               [("reserved", ctypes.c_int64 * 4)] + \
                [("cell_edge", ctypes.c_float), ("rnl_max", ctypes.c_float),
                 ("grid", ctypes.c_int32 * 3), ("pad", ctypes.c_int32)]
 
@@ -183,10 +183,9 @@ def lvb_step(ctx, pos_r, vel=None, acc=None):
     return _lib.lvb_step(ctx, pos_r, vel, acc)
 
 
-LVB_OPT_GRAPH, LVB_OPT_SMALL_MAX, LVB_OPT_MEDIUM_MAX, LVB_OPT_TRACE, LVB_OPT_CHECK_THREADS = \
-    0, 1, 2, 3, 4
-TRACE_SLOTS = ["check", "one_block", "inc_rows", "inc_append", "rows", "relayout", "integrate",
-               "forces"]
+LVB_OPT_TRACE, LVB_OPT_BLOCK_THREADS, LVB_OPT_COMPACT = 3, 4, 5
+LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
+TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]
 
 
 def lvb_trace(ctx, sum_ns, count):
@@ -453,7 +452,7 @@ class LVB:
     def stats(self):
         st = lvb_stats_t()
         _check(lvb_stats(self.ctx, ctypes.byref(st)), "lvb_stats")
-        return {k: (list(getattr(st, k)) if k in ("grid", "fused_phase_cycles") else getattr(st, k))
+        return {k: (list(getattr(st, k)) if k in ("grid", "reserved") else getattr(st, k))
                 for k, _ in lvb_stats_t._fields_ if k != "pad"}
 
     def close(self):

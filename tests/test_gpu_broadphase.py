@@ -108,27 +108,22 @@ def test_ballistic_paper_rule_parity(orc):
     _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 600), 0, 2, 200.0, every=2)
 
 
-@pytest.mark.parametrize("path", ["auto", "one_block", "medium_grid", "big_grid", "direct"])
-def test_hot_gas_many_rebuilds_parity(orc, path):
-    # fast particles: many flags, cell moves and row changes per step, through
-    # each way a step can run: graph with the automatic choice, graph forced
-    # to the one-block rest of the rebuild, to the grid-wide passes on the
-    # medium grid, on the big grid, and direct launches without a graph
+SHAPES = [(1024, 0), (1024, 1), (512, 0), (256, 1)]
+
+
+@pytest.mark.parametrize("threads,compact", SHAPES)
+def test_hot_gas_many_rebuilds_parity(orc, threads, compact):
+    # fast particles: many flags, cell moves and row changes per step, with
+    # every launch shape of the step kernel (block size; flag compaction
+    # per warp chunk or per block tile)
     lvb = _cuda()
-    opts = {"auto": (), "one_block": ((lvb.LVB_OPT_SMALL_MAX, 1 << 30),),
-            "medium_grid": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 1 << 30)),
-            "big_grid": ((lvb.LVB_OPT_SMALL_MAX, 0), (lvb.LVB_OPT_MEDIUM_MAX, 0)),
-            "direct": ((lvb.LVB_OPT_GRAPH, 0),)}[path]
+    opts = ((lvb.LVB_OPT_BLOCK_THREADS, threads), (lvb.LVB_OPT_COMPACT, compact))
     s = scenes.ballistic(n=3000, seed=5, phi=0.3, vsigma=3.0)
     st, _ = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 150), 0, 1, 0.1,
                             options=opts)
     assert st["updated_total"] > s.n
-    if path == "one_block":      # every step with at most 1024 flagged
-        assert st["small_path_steps"] > 0 and st["small_max"] == 1024
-    if path in ("medium_grid", "big_grid"):
-        assert st["small_path_steps"] == 0
-    if path == "direct":
-        assert st["graphs"] == 0
+    assert st["block_threads"] == threads and st["compaction"] == compact
+    assert st["barriers"] >= st["steps"]
 
 
 def _random_walk(scene, steps, sigma, seed=0):
@@ -189,8 +184,8 @@ def test_static_particles_never_flag(orc):
     ctx.close()
 
 
-@pytest.mark.parametrize("small_max,medium_max", [(32, 2048), (0, 2048), (0, 0)])
-def test_relayout_when_rows_grow(orc, small_max, medium_max):
+@pytest.mark.parametrize("threads,compact", [(1024, 0), (256, 1)])
+def test_relayout_when_rows_grow(orc, threads, compact):
     # contract the cloud towards its centre: rows grow past their slack and
     # the row store is re-laid out on the device; parity must hold throughout
     lvb = _cuda()
@@ -204,8 +199,8 @@ def test_relayout_when_rows_grow(orc, small_max, medium_max):
             yield pos.copy(), s.vel
 
     st, _ = _run_trajectory(orc, s, shrink(60), 0, 1, 0.1,
-                            options=((lvb.LVB_OPT_SMALL_MAX, small_max),
-                                     (lvb.LVB_OPT_MEDIUM_MAX, medium_max)))
+                            options=((lvb.LVB_OPT_BLOCK_THREADS, threads),
+                                     (lvb.LVB_OPT_COMPACT, compact)))
     assert st["relayouts"] > 0
 
 
@@ -244,12 +239,13 @@ def test_store_growth_keeps_parity(orc):
     ctx.close()
 
 
-def test_global_and_always_direct_launches(orc):
+@pytest.mark.parametrize("threads", [1024, 256])
+def test_global_and_always_small_blocks(orc, threads):
     lvb = _cuda()
     s = scenes.ballistic(n=1500, seed=12, vsigma=1.0)
     for trig in (1, 2):
         _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 40), trig, 1, 0.1,
-                        options=((lvb.LVB_OPT_GRAPH, 0),))
+                        options=((lvb.LVB_OPT_BLOCK_THREADS, threads),))
 
 
 def test_resume_from_saved_reference(orc):
