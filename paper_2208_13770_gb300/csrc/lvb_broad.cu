@@ -132,7 +132,7 @@ k_rows(DevState s, int gate, int fill)
     if (!nitems) return;
     count_kernel(s);
     tr_enter(s, TR_ROWS);
-    ph_rows(s, nitems, false, fill, (blockIdx.x * kThreads + threadIdx.x) >> 5,
+    ph_rows(s, nitems, fill, (blockIdx.x * kThreads + threadIdx.x) >> 5,
             (gridDim.x * kThreads) >> 5, &s.cnt->row_overflow);
     tr_exit(s, TR_ROWS);
 }
@@ -285,11 +285,14 @@ __global__ void k_max_int(const int *v, long long n, int *out)
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-__global__ void k_sum_int(const int *v, int n, unsigned long long *out)
+// Live entries of the list (rows hold -1 where a pair was removed).
+__global__ void k_count_live(DevState s, unsigned long long *out)
 {
     unsigned long long m = 0;
-    for (int c = blockIdx.x * kThreads + threadIdx.x; c < n; c += gridDim.x * kThreads)
-        m += (unsigned)v[c];
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < s.n; i += gridDim.x * kThreads) {
+        const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
+        for (int e = 0; e < len; ++e) m += s.col[off + e] >= 0 ? 1u : 0u;
+    }
     for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(FULL, m, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(out, m);
 }
@@ -302,6 +305,7 @@ __global__ void k_sum_int(const int *v, int n, unsigned long long *out)
 __device__ __forceinline__ bool ex_keep(const DevState &s, int mode, int i, int j,
                                         const float4 *pos, float4 pi, float *dl)
 {
+    if (j < 0) return false;   // a removed pair's slot
     if (mode == 0) return true;
     if (j <= i) return false;
     if (mode == 1) return true;
@@ -409,8 +413,8 @@ cudaError_t dalloc(T **p, long long count)
 void free_all(lvb_ctx *c)
 {
     DevState &s = c->s;
-    void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.prevcell, s.bits, s.fid, s.row_off,
-                    s.row_len, s.row_cap, s.col, s.trow, s.trow_mark, s.cell_cnt, s.cell_id,
+    void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.fref, s.oref, s.bits, s.fid, s.row_off,
+                    s.row_len, s.row_cap, s.col, s.cell_cnt, s.cell_id,
                     s.cell_ref, s.cnt, s.blk, c->ex_cnt, c->ex_off, c->ex_i, c->ex_j, c->ex_d,
                     c->scratch, c->sum64, c->sg_d, c->scene_of_d, s.born, s.cell_live,
                     s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf};
@@ -771,14 +775,13 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (e == cudaSuccess) e = dalloc(&s.rad, n);
     if (e == cudaSuccess) e = dalloc(&s.cell_of, n);
     if (e == cudaSuccess) e = dalloc(&s.slot_of, n);
-    if (e == cudaSuccess) e = dalloc(&s.prevcell, n);
+    if (e == cudaSuccess) e = dalloc(&s.fref, n);
+    if (e == cudaSuccess) e = dalloc(&s.oref, n);
     if (e == cudaSuccess) e = dalloc(&s.bits, c->nwords);
     if (e == cudaSuccess) e = dalloc(&s.fid, n);
     if (e == cudaSuccess) e = dalloc(&s.row_off, n);
     if (e == cudaSuccess) e = dalloc(&s.row_len, n);
     if (e == cudaSuccess) e = dalloc(&s.row_cap, n);
-    if (e == cudaSuccess) e = dalloc(&s.trow, n);
-    if (e == cudaSuccess) e = dalloc(&s.trow_mark, n);
     if (e == cudaSuccess) e = dalloc(&s.cell_cnt, ncells);
     if (e == cudaSuccess) e = dalloc(&s.cell_live, ncells);
     if (e == cudaSuccess) e = dalloc(&s.born, n);
@@ -787,7 +790,6 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     // re-layout one per block (at most 4 per SM)
     if (e == cudaSuccess) e = dalloc(&s.blk, std::max<long long>(c->nblk + 1, 4096));
     if (e != cudaSuccess) return fail(from_cuda(e));
-    cudaMemsetAsync(s.trow_mark, 0, sizeof(int) * n, st);
     cudaMemsetAsync(s.born, 0, sizeof(int) * n, st);
     cudaMemsetAsync(s.cell_live, 0, sizeof(int) * ncells, st);
     cudaMemsetAsync(s.cnt, 0, sizeof(DevCounters), st);
@@ -1114,7 +1116,7 @@ int lvb_stats(lvb_ctx *c, lvb_stats_t *o)
     int rc = sync_counters(c);
     if (rc) return rc;
     cudaMemsetAsync(c->sum64, 0, sizeof(unsigned long long), c->stream);
-    k_sum_int<<<items_grid(c), kThreads, 0, c->stream>>>(c->s.row_len, (int)c->n, c->sum64);
+    k_count_live<<<items_grid(c), kThreads, 0, c->stream>>>(c->s, c->sum64);
     unsigned long long entries = 0;
     cudaError_t e = cudaMemcpyAsync(&entries, c->sum64, sizeof(entries), cudaMemcpyDeviceToHost,
                                     c->stream);

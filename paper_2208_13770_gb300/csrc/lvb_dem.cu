@@ -146,6 +146,7 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
         const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
         for (int e = 0; e < len; ++e) {
             const int j = d.rows.col[off + e];
+            if (j < 0) continue;            // a removed pair's slot
             const float4 xj = d.pos[j];
             float h[3], l[3];
             two_diff(xi.x, xj.x, h[0], l[0]);

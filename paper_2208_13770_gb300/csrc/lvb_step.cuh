@@ -3,22 +3,24 @@
 // One step of the local Verlet buffer is one cooperative kernel, k_step,
 // whose phases are separated by grid-wide barriers (all its blocks are
 // co-resident: cooperative launch, grid sized by occupancy):
+//   re-layout  first, only if the previous step left a row overflowed
 //   check      every particle: displacement check (Eq. update), ballot
 //              words, compaction of the flagged ids; with the PARTIAL
-//              trigger the warp that flags a particle also gives it its new
+//              trigger the warp that flags a particle also computes its new
 //              reference state and skin (Eq. skin_formulus1 or another
-//              policy, capped per Eq. skin_formulus_mincell), moves it to
-//              its new cell slot and queues the rows that listed it
+//              policy, capped per Eq. skin_formulus_mincell)
 //   -- barrier --
-//   rebuild    PARTIAL: rows of the flagged particles by the 27-cell stencil
-//              (Algorithm 1 on the extended spheres, Eq. bounding_sphere)
-//              and removal of the flagged entries from the queued rows;
-//              -- barrier -- insertion of each flagged particle into its
-//              unflagged partners' rows; -- barrier --
+//   rebuild    PARTIAL: each flagged particle moves to its new cell slot,
+//              gets its new row by the 27-cell stencil (Algorithm 1 on the
+//              extended spheres, Eq. bounding_sphere) plus a direct test
+//              against the other flagged particles, and patches the rows of
+//              its unflagged partners in place (removed pairs become -1,
+//              new pairs take a -1 slot or the row's end) -- one phase, no
+//              barrier (many flagged particles: moves first, then a barrier)
 //              GLOBAL / ALWAYS (Def. autoverlet / no buffer): new reference
 //              states, cells and rows of every particle
-//   re-layout  only when a row outgrew its slack: count, scan, fill
-//   tail       the DEM driver's forces (k_step instantiated by lvb_dem.cu)
+//   tail       the DEM driver's forces (k_step instantiated by lvb_dem.cu),
+//              after a barrier and the re-layout of overflowed rows
 // A step with nothing flagged is the check and one barrier.  The kernel is
 // included by lvb_broad.cu (the broad phase alone) and lvb_dem.cu (a whole
 // DEM step per launch).
@@ -30,6 +32,7 @@ namespace lvb {
 
 constexpr int kStepMaxThreads = 1024;     // block size limit of k_step (one block per SM)
 constexpr int kCheckUnroll = 2;           // 32-particle chunks a warp has in flight
+constexpr int kFlaggedDirectMax = 4096;   // flagged particles tested pairwise directly
 constexpr unsigned kBarrierSpins = 1u << 22;   // ~1-3 s of polling (L2 round trips) before a barrier gives up
 
 // Written by kernels straight into mapped host memory: requests to grow a
@@ -50,12 +53,15 @@ struct DevState {
     float4 *ref;
     float *rad;
     int *cell_of, *slot_of;
-    int *prevcell;    // cell of each flagged particle before its update
     uint32_t *bits;
-    int *fid;
+    int *fid;         // flagged ids of the step, in compaction order
+    float4 *fref;     // their new (xref, R_NL), same order
+    float4 *oref;     // their old (xref, R_NL), same order
+    // rows: row i is col[row_off[i], row_off[i] + row_cap[i]); entries below
+    // row_len[i] are partners or -1 (a removed pair), entries at or above
+    // it are -1; row_len[i] > row_cap[i] means the row overflowed
     int *row_off, *row_len, *row_cap, *col;
     long long col_cap;
-    int *trow, *trow_mark;
     int *cell_cnt, *cell_id;
     float4 *cell_ref;
     DevCounters *cnt;
@@ -164,88 +170,82 @@ __device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g
 }
 
 
-// a2 + a3 for one flagged particle i, run inside the step kernel's check
-// pass by the warp that flagged it (PARTIAL trigger):
-//   * new reference position and skin (the policy's features come from the
-//     state before the update; `step` is the number of the step being taken);
-//   * its cell slot: a stayer refreshes the slot's copy of the reference
-//     state; a leaver leaves a tombstone (-1) in its old slot and takes a
-//     tombstone slot of its new cell (claimed with compare-and-swap) or a
-//     fresh one at the end.  Slots of unflagged particles never change, so
-//     after the check every cell holds the step's final reference states;
-//   * every partner j of its old row is queued (once) for the removal of
-//     the flagged entries; whether j is flagged itself is only known after
-//     the check, so the removal pass skips flagged rows;
-//   * the occupancy counts of the cells (a feature of the skin network) are
-//     left as they were before the step: the rows pass moves the counts
-//     after the check, from the old cell kept in prevcell[i].
-// (pos and vel may have been written earlier in the same kernel by the DEM
-// position half-step, so they are read through plain coherent loads.)
-// Not inlined: it runs only for flagged particles, and as a call it keeps
-// the check loop's registers free of its working set.
-static __device__ __noinline__ void update_move_warp(const DevState &s, int i, const float4 *pos,
-                                                 const float4 *vel, const float4 *acc, int step,
-                                                 int *ovf)
+// Live partners of row i (entries >= 0), counted by the warp.
+__device__ __forceinline__ int row_live_warp(const DevState &s, int i)
 {
     const int lane = threadIdx.x & 31;
-    const int ccap = s.ccap;
+    const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
+    int c = 0;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        c += __popc(__ballot_sync(FULL, e < len && s.col[off + e] >= 0));
+    }
+    return c;
+}
+
+// a2 for flagged particle i, run by the warp that flagged it inside the
+// check pass (PARTIAL trigger): new reference position and skin (the
+// policy's features come from the state before the update; `step` is the
+// number of the step being taken), kept with the old state at index k of
+// the flagged list.  (pos and vel may have been written earlier in the same
+// kernel by the DEM position half-step, so they are read through plain
+// coherent loads.)  Not inlined: it runs only for flagged particles, and as
+// a call it keeps the check loop's registers free of its working set.
+static __device__ __noinline__ void update_warp(const DevState &s, int i, int k, const float4 *pos,
+                                                const float4 *vel, const float4 *acc, int step)
+{
+    const int lane = threadIdx.x & 31;
     const float4 p = pos[i];
     const float r = s.rad[i];
     const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int oc = s.cell_of[i], so = s.slot_of[i];
-    const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
+    const float4 q = s.ref[i];
     const SceneGeom &g = geom_of(s, i);
-    const int nc = cell_key(g, p.x, p.y, p.z);
-    // issued now, used below: the new cell's slot count and the first 32
-    // partners of the old row (their latency overlaps the skin policy)
-    const int cn0 = nc != oc ? s.cell_cnt[nc] : 0;
-    const int j0 = lane < len ? s.col[off + lane] : -1;
     float f[LVB_MLP_IN];
     if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
         const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        skin_features(s, p, v, a, r, g, s.ref[i], len, step - s.born[i], s.cell_live[nc], f);
+        const int nc = cell_key(g, p.x, p.y, p.z);
+        skin_features(s, p, v, a, r, g, q, row_live_warp(s, i), step - s.born[i],
+                      s.cell_live[nc], f);
     }
     const float sk = warp_skin(s, g, r, v, f);
-    const float4 cr = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
     if (lane == 0) {
         s.ref[i] = make_float4(p.x, p.y, p.z, sk);
         s.born[i] = step;
-        s.prevcell[i] = oc;
+        s.fref[k] = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+        s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
         if (s.log_on && s.lg_t[i] < 0) {
             s.lg_t[i] = step;
             s.lg_x[i] = p;
             s.lg_m[i] = 0.0f;
 #pragma unroll
-            for (int q = 0; q < LVB_MLP_IN; ++q) s.lg_feat[(long long)i * LVB_MLP_IN + q] = f[q];
+            for (int t = 0; t < LVB_MLP_IN; ++t) s.lg_feat[(long long)i * LVB_MLP_IN + t] = f[t];
         }
     }
-    // old partners: queue their rows for the removal pass.  Queue slots are
-    // reserved for every partner at once (one atomic, issued together with
-    // the marks); a partner already queued leaves -1 in its slot.  The queue
-    // holds n slots; reservations beyond it raise the row-overflow flag, and
-    // the re-layout then rebuilds every row from the cells (and clears the
-    // marks).
-    for (int e0 = 0; e0 < len; e0 += 32) {
-        const int e = e0 + lane;
-        const int j = e0 == 0 ? j0 : (e < len ? s.col[off + e] : -1);
-        const unsigned m = __ballot_sync(FULL, e < len);
-        int q = 0;
-        if (lane == 0) q = atomicAdd(&s.cnt->ntrow, __popc(m));
-        const bool push = e < len && atomicExch(&s.trow_mark[j], 1) == 0;
-        q = __shfl_sync(FULL, q, 0) + __popc(m & lanemask_lt());
-        if (e < len) {
-            if (q < s.n) s.trow[q] = push ? j : -1;
-            else atomicExch(ovf, 1);
-        }
-    }
-    // cell slot
+}
+
+// a3 for flagged particle i (warp), qn its new (xref, R_NL): a stayer
+// refreshes its slot's copy of the reference state; a leaver leaves a
+// tombstone (-1) in its old slot and takes a tombstone slot of its new cell
+// (compare-and-swap) or a fresh one at the end; the cells' live counts
+// follow.  Slots of unflagged particles never change.
+__device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
+{
+    const int lane = threadIdx.x & 31;
+    const int ccap = s.ccap;
+    const SceneGeom &g = geom_of(s, i);
+    const int nc = cell_key(g, qn.x, qn.y, qn.z);
+    const int oc = s.cell_of[i], so = s.slot_of[i];
     if (nc == oc) {
-        if (lane == 0) s.cell_ref[(long long)oc * ccap + so] = cr;
+        if (lane == 0) s.cell_ref[(long long)oc * ccap + so] = qn;
         return;
     }
-    if (lane == 0) s.cell_id[(long long)oc * ccap + so] = -1;
+    if (lane == 0) {
+        s.cell_id[(long long)oc * ccap + so] = -1;
+        atomicSub(&s.cell_live[oc], 1);
+        atomicAdd(&s.cell_live[nc], 1);
+    }
     const long long base = (long long)nc * ccap;
-    const int cn = min(cn0, ccap);
+    const int cn = min(s.cell_cnt[nc], ccap);
     int slot = -1;
     for (int e0 = 0; e0 < cn && slot < 0; e0 += 32) {
         const int sl = e0 + lane;
@@ -267,91 +267,185 @@ static __device__ __noinline__ void update_move_warp(const DevState &s, int i, c
             else atomicOr(&s.cnt->err, DERR_CELL);
         }
         if (slot < ccap) {
-            s.cell_ref[base + slot] = cr;
+            s.cell_ref[base + slot] = qn;
             s.slot_of[i] = slot;
         }
         s.cell_of[i] = nc;
     }
+    __syncwarp();
 }
 
-// Occupancy counts of the cells a flagged particle left and entered.
-__device__ __forceinline__ void move_live_count(const DevState &s, int i)
+// Removes partner i from unflagged row j (warp): its entry becomes -1.
+__device__ __forceinline__ void row_remove_warp(const DevState &s, int j, int i)
 {
-    const int oc = s.prevcell[i], nc = s.cell_of[i];
-    if (oc != nc) {
-        atomicSub(&s.cell_live[oc], 1);
-        atomicAdd(&s.cell_live[nc], 1);
+    const int lane = threadIdx.x & 31;
+    const int off = s.row_off[j], len = min(s.row_len[j], s.row_cap[j]);
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        const bool hit = e < len && s.col[off + e] == i;
+        if (hit) s.col[off + e] = -1;
+        if (__any_sync(FULL, hit)) return;
     }
 }
 
-// a5 (removal): each queued unflagged row drops its flagged entries.  Rows
-// are short, so a warp takes four rows at a time, eight lanes each (stable
-// in-place compaction: every lane reads its entry before the ballot, and an
-// entry only moves to a lower index).  A queued row that is flagged itself
-// is rebuilt by the rows pass and only loses its queue mark here; -1
-// entries are reserved slots that a duplicate left empty.  `w0` and
-// `wstride` count warps.
-__device__ __forceinline__ void compact_rows(const DevState &s, int w0, int wstride)
+// Adds partner i to unflagged row j (warp): a -1 entry below row_len,
+// claimed with compare-and-swap, else the next slot at the end (also by
+// compare-and-swap: a slot past row_len holds -1 and another warp's search
+// may claim it first).  A full row raises *ovf (the re-layout rebuilds it).
+__device__ __forceinline__ void row_insert_warp(const DevState &s, int j, int i, int *ovf)
 {
-    const int lane = threadIdx.x & 31, sub = lane >> 3, l8 = lane & 7;
-    const unsigned below = lanemask_lt() & (0xFFu << (sub * 8));
-    const int ntrow = min(s.cnt->ntrow, s.n);
-    for (int k0 = w0 * 4; k0 < ntrow; k0 += wstride * 4) {
-        const int k = k0 + sub;
-        int j = -1, off = 0, len = 0;
-        bool act = k < ntrow;
-        if (act) {
-            j = s.trow[k];
-            if (j < 0) {
-                act = false;            // a duplicate's reserved slot
-            } else if (bit_of(s.bits, j)) {
-                act = false;
-                if (l8 == 0) s.trow_mark[j] = 0;
-            } else {
-                off = s.row_off[j];
-                len = min(s.row_len[j], s.row_cap[j]);
+    const int lane = threadIdx.x & 31;
+    const int off = s.row_off[j], cap = s.row_cap[j], len = min(s.row_len[j], cap);
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        unsigned m = __ballot_sync(FULL, e < len && s.col[off + e] < 0);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            int won = 0;
+            if (lane == src) won = atomicCAS(&s.col[off + e], -1, i) == -1;
+            if (__shfl_sync(FULL, won, src)) return;
+            m &= m - 1;
+        }
+    }
+    if (lane == 0) {
+        for (int t = 0; t <= cap; ++t) {
+            const int p = atomicAdd(&s.row_len[j], 1);
+            if (p >= cap) {
+                atomicExch(ovf, 1);
+                break;
+            }
+            if (atomicCAS(&s.col[off + p], -1, i) == -1) break;
+        }
+    }
+    __syncwarp();
+}
+
+// a4 + a5 for flagged particle k of the list (warp), i = fid[k]:
+//   1. each old partner j that is unflagged and no longer a pair (test on
+//      i's new reference state) loses i from its row;
+//   2. the new row of i: the 27-cell stencil around its new cell over the
+//      cells' reference states.  direct: the moves of the flagged particles
+//      run at the same time, so flagged particles found in the cells are
+//      skipped and the flagged partners come from a direct test against the
+//      flagged list; otherwise the cells are final and hold everyone;
+//   3. each new partner j that is unflagged and was not a pair before (test
+//      on i's old reference state) gets i in its row.
+// A pair is a function of the two reference states (Def. verletlist) and an
+// unflagged particle's state does not change, so these tests decide exactly
+// which entries of the unflagged rows change; no other warp touches row i.
+static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF, bool direct,
+                                               int *ovf)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int ccap = s.ccap;
+    const int i = s.fid[k];
+    const float4 qn = s.fref[k], qo = s.oref[k];
+    const int off = s.row_off[i], cap = s.row_cap[i], len0 = min(s.row_len[i], cap);
+    // the stencil's cell counts first: their loads overlap the removals
+    const SceneGeom &g = geom_of(s, i);
+    const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
+    const int ci = cell_key(g, qn.x, qn.y, qn.z) - g.cell_base;
+    const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
+    int cnt_l = 0, cid = 0;
+    if (lane < 27) {
+        const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+        if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+            cid = g.cell_base + (z * d1 + y) * d0 + x;
+            cnt_l = s.cell_cnt[cid];
+        }
+    }
+    // 1. removals
+    for (int e0 = 0; e0 < len0; e0 += 32) {
+        const int e = e0 + lane;
+        int j = -1;
+        bool rm = false;
+        if (e < len0) {
+            j = s.col[off + e];
+            if (j >= 0 && !bit_of(s.bits, j)) {
+                const float4 rj = s.ref[j];
+                rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
             }
         }
-        int mx = len;
+        for (unsigned m = __ballot_sync(FULL, rm); m; m &= m - 1)
+            row_remove_warp(s, __shfl_sync(FULL, j, __ffs(m) - 1), i);
+    }
+    // 2. stencil (+ direct test) and 3. insertions
+    cnt_l = min(cnt_l, ccap);
+    const int incl = warp_incl_scan(cnt_l);
+    const int excl = incl - cnt_l;
+    const int total = __shfl_sync(FULL, incl, 31);
+    int found = 0;
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const int kk = b0 + lane;
+        int c = 0;
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-        int w = 0;
-        for (int e0 = 0; e0 < mx; e0 += 8) {
-            const int e = e0 + l8;
-            int c = 0;
-            bool keep = false;
-            if (act && e < len) {
-                c = s.col[off + e];
-                keep = !bit_of(s.bits, c);
+        for (int st = 16; st >= 1; st >>= 1)
+            c += (__shfl_sync(FULL, incl, c + st - 1) <= kk) ? st : 0;
+        const int cc = __shfl_sync(FULL, cid, c);
+        const int ex = __shfl_sync(FULL, excl, c);
+        bool hit = false, ins = false;
+        int j = -1;
+        if (kk < total) {
+            const long long idx = (long long)cc * ccap + (kk - ex);
+            j = s.cell_id[idx];
+            if (j >= 0 && j != i) {
+                const bool fj = bit_of(s.bits, j);
+                if (!(direct && fj)) {
+                    const float4 rj = s.cell_ref[idx];
+                    hit = pair_hit(qn, rj);
+                    ins = hit && !fj && !pair_hit(qo, rj);
+                }
             }
-            const unsigned m = __ballot_sync(FULL, keep);
-            if (keep) s.col[off + w + __popc(m & below)] = c;
-            w += __popc((m >> (sub * 8)) & 0xFFu);
         }
-        if (act && l8 == 0) {
-            s.row_len[j] = w;
-            s.trow_mark[j] = 0;
+        const unsigned m = __ballot_sync(FULL, hit);
+        if (hit) {
+            const int p = found + __popc(m & lt);
+            if (p < cap) s.col[off + p] = j;
         }
+        found += __popc(m);
+        for (unsigned mi = __ballot_sync(FULL, ins); mi; mi &= mi - 1)
+            row_insert_warp(s, __shfl_sync(FULL, j, __ffs(mi) - 1), i, ovf);
+    }
+    if (direct) {
+        for (int b0 = 0; b0 < nF; b0 += 32) {
+            const int kk = b0 + lane;
+            bool hit = false;
+            int j = -1;
+            if (kk < nF && kk != k) {
+                j = s.fid[kk];
+                hit = pair_hit(qn, s.fref[kk]);
+            }
+            const unsigned m = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int p = found + __popc(m & lt);
+                if (p < cap) s.col[off + p] = j;
+            }
+            found += __popc(m);
+        }
+    }
+    for (int e = found + lane; e < len0; e += 32) s.col[off + e] = -1;
+    if (lane == 0) {
+        s.row_len[i] = found;
+        if (found > cap) atomicExch(ovf, 1);
     }
 }
 
-// a4: rows by the 27-cell stencil, one warp per row.  Lanes 0..26 each own
+// a4: rows of every particle by the 27-cell stencil, one warp per row
+// (init, store growth, re-layout, GLOBAL / ALWAYS).  Lanes 0..26 each own
 // one neighbour cell; a warp scan of their occupancies flattens the
 // candidates, and every lane finds its candidate's cell with a 5-step
 // shuffle binary search, so lanes stay busy across cell boundaries.
 // fill = 0 counts only (row_len = count); fill = 1 also writes up to the
-// row's capacity and raises *ovf if the row does not fit.
-// Items are fid[w] when `from_list`, else particle w.  Cell slots holding a
-// tombstone (id < 0) are skipped.  The cells must hold the step's final
-// reference states (after the check kernel's moves, or a full re-bin).
-__device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from_list, int fill,
-                                        int w0, int wstride, int *ovf)
+// row's capacity, clears the rest of the row to -1 and raises *ovf if the
+// row does not fit.  The cells must hold the final reference states.
+__device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill, int w0,
+                                        int wstride, int *ovf)
 {
     const int lane = threadIdx.x & 31;
     const int ccap = s.ccap;
     const unsigned lt = lanemask_lt();
-    for (int w = w0; w < nitems; w += wstride) {
-        const int i = from_list ? s.fid[w] : w;
+    for (int i = w0; i < nitems; i += wstride) {
         const SceneGeom &g = geom_of(s, i);
         const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
         const float4 q = s.ref[i];
@@ -376,8 +470,8 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
             const int k = b0 + lane;
             int c = 0;
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1)
-                c += (__shfl_sync(FULL, incl, c + step - 1) <= k) ? step : 0;
+            for (int st = 16; st >= 1; st >>= 1)
+                c += (__shfl_sync(FULL, incl, c + st - 1) <= k) ? st : 0;
             const int cc = __shfl_sync(FULL, cid, c);
             const int ex = __shfl_sync(FULL, excl, c);
             bool hit = false;
@@ -394,30 +488,11 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, bool from
             }
             found += __popc(m);
         }
+        if (fill)
+            for (int e = found + lane; e < cap; e += 32) s.col[off + e] = -1;
         if (lane == 0) {
             s.row_len[i] = found;
             if (fill && found > cap) atomicExch(ovf, 1);
-        }
-    }
-}
-
-// a5 (insertion): flagged i joins the row of each unflagged partner; one
-// warp per flagged particle, one lane per partner.  Runs after the removal
-// pass, so a pair that survives the update is removed and re-added once.
-__device__ __forceinline__ void ph_append(const DevState &s, int nF, int w0, int wstride, int *ovf)
-{
-    const int lane = threadIdx.x & 31;
-    for (int k = w0; k < nF; k += wstride) {
-        const int i = s.fid[k];
-        const int len = s.row_len[i];
-        if (len > s.row_cap[i]) continue;     // re-layout rebuilds everything
-        const int off = s.row_off[i];
-        for (int e = lane; e < len; e += 32) {
-            const int j = s.col[off + e];
-            if (bit_of(s.bits, j)) continue;  // j's own new row lists i
-            const int p = atomicAdd(&s.row_len[j], 1);
-            if (p < s.row_cap[j]) s.col[s.row_off[j] + p] = i;
-            else atomicExch(ovf, 1);
         }
     }
 }
@@ -513,19 +588,20 @@ __device__ __forceinline__ long long block_scan_any(long long v, long long *tota
 }
 
 // ---------------------------------------------------------------------------
-// a1 (+ a2, a3 with the PARTIAL trigger): the check pass.  Block b takes
+// a1 (+ a2 with the PARTIAL trigger): the check pass.  Block b takes
 // tiles b, b + grid, ... of blockDim * kCheckUnroll particles; in a tile each
 // warp checks kCheckUnroll chunks of 32 consecutive particles (loads of all
 // chunks first, so several are in flight), writes one ballot word per chunk
 // and compacts the flagged ids, either with one atomic per chunk that has
 // flags (warp scheme) or with one per tile (block scheme, two barriers per
-// tile that has flags).  The warp then updates the particles it flagged.
+// tile that has flags).  The warp then computes the new reference states of
+// the particles it flagged (update_warp).
 // ---------------------------------------------------------------------------
 template <bool kFused>
 __device__ __forceinline__ void check_pass(const DevState &s, const float4 *__restrict__ pos_in,
                                            const float4 *vel, const float4 *acc,
                                            const IntegrateArgs &ia, bool inc, int step,
-                                           int *nF_acc, int *ovf)
+                                           int *nF_acc)
 {
     __shared__ int s_cnt[32];
     __shared__ int s_base;
@@ -582,8 +658,10 @@ __device__ __forceinline__ void check_pass(const DevState &s, const float4 *__re
             k0 = __shfl_sync(FULL, k0, 0);
         }
         if (!cnt) continue;
+        int kb[kCheckUnroll];
 #pragma unroll
         for (int u = 0; u < kCheckUnroll; ++u) {
+            kb[u] = k0;
             if (b[u] >> lane & 1u) s.fid[k0 + __popc(b[u] & lt)] = t0 + u * blockDim.x + warp * 32 + lane;
             k0 += __popc(b[u]);
         }
@@ -593,31 +671,15 @@ __device__ __forceinline__ void check_pass(const DevState &s, const float4 *__re
             __syncwarp();
 #pragma unroll
             for (int u = 0; u < kCheckUnroll; ++u)
-                for (unsigned m = b[u]; m; m &= m - 1)
-                    update_move_warp(s, t0 + u * blockDim.x + warp * 32 + __ffs(m) - 1, pos, vel,
-                                     acc, step, ovf);
+                for (unsigned m = b[u]; m; m &= m - 1) {
+                    const int src = __ffs(m) - 1;
+                    update_warp(s, t0 + u * blockDim.x + warp * 32 + src,
+                                kb[u] + __popc(b[u] & ((1u << src) - 1u)), pos, vel, acc, step);
+                }
         }
     }
 }
 
-// a4 + a5 (removal) of a partial rebuild, then (after a barrier) a5
-// (insertion); w0 / nw count warps of the grid, t / nt threads.
-static __device__ __noinline__ void partial_rows_pass(const DevState &s, int nF, int *ovf)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    ph_rows(s, nF, true, 1, t >> 5, nt >> 5, ovf);
-    compact_rows(s, t >> 5, nt >> 5);
-    for (int k = t; k < nF; k += nt) move_live_count(s, s.fid[k]);
-}
-
-static __device__ __noinline__ void partial_append_pass(const DevState &s, int nF, int *ovf)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    ph_append(s, nF, t >> 5, nt >> 5, ovf);
-}
-
-// GLOBAL / ALWAYS: new reference state of every particle (the learned
-// policy needs the partial trigger), and cleared cells.
 static __device__ __noinline__ void full_update_pass(const DevState &s, const float4 *pos,
                                               const float4 *vel)
 {
@@ -659,7 +721,7 @@ static __device__ __noinline__ void full_insert_pass(const DevState &s)
 static __device__ __noinline__ void all_rows_pass(const DevState &s, int fill, int *ovf)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    ph_rows(s, s.n, false, fill, t >> 5, nt >> 5, ovf);
+    ph_rows(s, s.n, fill, t >> 5, nt >> 5, ovf);
 }
 
 // Re-layout of the row store after a row outgrew its slack: rows counted
@@ -670,8 +732,6 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
 {
     DevCounters *c = s.cnt;
     all_rows_pass(s, 0, nullptr);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x)
-        s.trow_mark[i] = 0;   // queue marks left by an overflowed queue
     if (!grid_barrier(s)) return false;
     const long long per = ((long long)s.n + gridDim.x - 1) / gridDim.x;
     const int lo = (int)min((long long)s.n, blockIdx.x * per);
@@ -769,12 +829,38 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
     c->tr_cnt[slot] += 1;
 }
 
+
+// The rebuild of a partial step (nF flagged).  Up to kFlaggedDirectMax
+// flagged particles: moves and patches in one phase, on different warps
+// (work items 0..nF-1 patch rows, nF..2nF-1 move cell slots; the patches
+// skip the flagged particles in the cells and test them directly); more:
+// the moves first and a barrier, then the patches on final cells.  Returns
+// false when the step must be abandoned.
+static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int *ovf)
+{
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const bool direct = nF <= kFlaggedDirectMax;
+    if (!direct) {
+        for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
+        if (!grid_barrier(s)) return false;
+        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, ovf);
+        return true;
+    }
+    for (int w = w0; w < 2 * nF; w += nw) {
+        if (w < nF) patch_warp(s, w, nF, true, ovf);
+        else move_warp(s, s.fid[w - nF], s.fref[w - nF]);
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // One step.  pos_in / vel / acc: the caller's positions, velocities (policy
 // input) and accelerations; with kFused the positions come from the DEM
 // half-step (ia) instead.  Launched cooperatively with every block resident.
 // Per-step counts live in two slots chosen by the step's parity, so that the
-// slots of the next step can be cleared while this one is read.
+// slots of the next step can be cleared while this one is read.  The list
+// is final when the kernel ends (and before the tail).
 // ---------------------------------------------------------------------------
 template <bool kFused, class Tail>
 __global__ void __launch_bounds__(kStepMaxThreads, 1)
@@ -785,16 +871,16 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long t0 = (s.trace && lead) ? global_ns() : 0ULL;
     // every thread reads the counters it needs (one broadcast load each, no
-    // block barrier before the check's loads); the values are stable while
-    // the check runs
+    // block barrier before the check's loads); they are stable while the
+    // check runs
     const unsigned err = c->err;
+    if (err & DERR_SYNC) return;   // a barrier failed earlier: the context is unusable
     const bool inc = s.trigger == LVB_TRIGGER_PARTIAL && !(err & DERR_STORE);
     const int step = (int)c->steps + 1, par = step & 1;
     const float4 *pos = kFused ? ia.pos : pos_in;
     int *ovf = &c->ovf[par];
 
-    check_pass<kFused>(s, pos_in, vel, acc, ia, inc, step, &c->nF_acc[par], ovf);
-    if (err & DERR_SYNC) return;   // a barrier failed earlier: the context is unusable
+    check_pass<kFused>(s, pos_in, vel, acc, ia, inc, step, &c->nF_acc[par]);
     if (!grid_barrier(s)) return;
     const int nF = *(volatile int *)&c->nF_acc[par];
     int upd;
@@ -816,7 +902,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         if (s.trace) {
             t1 = global_ns();
             trace_add(c, TR_CHECK, t0, t1);
-            // separate kernels (DEM phases) since the last step
+            // separate kernels (DEM phases, full-build rows) since the last step
             for (int k = TR_INTEGRATE; k <= TR_ROWS; ++k) {
                 const unsigned long long a = c->tr_start[k], b = c->tr_end[k];
                 if (b != 0 && b >= a) trace_add(c, k, a, b);
@@ -825,13 +911,11 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
             }
         }
     }
+    bool changed = false;
     if (inc) {
         if (nF > 0) {
-            partial_rows_pass(s, nF, ovf);
-            if (!grid_barrier(s)) return;
-            if (lead) c->ntrow = 0;
-            partial_append_pass(s, nF, ovf);
-            if (!grid_barrier(s)) return;
+            if (!partial_pass(s, nF, ovf)) return;
+            changed = true;
         }
     } else if (upd > 0 && !store_failed(s)) {
         full_update_pass(s, pos, vel);
@@ -839,27 +923,27 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         full_insert_pass(s);
         if (!grid_barrier(s)) return;
         all_rows_pass(s, 1, ovf);
+        changed = true;
+    }
+    if (changed) {
         if (!grid_barrier(s)) return;
-    }
-    unsigned long long t2 = 0;
-    if (s.trace && lead) {
-        t2 = global_ns();
-        trace_add(c, TR_REBUILD, t1, t2);
-    }
-    if (*(volatile int *)ovf && !store_failed(s)) {
-        if (!relayout_pass(s)) return;
+        unsigned long long t2 = 0;
         if (s.trace && lead) {
-            const unsigned long long t3 = global_ns();
-            trace_add(c, TR_RELAYOUT, t2, t3);
-            t2 = t3;
+            t2 = global_ns();
+            trace_add(c, TR_REBUILD, t1, t2);
+        }
+        if (*(volatile int *)ovf && !store_failed(s)) {
+            if (!relayout_pass(s)) return;
+            if (s.trace && lead) trace_add(c, TR_RELAYOUT, t2, global_ns());
         }
     }
     if (s.log_on) log_pass(s, pos, step);
     if (Tail::kActive) {
+        const unsigned long long t3 = (s.trace && lead) ? global_ns() : 0ULL;
         tail(blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
         if (s.trace) {
             if (!grid_barrier(s)) return;
-            if (lead) trace_add(c, TR_TAIL, t2, global_ns());
+            if (lead) trace_add(c, TR_TAIL, t3, global_ns());
         }
     }
 }
