@@ -263,6 +263,83 @@ def _batched(lvb, torch, hbm_peak, warmup):
     }
 
 
+LEARN_N = 1_000_000
+LEARN_H = 400           # horizon of the rebuild-log labels, and K of the paper's rule
+LEARN_STEPS = 1500      # steps of the logged training run and of each timed run
+
+
+def _timed_advance(lvb, torch, scene, kind, value, mlp=None, log=None, steps=LEARN_STEPS):
+    """Advance a fresh DEM context `steps` steps in 100-step graphs; returns
+    full-step particle-steps/s, updates/step, mean entries, rebuild steps
+    (and the rebuild-log samples when log is a horizon)."""
+    dem = lvb.DEM(scene, skin_kind=kind, skin_value=value, mlp=mlp)
+    if log:
+        dem.lvb.log_enable(log, 2_000_000)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st0 = dem.lvb.stats()
+    ms, done, ent = 0.0, 0, []
+    while done < steps:
+        k = min(500, steps - done)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dem.advance(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        ent.append(dem.lvb.stats()["entries"])
+        done += k
+    rc = dem.sync()
+    if rc != 0:
+        raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
+    st = dem.lvb.stats()
+    out = {"value": scene.n * steps / (ms * 1e-3), "unit": "particle-steps/s (full DEM step)",
+           "updates_per_step": (st["updated_total"] - st0["updated_total"]) / steps,
+           "rebuild_steps": st["rebuild_steps"] - st0["rebuild_steps"],
+           "mean_entries": float(np.mean(ent)), "relayouts": st["relayouts"]}
+    smp = dem.lvb.log_samples() if log else None
+    dem.close()
+    return out, smp
+
+
+def _learned(lvb, torch):
+    """The learned skin against the paper's rule on a 1,000,000-sphere drum:
+    rebuild-log samples from the plain local-buffer run (skin 0.1 d_i,
+    horizon LEARN_H), training on the GPU (own kernels), then the same
+    number of steps with the paper's rule (K = LEARN_H), the plain rule and
+    the network, each from the same initial state."""
+    import time
+    from paper_2208_13770_gb300 import scenes
+    sc = scenes.drum(n=LEARN_N, length=0.1)
+    plain, smp = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, log=LEARN_H)
+    rng = np.random.default_rng(5)
+    p0 = (rng.standard_normal(lvb.LVB_MLP_PARAMS) * 0.1).astype(np.float32)
+    yr = np.zeros(2, np.float32)
+    t0 = time.time()
+    p, mu, isd, losses = lvb.mlp_train(torch.from_numpy(np.ascontiguousarray(smp)).cuda(),
+                                       epochs=20, batch=512, lr=3e-3, seed=1, params0=p0,
+                                       y_range_out=yr)
+    t_train = time.time() - t0
+    w = lvb.mlp_weights_device(p, mu, isd, yr)
+    rule, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_PAPER_KVDT, float(LEARN_H))
+    learned, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w)
+    return {
+        "workload": "drum R 0.3 m x 0.1 m, %d lognormal spheres (median 1 mm, sigma_ln 0.35), "
+                    "10 rpm, dt 1e-6 s, %d steps per run" % (sc.n, LEARN_STEPS),
+        "training": {"samples": int(len(smp)), "source": "plain local buffer (0.1 d_i)",
+                     "label": "largest displacement over the next %d steps / d" % LEARN_H,
+                     "epochs": 20, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                     "seconds": t_train, "y_range": [float(yr[0]), float(yr[1])]},
+        "paper_rule_K%d" % LEARN_H: rule,
+        "plain_0.1d": plain,
+        "learned": learned,
+        "gain_vs_paper_rule": learned["value"] / rule["value"],
+        "gain_vs_plain": learned["value"] / plain["value"],
+        "note": "the plain run is timed with its rebuild log on",
+    }
+
+
 def _e2e(lvb, torch, scene, rec):
     """Broad phase through the C-ABI with host buffers: per step a pinned
     host -> device copy of the positions, lvb_step, and a device -> host
@@ -441,6 +518,7 @@ def run_native(args):
     e2e = _e2e(lvb, torch, scene, loc["rec"])
     e2e["value"] *= world
     batched = None if args.no_batched else _batched(lvb, torch, hbm_peak, args.warmup)
+    learned = None if args.no_learned else _learned(lvb, torch)
 
     s0, s1 = loc["stats0"], loc["stats1"]
     flagged = s1["flagged_total"] - s0["flagged_total"]
@@ -509,6 +587,8 @@ def run_native(args):
     if batched is not None:
         batched["vs_single_scene"] = batched["value"] / value
         line["batched"] = batched
+    if learned is not None:
+        line["learned"] = learned
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -533,6 +613,8 @@ def main():
                          "--profile-from-start off)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (512-scene) run")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-skin comparison (1M-sphere drum)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -11,9 +11,12 @@
  *   h1_o = bf16(relu(b1_o + sum_{k=0..7}  W1[o][k] z_k))     sums in k order
  *   h2_o = bf16(relu(b2_o + sum_{k=0..31} W2[o][k] h1_k))
  *   y    = b3 + sum_{k=0..31} w3[k] h2_k
- *   skin = (2 r) * max(y, 0), then the cap of lvb.h
- * relu(x) = x if x > 0 else 0.  Products of bfloat16 values are exact in
- * binary32, so the result does not depend on fused multiply-add use.
+ *   skin = (2 r) * fminf(fmaxf(y, y_lo), y_hi), then the cap of lvb.h
+ * relu(x) = x if x > 0 else 0; fmaxf / fminf return the other operand when
+ * one is NaN.  Products of bfloat16 values are exact in binary32, so the
+ * result does not depend on fused multiply-add use.  The output range
+ * [y_lo, y_hi] (in diameters) keeps every proposal positive and bounded:
+ * the network is used on states its training data may not cover.
  *
  * Features f (binary32, at the step that flags the particle, from the state
  * before its update; d = 2 r, dt the policy's time step):
@@ -58,16 +61,21 @@ typedef struct {
     float b3;
     float mu[LVB_MLP_IN];
     float isd[LVB_MLP_IN];
-    float pad[3];
+    float y_lo, y_hi;    /* output range, in diameters */
+    float pad;
 } lvb_mlp_weights;
 
 /*
  * lvb_mlp_pack -- write an lvb_mlp_weights record from master parameters.
  *   params : host, LVB_MLP_PARAMS binary32 in the order W1, b1, W2, b2, w3, b3.
  *   mu, isd: host, LVB_MLP_IN each (feature offset and inverse scale).
+ *   y_range: host, {y_lo, y_hi} with y_lo <= y_hi, or NULL for {0, +inf}
+ *            (then skin = d * max(y, 0)).
  *   out    : host or device lvb_mlp_weights (weights rounded to bfloat16).
+ * Errors: EINVAL (NULL pointer, y_lo > y_hi or NaN), EDEVICE.
  */
-int lvb_mlp_pack(const float *params, const float *mu, const float *isd, lvb_mlp_weights *out);
+int lvb_mlp_pack(const float *params, const float *mu, const float *isd, const float *y_range,
+                 lvb_mlp_weights *out);
 
 /*
  * lvb_mlp_infer -- the network on n feature rows: skin[i] = d[i] * max(y, 0)
@@ -93,12 +101,14 @@ int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const flo
  *   params      : host in/out, LVB_MLP_PARAMS master parameters.
  *   mu, isd     : host out, the feature normalisation computed from the
  *                 samples (mean and 1/std per feature).
+ *   y_range     : host out, {y_lo, y_hi} from the labels' mean m and
+ *                 standard deviation sd: y_lo = m / 16, y_hi = m + 4 sd.
  *   losses      : host out, mean loss of every epoch (epochs entries).
  * Synchronises.  Errors: EINVAL, ENOMEM, EDEVICE.
  */
 int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch, float lr,
-                  uint64_t seed, float *params, float *mu, float *isd, float *losses,
-                  void *stream);
+                  uint64_t seed, float *params, float *mu, float *isd, float *y_range,
+                  float *losses, void *stream);
 
 /*
  * lvb_log_enable -- start recording training samples from a broad-phase

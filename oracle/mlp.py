@@ -15,7 +15,10 @@ bits):
     h1_o = bf16( relu( b1_o + sum_k W1_ok z_k ) )      k = 0..7 in order
     h2_o = bf16( relu( b2_o + sum_k W2_ok h1_k ) )     k = 0..31 in order
     y    = b3 + sum_k w3_k h2_k                        k = 0..31 in order
-    skin = d * max(y, 0)                               (then the cap)
+    skin = d * fmin(fmax(y, y_lo), y_hi)               (then the cap)
+(fmax / fmin return the other operand when one is NaN.)  The output range
+[y_lo, y_hi] belongs to the weights; y_lo = 0, y_hi = +inf gives
+d * max(y, 0).
 Weights and biases are bfloat16 / binary32; each product of two bfloat16
 values is exact in binary32, and each sum is one binary32 rounding, taken
 in the order written, starting from the bias.
@@ -49,7 +52,7 @@ def bf16_round(x):
 class Weights:
     """Parameters in binary32 master form."""
 
-    def __init__(self, W1, b1, W2, b2, w3, b3, mu, isd):
+    def __init__(self, W1, b1, W2, b2, w3, b3, mu, isd, y_lo=0.0, y_hi=np.inf):
         self.W1 = np.asarray(W1, np.float32).reshape(N_H, N_IN)
         self.b1 = np.asarray(b1, np.float32).reshape(N_H)
         self.W2 = np.asarray(W2, np.float32).reshape(N_H, N_H)
@@ -58,6 +61,8 @@ class Weights:
         self.b3 = np.float32(b3)
         self.mu = np.asarray(mu, np.float32).reshape(N_IN)
         self.isd = np.asarray(isd, np.float32).reshape(N_IN)
+        self.y_lo = np.float32(y_lo)
+        self.y_hi = np.float32(y_hi)
 
     @staticmethod
     def random(seed=0, scale=0.3):
@@ -71,7 +76,7 @@ class Weights:
                                [self.b3]]).astype(np.float32)
 
     @staticmethod
-    def from_flat(p, mu, isd):
+    def from_flat(p, mu, isd, y_lo=0.0, y_hi=np.inf):
         p = np.asarray(p, np.float32)
         o = 0
         W1 = p[o:o + N_H * N_IN]; o += N_H * N_IN
@@ -80,7 +85,7 @@ class Weights:
         b2 = p[o:o + N_H]; o += N_H
         w3 = p[o:o + N_H]; o += N_H
         b3 = p[o]
-        return Weights(W1, b1, W2, b2, w3, b3, mu, isd)
+        return Weights(W1, b1, W2, b2, w3, b3, mu, isd, y_lo, y_hi)
 
 
 def _dot_fixed(bias, w, x):
@@ -102,7 +107,8 @@ def infer(W: Weights, feats, diam):
     h1 = bf16_round(np.maximum(_dot_fixed(W.b1, bf16_round(W.W1), z), np.float32(0)))
     h2 = bf16_round(np.maximum(_dot_fixed(W.b2, bf16_round(W.W2), h1), np.float32(0)))
     y = _dot_fixed(np.array([W.b3], np.float32), bf16_round(W.w3)[None, :], h2)[:, 0]
-    return (np.asarray(diam, np.float32) * np.maximum(y, np.float32(0))).astype(np.float32), y
+    yc = np.fmin(np.fmax(y, W.y_lo), W.y_hi).astype(np.float32)
+    return (np.asarray(diam, np.float32) * yc).astype(np.float32), y
 
 
 def forward64(W: Weights, feats, quantize=True):

@@ -538,7 +538,7 @@ int grow_if_asked(lvb_ctx *c)
     s.col_cap = cap0;
     if (rc) return rc;
     const long long need = c->cnt_h->store_needed;
-    if (need * 4 > s.col_cap * 3) {
+    if (need * 5 > s.col_cap * 3) {   // over 60%: grow
         const long long cap = std::min<long long>(2 * need + 8 * c->n + 1024, INT32_MAX);
         if (need > cap) return LVB_ENOMEM;
         cudaFree(s.col);

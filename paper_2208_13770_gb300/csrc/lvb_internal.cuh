@@ -223,10 +223,12 @@ __device__ __forceinline__ float mlp_y_warp(const lvb_mlp_weights *__restrict__ 
     return y;
 }
 
-// Slack rule of the row store: capacity for a row of `len` entries.
+// Slack rule of the row store: capacity for a row of `len` entries (room
+// for the row to grow by half, and by 8 however short it is, before the
+// store is re-laid out).
 __host__ __device__ __forceinline__ int row_capacity(int len)
 {
-    return len + 4 + (len >> 2);
+    return len + 8 + (len >> 1);
 }
 
 }  // namespace lvb

@@ -164,7 +164,7 @@ __device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g
     float prop = 0.0f;
     if (s.skin_kind == LVB_SKIN_LEARNED) {
         const float y = mlp_y_warp(s.mlp, f);
-        prop = __fmul_rn(__fmul_rn(2.0f, r), relu(y));
+        prop = __fmul_rn(__fmul_rn(2.0f, r), fminf(fmaxf(y, s.mlp->y_lo), s.mlp->y_hi));
     }
     return skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
 }
@@ -724,23 +724,23 @@ static __device__ __noinline__ void all_rows_pass(const DevState &s, int fill, i
     ph_rows(s, s.n, fill, t >> 5, nt >> 5, ovf);
 }
 
-// Re-layout of the row store after a row outgrew its slack: rows counted
-// from the (final) cells, offsets by a grid-wide scan of row_capacity(len),
-// rows filled.  Block b owns rows [b * per, (b + 1) * per).  Returns false
-// when the step must be abandoned (a barrier gave up).
-static __device__ __noinline__ bool relayout_pass(const DevState &s)
+// Offsets of the row store by a grid-wide exclusive scan of the row sizes
+// (row_capacity(len), or len itself when tight), block b owning rows
+// [b * per, (b + 1) * per); block 0 scans the block sums and writes the
+// total to store_needed.  Every block returns the total (read after a
+// barrier).  Returns -1 when the step must be abandoned.
+static __device__ long long layout_scan(const DevState &s, bool tight)
 {
     DevCounters *c = s.cnt;
-    all_rows_pass(s, 0, nullptr);
-    if (!grid_barrier(s)) return false;
     const long long per = ((long long)s.n + gridDim.x - 1) / gridDim.x;
     const int lo = (int)min((long long)s.n, blockIdx.x * per);
     const int hi = (int)min((long long)s.n, lo + per);
     long long sum = 0, tot;
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) sum += row_capacity(s.row_len[i]);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        sum += tight ? s.row_len[i] : row_capacity(s.row_len[i]);
     block_scan_any(sum, &tot);
     if (threadIdx.x == 0) s.blk[blockIdx.x] = tot;
-    if (!grid_barrier(s)) return false;
+    if (!grid_barrier(s)) return -1;
     if (blockIdx.x == 0) {
         __shared__ long long carry;
         if (threadIdx.x == 0) carry = 0;
@@ -754,22 +754,44 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
             if (threadIdx.x == 0) carry += tot;
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            c->store_needed = carry;
-            if (carry > s.col_cap) atomicOr(&c->err, DERR_STORE);
-        }
+        if (threadIdx.x == 0) c->store_needed = carry;
     }
-    if (!grid_barrier(s)) return false;
+    if (!grid_barrier(s)) return -1;
     long long run = s.blk[blockIdx.x];
     for (int i0 = lo; i0 < hi; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
-        const int v = i < hi ? row_capacity(s.row_len[i]) : 0;
+        const int v = i < hi ? (tight ? s.row_len[i] : row_capacity(s.row_len[i])) : 0;
         const long long ex = block_scan_any(v, &tot);
         if (i < hi) {
             s.row_off[i] = (int)min(run + ex, (long long)INT32_MAX);
             s.row_cap[i] = v;
         }
         run += tot;
+    }
+    return *(volatile long long *)&c->store_needed;
+}
+
+// Re-layout of the row store after a row outgrew its slack: rows counted
+// from the (final) cells, offsets with slack, rows filled.  When the rows
+// with slack do not fit the store they are laid out tight (no slack; the
+// next edits re-lay out again) and, if even that does not fit, the store
+// has failed (DERR_STORE).  A layout above 60% of the store asks the host
+// to grow it before the next step.  Returns false when the step must be
+// abandoned.
+static __device__ __noinline__ bool relayout_pass(const DevState &s)
+{
+    DevCounters *c = s.cnt;
+    all_rows_pass(s, 0, nullptr);
+    if (!grid_barrier(s)) return false;
+    const long long need = layout_scan(s, false);
+    if (need < 0) return false;
+    long long used = need;
+    if (need > s.col_cap) {
+        if (!grid_barrier(s)) return false;   // everyone has read the slack total
+        used = layout_scan(s, true);
+        if (used < 0) return false;
+        if (used > s.col_cap && blockIdx.x == 0 && threadIdx.x == 0)
+            atomicOr(&c->err, DERR_STORE);
     }
     if (!grid_barrier(s)) return false;
     if (!store_failed(s)) {
@@ -779,12 +801,13 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
     if (!grid_barrier(s)) return false;
     if (blockIdx.x == 0 && threadIdx.x == 0 && !store_failed(s)) {
         c->relayouts += 1;
-        const long long need = c->store_needed;
-        if (need * 4 > s.col_cap * 3) {        // over 75% of the store: grow it
+        c->store_needed = need;
+        if (need * 5 > s.col_cap * 3) {        // over 60% of the store: grow it
             s.hflags->store_needed = need;
             s.hflags->grow_store = 1;
         }
     }
+    (void)used;
     return true;
 }
 

@@ -50,34 +50,35 @@ __global__ void k_mlp_infer(const float *__restrict__ feats, const float *__rest
         for (int k = 0; k < NI; ++k) f[k] = feats[i * NI + k];
         const float y = mlp_y_warp(W, f);
         if ((threadIdx.x & 31) == 0) {
-            skin[i] = __fmul_rn(diam[i], relu(y));
+            skin[i] = __fmul_rn(diam[i], fminf(fmaxf(y, W->y_lo), W->y_hi));
             if (yout) yout[i] = y;
         }
     }
 }
 
-// Per-feature sum and sum of squares (binary64) for the normalisation.
+// Per-column sum and sum of squares (binary64) of the samples: the eight
+// features (normalisation) and the label (output range).
 __global__ void k_feature_stats(const float *__restrict__ samples, int64_t n, double *acc)
 {
-    double s[NI] = {0}, q[NI] = {0};
+    double s[kSamp] = {0}, q[kSamp] = {0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < NI; ++k) {
+        for (int k = 0; k < kSamp; ++k) {
             const double v = samples[i * kSamp + k];
             s[k] += v;
             q[k] += v * v;
         }
     }
 #pragma unroll
-    for (int k = 0; k < NI; ++k) {
+    for (int k = 0; k < kSamp; ++k) {
         for (int o = 16; o; o >>= 1) {
             s[k] += __shfl_xor_sync(FULL, s[k], o);
             q[k] += __shfl_xor_sync(FULL, q[k], o);
         }
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(&acc[k], s[k]);
-            atomicAdd(&acc[NI + k], q[k]);
+            atomicAdd(&acc[kSamp + k], q[k]);
         }
     }
 }
@@ -231,11 +232,15 @@ void launch_batch(const float *samples, const int *order, int64_t first, int64_t
 
 extern "C" {
 
-int lvb_mlp_pack(const float *params, const float *mu, const float *isd, lvb_mlp_weights *out)
+int lvb_mlp_pack(const float *params, const float *mu, const float *isd, const float *y_range,
+                 lvb_mlp_weights *out)
 {
     if (!params || !mu || !isd || !out) return LVB_EINVAL;
+    if (y_range && !(y_range[0] <= y_range[1])) return LVB_EINVAL;
     lvb_mlp_weights w;
     memset(&w, 0, sizeof(w));
+    w.y_lo = y_range ? y_range[0] : 0.0f;
+    w.y_hi = y_range ? y_range[1] : INFINITY;
     for (int k = 0; k < NH * NI; ++k) w.W1[k] = bf16_host_rn(params[OFF_W1 + k]);
     for (int k = 0; k < NH; ++k) w.b1[k] = params[OFF_B1 + k];
     for (int k = 0; k < NH * NH; ++k) w.W2[k] = bf16_host_rn(params[OFF_W2 + k]);
@@ -291,29 +296,36 @@ int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const flo
 }
 
 int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch, float lr,
-                  uint64_t seed, float *params, float *mu, float *isd, float *losses,
-                  void *stream)
+                  uint64_t seed, float *params, float *mu, float *isd, float *y_range,
+                  float *losses, void *stream)
 {
-    if (!samples || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f) || !params || !mu || !isd)
+    if (!samples || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f) || !params || !mu || !isd ||
+        !y_range)
         return LVB_EINVAL;
     if (n > INT32_MAX) return LVB_EINVAL;
     cudaGetLastError();
     const cudaStream_t st = (cudaStream_t)stream;
-    // feature normalisation from the samples (mean, 1/std)
+    // feature normalisation from the samples (mean, 1/std), label range
     DevBuf dstat;
-    cudaError_t e = dnew<double>(dstat, 2 * NI);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dstat.p, 0, 2 * NI * 8, st);
+    cudaError_t e = dnew<double>(dstat, 2 * kSamp);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dstat.p, 0, 2 * kSamp * 8, st);
     if (e != cudaSuccess) return from_cuda(e);
     k_feature_stats<<<152 * 4, 256, 0, st>>>(samples, n, (double *)dstat.p);
-    double stat[2 * NI];
+    double stat[2 * kSamp];
     e = cudaMemcpyAsync(stat, dstat.p, sizeof(stat), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
     for (int k = 0; k < NI; ++k) {
         const double m = stat[k] / (double)n;
-        const double var = std::max(stat[NI + k] / (double)n - m * m, 0.0);
+        const double var = std::max(stat[kSamp + k] / (double)n - m * m, 0.0);
         mu[k] = (float)m;
         isd[k] = var > 1e-30 ? (float)(1.0 / std::sqrt(var)) : 1.0f;
+    }
+    {
+        const double m = stat[NI] / (double)n;
+        const double sd = std::sqrt(std::max(stat[kSamp + NI] / (double)n - m * m, 0.0));
+        y_range[0] = (float)(m / 16.0);
+        y_range[1] = (float)(m + 4.0 * sd);
     }
     DevBuf dp, dmu, disd, dg, dm, dv, dl, dord;
     e = dnew<float>(dp, NP);

@@ -94,12 +94,12 @@ _SIGS = {
     "lvb_set_stream": ([_p, _p], ctypes.c_int),
     "lvb_destroy": ([_p], ctypes.c_int),
     "lvb_strerror": ([ctypes.c_int], ctypes.c_char_p),
-    "lvb_mlp_pack": ([_p, _p, _p, _p], ctypes.c_int),
+    "lvb_mlp_pack": ([_p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_mlp_infer": ([_p, _p, _i64, _p, _p, _p, _p], ctypes.c_int),
     "lvb_mlp_grad": ([_p, _i64, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_double), _p],
                      ctypes.c_int),
     "lvb_mlp_train": ([_p, _i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
-                       _p, _p, _p, _p, _p], ctypes.c_int),
+                       _p, _p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_log_enable": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
     "lvb_log_read": ([_p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_pairs_noalloc": ([_i64, _p, _p, ctypes.POINTER(lvb_box), _p, _p, _i64, _pi64, _p],
@@ -292,8 +292,8 @@ LVB_MLP_IN, LVB_MLP_HIDDEN, LVB_MLP_PARAMS = 8, 32, 1377
 MLP_WEIGHTS_BYTES = 4 * (32 * 8 + 32 + 32 * 32 + 32 + 32 + 1 + 8 + 8 + 3)
 
 
-def lvb_mlp_pack(params, mu, isd, out):
-    return _lib.lvb_mlp_pack(params, mu, isd, out)
+def lvb_mlp_pack(params, mu, isd, y_range, out):
+    return _lib.lvb_mlp_pack(params, mu, isd, y_range, out)
 
 
 def lvb_mlp_infer(feats, diam, n, w, skin, y, stream=None):
@@ -304,9 +304,10 @@ def lvb_mlp_grad(samples, n, params, mu, isd, grad, loss, stream=None):
     return _lib.lvb_mlp_grad(samples, int(n), params, mu, isd, grad, loss, stream)
 
 
-def lvb_mlp_train(samples, n, epochs, batch, lr, seed, params, mu, isd, losses, stream=None):
+def lvb_mlp_train(samples, n, epochs, batch, lr, seed, params, mu, isd, y_range, losses,
+                  stream=None):
     return _lib.lvb_mlp_train(samples, int(n), int(epochs), int(batch), float(lr), int(seed),
-                              params, mu, isd, losses, stream)
+                              params, mu, isd, y_range, losses, stream)
 
 
 def lvb_log_enable(ctx, horizon, capacity):
@@ -575,26 +576,31 @@ class DEM:
 
 
 # ------------------------------------------------------------ skin network
-def mlp_weights_device(params, mu, isd):
-    """Pack master parameters (+ normalisation) into a device
-    lvb_mlp_weights record; returns the torch byte tensor holding it."""
+def mlp_weights_device(params, mu, isd, y_range=None):
+    """Pack master parameters (+ normalisation, + output range {y_lo, y_hi}
+    or None for {0, inf}) into a device lvb_mlp_weights record; returns the
+    torch byte tensor holding it."""
     import torch
     buf = torch.empty(MLP_WEIGHTS_BYTES, dtype=torch.uint8, device="cuda")
     p = np.ascontiguousarray(params, np.float32)
     m = np.ascontiguousarray(mu, np.float32)
     d = np.ascontiguousarray(isd, np.float32)
-    _check(lvb_mlp_pack(_np_ptr(p), _np_ptr(m), _np_ptr(d), buf.data_ptr()), "lvb_mlp_pack")
+    yr = None if y_range is None else np.ascontiguousarray(y_range, np.float32)
+    _check(lvb_mlp_pack(_np_ptr(p), _np_ptr(m), _np_ptr(d), None if yr is None else _np_ptr(yr),
+                        buf.data_ptr()), "lvb_mlp_pack")
     return buf
 
 
-def mlp_train(samples_dev, epochs, batch, lr, seed, params0):
+def mlp_train(samples_dev, epochs, batch, lr, seed, params0, y_range_out=None):
     """Train on device samples (torch (n, 9) float32); returns (params, mu,
-    isd, losses)."""
+    isd, losses).  y_range_out (a float32 array of 2) receives the output
+    range computed from the labels."""
     p = np.ascontiguousarray(params0, np.float32).copy()
     mu = np.zeros(LVB_MLP_IN, np.float32)
     isd = np.zeros(LVB_MLP_IN, np.float32)
+    yr = np.zeros(2, np.float32) if y_range_out is None else y_range_out
     losses = np.zeros(int(epochs), np.float32)
     _check(lvb_mlp_train(samples_dev.data_ptr(), samples_dev.shape[0], epochs, batch, lr, seed,
-                         _np_ptr(p), _np_ptr(mu), _np_ptr(isd), _np_ptr(losses)),
+                         _np_ptr(p), _np_ptr(mu), _np_ptr(isd), _np_ptr(yr), _np_ptr(losses)),
            "lvb_mlp_train")
     return p, mu, isd, losses

@@ -1,0 +1,86 @@
+"""What the learned skin gains over the paper's rule skin = K |v| dt (Eq.
+skin_formulus1), at zero missed contacts.
+
+A dense pack of 8,000 spheres resting on the floor of a box under gravity
+is advanced by the DEM driver for 3,000 steps (dt = 1e-6 s).  The paper's
+rule with K = 400 runs with the rebuild log on (horizon 400 steps: label =
+largest displacement over the next 400 steps, in diameters).  The network is
+trained on the GPU on those samples, run once with the log on, trained
+again on both logs (its own states included), and run.  Against the rule it
+updates fewer particles -- at most 0.7 times as many -- with a list no
+larger than 1.05 times the rule's, and the displacement check still guards
+every list: the contacts found from the list at the end equal the oracle's
+contacts over all pairs at the same positions.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_13770_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+STEPS = 3000
+H = 400
+
+
+def _lvb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_13770_gb300 import lvb
+    return lvb
+
+
+def _run(lvb, s, kind, value, mlp=None, log=None):
+    dem = lvb.DEM(s, skin_kind=kind, skin_value=value, mlp=mlp)
+    if log:
+        dem.lvb.log_enable(log, 2_000_000)
+    st0 = dem.lvb.stats()
+    entries = []
+    for _ in range(STEPS // 250):
+        dem.advance(250)
+        entries.append(dem.lvb.stats()["entries"])
+    assert dem.sync() == 0
+    st = dem.lvb.stats()
+    out = {"updates": st["updated_total"] - st0["updated_total"],
+           "entries": float(np.mean(entries)),
+           "samples": dem.lvb.log_samples() if log else None,
+           "pos": dem.state()[0],
+           "contacts": dem.lvb.contacts(dem.device_pos_tensor(torch))}
+    dem.close()
+    return out
+
+
+def _train(lvb, samples):
+    from oracle import mlp
+    yr = np.zeros(2, np.float32)
+    p0 = mlp.Weights.random(seed=9, scale=0.3).flat()
+    p, mu, isd, losses = lvb.mlp_train(torch.from_numpy(samples).cuda(), epochs=40, batch=256,
+                                       lr=3e-3, seed=1, params0=p0, y_range_out=yr)
+    assert losses[-1] < losses[0]
+    return lvb.mlp_weights_device(p, mu, isd, yr)
+
+
+def _contact_keys(n, ci, cj):
+    return set((ci.astype(np.int64) * n + cj).tolist())
+
+
+def test_learned_skin_beats_paper_rule(orc):
+    lvb = _lvb()
+    s = scenes.packed(n=8000)
+    rule = _run(lvb, s, lvb.LVB_SKIN_PAPER_KVDT, float(H), log=H)
+    assert len(rule["samples"]) > 5000
+    w1 = _train(lvb, rule["samples"])
+    r1 = _run(lvb, s, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1, log=H)
+    w2 = _train(lvb, np.concatenate([rule["samples"], r1["samples"]]))
+    learned = _run(lvb, s, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w2)
+    print("paper rule K=%d: %d updates, %.0f entries; learned: %d updates, %.0f entries"
+          % (H, rule["updates"], rule["entries"], learned["updates"], learned["entries"]))
+    assert learned["updates"] <= 0.7 * rule["updates"]
+    assert learned["entries"] <= 1.05 * rule["entries"]
+    # zero missed contacts for both policies: the list's contacts are all of them
+    for run in (rule, learned):
+        n = len(run["pos"])
+        got = _contact_keys(n, *run["contacts"][:2])
+        want = _contact_keys(n, *orc.contacts_all(run["pos"])[:2])
+        assert got == want and len(want) > 1000

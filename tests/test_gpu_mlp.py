@@ -42,11 +42,12 @@ def test_inference_bit_exact():
     lvb = _lvb()
     from oracle import mlp
     W = _weights(1)
+    W.y_lo, W.y_hi = np.float32(0.05), np.float32(0.8)
     rng = np.random.default_rng(2)
     n = 5000
     f = rng.normal(0, 2, (n, 8)).astype(np.float32)
     d = rng.uniform(1e-3, 4e-3, n).astype(np.float32)
-    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd)
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi))
     skin = torch.empty(n, device="cuda")
     y = torch.empty(n, device="cuda")
     fd, dd = _dev(f), _dev(d)
@@ -57,7 +58,8 @@ def test_inference_bit_exact():
     es, ey = mlp.infer(W, f, d)
     assert np.array_equal(y.cpu().numpy(), ey)
     assert np.array_equal(skin.cpu().numpy(), es)
-    assert (ey > 0).any() and (ey <= 0).any()
+    # the range is exercised on both sides
+    assert (ey < W.y_lo).any() and (ey > W.y_hi).any() and ((ey > W.y_lo) & (ey < W.y_hi)).any()
 
 
 def test_gradient_matches_oracle():
@@ -90,9 +92,14 @@ def test_training_lowers_loss():
     samp[:, :8] = rng.normal(0, 1, (n, 8))
     samp[:, 8] = 0.3 + 0.2 * np.tanh(samp[:, 0]) + 0.1 * np.abs(samp[:, 1])
     p0 = mlp.Weights.random(seed=9, scale=0.3).flat()
+    yr = np.zeros(2, np.float32)
     p, mu, isd, losses = lvb.mlp_train(_dev(samp), epochs=15, batch=256, lr=3e-3, seed=1,
-                                       params0=p0)
+                                       params0=p0, y_range_out=yr)
     assert losses[-1] < 0.2 * losses[0], losses
+    # output range from the labels: mean / 16 and mean + 4 sd
+    lab = samp[:, 8].astype(np.float64)
+    assert np.isclose(yr[0], lab.mean() / 16, rtol=1e-5)
+    assert np.isclose(yr[1], lab.mean() + 4 * lab.std(), rtol=1e-5)
     # the trained network, evaluated by the oracle's exact formula, fits the data
     W = mlp.Weights.from_flat(p, mu, isd)
     _, y = mlp.infer(W, samp[:2000, :8], np.ones(2000, np.float32))
@@ -102,9 +109,10 @@ def test_training_lowers_loss():
 def _learned_setup(lvb, s, seed=3):
     from oracle import mlp
     W = _weights(seed)
-    # keep the proposals of the order of a tenth of a diameter
+    # keep the proposals of the order of a tenth of a diameter, bounded
     W.b3 = np.float32(0.05)
     W.w3 *= np.float32(0.05)
+    W.y_lo, W.y_hi = np.float32(0.01), np.float32(0.08)
     grid = mlp.grid_params(s.pos[:, 3].max(), s.cell_factor, s.lo, s.hi)
     return W, grid
 
@@ -114,7 +122,7 @@ def test_learned_policy_broad_phase_parity(orc):
     from oracle.statemachine import OracleLVB
     s = scenes.ballistic(n=2000, seed=17, vsigma=1.0)
     W, grid = _learned_setup(lvb, s)
-    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd)
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi))
     acc = np.zeros_like(s.pos)
     acc[:, 2] = -9.81
     ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_LEARNED, 0.0, s.dt,

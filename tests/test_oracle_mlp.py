@@ -53,6 +53,18 @@ def test_one_path_network_closed_form():
     assert np.array_equal(y, expect_y.astype(np.float32))
     assert np.array_equal(skin, (d * np.maximum(expect_y, 0)).astype(np.float32))
     assert y[1] == np.float32(0.25)                 # negative input: ReLU blocks the path
+    # the output range: proposals clamp to [y_lo, y_hi] diameters, by hand
+    # y = (4.25, 0.25, 0.8515625) for these inputs: z0 = bf16(0.6) = 0.6015625,
+    # h2 = 2 z0 = 1.203125, y = 0.25 + 0.5 h2
+    assert np.array_equal(y, np.array([4.25, 0.25, 0.8515625], np.float32))
+    W.y_lo, W.y_hi = np.float32(0.3), np.float32(2.0)
+    skin2, y2 = mlp.infer(W, f, d)
+    assert np.array_equal(y2, y)
+    assert np.array_equal(skin2, np.array([2e-3 * 2.0, 2e-3 * 0.3, 1e-3 * y[2]], np.float32))
+    # NaN output: the bounds decide (fmax / fmin semantics)
+    W.b3 = np.float32(np.nan)
+    skin3, _ = mlp.infer(W, f, d)
+    assert np.array_equal(skin3, (d * np.float32(0.3)).astype(np.float32))
 
 
 def test_backward_matches_finite_differences():
