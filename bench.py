@@ -59,10 +59,8 @@ def _peaks():
 
 
 def _dist():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2208_13770_gb300 import replicas
+    return replicas.rank_info()
 
 
 class Clocks:
@@ -118,8 +116,8 @@ class Clocks:
 
 
 def _scene(rank):
-    from paper_2208_13770_gb300 import scenes
-    return scenes.settling(seed=scenes.SEED_BASE + 1 + rank)
+    from paper_2208_13770_gb300 import replicas, scenes
+    return scenes.settling(seed=replicas.replica_seed(scenes.SEED_BASE + 1, rank))
 
 
 def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, flush,
@@ -488,14 +486,10 @@ def run_native(args):
                        record=(rec_start, m_e2e) if m_e2e else None,
                        profile_from=args.profile_from)
     torch.cuda.synchronize()
-    bp_ms = float(loc["phase_ms"][1])
-    if world > 1:
-        t = torch.tensor([bp_ms, float(loc["phase_ms"].sum())], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        bp_ms, step_ms_tot = float(t[0]), float(t[1])
-    else:
-        step_ms_tot = float(loc["phase_ms"].sum())
-    value = world * n * args.steps / (bp_ms * 1e-3)
+    from paper_2208_13770_gb300 import replicas
+    bp_ms, step_ms_tot = replicas.max_over_ranks(
+        [float(loc["phase_ms"][1]), float(loc["phase_ms"].sum())], device="cuda")
+    value = replicas.job_throughput(world, n, args.steps, bp_ms)
 
     if args.only_local:
         if rank == 0:
@@ -508,7 +502,7 @@ def run_native(args):
     dmean = float(2.0 * scene.pos[:, 3].astype(np.float64).mean())
     glob = _run_dem(lvb, torch, scene, lvb.LVB_TRIGGER_GLOBAL, lvb.LVB_SKIN_GLOBAL,
                     0.1 * dmean, args.steps, args.warmup, flush)
-    g_bp_ms = float(glob["phase_ms"][1])
+    g_bp_ms, = replicas.max_over_ranks([float(glob["phase_ms"][1])], device="cuda")
 
     if rank != 0:
         if world > 1:

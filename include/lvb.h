@@ -222,6 +222,15 @@ int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *ac
                                 (two or four per SM) */
 #define LVB_OPT_COMPACT   5  /* compaction of the flagged ids in the check:
                                 LVB_COMPACT_WARP (default) or LVB_COMPACT_BLOCK */
+/* Failure test hooks (the grid-wide barrier's bounded wait): */
+#define LVB_OPT_BARRIER_EXTRA 6 /* 1: every barrier waits for one arrival more
+                                than the grid has, so the next step's wait
+                                runs out: the step is abandoned and the
+                                context reports LVB_ETIMEOUT (as after a
+                                real stall); 0 (default): normal */
+#define LVB_OPT_BARRIER_SPINS 7 /* polls (L2 round trips) before a barrier gives
+                                up, 1 .. 2^22 (default 2^22, about a second or
+                                two) */
 
 /* Values of LVB_OPT_COMPACT. */
 #define LVB_COMPACT_WARP  0  /* one atomic per 32-particle chunk with flags,

@@ -797,6 +797,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     cudaMemsetAsync(s.bits, 0, sizeof(uint32_t) * c->nwords, st);
 
     s.n = (int)n;
+    s.bar_spins = kBarrierSpins;
     s.nwords = c->nwords;
     s.trigger = trigger;
     s.skin_kind = skin->kind;
@@ -958,6 +959,12 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     } else if (option == LVB_OPT_COMPACT) {
         if (value != LVB_COMPACT_WARP && value != LVB_COMPACT_BLOCK) return LVB_EINVAL;
         c->s.compact_block = value == LVB_COMPACT_BLOCK;
+    } else if (option == LVB_OPT_BARRIER_EXTRA) {
+        if (value != 0 && value != 1) return LVB_EINVAL;
+        c->s.bar_extra = (unsigned)value;
+    } else if (option == LVB_OPT_BARRIER_SPINS) {
+        if (value < 1 || value > kBarrierSpins) return LVB_EINVAL;
+        c->s.bar_spins = (unsigned)value;
     } else {
         return LVB_EINVAL;
     }

@@ -81,6 +81,10 @@ struct DevState {
     int trace;            // record per-phase device time (LVB_OPT_TRACE)
     int compact_block;    // flag compaction: 0 one atomic per warp chunk,
                           // 1 one per block tile (LVB_OPT_COMPACT)
+    unsigned bar_extra;   // arrivals a barrier waits for beyond the grid's
+                          // blocks: 0, or 1 to make every wait run out (the
+                          // failure test, LVB_OPT_BARRIER_EXTRA)
+    unsigned bar_spins;   // polls before a barrier gives up
 };
 
 // gate modes of the separate full-build kernels (init, store growth)
@@ -503,9 +507,10 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill,
 // 0 of each block arrives with one acquire-release add; the last arrival
 // adds 2^32 - blocks (next generation, arrivals back to zero) with release
 // semantics, the others poll the generation with acquire loads.  Polling is
-// bounded: after kBarrierSpins polls the block records DERR_SYNC and
-// leaves; every block then returns, and later steps do nothing (the context
-// reports the error).  Returns false when the step must be abandoned.
+// bounded: after s.bar_spins polls (kBarrierSpins unless a test lowers it)
+// the block records DERR_SYNC and leaves; every block then returns, and
+// later steps do nothing (the context reports LVB_ETIMEOUT).  Returns false
+// when the step must be abandoned.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long *p,
                                                                unsigned long long v)
@@ -534,7 +539,7 @@ __device__ __forceinline__ bool grid_barrier(const DevState &s)
     __syncthreads();
     if (threadIdx.x == 0) {
         DevCounters *c = s.cnt;
-        const unsigned nb = gridDim.x;
+        const unsigned nb = gridDim.x + s.bar_extra;
         const unsigned long long old = atom_add_acq_rel(&c->bar_word, 1ULL);
         int ok = 1;
         if ((unsigned)old == nb - 1) {
@@ -544,7 +549,7 @@ __device__ __forceinline__ bool grid_barrier(const DevState &s)
             const unsigned gen = (unsigned)(old >> 32);
             unsigned it = 0;
             while ((unsigned)(ld_acquire(&c->bar_word) >> 32) == gen) {
-                if (++it > kBarrierSpins) {
+                if (++it > s.bar_spins) {
                     atomicOr(&c->err, DERR_SYNC);
                     ok = 0;
                     break;
