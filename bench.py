@@ -462,6 +462,23 @@ def run_reference(args):
     return 0
 
 
+def _only_batched(lvb, torch, args, rank):
+    """The batched workload alone, phase by phase with CUDA events (for
+    profiling: --profile-from brackets the timed steps), default launch
+    choice.  Prints one short JSON line."""
+    from paper_2208_13770_gb300 import scenes
+    sc = scenes.batch()
+    n = int(sum(q.n for q in sc))
+    res = _run_dem(lvb, torch, sc, lvb.LVB_TRIGGER_PARTIAL, sc[0].skin_kind, sc[0].skin_value,
+                   args.steps, args.warmup, None, profile_from=args.profile_from)
+    if rank == 0:
+        ph = res["phase_ms"] / args.steps
+        print(json.dumps({"only_batched": True, "n": n, "phases_ms_per_step": list(ph),
+                          "value": n * args.steps / (res["phase_ms"][1] * 1e-3),
+                          "stats": res["stats1"]}))
+    return 0
+
+
 def run_native(args):
     import torch
     rank, world, local = _dist()
@@ -471,6 +488,8 @@ def run_native(args):
         dist.init_process_group("nccl")
     from paper_2208_13770_gb300 import lvb
     hbm_peak, peak_kind = _peaks()
+    if args.only_batched:
+        return _only_batched(lvb, torch, args, rank)
     scene = _scene(rank)
     n = scene.n
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -609,6 +628,9 @@ def main():
                     help="skip the batched (512-scene) run")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-skin comparison (1M-sphere drum)")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time the batched (512-scene) workload alone, phase by phase "
+                         "(for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
