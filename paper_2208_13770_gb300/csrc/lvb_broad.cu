@@ -478,9 +478,13 @@ int size_step(lvb_ctx *c)
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem = check_smem_bytes(c->block_threads);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step<false, NoTail>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<false, NoTail>,
-                                                          c->block_threads, 0);
+                                                          c->block_threads, smem);
     if (e != cudaSuccess) return from_cuda(e);
     if (per_sm < 1) return LVB_EDEVICE;
     const long long want = (c->n + (long long)c->block_threads * kCheckUnroll - 1) /
@@ -935,7 +939,8 @@ int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
         if (rc) return rc;
     }
     const cudaError_t e =
-        launch_coop(k_step<false, NoTail>, dim3(c->step_blocks), dim3(c->block_threads), c->stream,
+        launch_coop(k_step<false, NoTail>, dim3(c->step_blocks), dim3(c->block_threads),
+                    (size_t)check_smem_bytes(c->block_threads), c->stream,
                     (const float4 *)pos_r, (const float4 *)vel, a4, c->s, IntegrateArgs{},
                     NoTail{});
     return from_cuda(e);

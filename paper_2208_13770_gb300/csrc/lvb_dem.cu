@@ -336,7 +336,7 @@ int launch_fused(dem_ctx *c)
     rc = fused_shape(c, &grid, &block);
     if (rc) return rc;
     const DemDev &d = c->d;
-    return from_cuda(launch_coop(k_step<true, DemTail>, grid, block, c->stream,
+    return from_cuda(launch_coop(k_step<true, DemTail>, grid, block, 0, c->stream,
                                  (const float4 *)d.pos, (const float4 *)d.vstar,
                                  (const float4 *)d.acc, step_state(c->bp), integrate_args(d),
                                  DemTail{d}));

@@ -330,16 +330,17 @@ cudaError_t add_coop_kernel(cudaGraphNode_t *out, cudaGraph_t g, const cudaGraph
     return cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &v);
 }
 
-// Launches fn(args...) cooperatively on `stream`.
+// Launches fn(args...) cooperatively on `stream` with `smem` bytes of
+// dynamic shared memory.
 template <typename... P, typename... A>
-cudaError_t launch_coop(void (*fn)(P...), dim3 grid, dim3 block, cudaStream_t stream,
+cudaError_t launch_coop(void (*fn)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
                         A... args)
 {
     static_assert(sizeof...(P) == sizeof...(A), "argument count");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;

@@ -593,96 +593,272 @@ __device__ __forceinline__ long long block_scan_any(long long v, long long *tota
 }
 
 // ---------------------------------------------------------------------------
-// a1 (+ a2 with the PARTIAL trigger): the check pass.  Block b takes
-// tiles b, b + grid, ... of blockDim * kCheckUnroll particles; in a tile each
-// warp checks kCheckUnroll chunks of 32 consecutive particles (loads of all
-// chunks first, so several are in flight), writes one ballot word per chunk
-// and compacts the flagged ids, either with one atomic per chunk that has
-// flags (warp scheme) or with one per tile (block scheme, two barriers per
-// tile that has flags).  The warp then computes the new reference states of
-// the particles it flagged (update_warp).
-// ---------------------------------------------------------------------------
-template <bool kFused>
-__device__ __forceinline__ void check_pass(const DevState &s, const float4 *__restrict__ pos_in,
-                                           const float4 *vel, const float4 *acc,
-                                           const IntegrateArgs &ia, bool inc, int step,
-                                           int *nF_acc)
+// Flagged particles a warp found in the check and has yet to update: their
+// ids and indices in the flagged list, in shared memory (per warp), so that
+// the updates' dependent loads run after the warp's tiles instead of
+// holding up the block's stream of tiles.
+constexpr int kPending = 32;
+
+struct Pending {
+    int *id;    // kPending entries of this warp
+    int *k;
+    int n;      // warp-uniform count
+};
+
+// Updates the warp's pending flagged particles (update_warp) and empties
+// the list.  New positions written earlier in this kernel by the warp's own
+// lanes (DEM form) are made visible to the whole warp first.
+__device__ __forceinline__ void flush_pending(const DevState &s, Pending &pd, const float4 *pos,
+                                              const float4 *vel, const float4 *acc, int step)
+{
+    __syncwarp();
+    for (int t = 0; t < pd.n; ++t) update_warp(s, pd.id[t], pd.k[t], pos, vel, acc, step);
+    __syncwarp();
+    pd.n = 0;
+}
+
+// a1 (+ a2 with the PARTIAL trigger) for U chunks of 32 consecutive
+// particles held by one warp (chunk u starts at cu[u], a multiple of 32; f[u]
+// is this lane's flag in it): one ballot word per chunk, compaction of the
+// flagged ids -- one atomic per warp's chunks with flags (warp scheme), or
+// one per block tile after a block scan (block scheme: two block barriers,
+// so every thread of the block makes the same calls) -- and, with inc, the
+// flagged particles join the warp's pending list (updated when it fills
+// and after the pass).
+template <int U>
+__device__ __forceinline__ void flag_chunks(const DevState &s, const int (&cu)[U],
+                                            const bool (&f)[U], const float4 *pos,
+                                            const float4 *vel, const float4 *acc, bool inc,
+                                            int step, int *nF_acc, Pending &pd)
 {
     __shared__ int s_cnt[32];
     __shared__ int s_base;
-    const float4 *pos = kFused ? ia.pos : pos_in;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
+    unsigned b[U];
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        b[u] = __ballot_sync(FULL, f[u]);
+        if (lane == 0 && cu[u] < s.n) s.bits[cu[u] >> 5] = b[u];
+        cnt += __popc(b[u]);
+    }
+    int k0 = 0;
+    if (s.compact_block) {
+        if (!__syncthreads_or(cnt)) return;
+        if (lane == 0) s_cnt[warp] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const int v = s_cnt[w];
+                s_cnt[w] = run;
+                run += v;
+            }
+            s_base = atomicAdd(nF_acc, run);
+        }
+        __syncthreads();
+        k0 = s_base + s_cnt[warp];
+    } else {
+        if (!cnt) return;
+        if (lane == 0) k0 = atomicAdd(nF_acc, cnt);
+        k0 = __shfl_sync(FULL, k0, 0);
+    }
+    if (!cnt) return;
+    int kb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        kb[u] = k0;
+        if (b[u] >> lane & 1u) s.fid[k0 + __popc(b[u] & lt)] = cu[u] + lane;
+        k0 += __popc(b[u]);
+    }
+    if (inc) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (pd.n + __popc(b[u]) > kPending) flush_pending(s, pd, pos, vel, acc, step);
+            if (b[u] >> lane & 1u) {
+                const int r = __popc(b[u] & lt);
+                pd.id[pd.n + r] = cu[u] + lane;
+                pd.k[pd.n + r] = kb[u] + r;
+            }
+            pd.n += __popc(b[u]);
+        }
+    }
+}
+
+// The check pass of the DEM form: each thread first performs the driver's
+// position half-step of its particles (integrate_one), so the positions are
+// produced here and read back from registers.  Block b takes tiles b,
+// b + grid, ... of blockDim * kCheckUnroll particles; in a tile each warp
+// checks kCheckUnroll chunks of 32 (loads of all chunks first).
+__device__ __forceinline__ void check_pass_fused(const DevState &s, const float4 *vel,
+                                                 const float4 *acc, const IntegrateArgs &ia,
+                                                 bool inc, int step, int *nF_acc)
+{
+    __shared__ int pend_id[kStepMaxThreads / 32][kPending], pend_k[kStepMaxThreads / 32][kPending];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Pending pd{pend_id[warp], pend_k[warp], 0};
     const int tile = blockDim.x * kCheckUnroll;
     for (int t0 = blockIdx.x * tile; t0 < s.n; t0 += gridDim.x * tile) {
         float4 p[kCheckUnroll], q[kCheckUnroll];
+        int cu[kCheckUnroll];
+        bool f[kCheckUnroll];
 #pragma unroll
         for (int u = 0; u < kCheckUnroll; ++u) {
-            const int i = t0 + u * blockDim.x + warp * 32 + lane;
+            cu[u] = t0 + u * blockDim.x + warp * 32;
+            const int i = cu[u] + lane;
             if (i < s.n) {
-                p[u] = kFused ? integrate_one(ia, geom_of(s, i), i) : __ldg(pos_in + i);
+                p[u] = integrate_one(ia, geom_of(s, i), i);
                 q[u] = s.ref[i];
             }
         }
-        unsigned b[kCheckUnroll];
-        int cnt = 0;
 #pragma unroll
         for (int u = 0; u < kCheckUnroll; ++u) {
-            const int cu = t0 + u * blockDim.x + warp * 32;   // chunk start, a multiple of 32
-            const int i = cu + lane;
-            bool f = false;
+            const int i = cu[u] + lane;
+            f[u] = false;
             if (i < s.n) {
-                f = violates(p[u], q[u]);
+                f[u] = violates(p[u], q[u]);
                 if (!(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(p[u].z)))
                     atomicOr(&s.cnt->err, DERR_NAN);
             }
-            b[u] = __ballot_sync(FULL, f);
-            if (lane == 0 && cu < s.n) s.bits[cu >> 5] = b[u];
-            cnt += __popc(b[u]);
         }
-        int k0 = 0;
-        if (s.compact_block) {
-            // one atomic per tile: warp counts, block scan by thread 0
-            if (!__syncthreads_or(cnt)) continue;
-            if (lane == 0) s_cnt[warp] = cnt;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int run = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                    const int v = s_cnt[w];
-                    s_cnt[w] = run;
-                    run += v;
-                }
-                s_base = atomicAdd(nF_acc, run);
-            }
-            __syncthreads();
-            k0 = s_base + s_cnt[warp];
-        } else {
-            if (!cnt) continue;
-            if (lane == 0) k0 = atomicAdd(nF_acc, cnt);
-            k0 = __shfl_sync(FULL, k0, 0);
-        }
-        if (!cnt) continue;
-        int kb[kCheckUnroll];
-#pragma unroll
-        for (int u = 0; u < kCheckUnroll; ++u) {
-            kb[u] = k0;
-            if (b[u] >> lane & 1u) s.fid[k0 + __popc(b[u] & lt)] = t0 + u * blockDim.x + warp * 32 + lane;
-            k0 += __popc(b[u]);
-        }
-        if (inc) {
-            // the new positions of these chunks were written by the warp's
-            // own lanes (DEM form): make them visible to the whole warp
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < kCheckUnroll; ++u)
-                for (unsigned m = b[u]; m; m &= m - 1) {
-                    const int src = __ffs(m) - 1;
-                    update_warp(s, t0 + u * blockDim.x + warp * 32 + src,
-                                kb[u] + __popc(b[u] & ((1u << src) - 1u)), pos, vel, acc, step);
-                }
-        }
+        flag_chunks<kCheckUnroll>(s, cu, f, ia.pos, vel, acc, inc, step, nF_acc, pd);
     }
+    if (pd.n) flush_pending(s, pd, ia.pos, vel, acc, step);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk copies into shared memory (cp.async.bulk, completion counted by an
+// mbarrier), for the check pass of the broad phase alone.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 4;                 // tiles in flight per block
+constexpr unsigned kStageWaitSpins = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Global -> shared bulk copy of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) that completes `bytes` transactions on *bar.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    unsigned long long g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(g), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for a stage: true when its copies have landed.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < kStageWaitSpins; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Dynamic shared memory of the check pass for a block of `threads`.
+__host__ __device__ constexpr int check_smem_bytes(int threads)
+{
+    return kStages * threads * 2 * (int)sizeof(float4);
+}
+
+// The check pass of the broad phase alone.  Block b takes tiles b, b + grid,
+// ... of blockDim particles; thread 0 keeps kStages tiles of pos and ref in
+// flight as bulk copies into a ring of shared-memory stages, every thread
+// checks its particle from shared memory, and the stage is refilled once
+// the whole block is done with it.  A stage whose copies do not land within
+// kStageWaitSpins polls is reported (DERR_SYNC) and skipped, never waited
+// for indefinitely.
+__device__ __forceinline__ void check_pass_stream(const DevState &s, const float4 *__restrict__ pos,
+                                                  const float4 *vel, const float4 *acc, bool inc,
+                                                  int step, int *nF_acc)
+{
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar[kStages];
+    __shared__ int pend_id[kStepMaxThreads / 32][kPending], pend_k[kStepMaxThreads / 32][kPending];
+    const int T = blockDim.x, tid = threadIdx.x, warp = tid >> 5;
+    Pending pd{pend_id[warp], pend_k[warp], 0};
+    float4 *spos = reinterpret_cast<float4 *>(dsm);
+    float4 *sref = spos + kStages * T;
+    const int ntiles = (s.n + T - 1) / T;
+    const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int j) {   // thread 0 only
+        const int t0 = (blockIdx.x + j * gridDim.x) * T;
+        const unsigned bytes = (unsigned)min(T, s.n - t0) * (unsigned)sizeof(float4);
+        const int st = j % kStages;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[st], 2u * bytes);
+        bulk_load(spos + st * T, pos + t0, bytes, &bar[st]);
+        bulk_load(sref + st * T, s.ref + t0, bytes, &bar[st]);
+    };
+    int issued = 0;   // meaningful in thread 0
+    if (tid == 0)
+        for (; issued < min(kStages, mine); ++issued) issue(issued);
+    bool failed = false;
+    int j = 0;
+    for (; j < mine; ++j) {
+        const int st = j % kStages;
+        const bool landed = stage_wait(&bar[st], (unsigned)(j / kStages) & 1u);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) atomicOr(&s.cnt->err, DERR_SYNC);
+            failed = true;
+            break;
+        }
+        const int t0 = (blockIdx.x + j * gridDim.x) * T;
+        const int i = t0 + tid;
+        const int cu[1] = {t0 + warp * 32};
+        bool f[1] = {false};
+        if (i < s.n) {
+            const float4 p = spos[st * T + tid];
+            f[0] = violates(p, sref[st * T + tid]);
+            if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z)))
+                atomicOr(&s.cnt->err, DERR_NAN);
+        }
+        flag_chunks<1>(s, cu, f, pos, vel, acc, inc, step, nF_acc, pd);
+        __syncthreads();   // the block is done with this stage
+        if (tid == 0 && j + kStages < mine) issue(issued++);
+    }
+    if (failed && tid == 0) {
+        // copies still in flight land before the block leaves (bounded)
+        for (int k = j; k < issued; ++k)
+            stage_wait(&bar[k % kStages], (unsigned)(k / kStages) & 1u);
+    }
+    if (pd.n) flush_pending(s, pd, pos, vel, acc, step);
 }
 
 static __device__ __noinline__ void full_update_pass(const DevState &s, const float4 *pos,
@@ -908,7 +1084,10 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     const float4 *pos = kFused ? ia.pos : pos_in;
     int *ovf = &c->ovf[par];
 
-    check_pass<kFused>(s, pos_in, vel, acc, ia, inc, step, &c->nF_acc[par]);
+    if constexpr (kFused)
+        check_pass_fused(s, vel, acc, ia, inc, step, &c->nF_acc[par]);
+    else
+        check_pass_stream(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
     if (!grid_barrier(s)) return;
     const int nF = *(volatile int *)&c->nF_acc[par];
     int upd;
