@@ -279,49 +279,47 @@ __device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
     __syncwarp();
 }
 
-// Removes partner i from unflagged row j (warp): its entry becomes -1.
-__device__ __forceinline__ void row_remove_warp(const DevState &s, int j, int i)
+// Removes partner i from unflagged row j (one lane): its entry becomes -1.
+// Rows are short; four entries are loaded at a time.
+__device__ __forceinline__ void lane_remove(const DevState &s, int j, int i)
 {
-    const int lane = threadIdx.x & 31;
     const int off = s.row_off[j], len = min(s.row_len[j], s.row_cap[j]);
-    for (int e0 = 0; e0 < len; e0 += 32) {
-        const int e = e0 + lane;
-        const bool hit = e < len && s.col[off + e] == i;
-        if (hit) s.col[off + e] = -1;
-        if (__any_sync(FULL, hit)) return;
+    for (int e = 0; e < len; e += 4) {
+        int v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = e + u < len ? s.col[off + e + u] : -2;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (v[u] == i) {
+                s.col[off + e + u] = -1;
+                return;
+            }
     }
 }
 
-// Adds partner i to unflagged row j (warp): a -1 entry below row_len,
+// Adds partner i to unflagged row j (one lane): a -1 entry below row_len,
 // claimed with compare-and-swap, else the next slot at the end (also by
 // compare-and-swap: a slot past row_len holds -1 and another warp's search
 // may claim it first).  A full row raises *ovf (the re-layout rebuilds it).
-__device__ __forceinline__ void row_insert_warp(const DevState &s, int j, int i, int *ovf)
+__device__ __forceinline__ void lane_insert(const DevState &s, int j, int i, int *ovf)
 {
-    const int lane = threadIdx.x & 31;
     const int off = s.row_off[j], cap = s.row_cap[j], len = min(s.row_len[j], cap);
-    for (int e0 = 0; e0 < len; e0 += 32) {
-        const int e = e0 + lane;
-        unsigned m = __ballot_sync(FULL, e < len && s.col[off + e] < 0);
-        while (m) {
-            const int src = __ffs(m) - 1;
-            int won = 0;
-            if (lane == src) won = atomicCAS(&s.col[off + e], -1, i) == -1;
-            if (__shfl_sync(FULL, won, src)) return;
-            m &= m - 1;
-        }
+    for (int e = 0; e < len; e += 4) {
+        int v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = e + u < len ? s.col[off + e + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (v[u] < 0 && atomicCAS(&s.col[off + e + u], -1, i) == -1) return;
     }
-    if (lane == 0) {
-        for (int t = 0; t <= cap; ++t) {
-            const int p = atomicAdd(&s.row_len[j], 1);
-            if (p >= cap) {
-                atomicExch(ovf, 1);
-                break;
-            }
-            if (atomicCAS(&s.col[off + p], -1, i) == -1) break;
+    for (int t = 0; t <= cap; ++t) {
+        const int p = atomicAdd(&s.row_len[j], 1);
+        if (p >= cap) {
+            atomicExch(ovf, 1);
+            return;
         }
+        if (atomicCAS(&s.col[off + p], -1, i) == -1) return;
     }
-    __syncwarp();
 }
 
 // a4 + a5 for flagged particle k of the list (warp), i = fid[k]:
@@ -337,6 +335,8 @@ __device__ __forceinline__ void row_insert_warp(const DevState &s, int j, int i,
 // A pair is a function of the two reference states (Def. verletlist) and an
 // unflagged particle's state does not change, so these tests decide exactly
 // which entries of the unflagged rows change; no other warp touches row i.
+// The edits of other rows run one per lane, in parallel; the first 32 old
+// partners and the first 32 stencil candidates are loaded together.
 static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF, bool direct,
                                                int *ovf)
 {
@@ -346,7 +346,6 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     const int i = s.fid[k];
     const float4 qn = s.fref[k], qo = s.oref[k];
     const int off = s.row_off[i], cap = s.row_cap[i], len0 = min(s.row_len[i], cap);
-    // the stencil's cell counts first: their loads overlap the removals
     const SceneGeom &g = geom_of(s, i);
     const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
     const int ci = cell_key(g, qn.x, qn.y, qn.z) - g.cell_base;
@@ -359,47 +358,57 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
             cnt_l = s.cell_cnt[cid];
         }
     }
-    // 1. removals
-    for (int e0 = 0; e0 < len0; e0 += 32) {
-        const int e = e0 + lane;
-        int j = -1;
-        bool rm = false;
-        if (e < len0) {
-            j = s.col[off + e];
-            if (j >= 0 && !bit_of(s.bits, j)) {
-                const float4 rj = s.ref[j];
-                rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
-            }
-        }
-        for (unsigned m = __ballot_sync(FULL, rm); m; m &= m - 1)
-            row_remove_warp(s, __shfl_sync(FULL, j, __ffs(m) - 1), i);
-    }
-    // 2. stencil (+ direct test) and 3. insertions
+    const int jo0 = lane < len0 ? s.col[off + lane] : -1;
     cnt_l = min(cnt_l, ccap);
     const int incl = warp_incl_scan(cnt_l);
     const int excl = incl - cnt_l;
     const int total = __shfl_sync(FULL, incl, 31);
-    int found = 0;
-    for (int b0 = 0; b0 < total; b0 += 32) {
-        const int kk = b0 + lane;
+    // candidate kk of the stencil: its cell by a 5-step shuffle search
+    auto cand_idx = [&](int kk) {
         int c = 0;
 #pragma unroll
         for (int st = 16; st >= 1; st >>= 1)
             c += (__shfl_sync(FULL, incl, c + st - 1) <= kk) ? st : 0;
         const int cc = __shfl_sync(FULL, cid, c);
         const int ex = __shfl_sync(FULL, excl, c);
-        bool hit = false, ins = false;
+        return (long long)cc * ccap + (kk - ex);
+    };
+    const long long idx0 = cand_idx(lane);
+    const int jc0 = lane < total ? s.cell_id[idx0] : -1;
+    const float4 rc0 = lane < total ? s.cell_ref[idx0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // 1. removals
+    for (int e0 = 0; e0 < len0; e0 += 32) {
+        const int e = e0 + lane;
+        const int j = e0 == 0 ? jo0 : (e < len0 ? s.col[off + e] : -1);
+        bool rm = false;
+        if (e < len0 && j >= 0 && !bit_of(s.bits, j)) {
+            const float4 rj = s.ref[j];
+            rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
+        }
+        if (rm) lane_remove(s, j, i);
+    }
+    // 2. stencil (+ direct test) and 3. insertions
+    int found = 0;
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const int kk = b0 + lane;
         int j = -1;
-        if (kk < total) {
-            const long long idx = (long long)cc * ccap + (kk - ex);
-            j = s.cell_id[idx];
-            if (j >= 0 && j != i) {
-                const bool fj = bit_of(s.bits, j);
-                if (!(direct && fj)) {
-                    const float4 rj = s.cell_ref[idx];
-                    hit = pair_hit(qn, rj);
-                    ins = hit && !fj && !pair_hit(qo, rj);
-                }
+        float4 rj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (b0 == 0) {
+            j = jc0;
+            rj = rc0;
+        } else {
+            const long long idx = cand_idx(kk);
+            if (kk < total) {
+                j = s.cell_id[idx];
+                rj = s.cell_ref[idx];
+            }
+        }
+        bool hit = false, ins = false;
+        if (kk < total && j >= 0 && j != i) {
+            const bool fj = bit_of(s.bits, j);
+            if (!(direct && fj)) {
+                hit = pair_hit(qn, rj);
+                ins = hit && !fj && !pair_hit(qo, rj);
             }
         }
         const unsigned m = __ballot_sync(FULL, hit);
@@ -408,8 +417,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
             if (p < cap) s.col[off + p] = j;
         }
         found += __popc(m);
-        for (unsigned mi = __ballot_sync(FULL, ins); mi; mi &= mi - 1)
-            row_insert_warp(s, __shfl_sync(FULL, j, __ffs(mi) - 1), i, ovf);
+        if (ins) lane_insert(s, j, i, ovf);
     }
     if (direct) {
         for (int b0 = 0; b0 < nF; b0 += 32) {
