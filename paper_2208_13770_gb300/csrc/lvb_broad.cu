@@ -479,9 +479,12 @@ int size_step(lvb_ctx *c)
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int smem = check_smem_bytes(c->block_threads);
+    // the attribute belongs to the kernel, for every context of the process:
+    // always the largest any block size needs
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_step<false, NoTail>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 check_smem_bytes(kStepMaxThreads));
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<false, NoTail>,
                                                           c->block_threads, smem);
