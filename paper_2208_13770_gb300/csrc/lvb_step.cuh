@@ -551,7 +551,7 @@ __device__ __forceinline__ bool grid_barrier(const DevState &s)
         const unsigned long long old = atom_add_acq_rel(&c->bar_word, 1ULL);
         int ok = 1;
         if ((unsigned)old == nb - 1) {
-            c->barriers += 1;
+            atomicAdd(&c->barriers, 1ULL);
             red_add_release(&c->bar_word, (1ULL << 32) - nb);
         } else {
             const unsigned gen = (unsigned)(old >> 32);
@@ -1104,15 +1104,16 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     else upd = s.n;
     unsigned long long t1 = 0;
     if (lead) {
+        // stores and reductions only: no load on the step's last path
         c->nF_acc[par ^ 1] = 0;
         c->ovf[par ^ 1] = 0;
         c->nF = nF;
-        c->steps += 1;
-        c->flagged_total += nF;
-        c->updated_total += upd;
-        if (upd) c->rebuild_steps += 1;
         c->last_flagged = nF;
         c->last_updated = upd;
+        atomicAdd((unsigned long long *)&c->steps, 1ULL);
+        atomicAdd((unsigned long long *)&c->flagged_total, (unsigned long long)nF);
+        atomicAdd((unsigned long long *)&c->updated_total, (unsigned long long)upd);
+        if (upd) atomicAdd((unsigned long long *)&c->rebuild_steps, 1ULL);
         atomicAdd(&c->kernels, 1ULL);
         if (s.trace) {
             t1 = global_ns();
