@@ -200,6 +200,13 @@ def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, f
 
 BATCH_STEPS = 2000
 
+# DRAM bytes (read + write) per launch of the broad-phase step kernel, from
+# one ncu capture of the current kernel on each workload (mean of two
+# launches; the command and the counters are in profiles/).  They go stale
+# when the kernel changes: set them to None until the capture is repeated.
+NCU_TRAFFIC_SETTLING = 7.04e6      # profiles/k_step_settling200k_ncu.txt
+NCU_TRAFFIC_BATCHED = 213.5e6      # profiles/k_step_batched512_ncu.txt
+
 
 def _batched(lvb, torch, hbm_peak, warmup):
     """512 independent settling scenes (6.2M particles) advanced together:
@@ -250,6 +257,7 @@ def _batched(lvb, torch, hbm_peak, warmup):
                                "broad": t_ms, "forces": float(ph["phase_ms"][2]) / BATCH_STEPS},
         "roofline": {"bound": "hbm", "kernel": "broad phase (check + partial rebuild)",
                      "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "traffic": NCU_TRAFFIC_BATCHED, "traffic_source": "ncu capture",
                      "bytes_per_launch": bytes_bp, "ms_per_launch": t_ms},
         "flagged_per_step": F,
         "rebuild_fraction": (s1["updated_total"] - s0["updated_total"]) / (n * BATCH_STEPS),
@@ -571,7 +579,8 @@ def run_native(args):
     achieved = b / (t_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "bytes_per_launch": b, "ms_per_launch": t_ms}
+            "traffic": NCU_TRAFFIC_SETTLING if dom.startswith("broad") else None,
+            "traffic_source": "ncu capture", "bytes_per_launch": b, "ms_per_launch": t_ms}
     bp_ach = bytes_bp / (ph[1] * 1e-3) / 1e9
 
     cpu = None
