@@ -231,6 +231,13 @@ int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *ac
 #define LVB_OPT_BARRIER_SPINS 7 /* polls (L2 round trips) before a barrier gives
                                 up, 1 .. 2^22 (default 2^22, about a second or
                                 two) */
+#define LVB_OPT_DIRECT_MAX 8  /* largest flagged count whose rebuild runs in one
+                                phase (cell moves and rows together, flagged
+                                pairs found by a direct test of the flagged
+                                particles against each other); above it the
+                                moves come first, then a barrier, then the
+                                rows from the final cells.  0 .. 2^20
+                                (default 4096) */
 
 /* Values of LVB_OPT_COMPACT. */
 #define LVB_COMPACT_WARP  0  /* one atomic per 32-particle chunk with flags,

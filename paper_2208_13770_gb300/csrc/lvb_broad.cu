@@ -805,6 +805,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
 
     s.n = (int)n;
     s.bar_spins = kBarrierSpins;
+    s.direct_max = kFlaggedDirectMax;
     s.nwords = c->nwords;
     s.trigger = trigger;
     s.skin_kind = skin->kind;
@@ -973,6 +974,9 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     } else if (option == LVB_OPT_BARRIER_SPINS) {
         if (value < 1 || value > kBarrierSpins) return LVB_EINVAL;
         c->s.bar_spins = (unsigned)value;
+    } else if (option == LVB_OPT_DIRECT_MAX) {
+        if (value < 0 || value > (1 << 20)) return LVB_EINVAL;
+        c->s.direct_max = (int)value;
     } else {
         return LVB_EINVAL;
     }

@@ -47,7 +47,7 @@ struct DevCounters {
     int last_flagged;
     int last_updated;
     int pad0, pad1;
-    unsigned long long bar_word;  // grid barrier: generation << 32 | arrivals
+    unsigned long long bar_cnt[2];  // grid-barrier arrivals in the step kernel, by step parity
     long long steps;
     long long rebuild_steps;
     long long flagged_total;

@@ -3,7 +3,6 @@
 // One step of the local Verlet buffer is one cooperative kernel, k_step,
 // whose phases are separated by grid-wide barriers (all its blocks are
 // co-resident: cooperative launch, grid sized by occupancy):
-//   re-layout  first, only if the previous step left a row overflowed
 //   check      every particle: displacement check (Eq. update), ballot
 //              words, compaction of the flagged ids; with the PARTIAL
 //              trigger the warp that flags a particle also computes its new
@@ -13,14 +12,16 @@
 //   rebuild    PARTIAL: each flagged particle moves to its new cell slot,
 //              gets its new row by the 27-cell stencil (Algorithm 1 on the
 //              extended spheres, Eq. bounding_sphere) plus a direct test
-//              against the other flagged particles, and patches the rows of
-//              its unflagged partners in place (removed pairs become -1,
-//              new pairs take a -1 slot or the row's end) -- one phase, no
-//              barrier (many flagged particles: moves first, then a barrier)
+//              against the other flagged particles of its scene, and
+//              patches the rows of its unflagged partners in place (removed
+//              pairs become -1, new pairs take a -1 slot or the row's end)
+//              -- one phase, no barrier (many flagged particles: moves
+//              first, then a barrier)
 //              GLOBAL / ALWAYS (Def. autoverlet / no buffer): new reference
 //              states, cells and rows of every particle
-//   tail       the DEM driver's forces (k_step instantiated by lvb_dem.cu),
-//              after a barrier and the re-layout of overflowed rows
+//   -- barrier --
+//   re-layout  only if a row overflowed in the rebuild
+//   tail       the DEM driver's forces (k_step instantiated by lvb_dem.cu)
 // A step with nothing flagged is the check and one barrier.  The kernel is
 // included by lvb_broad.cu (the broad phase alone) and lvb_dem.cu (a whole
 // DEM step per launch).
@@ -32,7 +33,8 @@ namespace lvb {
 
 constexpr int kStepMaxThreads = 1024;     // block size limit of k_step (one block per SM)
 constexpr int kCheckUnroll = 2;           // 32-particle chunks a warp has in flight
-constexpr int kFlaggedDirectMax = 4096;   // flagged particles tested pairwise directly
+constexpr int kFlaggedDirectMax = 4096;   // default of DevState::direct_max
+constexpr int kDirectUnroll = 4;          // flagged reference states per lane in flight
 constexpr unsigned kBarrierSpins = 1u << 22;   // ~1-3 s of polling (L2 round trips) before a barrier gives up
 
 // Written by kernels straight into mapped host memory: requests to grow a
@@ -85,6 +87,8 @@ struct DevState {
                           // blocks: 0, or 1 to make every wait run out (the
                           // failure test, LVB_OPT_BARRIER_EXTRA)
     unsigned bar_spins;   // polls before a barrier gives up
+    int direct_max;       // largest flagged count rebuilt in one phase with
+                          // the direct flagged-pair test (LVB_OPT_DIRECT_MAX)
 };
 
 // gate modes of the separate full-build kernels (init, store growth)
@@ -322,6 +326,52 @@ __device__ __forceinline__ void lane_insert(const DevState &s, int j, int i, int
     }
 }
 
+// One removal (partner i leaves row jr) and one insertion (partner i joins
+// row ji) by one lane, their loads interleaved so that both edits take the
+// latency of one: the two rows' bounds together, then four entries of each
+// at a time.  jr or ji < 0: no such edit.  Same rules as lane_remove and
+// lane_insert (the two rows differ: a removed pair is not a new one).
+__device__ __forceinline__ void lane_edit(const DevState &s, int jr, int ji, int i, int *ovf)
+{
+    int offr = 0, lenr = 0, offi = 0, capi = 0, leni = 0;
+    if (jr >= 0) {
+        offr = s.row_off[jr];
+        lenr = min(s.row_len[jr], s.row_cap[jr]);
+    }
+    if (ji >= 0) {
+        offi = s.row_off[ji];
+        capi = s.row_cap[ji];
+        leni = min(s.row_len[ji], capi);
+    }
+    bool dr = jr < 0 || lenr == 0, di = ji < 0;
+    for (int e = 0; !dr || (!di && e < leni); e += 4) {
+        int vr[4], vi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            vr[u] = !dr && e + u < lenr ? s.col[offr + e + u] : -2;
+            vi[u] = !di && e + u < leni ? s.col[offi + e + u] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!dr && vr[u] == i) {
+                s.col[offr + e + u] = -1;
+                dr = true;
+            }
+            if (!di && vi[u] < 0 && atomicCAS(&s.col[offi + e + u], -1, i) == -1) di = true;
+        }
+        if (e + 4 >= lenr) dr = true;
+    }
+    if (di) return;
+    for (int t = 0; t <= capi; ++t) {
+        const int p = atomicAdd(&s.row_len[ji], 1);
+        if (p >= capi) {
+            atomicExch(ovf, 1);
+            return;
+        }
+        if (atomicCAS(&s.col[offi + p], -1, i) == -1) return;
+    }
+}
+
 // a4 + a5 for flagged particle k of the list (warp), i = fid[k]:
 //   1. each old partner j that is unflagged and no longer a pair (test on
 //      i's new reference state) loses i from its row;
@@ -376,7 +426,11 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     const long long idx0 = cand_idx(lane);
     const int jc0 = lane < total ? s.cell_id[idx0] : -1;
     const float4 rc0 = lane < total ? s.cell_ref[idx0] : make_float4(0.f, 0.f, 0.f, 0.f);
-    // 1. removals
+    // 1. removals.  An old row of up to 32 entries is held in registers
+    // (jo0), so the new row may overwrite it at once: the removals of that
+    // row are only decided here and made together with the first batch of
+    // insertions (lane_edit); a longer row is done first, entry by entry.
+    int jr0 = -1;
     for (int e0 = 0; e0 < len0; e0 += 32) {
         const int e = e0 + lane;
         const int j = e0 == 0 ? jo0 : (e < len0 ? s.col[off + e] : -1);
@@ -385,10 +439,12 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
             const float4 rj = s.ref[j];
             rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
         }
-        if (rm) lane_remove(s, j, i);
+        if (len0 <= 32) jr0 = rm ? j : -1;
+        else if (rm) lane_remove(s, j, i);
     }
     // 2. stencil (+ direct test) and 3. insertions
     int found = 0;
+    if (total == 0 && jr0 >= 0) lane_remove(s, jr0, i);
     for (int b0 = 0; b0 < total; b0 += 32) {
         const int kk = b0 + lane;
         int j = -1;
@@ -417,23 +473,39 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
             if (p < cap) s.col[off + p] = j;
         }
         found += __popc(m);
-        if (ins) lane_insert(s, j, i, ovf);
+        if (b0 == 0) {
+            lane_edit(s, jr0, ins ? j : -1, i, ovf);
+        } else if (ins) {
+            lane_insert(s, j, i, ovf);
+        }
     }
     if (direct) {
-        for (int b0 = 0; b0 < nF; b0 += 32) {
-            const int kk = b0 + lane;
-            bool hit = false;
-            int j = -1;
-            if (kk < nF && kk != k) {
-                j = s.fid[kk];
-                hit = pair_hit(qn, s.fref[kk]);
+        // kDirectUnroll reference states per lane in flight; the id is
+        // loaded only for a hit, and a hit in another scene (scenes share
+        // one coordinate frame) is dropped
+        const int lo = g.first, hi = g.first + g.count;
+        for (int b0 = 0; b0 < nF; b0 += 32 * kDirectUnroll) {
+            float4 rf[kDirectUnroll];
+#pragma unroll
+            for (int u = 0; u < kDirectUnroll; ++u) {
+                const int kk = b0 + u * 32 + lane;
+                rf[u] = kk < nF ? s.fref[kk] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const unsigned m = __ballot_sync(FULL, hit);
-            if (hit) {
-                const int p = found + __popc(m & lt);
-                if (p < cap) s.col[off + p] = j;
+#pragma unroll
+            for (int u = 0; u < kDirectUnroll; ++u) {
+                const int kk = b0 + u * 32 + lane;
+                int j = -1;
+                if (kk < nF && kk != k && pair_hit(qn, rf[u])) {
+                    j = s.fid[kk];
+                    if (j < lo || j >= hi) j = -1;
+                }
+                const unsigned m = __ballot_sync(FULL, j >= 0);
+                if (j >= 0) {
+                    const int p = found + __popc(m & lt);
+                    if (p < cap) s.col[off + p] = j;
+                }
+                found += __popc(m);
             }
-            found += __popc(m);
         }
     }
     for (int e = found + lane; e < len0; e += 32) s.col[off + e] = -1;
@@ -510,25 +582,17 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill,
 }
 
 // ---------------------------------------------------------------------------
-// Grid-wide barrier of the step kernel (all blocks co-resident).  One 64-bit
-// word holds the generation (high half) and the arrivals (low half).  Thread
-// 0 of each block arrives with one acquire-release add; the last arrival
-// adds 2^32 - blocks (next generation, arrivals back to zero) with release
-// semantics, the others poll the generation with acquire loads.  Polling is
-// bounded: after s.bar_spins polls (kBarrierSpins unless a test lowers it)
-// the block records DERR_SYNC and leaves; every block then returns, and
-// later steps do nothing (the context reports LVB_ETIMEOUT).  Returns false
-// when the step must be abandoned.
+// Grid-wide barrier of the step kernel (all blocks co-resident).  A 64-bit
+// arrival counter per step parity: the kernel of a step counts on
+// bar_cnt[parity] (which starts at zero) and clears the other one for the
+// next step.  Thread 0 of each block arrives with a release add (no
+// return value to wait for) and polls with acquire loads until the counter
+// holds the arrivals of this barrier and of all earlier ones in the kernel.
+// Polling is bounded: after s.bar_spins polls (kBarrierSpins unless a test
+// lowers it) the block records DERR_SYNC and leaves; every block then
+// returns, and later steps do nothing (the context reports LVB_ETIMEOUT).
+// Returns false when the step must be abandoned.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long *p,
-                                                               unsigned long long v)
-{
-    unsigned long long old;
-    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
-                 : "=l"(old) : "l"(p), "l"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ void red_add_release(unsigned long long *p, unsigned long long v)
 {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
@@ -541,29 +605,40 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
+// the barrier state of this block (used by its thread 0 only)
+static __shared__ unsigned long long s_bar_need;   // arrivals up to the last barrier
+static __shared__ int s_bar_par;                   // parity of the step
+
+// Called by every thread at the start of the step kernel, before any barrier.
+__device__ __forceinline__ void grid_barrier_begin(const DevState &s, int par)
+{
+    if (threadIdx.x == 0) {
+        s_bar_need = 0;
+        s_bar_par = par;
+        if (blockIdx.x == 0) s.cnt->bar_cnt[par ^ 1] = 0;
+    }
+}
+
 __device__ __forceinline__ bool grid_barrier(const DevState &s)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         DevCounters *c = s.cnt;
-        const unsigned nb = gridDim.x + s.bar_extra;
-        const unsigned long long old = atom_add_acq_rel(&c->bar_word, 1ULL);
+        unsigned long long *w = &c->bar_cnt[s_bar_par];
+        const unsigned long long need = s_bar_need + gridDim.x + s.bar_extra;
+        s_bar_need = need;
+        red_add_release(w, 1ULL);
         int ok = 1;
-        if ((unsigned)old == nb - 1) {
-            atomicAdd(&c->barriers, 1ULL);
-            red_add_release(&c->bar_word, (1ULL << 32) - nb);
-        } else {
-            const unsigned gen = (unsigned)(old >> 32);
-            unsigned it = 0;
-            while ((unsigned)(ld_acquire(&c->bar_word) >> 32) == gen) {
-                if (++it > s.bar_spins) {
-                    atomicOr(&c->err, DERR_SYNC);
-                    ok = 0;
-                    break;
-                }
+        unsigned it = 0;
+        while (ld_acquire(w) < need) {
+            if (++it > s.bar_spins) {
+                atomicOr(&c->err, DERR_SYNC);
+                ok = 0;
+                break;
             }
         }
+        if (ok && blockIdx.x == 0) atomicAdd(&c->barriers, 1ULL);
         s_ok = ok;
     }
     __syncthreads();
@@ -1042,7 +1117,7 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
 }
 
 
-// The rebuild of a partial step (nF flagged).  Up to kFlaggedDirectMax
+// The rebuild of a partial step (nF flagged).  Up to s.direct_max
 // flagged particles: moves and patches in one phase, on different warps
 // (work items 0..nF-1 patch rows, nF..2nF-1 move cell slots; the patches
 // skip the flagged particles in the cells and test them directly); more:
@@ -1050,9 +1125,12 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
 // false when the step must be abandoned.
 static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int *ovf)
 {
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // work items go round the blocks first (item w to block w % grid), so
+    // that a few flagged particles spread over all SMs instead of filling
+    // the warps of the first blocks
+    const int w0 = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const bool direct = nF <= kFlaggedDirectMax;
+    const bool direct = nF <= s.direct_max;
     if (!direct) {
         for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
         if (!grid_barrier(s)) return false;
@@ -1076,9 +1154,18 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
 // ---------------------------------------------------------------------------
 template <bool kFused, class Tail>
 __global__ void __launch_bounds__(kStepMaxThreads, 1)
-k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, DevState s,
+k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, DevState sp,
        IntegrateArgs ia, Tail tail)
 {
+    // the context's state in shared memory: every phase (and the functions
+    // it calls) reads its fields from there rather than from the parameter
+    // space, whose lines miss on first use in each phase
+    __shared__ __align__(16) DevState s_sh;
+    static_assert(sizeof(DevState) % 4 == 0, "DevState is copied in words");
+    for (int t = threadIdx.x; t < (int)(sizeof(DevState) / 4); t += blockDim.x)
+        reinterpret_cast<int *>(&s_sh)[t] = reinterpret_cast<const int *>(&sp)[t];
+    __syncthreads();
+    const DevState &s = s_sh;
     DevCounters *c = s.cnt;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long t0 = (s.trace && lead) ? global_ns() : 0ULL;
@@ -1089,6 +1176,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     if (err & DERR_SYNC) return;   // a barrier failed earlier: the context is unusable
     const bool inc = s.trigger == LVB_TRIGGER_PARTIAL && !(err & DERR_STORE);
     const int step = (int)c->steps + 1, par = step & 1;
+    grid_barrier_begin(s, par);
     const float4 *pos = kFused ? ia.pos : pos_in;
     int *ovf = &c->ovf[par];
 

@@ -185,6 +185,7 @@ def lvb_step(ctx, pos_r, vel=None, acc=None):
 
 LVB_OPT_TRACE, LVB_OPT_BLOCK_THREADS, LVB_OPT_COMPACT = 3, 4, 5
 LVB_OPT_BARRIER_EXTRA, LVB_OPT_BARRIER_SPINS = 6, 7
+LVB_OPT_DIRECT_MAX = 8
 LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
 TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]
 

@@ -77,6 +77,43 @@ def test_batch_broad_phase_parity_per_scene(orc):
     ctx.close()
 
 
+def test_identical_scenes_never_pair_across_scenes(orc):
+    # four copies of the same scene in one context, moved by the same walk:
+    # every flagged particle has a flagged twin at the same position in each
+    # other scene, and the flagged counts stay small enough for the rebuild
+    # to test flagged particles against each other directly.  Each scene must
+    # still give exactly its own oracle result.
+    lvb = _lvb()
+    from oracle.statemachine import OracleLVB
+    one = scenes.settling(n=2500, seed=77, footprint=0.04, height=0.3)
+    sc = [one] * 4
+    off = np.concatenate([[0], np.cumsum([s.n for s in sc])]).astype(np.int64)
+    ctx = lvb.LVB(_dev(np.concatenate([s.pos for s in sc])), [s.lo for s in sc],
+                  [s.hi for s in sc], 1, 0.1, 1e-6, 0, 1.25, offsets=off)
+    rmax = np.float32(one.pos[:, 3].max())
+    H = np.float32(0.5 * 1.25 * 2.0 * float(rmax) * (1 + 2 ** -7) * (1 - 2 ** -8))
+    sm = OracleLVB(one.pos, 1, 0.1, 1e-6, H, 0)
+    rng = np.random.default_rng(8)
+    p = one.pos.copy()
+    flagged = 0
+    for k in range(8):
+        # a few percent of the particles jump past their skin each step
+        idx = rng.choice(one.n, 60, replace=False)
+        p[idx, :3] += rng.normal(0, 4e-4, size=(60, 3)).astype(np.float32)
+        ctx.step(_dev(np.concatenate([p] * 4)))
+        f, _ = sm.step(p)
+        flagged += int(f.sum())
+        pi, pj = ctx.pairs_ij()
+        ei = np.concatenate([sm.pi + off[q] for q in range(4)])
+        ej = np.concatenate([sm.pj + off[q] for q in range(4)])
+        assert np.array_equal(pi, ei) and np.array_equal(pj, ej), "step %d" % k
+    assert ctx.sync() == 0
+    st = ctx.stats()
+    assert st["flagged_total"] == 4 * flagged > 0
+    assert st["flagged_total"] // 8 < 4096
+    ctx.close()
+
+
 def test_batch_rejects_global_trigger():
     lvb = _lvb()
     sc = _scenes(2, seed=1)

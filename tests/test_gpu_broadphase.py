@@ -126,6 +126,20 @@ def test_hot_gas_many_rebuilds_parity(orc, threads, compact):
     assert st["barriers"] >= st["steps"]
 
 
+@pytest.mark.parametrize("direct_max", [0, 64])
+def test_hot_gas_two_phase_rebuild_parity(orc, direct_max):
+    # the rebuild with the cell moves first and a barrier before the rows
+    # (every step, or only on steps with more than 64 flagged) gives the
+    # same lists as the one-phase rebuild with the direct flagged test
+    lvb = _cuda()
+    s = scenes.ballistic(n=3000, seed=6, phi=0.3, vsigma=3.0)
+    st, _ = _run_trajectory(orc, s, scenes.ballistic_trajectory(s, 150), 0, 1, 0.1,
+                            options=((lvb.LVB_OPT_DIRECT_MAX, direct_max),))
+    assert st["updated_total"] > s.n
+    # one barrier after the check, one between moves and rows, one at the end
+    assert st["barriers"] >= st["steps"] + (st["rebuild_steps"] if direct_max == 0 else 0)
+
+
 def _random_walk(scene, steps, sigma, seed=0):
     rng = np.random.default_rng(seed)
     pos = scene.pos.copy()
@@ -284,3 +298,13 @@ def test_settling_full_size_parity(orc):
     s = scenes.settling()
     st, _ = _run_trajectory(orc, s, _random_walk(s, 6, 6e-5, seed=2), 0, 1, 0.1, every=3)
     assert st["n"] == 200_000
+
+
+def test_drum_full_size_parity(orc):
+    # the 2,000,000-sphere drum (lognormal radii, 0.2 m axis) at full size:
+    # complete pair-set, row, reference-state and contact parity after init
+    # and after three random-walk steps that flag a fifth of the particles
+    s = scenes.drum()
+    st, sm = _run_trajectory(orc, s, _random_walk(s, 3, 6e-5, seed=2), 0, 1, 0.1, every=3)
+    assert st["n"] == 2_000_000
+    assert st["flagged_total"] > 500_000

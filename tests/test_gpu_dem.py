@@ -179,3 +179,19 @@ def test_settling_full_size_step_parity(orc):
     st = dem.lvb.stats()
     assert st["steps"] == 201
     dem.close()
+
+
+def test_drum_full_size_step_parity(orc):
+    # 2,000,000 spheres in the rotating drum: 1,000 graph-replayed steps from
+    # the lattice start (the bed settles onto the wall), then one step checked
+    # over every particle
+    lvb = _lvb()
+    s = scenes.drum()
+    P = _params(orc, s)
+    dem = lvb.DEM(s)
+    dem.advance(1000)
+    in_contact = _check_step(orc, dem, s, P)
+    assert dem.sync() == 0
+    assert dem.lvb.stats()["steps"] == 1001
+    assert in_contact > 0
+    dem.close()
