@@ -217,7 +217,21 @@ def _batched(lvb, torch, hbm_peak, warmup):
     from paper_2208_13770_gb300 import autotune, scenes
     sc = scenes.batch()
     n = int(sum(q.n for q in sc))
-    best, trials = autotune.tune(sc)
+    # the candidates are tried on the batch as it is half-way through the
+    # workload (positions and velocities after BATCH_STEPS / 2 steps), where
+    # the particles move as they do in most of the timed steps
+    dem = lvb.DEM(sc)
+    dem.advance(BATCH_STEPS // 2)
+    x, v, _, _ = dem.state()
+    off = dem.offsets
+    dem.close()
+    mid = []
+    for q, s0 in enumerate(sc):
+        m = s0.copy()
+        m.pos[:] = x[off[q]:off[q + 1]]
+        m.vel[:, :3] = v[off[q]:off[q + 1], :3]
+        mid.append(m)
+    best, trials = autotune.tune(mid)
     dem = lvb.DEM(sc, cell_factor=best.cell_factor)
     best.apply(dem, lvb)
     dem.advance(warmup)
@@ -337,9 +351,12 @@ def _learned(lvb, torch):
     plain rule, each run from the same initial state."""
     from paper_2208_13770_gb300 import scenes
     sc = scenes.drum(n=LEARN_N, length=0.1)
-    plain, smp = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, log=LEARN_H)
+    # the logged runs give the training samples; every timed run has the log off
+    _, smp = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, log=LEARN_H)
+    plain, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1)
     w1, info1 = _train_skin(lvb, torch, smp, 1)
-    r1, smp1 = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1, log=LEARN_H)
+    _, smp1 = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1, log=LEARN_H)
+    r1, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1)
     w2, info2 = _train_skin(lvb, torch, np.concatenate([smp, smp1]), 2)
     r2, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w2)
     rule, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_PAPER_KVDT, float(LEARN_H))
@@ -358,8 +375,33 @@ def _learned(lvb, torch):
         "learned": learned,
         "gain_vs_paper_rule": learned["value"] / rule["value"],
         "gain_vs_plain": learned["value"] / plain["value"],
-        "note": "runs with a rebuild log on (plain, round 1) are timed with the log on",
+        "note": "samples come from separate runs with the rebuild log on; timed runs have it off",
     }
+
+
+def _fused_graph(lvb, torch, scene, steps, warmup):
+    """The same scene advanced as the driver runs it: graphs of
+    DEM_GRAPH_STEPS fused steps (integrate, broad phase and forces in one
+    cooperative launch per step), timed with CUDA events around the whole
+    run; no flush between steps."""
+    dem = lvb.DEM(scene)
+    dem.advance(warmup)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dem.advance(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rc = dem.sync()
+    if rc != 0:
+        raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
+    ms = e0.elapsed_time(e1)
+    dem.close()
+    return {"value": scene.n * steps / (ms * 1e-3), "unit": "particle-steps/s (full DEM step)",
+            "ms_per_step": ms / steps, "steps": steps,
+            "l2": "not flushed (graphs of 100 fused steps; the state stays in L2)"}
 
 
 def _e2e(lvb, torch, scene, rec):
@@ -387,10 +429,12 @@ def _e2e(lvb, torch, scene, rec):
         flagged += nf.value
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    st = ctx.stats()
     ctx.close()
     return {"value": scene.n * m / dt, "unit": "particle-steps/s",
             "h2d_bytes_per_step": scene.n * 16, "d2h_bytes_per_step": words.nbytes + 8,
-            "steps": m, "flagged": int(flagged)}
+            "steps": m, "flagged": int(flagged), "store_grows": st["grows"],
+            "relayouts": st["relayouts"]}
 
 
 def _oracle_sample(scene, t0_steps, m_steps, n_sub=None, time_budget=None, stride=10):
@@ -554,6 +598,7 @@ def run_native(args):
 
     e2e = _e2e(lvb, torch, scene, loc["rec"])
     e2e["value"] *= world
+    fused = _fused_graph(lvb, torch, scene, args.steps, args.warmup)
     batched = None if args.no_batched else _batched(lvb, torch, hbm_peak, args.warmup)
     learned = None if args.no_learned else _learned(lvb, torch)
 
@@ -606,6 +651,7 @@ def run_native(args):
                         "frac_hbm": bp_ach / hbm_peak, "bytes_per_step": bytes_bp},
         "phases_ms_per_step": {"integrate": ph[0], "broad": ph[1], "forces": ph[2]},
         "full_step_particle_steps_per_s": world * n * K / (step_ms_tot * 1e-3),
+        "full_step_graph": fused,
         "rebuild_fraction": upd / (n * K),
         "flagged_per_step": F,
         "global_buffer": {"value": world * n * K / (g_bp_ms * 1e-3),

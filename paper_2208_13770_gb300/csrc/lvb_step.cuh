@@ -1167,7 +1167,9 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     __syncthreads();
     const DevState &s = s_sh;
     DevCounters *c = s.cnt;
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    // the step's bookkeeping (counters, trace) runs on the last warp of
+    // block 0, whose rebuild work items come last
+    const bool lead = blockIdx.x == 0 && threadIdx.x == blockDim.x - 32;
     const unsigned long long t0 = (s.trace && lead) ? global_ns() : 0ULL;
     // every thread reads the counters it needs (one broadcast load each, no
     // block barrier before the check's loads); they are stable while the
