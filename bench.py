@@ -287,6 +287,7 @@ LEARN_N = 1_000_000
 LEARN_H = 400           # horizon of the rebuild-log labels, and K of the paper's rule
 LEARN_MARGIN = 1.3      # labels scaled by this margin before training
 LEARN_STEPS = 1500      # steps of the logged training run and of each timed run
+LEARN_LOSS = "relative"  # training loss: relative error of the label (or "squared")
 
 
 def _timed_advance(lvb, torch, scene, kind, value, mlp=None, log=None, steps=LEARN_STEPS):
@@ -334,9 +335,12 @@ def _train_skin(lvb, torch, samples, seed):
     p0 = (rng.standard_normal(lvb.LVB_MLP_PARAMS) * 0.1).astype(np.float32)
     yr = np.zeros(2, np.float32)
     t0 = time.time()
+    kind = lvb.LVB_MLP_LOSS_RELATIVE if LEARN_LOSS == "relative" else lvb.LVB_MLP_LOSS_SQUARED
     p, mu, isd, losses = lvb.mlp_train(torch.from_numpy(smp).cuda(), epochs=20, batch=512,
-                                       lr=3e-3, seed=seed, params0=p0, y_range_out=yr)
-    info = {"samples": int(len(smp)), "epochs": 20, "loss_first": float(losses[0]),
+                                       lr=3e-3, seed=seed, params0=p0, y_range_out=yr,
+                                       loss_kind=kind)
+    info = {"samples": int(len(smp)), "epochs": 20, "loss": LEARN_LOSS,
+            "loss_first": float(losses[0]),
             "loss_last": float(losses[-1]), "seconds": time.time() - t0,
             "y_range": [float(yr[0]), float(yr[1])]}
     return lvb.mlp_weights_device(p, mu, isd, yr), info

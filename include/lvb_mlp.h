@@ -85,19 +85,29 @@ int lvb_mlp_pack(const float *params, const float *mu, const float *isd, const f
 int lvb_mlp_infer(const float *feats, const float *diam, int64_t n, const lvb_mlp_weights *w,
                   float *skin, float *y, void *stream);
 
+/* Training losses (the paper has no learned part: an extension). */
+#define LVB_MLP_LOSS_SQUARED  0  /* mean of (y - t)^2 */
+#define LVB_MLP_LOSS_RELATIVE 1  /* mean of ((y - t) / max(t, floor))^2: every
+                                    label counts by its relative error, so
+                                    slow particles are fitted as closely as
+                                    fast ones (floor: the output range's
+                                    lower end y_lo) */
+
 /*
  * lvb_mlp_grad -- mean squared error of y against labels over n samples and
  * its gradient with respect to the master parameters (straight-through
  * through the bfloat16 roundings).  samples: device n x 9 (8 features,
- * label); params, mu, isd: host; grad: host LVB_MLP_PARAMS; loss: host.
- * Synchronises.
+ * label); params, mu, isd: host; rel_floor: 0 for the squared error, > 0
+ * for the relative error with that floor; grad: host LVB_MLP_PARAMS; loss:
+ * host.  Synchronises.  Errors: EINVAL (rel_floor < 0 or NaN).
  */
 int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const float *mu,
-                 const float *isd, float *grad, double *loss, void *stream);
+                 const float *isd, float rel_floor, float *grad, double *loss, void *stream);
 
 /*
  * lvb_mlp_train -- train the network on the GPU with Adam.
  *   samples     : device n x 9 (features, label).
+ *   loss_kind   : LVB_MLP_LOSS_SQUARED or LVB_MLP_LOSS_RELATIVE.
  *   params      : host in/out, LVB_MLP_PARAMS master parameters.
  *   mu, isd     : host out, the feature normalisation computed from the
  *                 samples (mean and 1/std per feature).
@@ -107,8 +117,8 @@ int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const flo
  * Synchronises.  Errors: EINVAL, ENOMEM, EDEVICE.
  */
 int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch, float lr,
-                  uint64_t seed, float *params, float *mu, float *isd, float *y_range,
-                  float *losses, void *stream);
+                  uint64_t seed, int32_t loss_kind, float *params, float *mu, float *isd,
+                  float *y_range, float *losses, void *stream);
 
 /*
  * lvb_log_enable -- start recording training samples from a broad-phase

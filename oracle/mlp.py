@@ -135,16 +135,22 @@ def forward64(W: Weights, feats, quantize=True):
     return y, (z, a1, h1, a2, h2, W2, w3)
 
 
-def loss_and_grad64(W: Weights, feats, labels, quantize=True):
+def loss_and_grad64(W: Weights, feats, labels, quantize=True, rel_floor=0.0):
     """Mean squared error and its gradient with respect to the flat
     parameters (order of Weights.flat), binary64; with quantize the bfloat16
-    roundings act in the forward pass and as the identity backwards."""
+    roundings act in the forward pass and as the identity backwards.  With
+    rel_floor > 0 the error of each sample is relative to its label (not
+    below rel_floor): mean of ((y - t) / max(t, rel_floor))^2."""
     y, (z, a1, h1, a2, h2, W2, w3) = forward64(W, feats, quantize)
     t = np.asarray(labels, np.float64).reshape(-1)
     B = len(t)
     r = y - t
-    loss = float(np.mean(r * r))
-    dy = 2.0 * r / B
+    if rel_floor > 0.0:
+        w = 1.0 / np.maximum(t, float(np.float32(rel_floor))) ** 2
+    else:
+        w = np.ones_like(t)
+    loss = float(np.mean(w * r * r))
+    dy = 2.0 * w * r / B
     gw3 = h2.T @ dy
     gb3 = dy.sum()
     dh2 = np.outer(dy, w3) * (a2 > 0)

@@ -90,8 +90,9 @@ struct TrainArgs {
     const float *params;    // master parameters
     const float *mu, *isd;
     float *grad;            // accumulated gradient (NP)
-    double *loss;           // accumulated sum of squared errors
+    double *loss;           // accumulated sum of (weighted) squared errors
     float dy_scale;         // 2 / batch size
+    float rel_floor;        // > 0: relative error, (y - t) / max(t, rel_floor)
 };
 
 __global__ void __launch_bounds__(kTB)
@@ -132,9 +133,15 @@ k_mlp_batch(TrainArgs a)
         }
         float y = b3;
         for (int k = 0; k < NH; ++k) y = fmaf(sw3[k], sh2[t][k], y);
-        const float r = y - smp[NI];
-        dy = a.dy_scale * r;
-        atomicAdd(a.loss, (double)r * (double)r);
+        const float lab = smp[NI];
+        float r = y - lab;
+        float w = 1.0f;   // d(loss)/d(r^2)
+        if (a.rel_floor > 0.0f) {
+            const float den = fmaxf(lab, a.rel_floor);
+            w = 1.0f / (den * den);
+        }
+        dy = a.dy_scale * w * r;
+        atomicAdd(a.loss, (double)w * (double)r * (double)r);
         for (int o = 0; o < NH; ++o) sd2[t][o] = sh2[t][o] > 0.0f ? dy * sw3[o] : 0.0f;
         for (int k = 0; k < NH; ++k) {
             float g = 0.0f;
@@ -211,7 +218,7 @@ cudaError_t dnew(DevBuf &b, size_t count)
 // one pass of k_mlp_batch over positions [first, first + count)
 void launch_batch(const float *samples, const int *order, int64_t first, int64_t count,
                   const float *params, const float *mu, const float *isd, float *grad,
-                  double *loss, cudaStream_t st)
+                  double *loss, float rel_floor, cudaStream_t st)
 {
     TrainArgs a;
     a.samples = samples;
@@ -224,6 +231,7 @@ void launch_batch(const float *samples, const int *order, int64_t first, int64_t
     a.grad = grad;
     a.loss = loss;
     a.dy_scale = 2.0f / (float)count;
+    a.rel_floor = rel_floor;
     const int64_t blocks = (count + kTB - 1) / kTB;
     k_mlp_batch<<<(unsigned)blocks, kTB, 0, st>>>(a);
 }
@@ -266,9 +274,10 @@ int lvb_mlp_infer(const float *feats, const float *diam, int64_t n, const lvb_ml
 }
 
 int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const float *mu,
-                 const float *isd, float *grad, double *loss, void *stream)
+                 const float *isd, float rel_floor, float *grad, double *loss, void *stream)
 {
     if (!samples || n < 1 || !params || !mu || !isd || !grad || !loss) return LVB_EINVAL;
+    if (!(rel_floor >= 0.0f)) return LVB_EINVAL;
     cudaGetLastError();
     const cudaStream_t st = (cudaStream_t)stream;
     DevBuf dp, dmu, disd, dg, dl;
@@ -284,7 +293,7 @@ int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const flo
     if (e == cudaSuccess) e = cudaMemsetAsync(dl.p, 0, 8, st);
     if (e != cudaSuccess) return from_cuda(e);
     launch_batch(samples, nullptr, 0, n, (const float *)dp.p, (const float *)dmu.p,
-                 (const float *)disd.p, (float *)dg.p, (double *)dl.p, st);
+                 (const float *)disd.p, (float *)dg.p, (double *)dl.p, rel_floor, st);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dg.p, NP * 4, cudaMemcpyDeviceToHost, st);
     double sse = 0.0;
@@ -296,11 +305,13 @@ int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const flo
 }
 
 int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch, float lr,
-                  uint64_t seed, float *params, float *mu, float *isd, float *y_range,
-                  float *losses, void *stream)
+                  uint64_t seed, int32_t loss_kind, float *params, float *mu, float *isd,
+                  float *y_range, float *losses, void *stream)
 {
     if (!samples || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f) || !params || !mu || !isd ||
         !y_range)
+        return LVB_EINVAL;
+    if (loss_kind != LVB_MLP_LOSS_SQUARED && loss_kind != LVB_MLP_LOSS_RELATIVE)
         return LVB_EINVAL;
     if (n > INT32_MAX) return LVB_EINVAL;
     cudaGetLastError();
@@ -327,6 +338,9 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
         y_range[0] = (float)(m / 16.0);
         y_range[1] = (float)(m + 4.0 * sd);
     }
+    // relative error: labels below the output range's floor count as the floor
+    const float rel_floor = loss_kind == LVB_MLP_LOSS_RELATIVE ? std::max(y_range[0], 1e-30f)
+                                                               : 0.0f;
     DevBuf dp, dmu, disd, dg, dm, dv, dl, dord;
     e = dnew<float>(dp, NP);
     if (e == cudaSuccess) e = dnew<float>(dmu, NI);
@@ -358,7 +372,7 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
             const int64_t cnt = std::min<int64_t>(batch, n - first);
             launch_batch(samples, (const int *)dord.p, first, cnt, (const float *)dp.p,
                          (const float *)dmu.p, (const float *)disd.p, (float *)dg.p,
-                         (double *)dl.p, st);
+                         (double *)dl.p, rel_floor, st);
             ++t;
             const float c1 = 1.0f - std::pow(b1, (float)t), c2 = 1.0f - std::pow(b2, (float)t);
             k_adam<<<(NP + 255) / 256, 256, 0, st>>>((float *)dp.p, (float *)dg.p, (float *)dm.p,

@@ -96,10 +96,10 @@ _SIGS = {
     "lvb_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "lvb_mlp_pack": ([_p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_mlp_infer": ([_p, _p, _i64, _p, _p, _p, _p], ctypes.c_int),
-    "lvb_mlp_grad": ([_p, _i64, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_double), _p],
-                     ctypes.c_int),
+    "lvb_mlp_grad": ([_p, _i64, _p, _p, _p, ctypes.c_float, _p, ctypes.POINTER(ctypes.c_double),
+                      _p], ctypes.c_int),
     "lvb_mlp_train": ([_p, _i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
-                       _p, _p, _p, _p, _p, _p], ctypes.c_int),
+                       ctypes.c_int32, _p, _p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_log_enable": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
     "lvb_log_read": ([_p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_pairs_noalloc": ([_i64, _p, _p, ctypes.POINTER(lvb_box), _p, _p, _i64, _pi64, _p],
@@ -291,6 +291,7 @@ def dem_destroy(ctx):
 
 
 LVB_MLP_IN, LVB_MLP_HIDDEN, LVB_MLP_PARAMS = 8, 32, 1377
+LVB_MLP_LOSS_SQUARED, LVB_MLP_LOSS_RELATIVE = 0, 1
 MLP_WEIGHTS_BYTES = 4 * (32 * 8 + 32 + 32 * 32 + 32 + 32 + 1 + 8 + 8 + 3)
 
 
@@ -302,14 +303,15 @@ def lvb_mlp_infer(feats, diam, n, w, skin, y, stream=None):
     return _lib.lvb_mlp_infer(feats, diam, int(n), w, skin, y, stream)
 
 
-def lvb_mlp_grad(samples, n, params, mu, isd, grad, loss, stream=None):
-    return _lib.lvb_mlp_grad(samples, int(n), params, mu, isd, grad, loss, stream)
+def lvb_mlp_grad(samples, n, params, mu, isd, rel_floor, grad, loss, stream=None):
+    return _lib.lvb_mlp_grad(samples, int(n), params, mu, isd, float(rel_floor), grad, loss,
+                             stream)
 
 
-def lvb_mlp_train(samples, n, epochs, batch, lr, seed, params, mu, isd, y_range, losses,
-                  stream=None):
+def lvb_mlp_train(samples, n, epochs, batch, lr, seed, loss_kind, params, mu, isd, y_range,
+                  losses, stream=None):
     return _lib.lvb_mlp_train(samples, int(n), int(epochs), int(batch), float(lr), int(seed),
-                              params, mu, isd, y_range, losses, stream)
+                              int(loss_kind), params, mu, isd, y_range, losses, stream)
 
 
 def lvb_log_enable(ctx, horizon, capacity):
@@ -593,16 +595,20 @@ def mlp_weights_device(params, mu, isd, y_range=None):
     return buf
 
 
-def mlp_train(samples_dev, epochs, batch, lr, seed, params0, y_range_out=None):
+def mlp_train(samples_dev, epochs, batch, lr, seed, params0, y_range_out=None,
+              loss_kind=None):
     """Train on device samples (torch (n, 9) float32); returns (params, mu,
     isd, losses).  y_range_out (a float32 array of 2) receives the output
-    range computed from the labels."""
+    range computed from the labels; loss_kind: LVB_MLP_LOSS_SQUARED
+    (default) or LVB_MLP_LOSS_RELATIVE."""
+    kind = LVB_MLP_LOSS_SQUARED if loss_kind is None else loss_kind
     p = np.ascontiguousarray(params0, np.float32).copy()
     mu = np.zeros(LVB_MLP_IN, np.float32)
     isd = np.zeros(LVB_MLP_IN, np.float32)
     yr = np.zeros(2, np.float32) if y_range_out is None else y_range_out
     losses = np.zeros(int(epochs), np.float32)
     _check(lvb_mlp_train(samples_dev.data_ptr(), samples_dev.shape[0], epochs, batch, lr, seed,
-                         _np_ptr(p), _np_ptr(mu), _np_ptr(isd), _np_ptr(yr), _np_ptr(losses)),
+                         kind, _np_ptr(p), _np_ptr(mu), _np_ptr(isd), _np_ptr(yr),
+                         _np_ptr(losses)),
            "lvb_mlp_train")
     return p, mu, isd, losses

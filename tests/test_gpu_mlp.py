@@ -62,7 +62,9 @@ def test_inference_bit_exact():
     assert (ey < W.y_lo).any() and (ey > W.y_hi).any() and ((ey > W.y_lo) & (ey < W.y_hi)).any()
 
 
-def test_gradient_matches_oracle():
+@pytest.mark.parametrize("rel_floor", [0.0, 0.2])
+def test_gradient_matches_oracle(rel_floor):
+    # squared error, and relative error with a floor some labels fall below
     lvb = _lvb()
     from oracle import mlp
     W = _weights(5)
@@ -75,9 +77,10 @@ def test_gradient_matches_oracle():
     loss = lvb.ctypes.c_double(0)
     p = W.flat()
     rc = lvb.lvb_mlp_grad(_dev(samp).data_ptr(), n, p.ctypes.data, W.mu.ctypes.data,
-                          W.isd.ctypes.data, grad.ctypes.data, lvb.ctypes.byref(loss))
+                          W.isd.ctypes.data, rel_floor, grad.ctypes.data, lvb.ctypes.byref(loss))
     assert rc == 0
-    eloss, eg = mlp.loss_and_grad64(W, samp[:, :8], samp[:, 8], quantize=True)
+    eloss, eg = mlp.loss_and_grad64(W, samp[:, :8], samp[:, 8], quantize=True,
+                                    rel_floor=rel_floor)
     assert abs(loss.value - eloss) <= 1e-5 * eloss
     err = np.abs(grad - eg).max()
     assert err <= 1e-4 * np.abs(eg).max(), err

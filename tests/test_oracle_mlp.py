@@ -67,12 +67,16 @@ def test_one_path_network_closed_form():
     assert np.array_equal(skin3, (d * np.float32(0.3)).astype(np.float32))
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("rel_floor", [0.0, 0.15])
+def test_backward_matches_finite_differences(rel_floor):
+    # squared error, and relative error with a floor that some labels fall below
     rng = np.random.default_rng(3)
     W = mlp.Weights.random(seed=4, scale=0.5)
     f = rng.normal(0, 1, (64, mlp.N_IN))
     t = rng.normal(0.2, 0.1, 64)
-    loss, g = mlp.loss_and_grad64(W, f, t, quantize=False)
+    if rel_floor:
+        assert (t < rel_floor).any() and (t > rel_floor).any()
+    loss, g = mlp.loss_and_grad64(W, f, t, quantize=False, rel_floor=rel_floor)
     p0 = W.flat().astype(np.float64)
     eps = 1e-6
     idx = rng.choice(len(p0), 60, replace=False)
@@ -90,7 +94,26 @@ def test_backward_matches_finite_differences():
                 size = int(np.prod(shape)) if shape else 1
                 parts.append(p[o:o + size].reshape(shape) if shape else p[o]); o += size
             Wk.W1, Wk.b1, Wk.W2, Wk.b2, Wk.w3, Wk.b3 = parts
-            return mlp.loss_and_grad64(Wk, f, t, quantize=False)[0]
+            return mlp.loss_and_grad64(Wk, f, t, quantize=False, rel_floor=rel_floor)[0]
         fd = (L(eps) - L(-eps)) / (2 * eps)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
     assert len(g) == mlp.N_PARAMS == 1377
+
+
+def test_relative_loss_special_cases():
+    # equal labels c above the floor: the relative error is the squared error
+    # over c^2 (loss and gradient); labels below the floor count as the floor
+    rng = np.random.default_rng(11)
+    W = mlp.Weights.random(seed=12, scale=0.5)
+    f = rng.normal(0, 1, (50, mlp.N_IN))
+    c = 0.25
+    t = np.full(50, c)
+    l2, g2 = mlp.loss_and_grad64(W, f, t, quantize=True)
+    lr, gr = mlp.loss_and_grad64(W, f, t, quantize=True, rel_floor=0.125)
+    assert lr == pytest.approx(l2 / c ** 2, rel=1e-12)
+    assert np.allclose(gr, g2 / c ** 2, rtol=1e-12, atol=0)
+    lo = np.full(50, 0.01)
+    l2, g2 = mlp.loss_and_grad64(W, f, lo, quantize=True)
+    lr, gr = mlp.loss_and_grad64(W, f, lo, quantize=True, rel_floor=0.125)
+    assert lr == pytest.approx(l2 / 0.125 ** 2, rel=1e-12)
+    assert np.allclose(gr, g2 / 0.125 ** 2, rtol=1e-12, atol=0)
