@@ -204,8 +204,8 @@ BATCH_STEPS = 2000
 # one ncu capture of the current kernel on each workload (mean of two
 # launches; the command and the counters are in profiles/).  They go stale
 # when the kernel changes: set them to None until the capture is repeated.
-NCU_TRAFFIC_SETTLING = None       # profiles/k_step_settling200k_ncu.txt
-NCU_TRAFFIC_BATCHED = None        # profiles/k_step_batched512_ncu.txt
+NCU_TRAFFIC_SETTLING = 7.04e6      # profiles/k_step_settling200k_ncu.txt
+NCU_TRAFFIC_BATCHED = 214.9e6      # profiles/k_step_batched512_ncu.txt
 
 
 def _batched(lvb, torch, hbm_peak, warmup):
@@ -364,7 +364,11 @@ def _learned(lvb, torch):
     w2, info2 = _train_skin(lvb, torch, np.concatenate([smp, smp1]), 2)
     r2, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w2)
     rule, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_PAPER_KVDT, float(LEARN_H))
+    sweep = {}
+    for K in (LEARN_H // 2, 2 * LEARN_H):
+        sweep["K%d" % K], _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_PAPER_KVDT, float(K))
     learned = max((r1, r2), key=lambda r: r["value"])
+    best_rule = max([rule] + list(sweep.values()), key=lambda r: r["value"])
     return {
         "workload": "drum R 0.3 m x 0.1 m, %d lognormal spheres (median 1 mm, sigma_ln 0.35), "
                     "10 rpm, dt 1e-6 s, %d steps per run" % (sc.n, LEARN_STEPS),
@@ -377,7 +381,9 @@ def _learned(lvb, torch):
         "learned_round1": r1,
         "learned_round2": r2,
         "learned": learned,
+        "paper_rule_other_K": sweep,
         "gain_vs_paper_rule": learned["value"] / rule["value"],
+        "gain_vs_best_paper_rule": learned["value"] / best_rule["value"],
         "gain_vs_plain": learned["value"] / plain["value"],
         "note": "samples come from separate runs with the rebuild log on; timed runs have it off",
     }
@@ -685,6 +691,35 @@ def run_native(args):
     return 0
 
 
+def run_k_sweep(args):
+    """Time and rebuild fractions against K of the paper's rule (Eq.
+    skin_formulus1) on the settling box, every run from the same initial
+    state, phase by phase with the L2 flushed before every step."""
+    import torch
+    from paper_2208_13770_gb300 import lvb
+    scene = _scene(0)
+    n = scene.n
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for K in (float(k) for k in args.k_sweep.split(",")):
+        r = _run_dem(lvb, torch, scene, lvb.LVB_TRIGGER_PARTIAL, lvb.LVB_SKIN_PAPER_KVDT, K,
+                     args.steps, args.warmup, flush)
+        ph = r["phase_ms"] / args.steps
+        s0, s1 = r["stats0"], r["stats1"]
+        rows.append({"K": K, "broad_ms": ph[1], "narrow_forces_ms": ph[2],
+                     "integrate_ms": ph[0], "step_ms": float(ph.sum()),
+                     "rebuild_fraction": (s1["updated_total"] - s0["updated_total"])
+                     / (n * args.steps),
+                     "rebuild_step_fraction": (s1["rebuild_steps"] - s0["rebuild_steps"])
+                     / args.steps,
+                     "entries": s1["entries"]})
+    print(json.dumps({"k_sweep": rows, "workload": WORKLOAD.replace("local skin 0.1 d_i",
+                                                                   "skin K |v| dt"),
+                      "steps": args.steps, "warmup": args.warmup,
+                      "l2": "flushed before every timed step (1 GiB write)"}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -706,11 +741,17 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched (512-scene) workload alone, phase by phase "
                          "(for profiling)")
+    ap.add_argument("--k-sweep", default="",
+                    help="comma-separated K values: the paper's skin rule K |v| dt on the "
+                         "settling box, phase by phase (broad phase, narrow phase + forces, "
+                         "rebuild fractions) for each K, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.k_sweep:
+        return run_k_sweep(args)
     return run_native(args)
 
 
