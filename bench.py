@@ -415,36 +415,59 @@ def _fused_graph(lvb, torch, scene, steps, warmup):
 
 
 def _e2e(lvb, torch, scene, rec):
-    """Broad phase through the C-ABI with host buffers: per step a pinned
-    host -> device copy of the positions, lvb_step, and a device -> host
-    read of the flags (lvb_get_flags synchronises)."""
-    dev = torch.empty((scene.n, 4), dtype=torch.float32, device="cuda")
-    ref = torch.from_numpy(rec["ref"]).cuda()
-    dev.copy_(torch.from_numpy(rec["pos0"]))
-    ctx = lvb.LVB(dev, scene.lo, scene.hi, scene.skin_kind, scene.skin_value, scene.dt,
-                  lvb.LVB_TRIGGER_PARTIAL, scene.cell_factor, ref=ref)
+    """Broad phase through the C-ABI with host buffers, steps m of a recorded
+    window of the run (the context resumes from the run's saved reference
+    state).  Pipelined: per step lvb_step_host copies the pinned host
+    positions in (overlapping the previous step's kernel) and the step's flag
+    words and count out to pinned host memory; one synchronisation at the
+    end.  Also the per-step synchronous form: copy in, lvb_step, then
+    lvb_get_flags (which waits) every step."""
     m = rec["m"]
-    words = np.zeros((scene.n + 31) // 32, dtype=np.uint32)
-    nf = lvb.ctypes.c_int64(0)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    t0 = time.perf_counter()
-    flagged = 0
-    for k in range(m):
-        dev.copy_(rec["pos"][k], non_blocking=True)
-        ctx.step(dev)
-        rc = lvb.lvb_get_flags(ctx.ctx, words.ctypes.data, lvb.ctypes.byref(nf))
-        if rc:
-            raise RuntimeError(lvb.lvb_strerror(rc))
-        flagged += nf.value
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    st = ctx.stats()
-    ctx.close()
-    return {"value": scene.n * m / dt, "unit": "particle-steps/s",
-            "h2d_bytes_per_step": scene.n * 16, "d2h_bytes_per_step": words.nbytes + 8,
-            "steps": m, "flagged": int(flagged), "store_grows": st["grows"],
-            "relayouts": st["relayouts"]}
+    nw = (scene.n + 31) // 32
+    ref = torch.from_numpy(rec["ref"]).cuda()
+    out = {}
+    for form in ("pipelined", "sync"):
+        dev = torch.empty((scene.n, 4), dtype=torch.float32, device="cuda")
+        dev.copy_(torch.from_numpy(rec["pos0"]))
+        ctx = lvb.LVB(dev, scene.lo, scene.hi, scene.skin_kind, scene.skin_value, scene.dt,
+                      lvb.LVB_TRIGGER_PARTIAL, scene.cell_factor, ref=ref)
+        bits = torch.zeros((m, nw), dtype=torch.int32, pin_memory=True)
+        nf = torch.zeros((m,), dtype=torch.int32, pin_memory=True)
+        words = np.zeros(nw, dtype=np.uint32)
+        nf64 = lvb.ctypes.c_int64(0)
+        torch.cuda.synchronize()
+        flagged = 0
+        t0 = time.perf_counter()
+        if form == "pipelined":
+            for k in range(m):
+                ctx.step_host(rec["pos"][k], bits=bits[k], n_flagged=nf[k:k + 1])
+            out["enqueue_s"] = time.perf_counter() - t0
+            rc = ctx.sync()
+            if rc:
+                raise RuntimeError(lvb.lvb_strerror(rc))
+            dt = time.perf_counter() - t0
+            flagged = int(nf.sum())
+        else:
+            for k in range(m):
+                dev.copy_(rec["pos"][k], non_blocking=True)
+                ctx.step(dev)
+                rc = lvb.lvb_get_flags(ctx.ctx, words.ctypes.data, lvb.ctypes.byref(nf64))
+                if rc:
+                    raise RuntimeError(lvb.lvb_strerror(rc))
+                flagged += nf64.value
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        st = ctx.stats()
+        ctx.close()
+        out[form] = {"value": scene.n * m / dt, "unit": "particle-steps/s",
+                     "h2d_bytes_per_step": scene.n * 16, "d2h_bytes_per_step": nw * 4 + 4,
+                     "steps": m, "flagged": flagged, "store_grows": st["grows"],
+                     "relayouts": st["relayouts"]}
+    e2e = dict(out["pipelined"])
+    e2e["api"] = "lvb_step_host (pinned host positions in, flag words and count out)"
+    e2e["sync_per_step"] = out["sync"]
+    e2e["host_enqueue_us_per_step"] = out["enqueue_s"] * 1e6 / m
+    return e2e
 
 
 def _oracle_sample(scene, t0_steps, m_steps, n_sub=None, time_budget=None, stride=10):

@@ -213,6 +213,31 @@ int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *r
  */
 int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *acc);
 
+/*
+ * lvb_step_host -- lvb_step with its inputs in host memory and the step's
+ * flags returned to host memory (the same step as lvb_step).
+ *   pos_r, vel, acc : host, n x 4 float as for lvb_step (vel / acc NULL
+ *                     unless the skin policy needs them).
+ *   bits            : host, ceil(n / 32) words out: the flag bits of this
+ *                     step (bit i % 32 of word i / 32); may be NULL.
+ *   n_flagged       : host, one int out: particles flagged at this step;
+ *                     may be NULL.
+ * Enqueues only.  The inputs are copied into one of two device staging
+ * slots owned by the context, on a copy stream of its own, so the copy of a
+ * step's inputs overlaps the previous step's kernel; the step waits for its
+ * copy.  Outputs in page-locked memory are written by the step kernel
+ * itself (over the host link, as the flags are found); outputs in pageable
+ * memory are copied back on the context's stream after the step.
+ * Every host buffer must stay valid, and the inputs unchanged, until
+ * lvb_sync (or another synchronising call) returns.  Page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister) lets the copies overlap; with
+ * pageable memory the results are the same but the copies serialise.  The
+ * staging slots are allocated on the first call (2 x n x 16 bytes per
+ * input given).  Errors: EINVAL (as lvb_step), ENOMEM, EDEVICE.
+ */
+int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *acc,
+                  uint32_t *bits, int32_t *n_flagged);
+
 /* Options of lvb_set_option.  None of them changes a result. */
 #define LVB_OPT_TRACE     3  /* 1: the step kernel records the device time of
                                 its phases, the DEM driver's separate kernels

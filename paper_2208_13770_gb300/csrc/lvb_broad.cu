@@ -390,6 +390,15 @@ struct lvb_ctx {
     int version = 0;                // bumped whenever the step kernel's arguments change
     HostFlags *hflags = nullptr;    // mapped pinned host memory
     long long grows = 0;            // store or cell-slot growths done
+    // lvb_step_host: two device staging slots for (pos, vel, acc), filled on
+    // a copy stream so that a step's input copy overlaps the previous step
+    struct {
+        float4 *buf[2][3] = {};
+        cudaStream_t copy = nullptr;
+        cudaEvent_t copied[2] = {}, consumed[2] = {};
+        int slot = 0;
+        bool ready = false;
+    } hs;
 };
 
 namespace {
@@ -422,6 +431,14 @@ void free_all(lvb_ctx *c)
         if (p) cudaFree(p);
     if (c->cnt_h) cudaFreeHost(c->cnt_h);
     if (c->hflags) cudaFreeHost(c->hflags);
+    for (auto &slot : c->hs.buf)
+        for (float4 *p : slot)
+            if (p) cudaFree(p);
+    for (int k = 0; k < 2; ++k) {
+        if (c->hs.copied[k]) cudaEventDestroy(c->hs.copied[k]);
+        if (c->hs.consumed[k]) cudaEventDestroy(c->hs.consumed[k]);
+    }
+    if (c->hs.copy) cudaStreamDestroy(c->hs.copy);
 }
 
 int from_cuda(cudaError_t e)
@@ -440,6 +457,20 @@ int from_derr(unsigned e)
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// The device address of a page-locked host buffer, or null when the device
+// cannot address it (pageable memory): then the outputs are copied instead.
+void *device_view(void *host)
+{
+    if (!host) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return at.devicePointer;
+}
 
 // Row-store scan of ctx rows (size = row_capacity(row_len)), gated.
 ScanArgs layout_args(lvb_ctx *c);
@@ -947,6 +978,65 @@ int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
                     (size_t)check_smem_bytes(c->block_threads), c->stream,
                     (const float4 *)pos_r, (const float4 *)vel, a4, c->s, IntegrateArgs{},
                     NoTail{});
+    return from_cuda(e);
+}
+
+int lvb_step_host(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc,
+                  uint32_t *bits, int32_t *n_flagged)
+{
+    if (!c || !pos_r) return LVB_EINVAL;
+    if (c->skin.kind == LVB_SKIN_PAPER_KVDT && !vel) return LVB_EINVAL;
+    if (c->skin.kind == LVB_SKIN_LEARNED && (!vel || !acc)) return LVB_EINVAL;
+    auto &hs = c->hs;
+    const size_t bytes = sizeof(float4) * (size_t)c->n;
+    cudaError_t e = cudaSuccess;
+    if (!hs.ready) {
+        e = cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&hs.copied[k], cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&hs.consumed[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return from_cuda(e);
+        hs.ready = true;
+    }
+    const float *src[3] = {pos_r, vel, acc};
+    const int k = hs.slot;
+    for (int a = 0; a < 3; ++a)
+        if (src[a] && !hs.buf[k][a]) {
+            e = cudaMalloc(&hs.buf[k][a], bytes);
+            if (e != cudaSuccess) {
+                hs.buf[k][a] = nullptr;
+                return from_cuda(e);
+            }
+        }
+    // the slot's previous step has read its inputs before they are replaced
+    e = cudaStreamWaitEvent(hs.copy, hs.consumed[k], 0);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+        if (src[a])
+            e = cudaMemcpyAsync(hs.buf[k][a], src[a], bytes, cudaMemcpyHostToDevice, hs.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(hs.copied[k], hs.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, hs.copied[k], 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    hs.slot ^= 1;
+    // outputs in page-locked memory are written by the step kernel itself
+    uint32_t *bits_d = (uint32_t *)device_view(bits);
+    int *nf_d = (int *)device_view(n_flagged);
+    c->s.bits_out = bits_d;
+    c->s.nf_out = nf_d;
+    const int rc = lvb_step(c, (const float *)hs.buf[k][0],
+                            vel ? (const float *)hs.buf[k][1] : nullptr,
+                            acc ? (const float *)hs.buf[k][2] : nullptr);
+    c->s.bits_out = nullptr;
+    c->s.nf_out = nullptr;
+    if (rc) return rc;
+    e = cudaEventRecord(hs.consumed[k], c->stream);
+    if (e == cudaSuccess && bits && !bits_d)
+        e = cudaMemcpyAsync(bits, c->s.bits, sizeof(uint32_t) * (size_t)c->nwords,
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && n_flagged && !nf_d)
+        e = cudaMemcpyAsync(n_flagged, &c->s.cnt->nF, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c->stream);
     return from_cuda(e);
 }
 

@@ -89,6 +89,11 @@ struct DevState {
     unsigned bar_spins;   // polls before a barrier gives up
     int direct_max;       // largest flagged count rebuilt in one phase with
                           // the direct flagged-pair test (LVB_OPT_DIRECT_MAX)
+    // second destination of this step's flag words and flagged count
+    // (lvb_step_host: the caller's page-locked host buffers, written over
+    // the host link by the kernel itself), or null
+    uint32_t *bits_out;
+    int *nf_out;
 };
 
 // gate modes of the separate full-build kernels (init, store growth)
@@ -723,7 +728,10 @@ __device__ __forceinline__ void flag_chunks(const DevState &s, const int (&cu)[U
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         b[u] = __ballot_sync(FULL, f[u]);
-        if (lane == 0 && cu[u] < s.n) s.bits[cu[u] >> 5] = b[u];
+        if (lane == 0 && cu[u] < s.n) {
+            s.bits[cu[u] >> 5] = b[u];
+            if (s.bits_out) s.bits_out[cu[u] >> 5] = b[u];
+        }
         cnt += __popc(b[u]);
     }
     int k0 = 0;
@@ -1198,6 +1206,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         c->nF_acc[par ^ 1] = 0;
         c->ovf[par ^ 1] = 0;
         c->nF = nF;
+        if (s.nf_out) *s.nf_out = nF;
         c->last_flagged = nF;
         c->last_updated = upd;
         atomicAdd((unsigned long long *)&c->steps, 1ULL);

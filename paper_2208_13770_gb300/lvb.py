@@ -82,6 +82,7 @@ _SIGS = {
                          ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p,
                          _p], ctypes.c_int),
     "lvb_step": ([_p, _p, _p, _p], ctypes.c_int),
+    "lvb_step_host": ([_p, _p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_sync": ([_p], ctypes.c_int),
     "lvb_set_option": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
     "lvb_trace": ([_p, _p, _p], ctypes.c_int),
@@ -181,6 +182,11 @@ def lvb_init_resume(n, pos_r, ref4, box, skin, trigger, cell_factor, vel=None, a
 
 def lvb_step(ctx, pos_r, vel=None, acc=None):
     return _lib.lvb_step(ctx, pos_r, vel, acc)
+
+
+def lvb_step_host(ctx, pos_r, vel=None, acc=None, bits=None, n_flagged=None):
+    """Host pointers (ints); see include/lvb.h."""
+    return _lib.lvb_step_host(ctx, pos_r, vel, acc, bits, n_flagged)
 
 
 LVB_OPT_TRACE, LVB_OPT_BLOCK_THREADS, LVB_OPT_COMPACT = 3, 4, 5
@@ -373,6 +379,18 @@ class LVB:
 
     def step(self, pos, vel=None, acc=None):
         _check(lvb_step(self.ctx, _dptr(pos), _dptr(vel), _dptr(acc)), "lvb_step")
+
+    def step_host(self, pos, vel=None, acc=None, bits=None, n_flagged=None):
+        """lvb_step_host on host tensors / arrays (pinned for overlap): pos,
+        vel, acc (n, 4) float32; bits (ceil(n/32),) uint32 and n_flagged
+        (1,) int32 receive the step's flags once the context is synchronised.
+        Every buffer must stay alive until then."""
+        def hp(a):
+            if a is None:
+                return None
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        _check(lvb_step_host(self.ctx, hp(pos), hp(vel), hp(acc), hp(bits), hp(n_flagged)),
+               "lvb_step_host")
 
     def sync(self):
         return lvb_sync(self.ctx)
