@@ -39,14 +39,12 @@ enum TraceSlot {
 
 struct DevCounters {
     int nF;            // flagged at the last step (final)
-    int ntrow;         // rows queued for removals this step
     int nF_acc[2];     // flagged count while the check runs (slot: step parity)
     int ovf[2];        // a row outgrew its capacity (slot: step parity)
     int row_overflow;  // same, for the separate full-build kernels
     unsigned err;      // sticky DERR_* bits
     int last_flagged;
     int last_updated;
-    int pad0, pad1;
     unsigned long long bar_cnt[2];  // grid-barrier arrivals in the step kernel, by step parity
     long long steps;
     long long rebuild_steps;

@@ -273,19 +273,53 @@ __device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
         }
     }
     if (lane == 0) {
-        if (slot < 0) {
-            slot = atomicAdd(&s.cell_cnt[nc], 1);
-            if (slot * 4 >= ccap * 3) s.hflags->grow_cells = 1;
-            if (slot < ccap) s.cell_id[base + slot] = i;
-            else atomicOr(&s.cnt->err, DERR_CELL);
+        // a fresh slot at the end, also claimed by compare-and-swap: once
+        // the count covers it, another mover's tombstone search may see it
+        // still holding -1 and take it first; then the next one is taken
+        for (int t = 0; slot < 0 && t <= ccap; ++t) {
+            const int sl = atomicAdd(&s.cell_cnt[nc], 1);
+            if (sl * 4 >= ccap * 3) s.hflags->grow_cells = 1;
+            if (sl >= ccap) {
+                atomicOr(&s.cnt->err, DERR_CELL);
+                break;
+            }
+            if (atomicCAS(&s.cell_id[base + sl], -1, i) == -1) slot = sl;
         }
-        if (slot < ccap) {
+        if (slot >= 0) {
             s.cell_ref[base + slot] = qn;
             s.slot_of[i] = slot;
         }
         s.cell_of[i] = nc;
     }
     __syncwarp();
+}
+
+// Whether stencil cell (x, y, z) of scene g can hold a partner of a particle
+// whose reference state is q (q.w = its R_NL): a partner j lies within
+// R_NL,i + R_NL,j <= q.w + H of it (every R_NL is capped at H, Eq.
+// skin_formulus_mincell), so a cell whose box is farther away holds none.
+// The box is widened by L/1024 on every side -- far more than the rounding
+// of the binned coordinates -- and open outward at the grid's border (where
+// particles outside the box are binned), and the reach is rounded up: a
+// cell with a partner is never skipped.  With polydisperse radii most of
+// the 27 cells are out of reach of a small particle.
+__device__ __forceinline__ bool cell_reachable(const SceneGeom &g, int x, int y, int z, float4 q)
+{
+    const float slack = g.L * (1.0f / 1024.0f);
+    const int c[3] = {x, y, z};
+    const float p[3] = {q.x, q.y, q.z};
+    float d2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = g.lo[k] + (float)c[k] * g.L - slack;
+        const float hi = g.lo[k] + (float)(c[k] + 1) * g.L + slack;
+        float d = 0.0f;
+        if (c[k] > 0 && p[k] < lo) d = lo - p[k];
+        if (c[k] < g.dim[k] - 1 && p[k] > hi) d = p[k] - hi;
+        d2 += d * d;
+    }
+    const float reach = (q.w + g.H) * 1.001f + slack;
+    return d2 <= reach * reach;
 }
 
 // Removes partner i from unflagged row j (one lane): its entry becomes -1.
@@ -408,7 +442,8 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     int cnt_l = 0, cid = 0;
     if (lane < 27) {
         const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
-        if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+        if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2 &&
+            cell_reachable(g, x, y, z, qn)) {
             cid = g.cell_base + (z * d1 + y) * d0 + x;
             cnt_l = s.cell_cnt[cid];
         }
@@ -544,7 +579,8 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill,
         int cnt_l = 0, cid = 0;
         if (lane < 27) {
             const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
-            if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+            if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2 &&
+                cell_reachable(g, x, y, z, qi)) {
                 cid = g.cell_base + (z * d1 + y) * d0 + x;
                 cnt_l = min(s.cell_cnt[cid], ccap);
             }
