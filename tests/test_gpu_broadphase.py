@@ -308,3 +308,70 @@ def test_drum_full_size_parity(orc):
     st, sm = _run_trajectory(orc, s, _random_walk(s, 3, 6e-5, seed=2), 0, 1, 0.1, every=3)
     assert st["n"] == 2_000_000
     assert st["flagged_total"] > 500_000
+
+
+def _crowd_moves(s, n_cells=20, per_cell=20, seed=31):
+    """One step in which `per_cell` particles jump into each of `n_cells`
+    cells at once while the particles that were in those cells jump out:
+    many concurrent movers reuse the cells' emptied slots and append new
+    ones.  Returns the snapshots (this step, then a step with no motion)."""
+    rng = np.random.default_rng(seed)
+    pos = s.pos.copy()
+    rmax = np.float32(pos[:, 3].max())
+    L = 1.25 * 2.0 * float(rmax) * (1 + 2 ** -7)
+    lo = np.array(s.lo, np.float64)
+    dims = np.ceil((np.array(s.hi, np.float64) - lo) / L).astype(int)
+    cell = np.clip(np.floor((pos[:, :3] - lo) / L).astype(int), 0, dims - 1)
+    key = (cell[:, 2] * dims[1] + cell[:, 1]) * dims[0] + cell[:, 0]
+    inner = np.array([c for c in range(dims.prod())
+                      if all(0 < v < d - 1 for v, d in zip(
+                          ((c % dims[0]), (c // dims[0]) % dims[1], c // (dims[0] * dims[1])),
+                          dims))])
+    targets = rng.choice(inner, n_cells, replace=False)
+    residents = np.nonzero(np.isin(key, targets))[0]
+    others = rng.permutation(np.nonzero(~np.isin(key, targets))[0])
+    movers = others[:n_cells * per_cell]
+    for t, c in enumerate(targets):
+        cx, cy, cz = c % dims[0], (c // dims[0]) % dims[1], c // (dims[0] * dims[1])
+        idx = movers[t * per_cell:(t + 1) * per_cell]
+        u = rng.uniform(0.2, 0.8, size=(per_cell, 3))
+        pos[idx, :3] = (lo + (np.array([cx, cy, cz]) + u) * L).astype(np.float32)
+    # the residents leave for random places elsewhere in the box
+    hi = np.array(s.hi, np.float64)
+    pos[residents, :3] = rng.uniform(lo + 2 * L, hi - 2 * L,
+                                     size=(len(residents), 3)).astype(np.float32)
+    return [(pos.copy(), s.vel), (pos.copy(), s.vel)], len(residents)
+
+
+def _tiny_and_big(n=6000, n_big=100, seed=32):
+    """Many tiny spheres among a few big ones, scattered in a 25 mm box: the
+    cell edge follows the big ones, so a cell has room for thousands of slots."""
+    rng = np.random.default_rng(seed)
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = rng.uniform(1e-3, 24e-3, size=(n, 3))
+    pos[:, 3] = 5e-5
+    pos[:n_big, 3] = 1e-3
+    return scenes.Scene("tiny_and_big", pos, np.zeros_like(pos), (0, 0, 0),
+                        (0.025, 0.025, 0.025), 1e-5, 2, "box")
+
+
+@pytest.mark.parametrize("direct_max", [4096, 0], ids=["one_phase", "two_phase"])
+@pytest.mark.parametrize("crowd", ["20x20", "1x2000"])
+def test_crowded_cell_moves_parity(orc, direct_max, crowd):
+    # particles move into a few cells in one step while the cells' former
+    # occupants move out: concurrent moves claim the freed slots and append
+    # new ones (up to 2,000 movers into one cell); every particle must end in
+    # exactly one slot, so the lists must still equal the oracle's
+    lvb = _cuda()
+    if crowd == "20x20":
+        s = scenes.ballistic(n=3000, seed=31, phi=0.3)
+        snaps, n_res = _crowd_moves(s)
+        moved = 400
+    else:
+        s = _tiny_and_big()
+        snaps, n_res = _crowd_moves(s, n_cells=1, per_cell=2000, seed=33)
+        moved = 2000
+    assert n_res > 0
+    st, _ = _run_trajectory(orc, s, snaps, 0, 1, 0.1,
+                            options=((lvb.LVB_OPT_DIRECT_MAX, direct_max),))
+    assert st["flagged_total"] >= moved + n_res
