@@ -182,3 +182,51 @@ def test_autotuner_picks_a_measured_candidate_and_keeps_results():
     assert ctxs[0].stats()["flagged_total"] == ctxs[1].stats()["flagged_total"] > 0
     for ctx in ctxs:
         ctx.close()
+
+
+def test_full_size_batch_sampled_parity(orc):
+    # the 512-scene, 6.2M-particle batch in the launch shape the autotuner
+    # picked (cell factor 1.0, 512-thread blocks): three random-walk steps,
+    # then, for a sample of scenes (the smallest, the largest and four
+    # others), flags, reference states and pair sets against the oracle run
+    # on that scene alone
+    lvb = _lvb()
+    from oracle.statemachine import OracleLVB
+    sc = scenes.batch()
+    off = np.concatenate([[0], np.cumsum([s.n for s in sc])]).astype(np.int64)
+    assert off[-1] > 6_000_000
+    pos0 = np.concatenate([s.pos for s in sc])
+    ctx = lvb.LVB(_dev(pos0), [s.lo for s in sc], [s.hi for s in sc], 1, 0.1, 1e-6, 0, 1.0,
+                  offsets=off)
+    ctx.set_option(lvb.LVB_OPT_BLOCK_THREADS, 512)
+    sizes = np.array([s.n for s in sc])
+    rng = np.random.default_rng(12)
+    pick = sorted({int(sizes.argmin()), int(sizes.argmax())}
+                  | set(rng.choice(len(sc), 4, replace=False).tolist()))
+    sms = {}
+    for q in pick:
+        rmax = np.float32(sc[q].pos[:, 3].max())
+        H = np.float32(0.5 * 1.0 * 2.0 * float(rmax) * (1 + 2 ** -7) * (1 - 2 ** -8))
+        assert ctx.scene_info(q)["rnl_max"] == H
+        sms[q] = OracleLVB(sc[q].pos, 1, 0.1, 1e-6, H, 0)
+    p = pos0.copy()
+    last = {}
+    for k in range(3):
+        p[:, :3] += rng.normal(0, 6e-5, size=(len(p), 3)).astype(np.float32)
+        ctx.step(_dev(p))
+        for q in pick:
+            last[q], _ = sms[q].step(p[off[q]:off[q + 1]])
+    assert ctx.sync() == 0
+    fl, ref = ctx.flags(), ctx.ref()
+    pi, pj = ctx.pairs_ij()
+    for q in pick:
+        a, b = off[q], off[q + 1]
+        sm = sms[q]
+        assert np.array_equal(fl[a:b], last[q]), "scene %d" % q
+        assert np.array_equal(ref[a:b], sm.ref), "scene %d" % q
+        sel = (pi >= a) & (pi < b)
+        assert ((pj[sel] >= a) & (pj[sel] < b)).all()
+        assert np.array_equal(pi[sel] - a, sm.pi) and np.array_equal(pj[sel] - a, sm.pj), \
+            "scene %d" % q
+    assert ctx.stats()["flagged_total"] > 100_000
+    ctx.close()
