@@ -148,6 +148,40 @@ def test_learned_policy_broad_phase_parity(orc):
     ctx.close()
 
 
+def test_learned_policy_full_size_drum_parity(orc):
+    # the learned policy on the 1,000,000-sphere drum (lognormal radii):
+    # skins proposed by the network at init and for every flagged particle of
+    # two random-walk steps; flags, reference states and pair sets equal the
+    # oracle's state machine with the same network
+    lvb = _lvb()
+    from oracle.statemachine import OracleLVB
+    s = scenes.drum(n=1_000_000, length=0.1)
+    W, grid = _learned_setup(lvb, s)
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi))
+    acc = np.zeros_like(s.pos)
+    acc[:, 2] = -9.81
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_LEARNED, 0.0, s.dt,
+                  lvb.LVB_TRIGGER_PARTIAL, s.cell_factor, vel=_dev(s.vel), acc=_dev(acc),
+                  mlp=wbuf)
+    sm = OracleLVB(s.pos, orc.SKIN_LEARNED, 0.0, s.dt, grid["H"], 0, vel4=s.vel,
+                   learned={"weights": W, "grid": grid}, acc4=acc)
+    assert np.array_equal(ctx.ref(), sm.ref)
+    rng = np.random.default_rng(4)
+    p = s.pos.copy()
+    nflag = 0
+    for k in range(2):
+        p[:, :3] += rng.normal(0, 3e-5, size=(len(p), 3)).astype(np.float32)
+        ctx.step(_dev(p), _dev(s.vel), _dev(acc))
+        f, _ = sm.step(p, vel4=s.vel, acc4=acc)
+        nflag += int(f.sum())
+        assert np.array_equal(ctx.flags(), f), k
+        assert np.array_equal(ctx.ref(), sm.ref), k
+    pi, pj = ctx.pairs_ij()
+    assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj)
+    assert nflag > 10_000
+    ctx.close()
+
+
 def test_rebuild_log_samples(orc):
     lvb = _lvb()
     s = scenes.ballistic(n=2000, seed=23, vsigma=1.0)
