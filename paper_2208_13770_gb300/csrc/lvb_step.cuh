@@ -59,6 +59,12 @@ struct DevState {
     int *fid;         // flagged ids of the step, in compaction order
     float4 *fref;     // their new (xref, R_NL), same order
     float4 *oref;     // their old (xref, R_NL), same order
+    // many scenes: the flagged particles of scene q also sit in its own
+    // segment [first_q, first_q + sc_cnt[par][q]) of sfid / sfref, so the
+    // direct flagged test scans only its scene (null with one scene)
+    int *sc_cnt;      // 2 x nscenes counters (by step parity)
+    int *sfid;
+    float4 *sfref;
     // rows: row i is col[row_off[i], row_off[i] + row_cap[i]); entries below
     // row_len[i] are partners or -1 (a removed pair), entries at or above
     // it are -1; row_len[i] > row_cap[i] means the row overflowed
@@ -222,10 +228,17 @@ static __device__ __noinline__ void update_warp(const DevState &s, int i, int k,
     }
     const float sk = warp_skin(s, g, r, v, f);
     if (lane == 0) {
+        const float4 qn = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
         s.ref[i] = make_float4(p.x, p.y, p.z, sk);
         s.born[i] = step;
-        s.fref[k] = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+        s.fref[k] = qn;
         s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
+        if (s.sc_cnt) {
+            const int sc = s.scene_of[i];
+            const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
+            s.sfid[slot] = i;
+            s.sfref[slot] = qn;
+        }
         if (s.log_on && s.lg_t[i] < 0) {
             s.lg_t[i] = step;
             s.lg_x[i] = p;
@@ -233,6 +246,35 @@ static __device__ __noinline__ void update_warp(const DevState &s, int i, int k,
 #pragma unroll
             for (int t = 0; t < LVB_MLP_IN; ++t) s.lg_feat[(long long)i * LVB_MLP_IN + t] = f[t];
         }
+    }
+}
+
+// a2 for up to 32 flagged particles at once, one per lane (lane t takes
+// entry t of the lists id / kk, t < m): the same update as update_warp for
+// the policies that need neither the network nor the rebuild log, with all
+// the lanes' loads in flight together.
+static __device__ __noinline__ void update_lanes(const DevState &s, const int *id, const int *kk, int m,
+                                          const float4 *pos, const float4 *vel, int step)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane >= m) return;
+    const int i = id[lane], k = kk[lane];
+    const float4 p = pos[i];
+    const float r = s.rad[i];
+    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 q = s.ref[i];
+    const SceneGeom &g = geom_of(s, i);
+    const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, 0.0f);
+    const float4 qn = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+    s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+    s.born[i] = step;
+    s.fref[k] = qn;
+    s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
+    if (s.sc_cnt) {
+        const int sc = s.scene_of[i];
+        const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
+        s.sfid[slot] = i;
+        s.sfref[slot] = qn;
     }
 }
 
@@ -427,7 +469,7 @@ __device__ __forceinline__ void lane_edit(const DevState &s, int jr, int ji, int
 // The edits of other rows run one per lane, in parallel; the first 32 old
 // partners and the first 32 stencil candidates are loaded together.
 static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF, bool direct,
-                                               int *ovf)
+                                               int par, int *ovf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -521,30 +563,34 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     }
     if (direct) {
         // kDirectUnroll reference states per lane in flight; the id is
-        // loaded only for a hit, and a hit in another scene (scenes share
-        // one coordinate frame) is dropped
-        const int lo = g.first, hi = g.first + g.count;
-        for (int b0 = 0; b0 < nF; b0 += 32 * kDirectUnroll) {
+        // loaded only for a hit.  Many scenes: the scene's own segment of
+        // the flagged particles (scenes share one coordinate frame, so the
+        // global list would also hold far-away twins)
+        const bool own = s.sc_cnt != nullptr;
+        const float4 *lst = own ? s.sfref + g.first : s.fref;
+        const int *ids = own ? s.sfid + g.first : s.fid;
+        const int m = own ? s.sc_cnt[par * s.nscenes + s.scene_of[i]] : nF;
+        for (int b0 = 0; b0 < m; b0 += 32 * kDirectUnroll) {
             float4 rf[kDirectUnroll];
 #pragma unroll
             for (int u = 0; u < kDirectUnroll; ++u) {
                 const int kk = b0 + u * 32 + lane;
-                rf[u] = kk < nF ? s.fref[kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+                rf[u] = kk < m ? lst[kk] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < kDirectUnroll; ++u) {
                 const int kk = b0 + u * 32 + lane;
                 int j = -1;
-                if (kk < nF && kk != k && pair_hit(qn, rf[u])) {
-                    j = s.fid[kk];
-                    if (j < lo || j >= hi) j = -1;
+                if (kk < m && pair_hit(qn, rf[u])) {
+                    j = ids[kk];
+                    if (j == i || j < g.first || j >= g.first + g.count) j = -1;
                 }
-                const unsigned m = __ballot_sync(FULL, j >= 0);
+                const unsigned msk = __ballot_sync(FULL, j >= 0);
                 if (j >= 0) {
-                    const int p = found + __popc(m & lt);
+                    const int p = found + __popc(msk & lt);
                     if (p < cap) s.col[off + p] = j;
                 }
-                found += __popc(m);
+                found += __popc(msk);
             }
         }
     }
@@ -736,7 +782,11 @@ __device__ __forceinline__ void flush_pending(const DevState &s, Pending &pd, co
                                               const float4 *vel, const float4 *acc, int step)
 {
     __syncwarp();
-    for (int t = 0; t < pd.n; ++t) update_warp(s, pd.id[t], pd.k[t], pos, vel, acc, step);
+    if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
+        for (int t = 0; t < pd.n; ++t) update_warp(s, pd.id[t], pd.k[t], pos, vel, acc, step);
+    } else {
+        update_lanes(s, pd.id, pd.k, pd.n, pos, vel, step);
+    }
     __syncwarp();
     pd.n = 0;
 }
@@ -1167,7 +1217,7 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
 // skip the flagged particles in the cells and test them directly); more:
 // the moves first and a barrier, then the patches on final cells.  Returns
 // false when the step must be abandoned.
-static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int *ovf)
+static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int par, int *ovf)
 {
     // work items go round the blocks first (item w to block w % grid), so
     // that a few flagged particles spread over all SMs instead of filling
@@ -1178,11 +1228,11 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
     if (!direct) {
         for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
         if (!grid_barrier(s)) return false;
-        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, ovf);
+        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, par, ovf);
         return true;
     }
     for (int w = w0; w < 2 * nF; w += nw) {
-        if (w < nF) patch_warp(s, w, nF, true, ovf);
+        if (w < nF) patch_warp(s, w, nF, true, par, ovf);
         else move_warp(s, s.fid[w - nF], s.fref[w - nF]);
     }
     return true;
@@ -1232,6 +1282,9 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         check_pass_stream(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
     if (!grid_barrier(s)) return;
     const int nF = *(volatile int *)&c->nF_acc[par];
+    if (s.sc_cnt && blockIdx.x == 0)   // the next step's scene counters
+        for (int q = threadIdx.x; q < s.nscenes; q += blockDim.x)
+            s.sc_cnt[(par ^ 1) * s.nscenes + q] = 0;
     int upd;
     if (s.trigger == LVB_TRIGGER_PARTIAL) upd = nF;
     else if (s.trigger == LVB_TRIGGER_GLOBAL) upd = nF ? s.n : 0;
@@ -1265,7 +1318,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     bool changed = false;
     if (inc) {
         if (nF > 0) {
-            if (!partial_pass(s, nF, ovf)) return;
+            if (!partial_pass(s, nF, par, ovf)) return;
             changed = true;
         }
     } else if (upd > 0 && !store_failed(s)) {
