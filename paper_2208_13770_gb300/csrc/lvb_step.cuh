@@ -250,15 +250,15 @@ static __device__ __noinline__ void update_warp(const DevState &s, int i, int k,
 }
 
 // a2 for up to 32 flagged particles at once, one per lane (lane t takes
-// entry t of the lists id / kk, t < m): the same update as update_warp for
+// particle id[t], list index k0 + t, t < m): the same update as update_warp for
 // the policies that need neither the network nor the rebuild log, with all
 // the lanes' loads in flight together.
-static __device__ __noinline__ void update_lanes(const DevState &s, const int *id, const int *kk, int m,
-                                          const float4 *pos, const float4 *vel, int step)
+static __device__ __noinline__ void update_lanes(const DevState &s, const int *id, int k0, int m,
+                                                 const float4 *pos, const float4 *vel, int step)
 {
     const int lane = threadIdx.x & 31;
     if (lane >= m) return;
-    const int i = id[lane], k = kk[lane];
+    const int i = id[lane], k = k0 + lane;
     const float4 p = pos[i];
     const float r = s.rad[i];
     const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -763,103 +763,107 @@ __device__ __forceinline__ long long block_scan_any(long long v, long long *tota
 }
 
 // ---------------------------------------------------------------------------
-// Flagged particles a warp found in the check and has yet to update: their
-// ids and indices in the flagged list, in shared memory (per warp), so that
-// the updates' dependent loads run after the warp's tiles instead of
-// holding up the block's stream of tiles.
+// Flagged particles a warp found in the check and has not yet entered in
+// the flagged list: their ids, in shared memory (per warp).  The list
+// indices are taken when the pending list is flushed (when it fills, and at
+// the end of the pass), so no atomic round trip holds up the block's stream
+// of tiles, and the updates' dependent loads run after the warp's tiles.
 constexpr int kPending = 32;
 
 struct Pending {
     int *id;    // kPending entries of this warp
-    int *k;
     int n;      // warp-uniform count
 };
 
-// Updates the warp's pending flagged particles (update_warp) and empties
-// the list.  New positions written earlier in this kernel by the warp's own
+// Enters the warp's pending particles in the flagged list at k0, k0 + 1, ...
+// (fid) and, with inc, updates them (update_lanes, one per lane, or
+// update_warp, one at a time for the network and the log); empties the
+// list.  New positions written earlier in this kernel by the warp's own
 // lanes (DEM form) are made visible to the whole warp first.
-__device__ __forceinline__ void flush_pending(const DevState &s, Pending &pd, const float4 *pos,
-                                              const float4 *vel, const float4 *acc, int step)
+__device__ __forceinline__ void enter_pending(const DevState &s, Pending &pd, int k0,
+                                              const float4 *pos, const float4 *vel,
+                                              const float4 *acc, bool inc, int step)
 {
+    const int lane = threadIdx.x & 31;
     __syncwarp();
-    if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
-        for (int t = 0; t < pd.n; ++t) update_warp(s, pd.id[t], pd.k[t], pos, vel, acc, step);
-    } else {
-        update_lanes(s, pd.id, pd.k, pd.n, pos, vel, step);
+    if (lane < pd.n) s.fid[k0 + lane] = pd.id[lane];
+    if (inc) {
+        if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
+            for (int t = 0; t < pd.n; ++t) update_warp(s, pd.id[t], k0 + t, pos, vel, acc, step);
+        } else {
+            update_lanes(s, pd.id, k0, pd.n, pos, vel, step);
+        }
     }
     __syncwarp();
     pd.n = 0;
 }
 
-// a1 (+ a2 with the PARTIAL trigger) for U chunks of 32 consecutive
-// particles held by one warp (chunk u starts at cu[u], a multiple of 32; f[u]
-// is this lane's flag in it): one ballot word per chunk, compaction of the
-// flagged ids -- one atomic per warp's chunks with flags (warp scheme), or
-// one per block tile after a block scan (block scheme: two block barriers,
-// so every thread of the block makes the same calls) -- and, with inc, the
-// flagged particles join the warp's pending list (updated when it fills
-// and after the pass).
+// The same with list indices from one atomic of this warp.
+__device__ __forceinline__ void flush_pending(const DevState &s, Pending &pd, const float4 *pos,
+                                              const float4 *vel, const float4 *acc, bool inc,
+                                              int step, int *nF_acc)
+{
+    int k0 = 0;
+    if ((threadIdx.x & 31) == 0) k0 = atomicAdd(nF_acc, pd.n);
+    k0 = __shfl_sync(FULL, k0, 0);
+    enter_pending(s, pd, k0, pos, vel, acc, inc, step);
+}
+
+// End of the check pass, every thread of the block: the pending particles
+// of all warps enter the list -- with one atomic per warp (warp scheme) or
+// one per block after a scan of the warps' counts (block scheme).
+__device__ __forceinline__ void flush_pending_final(const DevState &s, Pending &pd,
+                                                    const float4 *pos, const float4 *vel,
+                                                    const float4 *acc, bool inc, int step,
+                                                    int *nF_acc)
+{
+    if (!s.compact_block) {
+        if (pd.n) flush_pending(s, pd, pos, vel, acc, inc, step, nF_acc);
+        return;
+    }
+    __shared__ int s_cnt[32];
+    __shared__ int s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!__syncthreads_or(pd.n)) return;
+    if (lane == 0) s_cnt[warp] = pd.n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int v = s_cnt[w];
+            s_cnt[w] = run;
+            run += v;
+        }
+        s_base = atomicAdd(nF_acc, run);
+    }
+    __syncthreads();
+    if (pd.n) enter_pending(s, pd, s_base + s_cnt[warp], pos, vel, acc, inc, step);
+}
+
+// a1 for U chunks of 32 consecutive particles held by one warp (chunk u
+// starts at cu[u], a multiple of 32; f[u] is this lane's flag in it): one
+// ballot word per chunk; the flagged particles join the warp's pending list
+// (entered in the flagged list, and updated with the PARTIAL trigger, when
+// it fills and at the end of the pass).
 template <int U>
 __device__ __forceinline__ void flag_chunks(const DevState &s, const int (&cu)[U],
                                             const bool (&f)[U], const float4 *pos,
                                             const float4 *vel, const float4 *acc, bool inc,
                                             int step, int *nF_acc, Pending &pd)
 {
-    __shared__ int s_cnt[32];
-    __shared__ int s_base;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    unsigned b[U];
-    int cnt = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        b[u] = __ballot_sync(FULL, f[u]);
+        const unsigned b = __ballot_sync(FULL, f[u]);
         if (lane == 0 && cu[u] < s.n) {
-            s.bits[cu[u] >> 5] = b[u];
-            if (s.bits_out) s.bits_out[cu[u] >> 5] = b[u];
+            s.bits[cu[u] >> 5] = b;
+            if (s.bits_out) s.bits_out[cu[u] >> 5] = b;
         }
-        cnt += __popc(b[u]);
-    }
-    int k0 = 0;
-    if (s.compact_block) {
-        if (!__syncthreads_or(cnt)) return;
-        if (lane == 0) s_cnt[warp] = cnt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                const int v = s_cnt[w];
-                s_cnt[w] = run;
-                run += v;
-            }
-            s_base = atomicAdd(nF_acc, run);
-        }
-        __syncthreads();
-        k0 = s_base + s_cnt[warp];
-    } else {
-        if (!cnt) return;
-        if (lane == 0) k0 = atomicAdd(nF_acc, cnt);
-        k0 = __shfl_sync(FULL, k0, 0);
-    }
-    if (!cnt) return;
-    int kb[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        kb[u] = k0;
-        if (b[u] >> lane & 1u) s.fid[k0 + __popc(b[u] & lt)] = cu[u] + lane;
-        k0 += __popc(b[u]);
-    }
-    if (inc) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (pd.n + __popc(b[u]) > kPending) flush_pending(s, pd, pos, vel, acc, step);
-            if (b[u] >> lane & 1u) {
-                const int r = __popc(b[u] & lt);
-                pd.id[pd.n + r] = cu[u] + lane;
-                pd.k[pd.n + r] = kb[u] + r;
-            }
-            pd.n += __popc(b[u]);
-        }
+        if (!b) continue;
+        if (pd.n + __popc(b) > kPending) flush_pending(s, pd, pos, vel, acc, inc, step, nF_acc);
+        if (b >> lane & 1u) pd.id[pd.n + __popc(b & lt)] = cu[u] + lane;
+        pd.n += __popc(b);
     }
 }
 
@@ -872,9 +876,9 @@ __device__ __forceinline__ void check_pass_fused(const DevState &s, const float4
                                                  const float4 *acc, const IntegrateArgs &ia,
                                                  bool inc, int step, int *nF_acc)
 {
-    __shared__ int pend_id[kStepMaxThreads / 32][kPending], pend_k[kStepMaxThreads / 32][kPending];
+    __shared__ int pend_id[kStepMaxThreads / 32][kPending];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Pending pd{pend_id[warp], pend_k[warp], 0};
+    Pending pd{pend_id[warp], 0};
     const int tile = blockDim.x * kCheckUnroll;
     for (int t0 = blockIdx.x * tile; t0 < s.n; t0 += gridDim.x * tile) {
         float4 p[kCheckUnroll], q[kCheckUnroll];
@@ -901,7 +905,7 @@ __device__ __forceinline__ void check_pass_fused(const DevState &s, const float4
         }
         flag_chunks<kCheckUnroll>(s, cu, f, ia.pos, vel, acc, inc, step, nF_acc, pd);
     }
-    if (pd.n) flush_pending(s, pd, ia.pos, vel, acc, step);
+    flush_pending_final(s, pd, ia.pos, vel, acc, inc, step, nF_acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -982,9 +986,9 @@ __device__ __forceinline__ void check_pass_stream(const DevState &s, const float
 {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar[kStages];
-    __shared__ int pend_id[kStepMaxThreads / 32][kPending], pend_k[kStepMaxThreads / 32][kPending];
+    __shared__ int pend_id[kStepMaxThreads / 32][kPending];
     const int T = blockDim.x, tid = threadIdx.x, warp = tid >> 5;
-    Pending pd{pend_id[warp], pend_k[warp], 0};
+    Pending pd{pend_id[warp], 0};
     float4 *spos = reinterpret_cast<float4 *>(dsm);
     float4 *sref = spos + kStages * T;
     const int ntiles = (s.n + T - 1) / T;
@@ -1035,7 +1039,7 @@ __device__ __forceinline__ void check_pass_stream(const DevState &s, const float
         for (int k = j; k < issued; ++k)
             stage_wait(&bar[k % kStages], (unsigned)(k / kStages) & 1u);
     }
-    if (pd.n) flush_pending(s, pd, pos, vel, acc, step);
+    flush_pending_final(s, pd, pos, vel, acc, inc, step, nF_acc);
 }
 
 static __device__ __noinline__ void full_update_pass(const DevState &s, const float4 *pos,
