@@ -6,8 +6,9 @@
 // Training: one thread per sample runs the forward pass (the exact inference
 // formula) and the backward pass (straight-through the bfloat16 roundings);
 // a block of kTB samples stages its activations in shared memory and reduces
-// its share of every weight gradient before one atomic add per parameter.
-// Adam updates the binary32 master parameters.
+// its share of every weight gradient into its own row of partial sums; the
+// rows are then added in block order (no atomics), so training is bitwise
+// repeatable.  Adam updates the binary32 master parameters.
 #include "lvb_internal.cuh"
 #include "lvb_mlp.h"
 
@@ -58,7 +59,13 @@ __global__ void k_mlp_infer(const float *__restrict__ feats, const float *__rest
 
 // Per-column sum and sum of squares (binary64) of the samples: the eight
 // features (normalisation) and the label (output range).
-__global__ void k_feature_stats(const float *__restrict__ samples, int64_t n, double *acc)
+// Per-warp sums of every column and of its squares (binary64), written to
+// the warp's row of part (2 x kSamp values); the host adds the rows in warp
+// order, so the statistics do not depend on scheduling.
+constexpr int kStatBlocks = 152 * 4, kStatThreads = 256;
+constexpr int kStatWarps = kStatBlocks * kStatThreads / 32;
+
+__global__ void k_feature_stats(const float *__restrict__ samples, int64_t n, double *part)
 {
     double s[kSamp] = {0}, q[kSamp] = {0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -77,8 +84,9 @@ __global__ void k_feature_stats(const float *__restrict__ samples, int64_t n, do
             q[k] += __shfl_xor_sync(FULL, q[k], o);
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&acc[k], s[k]);
-            atomicAdd(&acc[kSamp + k], q[k]);
+            const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+            part[(size_t)w * 2 * kSamp + k] = s[k];
+            part[(size_t)w * 2 * kSamp + kSamp + k] = q[k];
         }
     }
 }
@@ -89,7 +97,7 @@ struct TrainArgs {
     int64_t first, count;   // positions [first, first + count) form the batch
     const float *params;    // master parameters
     const float *mu, *isd;
-    float *grad;            // accumulated gradient (NP)
+    float *part;            // per-block partial gradients (blocks x NP)
     double *loss;           // accumulated sum of (weighted) squared errors
     float dy_scale;         // 2 / batch size
     float rel_floor;        // > 0: relative error, (y - t) / max(t, rel_floor)
@@ -176,22 +184,34 @@ k_mlp_batch(TrainArgs a)
         } else {
             for (int q = 0; q < kTB; ++q) g += sdy[q];
         }
-        if (g != 0.0f) atomicAdd(&a.grad[p], g);
+        a.part[(size_t)blockIdx.x * NP + p] = g;
     }
 }
 
-__global__ void k_adam(float *p, float *g, float *m, float *v, int n, float lr, float b1,
-                       float b2, float eps, float c1, float c2)
+// grad[i] += the nb blocks' partial sums of parameter i, in block order.
+__global__ void k_fold_parts(const float *part, int nb, float *grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NP) return;
+    float g = grad[i];
+    for (int b = 0; b < nb; ++b) g += part[(size_t)b * NP + i];
+    grad[i] = g;
+}
+
+// One Adam step; the gradient is the sum of the nb blocks' partials, added
+// in block order.
+__global__ void k_adam(float *p, const float *part, int nb, float *m, float *v, int n, float lr,
+                       float b1, float b2, float eps, float c1, float c2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float gi = g[i];
+    float gi = 0.0f;
+    for (int b = 0; b < nb; ++b) gi += part[(size_t)b * NP + i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    g[i] = 0.0f;
 }
 
 int from_cuda(cudaError_t e)
@@ -215,10 +235,11 @@ cudaError_t dnew(DevBuf &b, size_t count)
     return cudaMalloc(&b.p, sizeof(T) * std::max<size_t>(count, 1));
 }
 
-// one pass of k_mlp_batch over positions [first, first + count)
-void launch_batch(const float *samples, const int *order, int64_t first, int64_t count,
-                  const float *params, const float *mu, const float *isd, float *grad,
-                  double *loss, float rel_floor, cudaStream_t st)
+// one pass of k_mlp_batch over positions [first, first + count) of a mean
+// over `total` samples; returns the number of blocks (rows of part)
+int launch_batch(const float *samples, const int *order, int64_t first, int64_t count,
+                 int64_t total, const float *params, const float *mu, const float *isd,
+                 float *part, double *loss, float rel_floor, cudaStream_t st)
 {
     TrainArgs a;
     a.samples = samples;
@@ -228,13 +249,16 @@ void launch_batch(const float *samples, const int *order, int64_t first, int64_t
     a.params = params;
     a.mu = mu;
     a.isd = isd;
-    a.grad = grad;
+    a.part = part;
     a.loss = loss;
-    a.dy_scale = 2.0f / (float)count;
+    a.dy_scale = 2.0f / (float)total;
     a.rel_floor = rel_floor;
     const int64_t blocks = (count + kTB - 1) / kTB;
     k_mlp_batch<<<(unsigned)blocks, kTB, 0, st>>>(a);
+    return (int)blocks;
 }
+
+constexpr int64_t kGradChunk = 1024 * kTB;   // samples per pass of lvb_mlp_grad
 
 }  // namespace
 
@@ -280,20 +304,27 @@ int lvb_mlp_grad(const float *samples, int64_t n, const float *params, const flo
     if (!(rel_floor >= 0.0f)) return LVB_EINVAL;
     cudaGetLastError();
     const cudaStream_t st = (cudaStream_t)stream;
-    DevBuf dp, dmu, disd, dg, dl;
+    DevBuf dp, dmu, disd, dg, dl, dpart;
     cudaError_t e = dnew<float>(dp, NP);
     if (e == cudaSuccess) e = dnew<float>(dmu, NI);
     if (e == cudaSuccess) e = dnew<float>(disd, NI);
     if (e == cudaSuccess) e = dnew<float>(dg, NP);
     if (e == cudaSuccess) e = dnew<double>(dl, 1);
+    if (e == cudaSuccess)
+        e = dnew<float>(dpart, (size_t)((std::min(n, kGradChunk) + kTB - 1) / kTB) * NP);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dp.p, params, NP * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dmu.p, mu, NI * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(disd.p, isd, NI * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dg.p, 0, NP * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dl.p, 0, 8, st);
     if (e != cudaSuccess) return from_cuda(e);
-    launch_batch(samples, nullptr, 0, n, (const float *)dp.p, (const float *)dmu.p,
-                 (const float *)disd.p, (float *)dg.p, (double *)dl.p, rel_floor, st);
+    for (int64_t first = 0; first < n; first += kGradChunk) {
+        const int nb = launch_batch(samples, nullptr, first, std::min(kGradChunk, n - first), n,
+                                    (const float *)dp.p, (const float *)dmu.p,
+                                    (const float *)disd.p, (float *)dpart.p, (double *)dl.p,
+                                    rel_floor, st);
+        k_fold_parts<<<(NP + 255) / 256, 256, 0, st>>>((const float *)dpart.p, nb, (float *)dg.p);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dg.p, NP * 4, cudaMemcpyDeviceToHost, st);
     double sse = 0.0;
@@ -318,14 +349,17 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
     const cudaStream_t st = (cudaStream_t)stream;
     // feature normalisation from the samples (mean, 1/std), label range
     DevBuf dstat;
-    cudaError_t e = dnew<double>(dstat, 2 * kSamp);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dstat.p, 0, 2 * kSamp * 8, st);
+    cudaError_t e = dnew<double>(dstat, (size_t)kStatWarps * 2 * kSamp);
     if (e != cudaSuccess) return from_cuda(e);
-    k_feature_stats<<<152 * 4, 256, 0, st>>>(samples, n, (double *)dstat.p);
-    double stat[2 * kSamp];
-    e = cudaMemcpyAsync(stat, dstat.p, sizeof(stat), cudaMemcpyDeviceToHost, st);
+    k_feature_stats<<<kStatBlocks, kStatThreads, 0, st>>>(samples, n, (double *)dstat.p);
+    std::vector<double> parts((size_t)kStatWarps * 2 * kSamp);
+    e = cudaMemcpyAsync(parts.data(), dstat.p, sizeof(double) * parts.size(),
+                        cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
+    double stat[2 * kSamp] = {0};
+    for (int w = 0; w < kStatWarps; ++w)
+        for (int k = 0; k < 2 * kSamp; ++k) stat[k] += parts[(size_t)w * 2 * kSamp + k];
     for (int k = 0; k < NI; ++k) {
         const double m = stat[k] / (double)n;
         const double var = std::max(stat[kSamp + k] / (double)n - m * m, 0.0);
@@ -345,7 +379,7 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
     e = dnew<float>(dp, NP);
     if (e == cudaSuccess) e = dnew<float>(dmu, NI);
     if (e == cudaSuccess) e = dnew<float>(disd, NI);
-    if (e == cudaSuccess) e = dnew<float>(dg, NP);
+    if (e == cudaSuccess) e = dnew<float>(dg, (size_t)((batch + kTB - 1) / kTB) * NP);
     if (e == cudaSuccess) e = dnew<float>(dm, NP);
     if (e == cudaSuccess) e = dnew<float>(dv, NP);
     if (e == cudaSuccess) e = dnew<double>(dl, 1);
@@ -353,7 +387,6 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
     if (e == cudaSuccess) e = cudaMemcpyAsync(dp.p, params, NP * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dmu.p, mu, NI * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(disd.p, isd, NI * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dg.p, 0, NP * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dm.p, 0, NP * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dv.p, 0, NP * 4, st);
     if (e != cudaSuccess) return from_cuda(e);
@@ -370,13 +403,15 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
         if (e != cudaSuccess) return from_cuda(e);
         for (int64_t first = 0; first < n; first += batch) {
             const int64_t cnt = std::min<int64_t>(batch, n - first);
-            launch_batch(samples, (const int *)dord.p, first, cnt, (const float *)dp.p,
-                         (const float *)dmu.p, (const float *)disd.p, (float *)dg.p,
-                         (double *)dl.p, rel_floor, st);
+            const int nb = launch_batch(samples, (const int *)dord.p, first, cnt, cnt,
+                                        (const float *)dp.p, (const float *)dmu.p,
+                                        (const float *)disd.p, (float *)dg.p, (double *)dl.p,
+                                        rel_floor, st);
             ++t;
             const float c1 = 1.0f - std::pow(b1, (float)t), c2 = 1.0f - std::pow(b2, (float)t);
-            k_adam<<<(NP + 255) / 256, 256, 0, st>>>((float *)dp.p, (float *)dg.p, (float *)dm.p,
-                                                     (float *)dv.p, NP, lr, b1, b2, eps, c1, c2);
+            k_adam<<<(NP + 255) / 256, 256, 0, st>>>((float *)dp.p, (const float *)dg.p, nb,
+                                                     (float *)dm.p, (float *)dv.p, NP, lr, b1, b2,
+                                                     eps, c1, c2);
         }
         double sse = 0.0;
         e = cudaGetLastError();
