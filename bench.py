@@ -426,8 +426,8 @@ def _e2e(lvb, torch, scene, rec):
     window of the run (the context resumes from the run's saved reference
     state).  Pipelined: per step lvb_step_host copies the pinned host
     positions in (overlapping the previous step's kernel) and the step's flag
-    words and count out to pinned host memory; one synchronisation at the
-    end.  Also the per-step synchronous form: copy in, lvb_step, then
+    words and count out to pinned host memory (overlapping the next step's
+    kernel); one synchronisation at the end.  Also the per-step synchronous form: copy in, lvb_step, then
     lvb_get_flags (which waits) every step."""
     m = rec["m"]
     nw = (scene.n + 31) // 32

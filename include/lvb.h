@@ -225,15 +225,16 @@ int lvb_step(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *ac
  * Enqueues only.  The inputs are copied into one of two device staging
  * slots owned by the context, on a copy stream of its own, so the copy of a
  * step's inputs overlaps the previous step's kernel; the step waits for its
- * copy.  Outputs in page-locked memory are written by the step kernel
- * itself (over the host link, as the flags are found); outputs in pageable
- * memory are copied back on the context's stream after the step.
+ * copy and writes its flags also into the slot, which a second copy stream
+ * of the context copies out to `bits` / `n_flagged` while the next step
+ * runs.
  * Every host buffer must stay valid, and the inputs unchanged, until
  * lvb_sync (or another synchronising call) returns.  Page-locked host
  * memory (cudaHostAlloc, cudaHostRegister) lets the copies overlap; with
  * pageable memory the results are the same but the copies serialise.  The
  * staging slots are allocated on the first call (2 x n x 16 bytes per
- * input given).  Errors: EINVAL (as lvb_step), ENOMEM, EDEVICE.
+ * input given, and 2 x (ceil(n / 32) + 1) x 4 bytes for the outputs).
+ * Errors: EINVAL (as lvb_step), ENOMEM, EDEVICE.
  */
 int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const float *acc,
                   uint32_t *bits, int32_t *n_flagged);

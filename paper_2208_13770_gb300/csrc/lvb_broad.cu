@@ -390,12 +390,16 @@ struct lvb_ctx {
     int version = 0;                // bumped whenever the step kernel's arguments change
     HostFlags *hflags = nullptr;    // mapped pinned host memory
     long long grows = 0;            // store or cell-slot growths done
-    // lvb_step_host: two device staging slots for (pos, vel, acc), filled on
-    // a copy stream so that a step's input copy overlaps the previous step
+    // lvb_step_host: two staging slots, each with device buffers for the
+    // inputs (pos, vel, acc) and the outputs (flag words, flagged count);
+    // the inputs come in on one copy stream and the outputs go out on
+    // another, so both copies overlap the neighbouring steps' kernels
     struct {
         float4 *buf[2][3] = {};
-        cudaStream_t copy = nullptr;
-        cudaEvent_t copied[2] = {}, consumed[2] = {};
+        uint32_t *flags[2] = {};
+        int *nf[2] = {};
+        cudaStream_t in = nullptr, out = nullptr;
+        cudaEvent_t copied[2] = {}, done[2] = {}, drained[2] = {};
         int slot = 0;
         bool ready = false;
     } hs;
@@ -436,10 +440,14 @@ void free_all(lvb_ctx *c)
         for (float4 *p : slot)
             if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k) {
+        if (c->hs.flags[k]) cudaFree(c->hs.flags[k]);
+        if (c->hs.nf[k]) cudaFree(c->hs.nf[k]);
         if (c->hs.copied[k]) cudaEventDestroy(c->hs.copied[k]);
-        if (c->hs.consumed[k]) cudaEventDestroy(c->hs.consumed[k]);
+        if (c->hs.done[k]) cudaEventDestroy(c->hs.done[k]);
+        if (c->hs.drained[k]) cudaEventDestroy(c->hs.drained[k]);
     }
-    if (c->hs.copy) cudaStreamDestroy(c->hs.copy);
+    if (c->hs.in) cudaStreamDestroy(c->hs.in);
+    if (c->hs.out) cudaStreamDestroy(c->hs.out);
 }
 
 int from_cuda(cudaError_t e)
@@ -459,19 +467,6 @@ int from_derr(unsigned e)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// The device address of a page-locked host buffer, or null when the device
-// cannot address it (pageable memory): then the outputs are copied instead.
-void *device_view(void *host)
-{
-    if (!host) return nullptr;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
-    return at.devicePointer;
-}
 
 // Row-store scan of ctx rows (size = row_capacity(row_len)), gated.
 ScanArgs layout_args(lvb_ctx *c);
@@ -530,6 +525,10 @@ int size_step(lvb_ctx *c)
 
 int sync_counters(lvb_ctx *c)
 {
+    if (c->hs.ready) {   // outputs of lvb_step_host still on their way
+        const cudaError_t eo = cudaStreamSynchronize(c->hs.out);
+        if (eo != cudaSuccess) return from_cuda(eo);
+    }
     cudaError_t e = cudaMemcpyAsync(c->cnt_h, c->s.cnt, sizeof(DevCounters),
                                     cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -996,13 +995,18 @@ int lvb_step_host(lvb_ctx *c, const float *pos_r, const float *vel, const float 
     if (c->skin.kind == LVB_SKIN_LEARNED && (!vel || !acc)) return LVB_EINVAL;
     auto &hs = c->hs;
     const size_t bytes = sizeof(float4) * (size_t)c->n;
+    const size_t fbytes = sizeof(uint32_t) * (size_t)c->nwords;
     cudaError_t e = cudaSuccess;
     if (!hs.ready) {
-        e = cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking);
+        e = cudaStreamCreateWithFlags(&hs.in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hs.out, cudaStreamNonBlocking);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaEventCreateWithFlags(&hs.copied[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hs.done[k], cudaEventDisableTiming);
             if (e == cudaSuccess)
-                e = cudaEventCreateWithFlags(&hs.consumed[k], cudaEventDisableTiming);
+                e = cudaEventCreateWithFlags(&hs.drained[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaMalloc(&hs.flags[k], fbytes);
+            if (e == cudaSuccess) e = cudaMalloc(&hs.nf[k], sizeof(int));
         }
         if (e != cudaSuccess) return from_cuda(e);
         hs.ready = true;
@@ -1017,33 +1021,37 @@ int lvb_step_host(lvb_ctx *c, const float *pos_r, const float *vel, const float 
                 return from_cuda(e);
             }
         }
-    // the slot's previous step has read its inputs before they are replaced
-    e = cudaStreamWaitEvent(hs.copy, hs.consumed[k], 0);
+    // inputs: after the slot's previous step has read them
+    e = cudaStreamWaitEvent(hs.in, hs.done[k], 0);
     for (int a = 0; a < 3 && e == cudaSuccess; ++a)
         if (src[a])
-            e = cudaMemcpyAsync(hs.buf[k][a], src[a], bytes, cudaMemcpyHostToDevice, hs.copy);
-    if (e == cudaSuccess) e = cudaEventRecord(hs.copied[k], hs.copy);
+            e = cudaMemcpyAsync(hs.buf[k][a], src[a], bytes, cudaMemcpyHostToDevice, hs.in);
+    if (e == cudaSuccess) e = cudaEventRecord(hs.copied[k], hs.in);
+    // the step: after its inputs, and after the slot's previous outputs left
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, hs.copied[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, hs.drained[k], 0);
     if (e != cudaSuccess) return from_cuda(e);
     hs.slot ^= 1;
-    // outputs in page-locked memory are written by the step kernel itself
-    uint32_t *bits_d = (uint32_t *)device_view(bits);
-    int *nf_d = (int *)device_view(n_flagged);
-    c->s.bits_out = bits_d;
-    c->s.nf_out = nf_d;
+    const bool outs = bits || n_flagged;
+    c->s.bits_out = outs ? hs.flags[k] : nullptr;
+    c->s.nf_out = outs ? hs.nf[k] : nullptr;
     const int rc = lvb_step(c, (const float *)hs.buf[k][0],
                             vel ? (const float *)hs.buf[k][1] : nullptr,
                             acc ? (const float *)hs.buf[k][2] : nullptr);
     c->s.bits_out = nullptr;
     c->s.nf_out = nullptr;
     if (rc) return rc;
-    e = cudaEventRecord(hs.consumed[k], c->stream);
-    if (e == cudaSuccess && bits && !bits_d)
-        e = cudaMemcpyAsync(bits, c->s.bits, sizeof(uint32_t) * (size_t)c->nwords,
-                            cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && n_flagged && !nf_d)
-        e = cudaMemcpyAsync(n_flagged, &c->s.cnt->nF, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                            c->stream);
+    e = cudaEventRecord(hs.done[k], c->stream);
+    // outputs: copied out while the next step runs
+    if (e == cudaSuccess && outs) {
+        e = cudaStreamWaitEvent(hs.out, hs.done[k], 0);
+        if (e == cudaSuccess && bits)
+            e = cudaMemcpyAsync(bits, hs.flags[k], fbytes, cudaMemcpyDeviceToHost, hs.out);
+        if (e == cudaSuccess && n_flagged)
+            e = cudaMemcpyAsync(n_flagged, hs.nf[k], sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                hs.out);
+        if (e == cudaSuccess) e = cudaEventRecord(hs.drained[k], hs.out);
+    }
     return from_cuda(e);
 }
 

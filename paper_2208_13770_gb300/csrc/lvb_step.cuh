@@ -96,8 +96,8 @@ struct DevState {
     int direct_max;       // largest flagged count rebuilt in one phase with
                           // the direct flagged-pair test (LVB_OPT_DIRECT_MAX)
     // second destination of this step's flag words and flagged count
-    // (lvb_step_host: the caller's page-locked host buffers, written over
-    // the host link by the kernel itself), or null
+    // (lvb_step_host: a staging slot copied out while the next step runs),
+    // or null
     uint32_t *bits_out;
     int *nf_out;
 };
