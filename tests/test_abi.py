@@ -48,3 +48,43 @@ def test_strerror_without_gpu():
     from paper_2208_13770_gb300 import lvb
     assert lvb.lvb_strerror(0) == "ok"
     assert "overflow" in lvb.lvb_strerror(lvb.LVB_EOVERFLOW)
+
+
+def test_argument_checks_without_gpu():
+    # every call below fails its argument checks before any device work, so
+    # it runs (and must return EINVAL) on a machine without a GPU: empty and
+    # oversized inputs, misaligned records, bad skin / trigger / cell factor,
+    # inverted boxes, null contexts
+    import numpy as np
+    from paper_2208_13770_gb300 import lvb
+    pos = np.zeros((8, 4), np.float32)
+    p = pos.ctypes.data
+    box = lvb.lvb_box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    skin = lvb.lvb_skin_policy(lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, 1e-5, None)
+
+    def init(n=8, ptr=p, b=box, s=skin, trigger=0, cf=1.25, vel=None):
+        ctx = lvb.ctypes.c_void_p()
+        return lvb._lib.lvb_init(lvb.ctypes.byref(ctx), n, ptr, lvb.ctypes.byref(b),
+                                 lvb.ctypes.byref(s), trigger, cf, vel, None, None)
+
+    E = lvb.LVB_EINVAL
+    assert init(n=0) == E                      # empty
+    assert init(n=-1) == E
+    assert init(n=2 ** 31) == E                # above the index range
+    assert init(ptr=None) == E
+    assert init(ptr=p + 4) == E                # not 16-byte aligned
+    assert init(trigger=3) == E
+    assert init(cf=0.99) == E                  # cells smaller than a diameter
+    assert init(cf=float("nan")) == E
+    assert init(b=lvb.lvb_box((0.0, 0.0, 0.0), (1.0, 0.0, 1.0))) == E
+    assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_DIAMETER_FACTOR, -0.1, 1e-5, None)) == E
+    assert init(s=lvb.lvb_skin_policy(7, 0.1, 1e-5, None)) == E
+    # the paper's rule needs velocities and a positive time step
+    assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_PAPER_KVDT, 200.0, 1e-5, None)) == E
+    assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_PAPER_KVDT, 200.0, 0.0, None), vel=p) == E
+    # the network needs weights, velocities and accelerations
+    assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_LEARNED, 0.0, 1e-5, None), vel=p) == E
+    assert lvb._lib.lvb_step(None, p, None, None) == E
+    assert lvb._lib.lvb_step_host(None, p, None, None, None, None) == E
+    assert lvb._lib.lvb_sync(None) == E
+    assert lvb._lib.lvb_destroy(None) == E
