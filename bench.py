@@ -208,6 +208,17 @@ NCU_TRAFFIC_SETTLING = 6.79e6      # profiles/k_step_settling200k_ncu.txt
 NCU_TRAFFIC_BATCHED = 213.9e6      # profiles/k_step_batched512_ncu.txt
 
 
+def _narrow_phase(n, entries, ms, hbm_peak):
+    """Roofline of the separate narrow-phase + forces kernel (k_forces): per
+    particle pos, v*, a, v (4 x 16 B) and the row bounds (12 B) read, v and a
+    (32 B) written, and 4 B per list entry; neighbour records are gathered
+    (mostly L2 hits) and not counted."""
+    b = n * (16.0 * 4 + 12.0 + 32.0) + 4.0 * entries
+    ach = b / (ms * 1e-3) / 1e9
+    return {"kernel": "k_forces", "ms_per_step": ms, "bytes_per_step": b,
+            "achieved_gbs": ach, "frac_hbm": ach / hbm_peak}
+
+
 def _batched(lvb, torch, hbm_peak, warmup):
     """512 independent settling scenes (6.2M particles) advanced together:
     autotuned launch choice, then the 2,000-step workload through graphs of
@@ -267,6 +278,8 @@ def _batched(lvb, torch, hbm_peak, warmup):
         "full_step_graph_value": n * BATCH_STEPS / (graph_ms * 1e-3),
         "graph_steps": 100, "graph_ms_per_step": graph_ms / BATCH_STEPS,
         "gpu_launches_graph_run": int(k1 - k0),
+        "narrow_phase": _narrow_phase(n, s1["entries"], float(ph["phase_ms"][2]) / BATCH_STEPS,
+                                      hbm_peak),
         "phases_ms_per_step": {"integrate": float(ph["phase_ms"][0]) / BATCH_STEPS,
                                "broad": t_ms, "forces": float(ph["phase_ms"][2]) / BATCH_STEPS},
         "roofline": {"bound": "hbm", "kernel": "broad phase (check + partial rebuild)",
@@ -689,6 +702,7 @@ def run_native(args):
         "roofline": roof,
         "broad_phase": {"ms_per_step": ph[1], "achieved_gbs": bp_ach,
                         "frac_hbm": bp_ach / hbm_peak, "bytes_per_step": bytes_bp},
+        "narrow_phase": _narrow_phase(n, entries, ph[2], hbm_peak),
         "phases_ms_per_step": {"integrate": ph[0], "broad": ph[1], "forces": ph[2]},
         "full_step_particle_steps_per_s": world * n * K / (step_ms_tot * 1e-3),
         "full_step_graph": fused,
