@@ -95,6 +95,7 @@ k_cells_clear(DevState s, int gate)
          c += (long long)gridDim.x * kThreads) {
         s.cell_cnt[c] = 0;
         s.cell_live[c] = 0;
+        s.cell_rmax[c] = 0;
     }
 }
 
@@ -113,9 +114,10 @@ k_cells_insert(DevState s, int gate, int count_only)
         atomicAdd(&s.cell_live[c], 1);
         if (sl < ccap) {
             const float4 q = s.ref[i];
+            const float R = __fadd_rn(s.rad[i], q.w);
             s.cell_id[(long long)c * ccap + sl] = i;
-            s.cell_ref[(long long)c * ccap + sl] =
-                make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
+            s.cell_ref[(long long)c * ccap + sl] = make_float4(q.x, q.y, q.z, R);
+            atomicMax(&s.cell_rmax[c], __float_as_int(R));
             s.slot_of[i] = sl;
         } else {
             atomicOr(&s.cnt->err, DERR_CELL);
@@ -431,6 +433,7 @@ void free_all(lvb_ctx *c)
                     s.row_len, s.row_cap, s.col, s.cell_cnt, s.cell_id,
                     s.cell_ref, s.cnt, s.blk, c->ex_cnt, c->ex_off, c->ex_i, c->ex_j, c->ex_d,
                     c->scratch, c->sum64, c->sg_d, c->scene_of_d, s.born, s.cell_live,
+                    s.cell_rmax,
                     s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -828,6 +831,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (e == cudaSuccess) e = dalloc(&s.row_cap, n);
     if (e == cudaSuccess) e = dalloc(&s.cell_cnt, ncells);
     if (e == cudaSuccess) e = dalloc(&s.cell_live, ncells);
+    if (e == cudaSuccess) e = dalloc(&s.cell_rmax, ncells);
     if (e == cudaSuccess) e = dalloc(&s.born, n);
     if (e == cudaSuccess) e = dalloc(&s.cnt, 1);
     // scan partials: the init/export scans use nblk, the step kernel's
@@ -836,6 +840,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (e != cudaSuccess) return fail(from_cuda(e));
     cudaMemsetAsync(s.born, 0, sizeof(int) * n, st);
     cudaMemsetAsync(s.cell_live, 0, sizeof(int) * ncells, st);
+    cudaMemsetAsync(s.cell_rmax, 0, sizeof(int) * ncells, st);
     cudaMemsetAsync(s.cnt, 0, sizeof(DevCounters), st);
     cudaMemsetAsync(&s.cnt->tr_start, 0xff, sizeof(s.cnt->tr_start), st);
     cudaMemsetAsync(s.bits, 0, sizeof(uint32_t) * c->nwords, st);

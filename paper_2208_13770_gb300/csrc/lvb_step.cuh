@@ -77,6 +77,9 @@ struct DevState {
     const lvb_mlp_weights *mlp;   // skin network (LVB_SKIN_LEARNED)
     int *born;        // step of each particle's last update
     int *cell_live;   // particles whose reference position lies in each cell
+    int *cell_rmax;   // per cell, an upper bound on the R_NL of its particles
+                      // (binary32 bits; raised by every insert, reset only
+                      // when the cells are rebuilt)
     // rebuild log (training samples of the skin network)
     int log_on, log_horizon;
     long long log_cap;
@@ -290,6 +293,7 @@ __device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
     const SceneGeom &g = geom_of(s, i);
     const int nc = cell_key(g, qn.x, qn.y, qn.z);
     const int oc = s.cell_of[i], so = s.slot_of[i];
+    if (lane == 0) atomicMax(&s.cell_rmax[nc], __float_as_int(qn.w));
     if (nc == oc) {
         if (lane == 0) s.cell_ref[(long long)oc * ccap + so] = qn;
         return;
@@ -336,16 +340,18 @@ __device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
     __syncwarp();
 }
 
-// Whether stencil cell (x, y, z) of scene g can hold a partner of a particle
-// whose reference state is q (q.w = its R_NL): a partner j lies within
-// R_NL,i + R_NL,j <= q.w + H of it (every R_NL is capped at H, Eq.
-// skin_formulus_mincell), so a cell whose box is farther away holds none.
-// The box is widened by L/1024 on every side -- far more than the rounding
-// of the binned coordinates -- and open outward at the grid's border (where
-// particles outside the box are binned), and the reach is rounded up: a
-// cell with a partner is never skipped.  With polydisperse radii most of
-// the 27 cells are out of reach of a small particle.
-__device__ __forceinline__ bool cell_reachable(const SceneGeom &g, int x, int y, int z, float4 q)
+// Squared distance from a particle's reference position q to the box of
+// stencil cell (x, y, z) of scene g.  A partner j lies within R_NL,i +
+// R_NL,j of it, and R_NL,j is at most H (the cap of Eq.
+// skin_formulus_mincell) and at most the cell's own bound cell_rmax, so a
+// cell whose box is farther away than R_NL,i plus either bound holds no
+// partner (within_reach).  The box is widened by L/1024 on every side --
+// far more than the rounding of the binned coordinates -- and open outward
+// at the grid's border (where particles outside the box are binned), and
+// the reach is rounded up: a cell with a partner is never skipped.  With
+// polydisperse radii most of the 27 cells are out of reach of a small
+// particle.
+__device__ __forceinline__ float cell_dist2(const SceneGeom &g, int x, int y, int z, float4 q)
 {
     const float slack = g.L * (1.0f / 1024.0f);
     const int c[3] = {x, y, z};
@@ -360,7 +366,14 @@ __device__ __forceinline__ bool cell_reachable(const SceneGeom &g, int x, int y,
         if (c[k] < g.dim[k] - 1 && p[k] > hi) d = p[k] - hi;
         d2 += d * d;
     }
-    const float reach = (q.w + g.H) * 1.001f + slack;
+    return d2;
+}
+
+// d2 from cell_dist2 against R_NL,i (q.w) plus a bound on the partners'
+// R_NL (H, or the cell's own bound), with the reach rounded up
+__device__ __forceinline__ bool within_reach(const SceneGeom &g, float d2, float q_w, float r_bound)
+{
+    const float reach = (q_w + r_bound) * 1.001f + g.L * (1.0f / 1024.0f);
     return d2 <= reach * reach;
 }
 
@@ -484,10 +497,13 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     int cnt_l = 0, cid = 0;
     if (lane < 27) {
         const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
-        if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2 &&
-            cell_reachable(g, x, y, z, qn)) {
-            cid = g.cell_base + (z * d1 + y) * d0 + x;
-            cnt_l = s.cell_cnt[cid];
+        if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+            const float dd = cell_dist2(g, x, y, z, qn);
+            if (within_reach(g, dd, qn.w, g.H)) {
+                cid = g.cell_base + (z * d1 + y) * d0 + x;
+                cnt_l = s.cell_cnt[cid];
+                if (!within_reach(g, dd, qn.w, __int_as_float(s.cell_rmax[cid]))) cnt_l = 0;
+            }
         }
     }
     const int jo0 = lane < len0 ? s.col[off + lane] : -1;
@@ -625,10 +641,13 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill,
         int cnt_l = 0, cid = 0;
         if (lane < 27) {
             const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
-            if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2 &&
-                cell_reachable(g, x, y, z, qi)) {
-                cid = g.cell_base + (z * d1 + y) * d0 + x;
-                cnt_l = min(s.cell_cnt[cid], ccap);
+            if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+                const float dd = cell_dist2(g, x, y, z, qi);
+                if (within_reach(g, dd, qi.w, g.H)) {
+                    cid = g.cell_base + (z * d1 + y) * d0 + x;
+                    cnt_l = min(s.cell_cnt[cid], ccap);
+                    if (!within_reach(g, dd, qi.w, __int_as_float(s.cell_rmax[cid]))) cnt_l = 0;
+                }
             }
         }
         const int incl = warp_incl_scan(cnt_l);
@@ -1057,6 +1076,7 @@ static __device__ __noinline__ void full_update_pass(const DevState &s, const fl
     for (long long c = t; c < s.ncells; c += nt) {
         s.cell_cnt[c] = 0;
         s.cell_live[c] = 0;
+        s.cell_rmax[c] = 0;
     }
 }
 
@@ -1070,8 +1090,10 @@ static __device__ __noinline__ void full_insert_pass(const DevState &s)
         atomicAdd(&s.cell_live[c], 1);
         if (sl < ccap) {
             const float4 q = s.ref[i];
+            const float R = __fadd_rn(s.rad[i], q.w);
             s.cell_id[(long long)c * ccap + sl] = i;
-            s.cell_ref[(long long)c * ccap + sl] = make_float4(q.x, q.y, q.z, __fadd_rn(s.rad[i], q.w));
+            s.cell_ref[(long long)c * ccap + sl] = make_float4(q.x, q.y, q.z, R);
+            atomicMax(&s.cell_rmax[c], __float_as_int(R));
             s.slot_of[i] = sl;
         } else {
             atomicOr(&s.cnt->err, DERR_CELL);
