@@ -285,7 +285,8 @@ static __device__ __noinline__ void update_lanes(const DevState &s, const int *i
 // refreshes its slot's copy of the reference state; a leaver leaves a
 // tombstone (-1) in its old slot and takes a tombstone slot of its new cell
 // (compare-and-swap) or a fresh one at the end; the cells' live counts
-// follow.  Slots of unflagged particles never change.
+// follow, and the new cell's R_NL bound is raised to qn.w if below.  Slots
+// of unflagged particles never change.
 __device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
 {
     const int lane = threadIdx.x & 31;
