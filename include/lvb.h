@@ -266,10 +266,14 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 (default 4096) */
 
 /* Values of LVB_OPT_COMPACT. */
-#define LVB_COMPACT_WARP  0  /* one atomic per 32-particle chunk with flags,
-                                no block barrier */
-#define LVB_COMPACT_BLOCK 1  /* one atomic per block tile with flags, two
-                                block barriers in such a tile */
+#define LVB_COMPACT_WARP  0  /* flagged ids gather in a per-warp list during
+                                the check; the list takes its indices with
+                                one atomic per warp when it fills and at the
+                                end of the check */
+#define LVB_COMPACT_BLOCK 1  /* the same, but at the end of the check the
+                                warps' lists take their indices together,
+                                with one atomic per block after a block scan
+                                (two block barriers) */
 
 /* Slots of lvb_trace. */
 #define LVB_TRACE_SLOTS 16
