@@ -440,13 +440,16 @@ def _e2e(lvb, torch, scene, rec):
     state).  Pipelined: per step lvb_step_host copies the pinned host
     positions in (overlapping the previous step's kernel) and the step's flag
     words and count out to pinned host memory (overlapping the next step's
-    kernel); one synchronisation at the end.  Also the per-step synchronous form: copy in, lvb_step, then
+    kernel); one synchronisation at the end; three passes, the median
+    reported (the host is shared with other jobs).  Also the per-step synchronous form: copy in, lvb_step, then
     lvb_get_flags (which waits) every step."""
     m = rec["m"]
     nw = (scene.n + 31) // 32
     ref = torch.from_numpy(rec["ref"]).cuda()
     out = {}
-    for form in ("pipelined", "sync"):
+    reps = []
+    pos0_pinned = torch.from_numpy(rec["pos0"]).pin_memory()
+    for form in ("pipelined", "pipelined", "pipelined", "sync"):
         dev = torch.empty((scene.n, 4), dtype=torch.float32, device="cuda")
         dev.copy_(torch.from_numpy(rec["pos0"]))
         ctx = lvb.LVB(dev, scene.lo, scene.hi, scene.skin_kind, scene.skin_value, scene.dt,
@@ -455,6 +458,13 @@ def _e2e(lvb, torch, scene, rec):
         nf = torch.zeros((m,), dtype=torch.int32, pin_memory=True)
         words = np.zeros(nw, dtype=np.uint32)
         nf64 = lvb.ctypes.c_int64(0)
+        if form == "pipelined":
+            # untimed: the first call allocates the context's staging slots;
+            # a step at the window's starting positions flags nothing
+            ctx.step_host(pos0_pinned, bits=bits[0], n_flagged=nf[0:1])
+            rc = ctx.sync()
+            if rc:
+                raise RuntimeError(lvb.lvb_strerror(rc))
         torch.cuda.synchronize()
         flagged = 0
         t0 = time.perf_counter()
@@ -479,14 +489,21 @@ def _e2e(lvb, torch, scene, rec):
             dt = time.perf_counter() - t0
         st = ctx.stats()
         ctx.close()
-        out[form] = {"value": scene.n * m / dt, "unit": "particle-steps/s",
-                     "h2d_bytes_per_step": scene.n * 16, "d2h_bytes_per_step": nw * 4 + 4,
-                     "steps": m, "flagged": flagged, "store_grows": st["grows"],
-                     "relayouts": st["relayouts"]}
-    e2e = dict(out["pipelined"])
+        res = {"value": scene.n * m / dt, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": scene.n * 16, "d2h_bytes_per_step": nw * 4 + 4,
+               "steps": m, "flagged": flagged, "store_grows": st["grows"],
+               "relayouts": st["relayouts"]}
+        if form == "pipelined":
+            res["host_enqueue_us_per_step"] = out.pop("enqueue_s") * 1e6 / m
+            reps.append(res)
+        else:
+            out[form] = res
+    # the host is shared: the median of three passes over the window
+    reps.sort(key=lambda r: r["value"])
+    e2e = dict(reps[1])
     e2e["api"] = "lvb_step_host (pinned host positions in, flag words and count out)"
+    e2e["passes"] = [r["value"] for r in reps]
     e2e["sync_per_step"] = out["sync"]
-    e2e["host_enqueue_us_per_step"] = out["enqueue_s"] * 1e6 / m
     return e2e
 
 
