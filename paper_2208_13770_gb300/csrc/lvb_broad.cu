@@ -1288,6 +1288,10 @@ int lvb_set_stream(lvb_ctx *c, void *stream)
 int lvb_destroy(lvb_ctx *c)
 {
     if (!c) return LVB_EINVAL;
+    if (c->hs.ready) {   // host-buffer copies still in flight land first
+        cudaStreamSynchronize(c->hs.in);
+        cudaStreamSynchronize(c->hs.out);
+    }
     cudaStreamSynchronize(c->stream);
     free_all(c);
     delete c;
