@@ -363,16 +363,17 @@ def _learned(lvb, torch):
     """The learned skin against the paper's rule on a 1,000,000-sphere drum:
     rebuild-log samples from the plain local-buffer run (skin 0.1 d_i,
     horizon LEARN_H), training on the GPU (own kernels), a run of the network
-    with its own log, training again on both logs, and a run of that network;
-    the better round is compared with the paper's rule (K = LEARN_H) and the
+    with its own log, training again on both logs, and a run of that network,
+    from three initial weight draws; the fastest of these networks is
+    compared with the paper's rule (K = LEARN_H, and K / 2, 2 K) and the
     plain rule, each run from the same initial state."""
     from paper_2208_13770_gb300 import scenes
     sc = scenes.drum(n=LEARN_N, length=0.1)
     # the logged runs give the training samples; every timed run has the log off
     _, smp = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, log=LEARN_H)
     plain, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1)
-    # three initial weight draws, each trained on the plain run's log (round
-    # 1) and again with its own run's log added (round 2); the fastest of
+    # three initial weight draws, each trained on the plain run's log (stage
+    # 1) and again with its own run's log added (stage 2); the fastest of
     # the six networks on this scene is kept
     cands = []
     for seed in (1, 2, 3):
@@ -381,7 +382,7 @@ def _learned(lvb, torch):
         r1, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1)
         w2, info2 = _train_skin(lvb, torch, np.concatenate([smp, smp1]), seed + 10)
         r2, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w2)
-        r1["seed"], r1["round"], r2["seed"], r2["round"] = seed, 1, seed, 2
+        r1["seed"], r1["stage"], r2["seed"], r2["stage"] = seed, 1, seed, 2
         cands += [r1, r2]
     rule, _ = _timed_advance(lvb, torch, sc, lvb.LVB_SKIN_PAPER_KVDT, float(LEARN_H))
     sweep = {}
@@ -395,8 +396,9 @@ def _learned(lvb, torch):
         "training": {"source": "plain local buffer (0.1 d_i), then the network's own run",
                      "label": "largest displacement over the next %d steps / d, x %.1f"
                               % (LEARN_H, LEARN_MARGIN),
-                     "selection": "fastest of 3 weight draws x 2 rounds on this scene",
-                     "last_round1": info1, "last_round2": info2},
+                     "selection": "fastest of 3 weight draws x 2 training stages on this "
+                                  "scene",
+                     "last_stage1": info1, "last_stage2": info2},
         "paper_rule_K%d" % LEARN_H: rule,
         "plain_0.1d": plain,
         "learned_candidates": cands,

@@ -603,7 +603,7 @@ ORC_API int orc_dem_forces(int64_t n, const float *x4, const float *v4,
  * so that trajectories cannot drift apart).
  * fmag (n, optional): per particle, the sum over its contacts of
  * |k_n delta| + |damping term| -- the scale of the terms summed into F,
- * against which a binary32 evaluation's rounding is judged.
+ * against which a binary32 evaluation's rounding is measured.
  * All arrays are binary64, 3n (r, fmag: n). */
 ORC_API int orc_dem_step64(int64_t n, const double *x, const double *v, const double *a,
                            const double *r, double dt, const orc_dem_params *P,

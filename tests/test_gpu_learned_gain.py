@@ -6,8 +6,8 @@ is advanced by the DEM driver for 3,000 steps (dt = 1e-6 s).  The paper's
 rule with K = 400 runs with the rebuild log on (horizon 400 steps: label =
 largest displacement over the next 400 steps, in diameters, times a margin
 of 1.3).  The network is trained on the GPU on those samples, run once with
-the log on (round 1), trained again on both logs -- its own states included
--- and run (round 2), from three initial weight draws; of these six
+the log on (stage 1), trained again on both logs -- its own states included
+-- and run (stage 2), from three initial weight draws; of these six
 networks the one with the fewest updates among those whose list is no
 larger than 1.05 times the rule's is kept (training itself is repeatable,
 but row order, hence force summation order, and so the logged samples vary
