@@ -72,11 +72,17 @@ def _check_step(orc, dem, s, P, idx=None):
     return int((fmag > 0).sum())
 
 
-def test_packed_box_per_step_parity(orc):
+@pytest.mark.parametrize("threads,compact", [(1024, 0), (512, 1), (256, 0)])
+def test_packed_box_per_step_parity(orc, threads, compact):
+    # every launch shape of the fused step (block size; flagged-list indices
+    # per warp or per block): graph replays and direct launches alike
     lvb = _lvb()
     s = scenes.packed(n=8000, vsigma=1.0)     # fast enough to flag within the run
     P = _params(orc, s)
     dem = lvb.DEM(s)
+    dem.lvb.set_option(lvb.LVB_OPT_BLOCK_THREADS, threads)
+    dem.lvb.set_option(lvb.LVB_OPT_COMPACT, compact)
+    dem.advance(120)                          # one graph of 100 steps, 20 direct
     touching = 0
     for k in range(300):
         if k % 25 == 0:
