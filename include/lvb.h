@@ -311,6 +311,26 @@ int lvb_get_pairs_ij(lvb_ctx *ctx, int32_t *pi, int32_t *pj, int64_t cap,
                      int64_t *n_pairs);
 
 /*
+ * lvb_get_near_cutoff -- the pairs i < j, in the list or not, whose squared
+ * reference distance d2 (the fixed binary32 formula of the definitions
+ * above, Def. verletlist) lies within a relative distance rel of their
+ * squared cutoff c2 = (R_NL,i + R_NL,j)^2 (binary32): |d2 - c2| <= rel c2,
+ * compared in binary64 from the two binary32 values.  These are the pairs
+ * whose membership rests on the last bits of the formula; they are listed
+ * apart from the list so that a comparison with another evaluation can
+ * tell a rounding difference from an error.
+ *   rel             : 0 <= rel <= 2^-8 (e.g. 1e-6); every such pair lies in
+ *                     the 27 cells around either particle's cell.
+ *   pi, pj          : host or device int32 out, cap entries each, in no
+ *                     particular order.
+ *   n_pairs         : out, the number of such pairs.
+ * Synchronises.  Errors: EINVAL, ECAPACITY (count written to *n_pairs),
+ * EDEVICE, and the context's device errors.
+ */
+int lvb_get_near_cutoff(lvb_ctx *ctx, double rel, int32_t *pi, int32_t *pj, int64_t cap,
+                        int64_t *n_pairs);
+
+/*
  * lvb_get_contacts -- narrow phase (Eq. delta) on the list at positions
  * pos_r: every pair i < j of the list with delta_ij > 0, sorted by (i, j),
  * with delta_ij (binary32 formula above).  Same capacity rule.

@@ -11,6 +11,7 @@ links or runs anything here, and nothing here imports the product package.
   step by step over position snapshots.
 * ``mlp``           -- the skin network in binary64 (training oracle) and the
   exact binary32/bfloat16 inference formula.
+* :func:`near_cutoff` -- the pairs near their cutoff, in numpy binary32.
 """
 from __future__ import annotations
 
@@ -179,6 +180,33 @@ def pairs_brute(ref4, rad):
 def pairs_cells(ref4, rad):
     """Pair set through Algorithm 1 (linked cells), sorted (i, j) with i < j."""
     return _pairs(lib().orc_pairs_cells, ref4, rad)
+
+
+def near_cutoff(ref4, rad, rel):
+    """Pairs i < j whose squared reference distance d2 lies within rel of the
+    squared cutoff c2 (Def. verletlist's inequality d2 <= c2, near its
+    boundary): d2 = ((dx dx) + (dy dy)) + dz dz of the binary32 differences,
+    c = R_i + R_j with R = r + skin, c2 = c c, every operation in binary32
+    (numpy, no fused multiply-add); |d2 - c2| <= rel c2 compared in binary64.
+    Brute force over all pairs (small inputs); sorted (i, j)."""
+    ref = np.ascontiguousarray(ref4, dtype=np.float32)
+    R = (np.asarray(rad, dtype=np.float32) + ref[:, 3]).astype(np.float32)
+    n = len(ref)
+    out_i, out_j = [], []
+    for i in range(n - 1):
+        j = np.arange(i + 1, n)
+        dx = ref[i, 0] - ref[j, 0]
+        dy = ref[i, 1] - ref[j, 1]
+        dz = ref[i, 2] - ref[j, 2]
+        d2 = (dx * dx + dy * dy) + dz * dz
+        c = R[i] + R[j]
+        c2 = c * c
+        m = np.abs(d2.astype(np.float64) - c2.astype(np.float64)) <= rel * c2.astype(np.float64)
+        out_i.append(np.full(int(m.sum()), i, dtype=np.int32))
+        out_j.append(j[m].astype(np.int32))
+    if not out_i:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    return np.concatenate(out_i), np.concatenate(out_j)
 
 
 def pairs(ref4, rad):

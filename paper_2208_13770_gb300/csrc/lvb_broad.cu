@@ -358,6 +358,47 @@ k_ex_write(DevState s, int mode, const float4 *__restrict__ pos, const int *out_
     }
 }
 
+// Pairs i < j whose squared reference distance (the fixed binary32 formula
+// of the list) lies within rel of their squared cutoff (binary32), compared
+// in binary64: one thread per particle over the 27 cells around its cell.
+// write = 0 counts into cnt[i]; 1 writes at off[i], ... (cell order).
+__global__ void __launch_bounds__(kThreads)
+k_near(DevState s, double rel, int write, int *cnt, const int *off, int *out_i, int *out_j)
+{
+    const int ccap = s.ccap;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < s.n; i += gridDim.x * kThreads) {
+        const SceneGeom &g = geom_of(s, i);
+        const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
+        const int ci = s.cell_of[i] - g.cell_base;
+        const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
+        const float4 q = s.ref[i];
+        const float Ri = __fadd_rn(s.rad[i], q.w);
+        int k = 0, o = write ? off[i] : 0;
+        for (int t = 0; t < 27; ++t) {
+            const int x = cx + t % 3 - 1, y = cy + (t / 3) % 3 - 1, z = cz + t / 9 - 1;
+            if (x < 0 || x >= d0 || y < 0 || y >= d1 || z < 0 || z >= d2) continue;
+            const long long base = (long long)(g.cell_base + (z * d1 + y) * d0 + x) * ccap;
+            const int m = min(s.cell_cnt[g.cell_base + (z * d1 + y) * d0 + x], ccap);
+            for (int e = 0; e < m; ++e) {
+                const int j = s.cell_id[base + e];
+                if (j <= i) continue;
+                const float4 rj = s.cell_ref[base + e];
+                const float dd = sqdist_rn(q.x, q.y, q.z, rj.x, rj.y, rj.z);
+                const float c = __fadd_rn(Ri, rj.w);
+                const float c2 = __fmul_rn(c, c);
+                if (fabs((double)dd - (double)c2) <= rel * (double)c2) {
+                    if (write) {
+                        out_i[o + k] = i;
+                        out_j[o + k] = j;
+                    }
+                    ++k;
+                }
+            }
+        }
+        if (!write) cnt[i] = k;
+    }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -624,12 +665,21 @@ int ensure_export(lvb_ctx *c, long long need)
 }
 
 // Count + scan the export of `mode`; returns the total through *total.
+int export_scan(lvb_ctx *c, long long *total);
+
 int export_layout(lvb_ctx *c, int mode, const float4 *pos, long long *total)
 {
     int rc = ensure_export(c, 0);
     if (rc) return rc;
     const int gi = items_grid(c);
     k_ex_count<<<gi, kThreads, 0, c->stream>>>(c->s, mode, pos, c->ex_cnt);
+    return export_scan(c, total);
+}
+
+// Exclusive scan of the per-particle counts ex_cnt into ex_off (n + 1
+// entries, the total last); waits for the total.
+int export_scan(lvb_ctx *c, long long *total)
+{
     ScanArgs a{};
     a.len = c->ex_cnt;
     a.off = c->ex_off;
@@ -1190,6 +1240,33 @@ int lvb_get_pairs_ij(lvb_ctx *c, int32_t *pi, int32_t *pj, int64_t cap, int64_t 
     if (rc) return rc;
     k_ex_write<<<items_grid(c), kThreads, 0, c->stream>>>(c->s, 1, nullptr, c->ex_off, c->ex_i,
                                                           c->ex_j, nullptr);
+    rc = copy_out(c, pi, c->ex_i, sizeof(int) * (size_t)total);
+    if (!rc) rc = copy_out(c, pj, c->ex_j, sizeof(int) * (size_t)total);
+    if (rc) return rc;
+    return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+int lvb_get_near_cutoff(lvb_ctx *c, double rel, int32_t *pi, int32_t *pj, int64_t cap,
+                        int64_t *n_pairs)
+{
+    // the 27 cells hold every pair up to the cell edge L >= 2H / (1 - 2^-8),
+    // so up to rel = 2^-8 no pair near its cutoff lies outside them
+    if (!c || !n_pairs || cap < 0 || !(rel >= 0.0) || !(rel <= 1.0 / 256.0)) return LVB_EINVAL;
+    int rc = sync_counters(c);
+    if (rc) return rc;
+    rc = ensure_export(c, 0);
+    if (rc) return rc;
+    k_near<<<items_grid(c), kThreads, 0, c->stream>>>(c->s, rel, 0, c->ex_cnt, nullptr, nullptr,
+                                                      nullptr);
+    long long total = 0;
+    rc = export_scan(c, &total);
+    if (rc) return rc;
+    *n_pairs = total;
+    if (total > cap || (total > 0 && (!pi || !pj))) return LVB_ECAPACITY;
+    rc = ensure_export(c, total);
+    if (rc) return rc;
+    k_near<<<items_grid(c), kThreads, 0, c->stream>>>(c->s, rel, 1, nullptr, c->ex_off, c->ex_i,
+                                                      c->ex_j);
     rc = copy_out(c, pi, c->ex_i, sizeof(int) * (size_t)total);
     if (!rc) rc = copy_out(c, pj, c->ex_j, sizeof(int) * (size_t)total);
     if (rc) return rc;

@@ -88,6 +88,7 @@ _SIGS = {
     "lvb_trace": ([_p, _p, _p], ctypes.c_int),
     "lvb_get_pairs": ([_p, _p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_get_pairs_ij": ([_p, _p, _p, _i64, _pi64], ctypes.c_int),
+    "lvb_get_near_cutoff": ([_p, ctypes.c_double, _p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_get_contacts": ([_p, _p, _p, _p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_get_flags": ([_p, _p, _pi64], ctypes.c_int),
     "lvb_get_ref": ([_p, _p], ctypes.c_int),
@@ -409,6 +410,22 @@ class LVB:
         _check(lvb_get_pairs_ij(self.ctx, _np_ptr(pi), _np_ptr(pj), cap, ctypes.byref(n)),
                "lvb_get_pairs_ij")
         return pi[:n.value], pj[:n.value]
+
+    def near_cutoff(self, rel=1e-6):
+        """Pairs i < j whose squared reference distance is within rel of the
+        squared cutoff (lvb_get_near_cutoff), sorted by (i, j)."""
+        n = ctypes.c_int64(0)
+        rc = _lib.lvb_get_near_cutoff(self.ctx, float(rel), None, None, 0, ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_get_near_cutoff")
+        cap = n.value
+        pi = np.empty(max(cap, 1), dtype=np.int32)
+        pj = np.empty(max(cap, 1), dtype=np.int32)
+        _check(_lib.lvb_get_near_cutoff(self.ctx, float(rel), _np_ptr(pi), _np_ptr(pj), cap,
+                                        ctypes.byref(n)), "lvb_get_near_cutoff")
+        pi, pj = pi[:n.value], pj[:n.value]
+        order = np.lexsort((pj, pi))
+        return pi[order], pj[order]
 
     def pairs_csr(self):
         n = ctypes.c_int64(0)

@@ -375,3 +375,43 @@ def test_crowded_cell_moves_parity(orc, direct_max, crowd):
     st, _ = _run_trajectory(orc, s, snaps, 0, 1, 0.1,
                             options=((lvb.LVB_OPT_DIRECT_MAX, direct_max),))
     assert st["flagged_total"] >= moved + n_res
+
+
+def test_near_cutoff_pairs_match_oracle(orc):
+    # the pairs whose squared distance is within rel of the squared cutoff:
+    # planted pairs at the cutoff and one or a few ulps away from it among
+    # background particles (skin 0), then a ballistic scene at rel 1e-3
+    # after steps with many flags
+    lvb = _cuda()
+    from tests.test_oracle_broadphase import _near_pairs_scene
+    ref, rad, expected = _near_pairs_scene()
+    rng = np.random.default_rng(14)
+    bg = np.zeros((300, 4), np.float32)
+    bg[:, :3] = rng.uniform((-1.5, -1.5, -1.5), (2.5, 41.5, 1.5), size=(300, 3))
+    bg[:, 3] = 0.3
+    pos = np.concatenate([ref, bg])
+    pos[:len(ref), 3] = rad
+    ctx = lvb.LVB(_dev(pos), (-2, -2, -2), (3, 43, 2), lvb.LVB_SKIN_GLOBAL, 0.0, 0.0,
+                  lvb.LVB_TRIGGER_PARTIAL, 1.25)
+    ref0 = pos.copy()
+    ref0[:, 3] = 0.0                     # (xref, skin) at init, skin 0
+    assert np.array_equal(ctx.ref(), ref0)
+    for rel in (0.0, 1e-6, 1e-5, 1e-3):
+        gi, gj = ctx.near_cutoff(rel)
+        oi, oj = orc.near_cutoff(ref0, pos[:, 3], rel)
+        assert np.array_equal(gi, oi) and np.array_equal(gj, oj), rel
+    gi, gj = ctx.near_cutoff(1e-6)
+    assert expected <= set(zip(gi.tolist(), gj.tolist()))
+    with pytest.raises(lvb.LVBError):
+        ctx.near_cutoff(0.01)            # beyond what the 27 cells cover
+    ctx.close()
+
+    s = scenes.ballistic(n=2000, seed=15, vsigma=1.0)
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, 1, 0.1, s.dt, 0, s.cell_factor)
+    for k, (p, _) in enumerate(scenes.ballistic_trajectory(s, 20)):
+        ctx.step(_dev(p))
+    gi, gj = ctx.near_cutoff(1e-3)
+    oi, oj = orc.near_cutoff(ctx.ref(), s.pos[:, 3], 1e-3)
+    assert len(oi) > 0
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
+    ctx.close()

@@ -246,3 +246,34 @@ def test_theorem1_violated_without_the_check(orc):
         c = orc.contacts_brute(pos)
         missed += len(set(zip(c[0].tolist(), c[1].tolist())) - frozen)
     assert missed > 0
+
+
+def _near_pairs_scene():
+    """Pairs along x, one per y row, at separations s around the cutoff
+    c = 0.5 + 0.5 = 1 (skin 0): s^2 in binary32 is 1, 1 +- 2^-21 (within
+    1e-6 of c^2) or 1 +- 2^-18 (outside).  Returns (ref4, rad, expected)."""
+    seps = [1.0, 1.0 + 2.0 ** -22, 1.0 - 2.0 ** -22, 1.0 + 2.0 ** -19, 1.0 - 2.0 ** -19]
+    ref = np.zeros((2 * len(seps), 4), np.float32)
+    for k, sep in enumerate(seps):
+        ref[2 * k] = (0.0, 10.0 * k, 0.0, 0.0)
+        ref[2 * k + 1] = (np.float32(sep), 10.0 * k, 0.0, 0.0)
+    rad = np.full(len(ref), 0.5, np.float32)
+    expected = {(0, 1), (2, 3), (4, 5)}
+    return ref, rad, expected
+
+
+def test_near_cutoff_closed_form(orc):
+    # separations of 1, 1 +- 2^-22 give s^2 = 1, 1 +- 2^-21 (4.8e-7 from the
+    # squared cutoff); 1 +- 2^-19 give 1 +- 2^-18 (3.8e-6): only the first
+    # three pairs are within 1e-6, and all five within 1e-5
+    ref, rad, expected = _near_pairs_scene()
+    pi, pj = orc.near_cutoff(ref, rad, 1e-6)
+    assert set(zip(pi.tolist(), pj.tolist())) == expected
+    pi, pj = orc.near_cutoff(ref, rad, 1e-5)
+    assert set(zip(pi.tolist(), pj.tolist())) == {(2 * k, 2 * k + 1) for k in range(5)}
+    pi, pj = orc.near_cutoff(ref, rad, 0.0)
+    assert set(zip(pi.tolist(), pj.tolist())) == {(0, 1)}
+    # the exact-cutoff pair is in the list, the outer ones are not
+    li, lj = orc.pairs_brute(ref, rad)
+    assert (0, 1) in set(zip(li.tolist(), lj.tolist()))
+    assert (6, 7) not in set(zip(li.tolist(), lj.tolist()))
