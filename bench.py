@@ -193,7 +193,8 @@ def _run_dem(lvb, torch, scene, trigger, skin_kind, skin_value, steps, warmup, f
     if rc != 0:
         raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
     st1 = dem.lvb.stats()
-    out = {"phase_ms": tot, "wall_ms": wall_ms, "stats0": st0, "stats1": st1, "rec": rec}
+    out = {"phase_ms": tot, "wall_ms": wall_ms, "stats0": st0, "stats1": st1, "rec": rec,
+           "near_cutoff": int(len(dem.lvb.near_cutoff(1e-6)[0]))}
     dem.close()
     return out
 
@@ -732,7 +733,8 @@ def run_native(args):
                           "skin": "uniform 0.1 * mean diameter = %.3g m" % (0.1 * dmean),
                           "ms_per_step": float(glob["phase_ms"].sum()) / K},
         "speedup_vs_global": g_bp_ms / bp_ms,
-        "list": {"entries": entries, "mean_row": row_len, "relayouts": s1["relayouts"]},
+        "list": {"entries": entries, "mean_row": row_len, "relayouts": s1["relayouts"],
+                 "near_cutoff_pairs_rel_1e-6": loc["near_cutoff"]},
         "e2e": e2e,
         "gpu_launches": int(s1["kernels_executed"] - s0["kernels_executed"]),
         "grid_barriers": int(s1["barriers"] - s0["barriers"]),
