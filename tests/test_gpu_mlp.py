@@ -120,7 +120,11 @@ def _learned_setup(lvb, s, seed=3):
     return W, grid
 
 
-def test_learned_policy_broad_phase_parity(orc):
+@pytest.mark.parametrize("log", [False, True])
+def test_learned_policy_broad_phase_parity(orc, log):
+    # with the rebuild log off each lane evaluates the network for its own
+    # flagged particle; with it on a warp evaluates it one particle at a
+    # time: both must give the oracle's skins bit for bit
     lvb = _lvb()
     from oracle.statemachine import OracleLVB
     s = scenes.ballistic(n=2000, seed=17, vsigma=1.0)
@@ -131,6 +135,8 @@ def test_learned_policy_broad_phase_parity(orc):
     ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_LEARNED, 0.0, s.dt,
                   lvb.LVB_TRIGGER_PARTIAL, s.cell_factor, vel=_dev(s.vel), acc=_dev(acc),
                   mlp=wbuf)
+    if log:
+        ctx.log_enable(10, 100000)
     sm = OracleLVB(s.pos, orc.SKIN_LEARNED, 0.0, s.dt, grid["H"], 0, vel4=s.vel,
                    learned={"weights": W, "grid": grid}, acc4=acc)
     assert np.array_equal(ctx.ref(), sm.ref)
