@@ -544,17 +544,6 @@ ScanArgs layout_args(lvb_ctx *c)
 // Blocks of the step kernel for the context's block size: as many as are
 // resident at once (every block must be, the step's barriers wait for all),
 // but no more than the check pass can use.
-using StepKernel = void (*)(const float4 *, const float4 *, const float4 *, DevState, IntegrateArgs,
-                           NoTail);
-
-// The step kernel for the context's policy (k_step's kNet form for the
-// learned one).
-StepKernel step_kernel(const lvb_ctx *c)
-{
-    return c->skin.kind == LVB_SKIN_LEARNED ? k_step<false, NoTail, true>
-                                            : k_step<false, NoTail, false>;
-}
-
 int size_step(lvb_ctx *c)
 {
     int dev = 0, sms = 0, per_sm = 0;
@@ -563,12 +552,12 @@ int size_step(lvb_ctx *c)
     const int smem = check_smem_bytes(c->block_threads);
     // the attribute belongs to the kernel, for every context of the process:
     // always the largest any block size needs
-    for (StepKernel k : {k_step<false, NoTail, false>, k_step<false, NoTail, true>})
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     check_smem_bytes(kStepMaxThreads));
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel(c),
+        e = cudaFuncSetAttribute(k_step<false, NoTail>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 check_smem_bytes(kStepMaxThreads));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<false, NoTail>,
                                                           c->block_threads, smem);
     if (e != cudaSuccess) return from_cuda(e);
     if (per_sm < 1) return LVB_EDEVICE;
@@ -1046,7 +1035,7 @@ int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
         if (rc) return rc;
     }
     const cudaError_t e =
-        launch_coop(step_kernel(c), dim3(c->step_blocks), dim3(c->block_threads),
+        launch_coop(k_step<false, NoTail>, dim3(c->step_blocks), dim3(c->block_threads),
                     (size_t)check_smem_bytes(c->block_threads), c->stream,
                     (const float4 *)pos_r, (const float4 *)vel, a4, c->s, IntegrateArgs{},
                     NoTail{});

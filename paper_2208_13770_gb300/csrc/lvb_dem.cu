@@ -310,17 +310,6 @@ int launch_phase(dem_ctx *c, int phase)
     return from_cuda(cudaGetLastError());
 }
 
-using FusedKernel = void (*)(const float4 *, const float4 *, const float4 *, DevState,
-                            IntegrateArgs, DemTail);
-
-// The fused step kernel for the broad phase's policy (k_step's kNet form for
-// the learned one).
-FusedKernel fused_kernel(const DevState &st)
-{
-    return st.skin_kind == LVB_SKIN_LEARNED ? k_step<true, DemTail, true>
-                                            : k_step<true, DemTail, false>;
-}
-
 // Launch shape of the fused step: the broad phase's block size, and no more
 // blocks than fit on the device at once for this kernel.
 int fused_shape(dem_ctx *c, dim3 *grid, dim3 *block)
@@ -330,8 +319,8 @@ int fused_shape(dem_ctx *c, dim3 *grid, dim3 *block)
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, fused_kernel(step_state(c->bp)), threads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<true, DemTail>, threads,
+                                                          0);
     if (e != cudaSuccess) return from_cuda(e);
     if (per_sm < 1) return LVB_EDEVICE;
     *grid = dim3(std::min(blocks, per_sm * sms));
@@ -349,10 +338,10 @@ int launch_fused(dem_ctx *c)
     rc = fused_shape(c, &grid, &block);
     if (rc) return rc;
     const DemDev &d = c->d;
-    const DevState st = step_state(c->bp);
-    return from_cuda(launch_coop(fused_kernel(st), grid, block, 0, c->stream,
+    return from_cuda(launch_coop(k_step<true, DemTail>, grid, block, 0, c->stream,
                                  (const float4 *)d.pos, (const float4 *)d.vstar,
-                                 (const float4 *)d.acc, st, integrate_args(d), DemTail{d}));
+                                 (const float4 *)d.acc, step_state(c->bp), integrate_args(d),
+                                 DemTail{d}));
 }
 
 }  // namespace
@@ -485,7 +474,7 @@ int dem_advance(dem_ctx *c, int64_t steps)
             cudaError_t e = cudaGraphCreate(&g, 0);
             cudaGraphNode_t dep = nullptr;
             for (int64_t k = 0; k < chunk && e == cudaSuccess; ++k)
-                e = add_coop_kernel(&dep, g, &dep, fused_kernel(st), grid, block,
+                e = add_coop_kernel(&dep, g, &dep, k_step<true, DemTail>, grid, block,
                                     (const float4 *)d.pos, (const float4 *)d.vstar,
                                     (const float4 *)d.acc, st, ia, DemTail{d});
             if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);

@@ -221,44 +221,6 @@ __device__ __forceinline__ float mlp_y_warp(const lvb_mlp_weights *__restrict__ 
     return y;
 }
 
-// The same network evaluated by one lane for its own particle (no shuffles,
-// so lanes may drop out): the same sums in the same order, so the result
-// equals mlp_y_warp's bit for bit.  The first hidden layer's values are
-// bfloat16 numbers and are held as such, two to a register (exact); layer 2
-// is streamed unit by unit into the output sum.
-__device__ __forceinline__ float mlp_y_lane(const lvb_mlp_weights *__restrict__ W,
-                                            const float f[LVB_MLP_IN])
-{
-    float z[LVB_MLP_IN];
-#pragma unroll
-    for (int k = 0; k < LVB_MLP_IN; ++k)
-        z[k] = bf16_rn(__fmul_rn(__fsub_rn(f[k], W->mu[k]), W->isd[k]));
-    __nv_bfloat162 h1[LVB_MLP_HIDDEN / 2];
-#pragma unroll
-    for (int o = 0; o < LVB_MLP_HIDDEN; o += 2) {
-        float a0 = W->b1[o], a1 = W->b1[o + 1];
-#pragma unroll
-        for (int k = 0; k < LVB_MLP_IN; ++k) {
-            a0 = fmaf(W->W1[o * LVB_MLP_IN + k], z[k], a0);
-            a1 = fmaf(W->W1[(o + 1) * LVB_MLP_IN + k], z[k], a1);
-        }
-        h1[o / 2] = __floats2bfloat162_rn(relu(a0), relu(a1));
-    }
-    float y = W->b3;
-#pragma unroll 1
-    for (int o = 0; o < LVB_MLP_HIDDEN; ++o) {
-        float acc = W->b2[o];
-#pragma unroll
-        for (int k = 0; k < LVB_MLP_HIDDEN; k += 2) {
-            const float2 h = __bfloat1622float2(h1[k / 2]);
-            acc = fmaf(W->W2[o * LVB_MLP_HIDDEN + k], h.x, acc);
-            acc = fmaf(W->W2[o * LVB_MLP_HIDDEN + k + 1], h.y, acc);
-        }
-        y = fmaf(W->w3[o], bf16_rn(relu(acc)), y);
-    }
-    return y;
-}
-
 // Slack rule of the row store: capacity for a row of `len` entries (room
 // for the row to grow by half, and by 8 however short it is, before the
 // store is re-laid out).

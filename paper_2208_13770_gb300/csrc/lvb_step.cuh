@@ -205,15 +205,13 @@ __device__ __forceinline__ int row_live_warp(const DevState &s, int i)
     return c;
 }
 
-// a2 for flagged particle i, run by the warp that flagged it inside the
-// check pass (PARTIAL trigger): new reference position and skin (the
-// policy's features come from the state before the update; `step` is the
-// number of the step being taken), kept with the old state at index k of
-// the flagged list.  (pos and vel may have been written earlier in the same
-// kernel by the DEM position half-step, so they are read through plain
-// coherent loads.)  Not inlined: it runs only for flagged particles, and as
-// a call it keeps the check loop's registers free of its working set.
-template <bool kNet>
+// a2 for flagged particle i by one warp, after the check pass (PARTIAL
+// trigger, deferred_update): new reference position and skin (the policy's
+// features come from the state before the update -- rows and cells change
+// only in the rebuild that follows; `step` is the number of the step being
+// taken), kept with the old state at index k of the flagged list.  (pos and
+// vel may have been written earlier in the same kernel by the DEM position
+// half-step, so they are read through plain coherent loads.)
 static __device__ __noinline__ void update_warp(const DevState &s, int i, int k, const float4 *pos,
                                                 const float4 *vel, const float4 *acc, int step)
 {
@@ -253,15 +251,22 @@ static __device__ __noinline__ void update_warp(const DevState &s, int i, int k,
     }
 }
 
-// Lane t's share of a2 (particle i, list index k, proposed skin prop for
-// the learned policy): new reference state and skin, kept with the old
-// state in the flagged list and, with several scenes, in its scene's
-// segment.
-__device__ __forceinline__ void update_one(const DevState &s, int i, int k, float4 p, float r,
-                                           float4 v, float4 q, const SceneGeom &g, float prop,
-                                           int step)
+// a2 for up to 32 flagged particles at once, one per lane (lane t takes
+// particle id[t], list index k0 + t, t < m): the same update as update_warp for
+// the policies that need neither the network nor the rebuild log, with all
+// the lanes' loads in flight together.
+static __device__ __noinline__ void update_lanes(const DevState &s, const int *id, int k0, int m,
+                                                 const float4 *pos, const float4 *vel, int step)
 {
-    const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
+    const int lane = threadIdx.x & 31;
+    if (lane >= m) return;
+    const int i = id[lane], k = k0 + lane;
+    const float4 p = pos[i];
+    const float r = s.rad[i];
+    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 q = s.ref[i];
+    const SceneGeom &g = geom_of(s, i);
+    const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, 0.0f);
     const float4 qn = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
     s.ref[i] = make_float4(p.x, p.y, p.z, sk);
     s.born[i] = step;
@@ -273,55 +278,6 @@ __device__ __forceinline__ void update_one(const DevState &s, int i, int k, floa
         s.sfid[slot] = i;
         s.sfref[slot] = qn;
     }
-}
-
-// a2 for up to 32 flagged particles at once, one per lane (lane t takes
-// particle id[t], list index k0 + t, t < m): the same update as update_warp
-// for the policies that need neither the network nor the rebuild log, with
-// all the lanes' loads in flight together.
-template <bool kNet>
-static __device__ __noinline__ void update_lanes(const DevState &s, const int *id, int k0, int m,
-                                                 const float4 *pos, const float4 *vel, int step)
-{
-    const int lane = threadIdx.x & 31;
-    if (lane >= m) return;
-    const int i = id[lane];
-    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    update_one(s, i, k0 + lane, pos[i], s.rad[i], v, s.ref[i], geom_of(s, i), 0.0f, step);
-}
-
-// Live partners of row i (entries >= 0), counted by one lane.
-__device__ __forceinline__ int row_live_lane(const DevState &s, int i)
-{
-    const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
-    int c = 0;
-    for (int e = 0; e < len; ++e) c += s.col[off + e] >= 0;
-    return c;
-}
-
-// The same for the learned policy while the rebuild log is off: each lane
-// evaluates the network for its own particle, from the features update_warp
-// takes and with its sums in the same order, so the skins are equal.
-static __device__ __noinline__ void update_lanes_learned(const DevState &s, const int *id, int k0,
-                                                         int m, const float4 *pos,
-                                                         const float4 *vel, const float4 *acc,
-                                                         int step)
-{
-    const int lane = threadIdx.x & 31;
-    if (lane >= m) return;
-    const int i = id[lane];
-    const float4 p = pos[i];
-    const float r = s.rad[i];
-    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 q = s.ref[i];
-    const SceneGeom &g = geom_of(s, i);
-    const int nc = cell_key(g, p.x, p.y, p.z);
-    float f[LVB_MLP_IN];
-    skin_features(s, p, v, a, r, g, q, row_live_lane(s, i), step - s.born[i], s.cell_live[nc], f);
-    const float y = mlp_y_lane(s.mlp, f);
-    const float prop = __fmul_rn(__fmul_rn(2.0f, r), fminf(fmaxf(y, s.mlp->y_lo), s.mlp->y_hi));
-    update_one(s, i, k0 + lane, p, r, v, q, g, prop, step);
 }
 
 // a3 for flagged particle i (warp), qn its new (xref, R_NL): a stayer
@@ -525,7 +481,6 @@ __device__ __forceinline__ void lane_edit(const DevState &s, int jr, int ji, int
 // which entries of the unflagged rows change; no other warp touches row i.
 // The edits of other rows run one per lane, in parallel; the first 32 old
 // partners and the first 32 stencil candidates are loaded together.
-template <bool kNet>
 static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF, bool direct,
                                                int par, int *ovf)
 {
@@ -839,29 +794,19 @@ struct Pending {
     int n;      // warp-uniform count
 };
 
-// a2 for the m pending particles id[0..m) at list indices k0, k0 + 1, ...
-// The step kernel of the learned policy (kNet) updates them one per lane
-// while the rebuild log is off; the other one keeps only the calls the
-// other policies need, so that its check loop keeps its registers.
-template <bool kNet>
-__device__ __forceinline__ void update_pending(const DevState &s, const int *id, int k0, int m,
-                                               const float4 *pos, const float4 *vel,
-                                               const float4 *acc, int step)
+// a2 of the learned policy, and of any policy while the rebuild log is on,
+// waits until the check pass has ended: then every warp of the grid takes
+// at most a few flagged particles (update_pass) instead of the warps that
+// flagged them taking all of theirs one after another inside the check.
+__device__ __forceinline__ bool deferred_update(const DevState &s)
 {
-    if (kNet && !s.log_on) {
-        update_lanes_learned(s, id, k0, m, pos, vel, acc, step);
-    } else if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
-        for (int t = 0; t < m; ++t) update_warp<kNet>(s, id[t], k0 + t, pos, vel, acc, step);
-    } else {
-        update_lanes<kNet>(s, id, k0, m, pos, vel, step);
-    }
+    return s.skin_kind == LVB_SKIN_LEARNED || s.log_on;
 }
 
 // Enters the warp's pending particles in the flagged list at k0, k0 + 1, ...
-// (fid) and, with inc, updates them (update_pending); empties the list.
-// New positions written earlier in this kernel by the warp's own
+// (fid) and, with inc, updates them one per lane (update_lanes) unless the
+// update is deferred; empties the list.  New positions written earlier in this kernel by the warp's own
 // lanes (DEM form) are made visible to the whole warp first.
-template <bool kNet>
 __device__ __forceinline__ void enter_pending(const DevState &s, Pending &pd, int k0,
                                               const float4 *pos, const float4 *vel,
                                               const float4 *acc, bool inc, int step)
@@ -869,13 +814,12 @@ __device__ __forceinline__ void enter_pending(const DevState &s, Pending &pd, in
     const int lane = threadIdx.x & 31;
     __syncwarp();
     if (lane < pd.n) s.fid[k0 + lane] = pd.id[lane];
-    if (inc) update_pending<kNet>(s, pd.id, k0, pd.n, pos, vel, acc, step);
+    if (inc && !deferred_update(s)) update_lanes(s, pd.id, k0, pd.n, pos, vel, step);
     __syncwarp();
     pd.n = 0;
 }
 
 // The same with list indices from one atomic of this warp.
-template <bool kNet>
 __device__ __forceinline__ void flush_pending(const DevState &s, Pending &pd, const float4 *pos,
                                               const float4 *vel, const float4 *acc, bool inc,
                                               int step, int *nF_acc)
@@ -883,20 +827,19 @@ __device__ __forceinline__ void flush_pending(const DevState &s, Pending &pd, co
     int k0 = 0;
     if ((threadIdx.x & 31) == 0) k0 = atomicAdd(nF_acc, pd.n);
     k0 = __shfl_sync(FULL, k0, 0);
-    enter_pending<kNet>(s, pd, k0, pos, vel, acc, inc, step);
+    enter_pending(s, pd, k0, pos, vel, acc, inc, step);
 }
 
 // End of the check pass, every thread of the block: the pending particles
 // of all warps enter the list -- with one atomic per warp (warp scheme) or
 // one per block after a scan of the warps' counts (block scheme).
-template <bool kNet>
 __device__ __forceinline__ void flush_pending_final(const DevState &s, Pending &pd,
                                                     const float4 *pos, const float4 *vel,
                                                     const float4 *acc, bool inc, int step,
                                                     int *nF_acc)
 {
     if (!s.compact_block) {
-        if (pd.n) flush_pending<kNet>(s, pd, pos, vel, acc, inc, step, nF_acc);
+        if (pd.n) flush_pending(s, pd, pos, vel, acc, inc, step, nF_acc);
         return;
     }
     __shared__ int s_cnt[32];
@@ -915,7 +858,7 @@ __device__ __forceinline__ void flush_pending_final(const DevState &s, Pending &
         s_base = atomicAdd(nF_acc, run);
     }
     __syncthreads();
-    if (pd.n) enter_pending<kNet>(s, pd, s_base + s_cnt[warp], pos, vel, acc, inc, step);
+    if (pd.n) enter_pending(s, pd, s_base + s_cnt[warp], pos, vel, acc, inc, step);
 }
 
 // a1 for U chunks of 32 consecutive particles held by one warp (chunk u
@@ -923,7 +866,7 @@ __device__ __forceinline__ void flush_pending_final(const DevState &s, Pending &
 // ballot word per chunk; the flagged particles join the warp's pending list
 // (entered in the flagged list, and updated with the PARTIAL trigger, when
 // it fills and at the end of the pass).
-template <bool kNet, int U>
+template <int U>
 __device__ __forceinline__ void flag_chunks(const DevState &s, const int (&cu)[U],
                                             const bool (&f)[U], const float4 *pos,
                                             const float4 *vel, const float4 *acc, bool inc,
@@ -939,7 +882,7 @@ __device__ __forceinline__ void flag_chunks(const DevState &s, const int (&cu)[U
             if (s.bits_out) s.bits_out[cu[u] >> 5] = b;
         }
         if (!b) continue;
-        if (pd.n + __popc(b) > kPending) flush_pending<kNet>(s, pd, pos, vel, acc, inc, step, nF_acc);
+        if (pd.n + __popc(b) > kPending) flush_pending(s, pd, pos, vel, acc, inc, step, nF_acc);
         if (b >> lane & 1u) pd.id[pd.n + __popc(b & lt)] = cu[u] + lane;
         pd.n += __popc(b);
     }
@@ -950,7 +893,6 @@ __device__ __forceinline__ void flag_chunks(const DevState &s, const int (&cu)[U
 // produced here and read back from registers.  Block b takes tiles b,
 // b + grid, ... of blockDim * kCheckUnroll particles; in a tile each warp
 // checks kCheckUnroll chunks of 32 (loads of all chunks first).
-template <bool kNet>
 __device__ __forceinline__ void check_pass_fused(const DevState &s, const float4 *vel,
                                                  const float4 *acc, const IntegrateArgs &ia,
                                                  bool inc, int step, int *nF_acc)
@@ -982,9 +924,9 @@ __device__ __forceinline__ void check_pass_fused(const DevState &s, const float4
                     atomicOr(&s.cnt->err, DERR_NAN);
             }
         }
-        flag_chunks<kNet, kCheckUnroll>(s, cu, f, ia.pos, vel, acc, inc, step, nF_acc, pd);
+        flag_chunks<kCheckUnroll>(s, cu, f, ia.pos, vel, acc, inc, step, nF_acc, pd);
     }
-    flush_pending_final<kNet>(s, pd, ia.pos, vel, acc, inc, step, nF_acc);
+    flush_pending_final(s, pd, ia.pos, vel, acc, inc, step, nF_acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1059,7 +1001,6 @@ __host__ __device__ constexpr int check_smem_bytes(int threads)
 // the whole block is done with it.  A stage whose copies do not land within
 // kStageWaitSpins polls is reported (DERR_SYNC) and skipped, never waited
 // for indefinitely.
-template <bool kNet>
 __device__ __forceinline__ void check_pass_stream(const DevState &s, const float4 *__restrict__ pos,
                                                   const float4 *vel, const float4 *acc, bool inc,
                                                   int step, int *nF_acc)
@@ -1110,7 +1051,7 @@ __device__ __forceinline__ void check_pass_stream(const DevState &s, const float
             if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z)))
                 atomicOr(&s.cnt->err, DERR_NAN);
         }
-        flag_chunks<kNet, 1>(s, cu, f, pos, vel, acc, inc, step, nF_acc, pd);
+        flag_chunks<1>(s, cu, f, pos, vel, acc, inc, step, nF_acc, pd);
         __syncthreads();   // the block is done with this stage
         if (tid == 0 && j + kStages < mine) issue(issued++);
     }
@@ -1119,10 +1060,9 @@ __device__ __forceinline__ void check_pass_stream(const DevState &s, const float
         for (int k = j; k < issued; ++k)
             stage_wait(&bar[k % kStages], (unsigned)(k / kStages) & 1u);
     }
-    flush_pending_final<kNet>(s, pd, pos, vel, acc, inc, step, nF_acc);
+    flush_pending_final(s, pd, pos, vel, acc, inc, step, nF_acc);
 }
 
-template <bool kNet>
 static __device__ __noinline__ void full_update_pass(const DevState &s, const float4 *pos,
                                               const float4 *vel)
 {
@@ -1142,7 +1082,6 @@ static __device__ __noinline__ void full_update_pass(const DevState &s, const fl
     }
 }
 
-template <bool kNet>
 static __device__ __noinline__ void full_insert_pass(const DevState &s)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -1165,7 +1104,6 @@ static __device__ __noinline__ void full_insert_pass(const DevState &s)
     }
 }
 
-template <bool kNet>
 static __device__ __noinline__ void all_rows_pass(const DevState &s, int fill, int *ovf)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -1226,11 +1164,10 @@ static __device__ long long layout_scan(const DevState &s, bool tight)
 // has failed (DERR_STORE).  A layout above 60% of the store asks the host
 // to grow it before the next step.  Returns false when the step must be
 // abandoned.
-template <bool kNet>
 static __device__ __noinline__ bool relayout_pass(const DevState &s)
 {
     DevCounters *c = s.cnt;
-    all_rows_pass<kNet>(s, 0, nullptr);
+    all_rows_pass(s, 0, nullptr);
     if (!grid_barrier(s)) return false;
     const long long need = layout_scan(s, false);
     if (need < 0) return false;
@@ -1245,7 +1182,7 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
     if (!grid_barrier(s)) return false;
     if (!store_failed(s)) {
         int unused = 0;
-        all_rows_pass<kNet>(s, 1, &unused);
+        all_rows_pass(s, 1, &unused);
     }
     if (!grid_barrier(s)) return false;
     if (blockIdx.x == 0 && threadIdx.x == 0 && !store_failed(s)) {
@@ -1263,7 +1200,6 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
 // Rebuild log: every open record tracks the particle's largest displacement
 // since it opened, and closes `horizon` steps later with label
 // sqrt(max |x - x_open|^2) / d.
-template <bool kNet>
 static __device__ __noinline__ void log_pass(const DevState &s, const float4 *pos, int step)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -1302,6 +1238,16 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
     c->tr_cnt[slot] += 1;
 }
 
+// The deferred a2 (deferred_update) for the nF flagged particles of the
+// step, one warp per particle, items spread over the blocks first as in
+// partial_pass; list index k keeps the check's order.
+static __device__ __noinline__ void update_pass(const DevState &s, int nF, const float4 *pos,
+                                                const float4 *vel, const float4 *acc, int step)
+{
+    const int w0 = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = w0; k < nF; k += nw) update_warp(s, s.fid[k], k, pos, vel, acc, step);
+}
 
 // The rebuild of a partial step (nF flagged).  Up to s.direct_max
 // flagged particles: moves and patches in one phase, on different warps
@@ -1309,7 +1255,6 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
 // skip the flagged particles in the cells and test them directly); more:
 // the moves first and a barrier, then the patches on final cells.  Returns
 // false when the step must be abandoned.
-template <bool kNet>
 static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int par, int *ovf)
 {
     // work items go round the blocks first (item w to block w % grid), so
@@ -1321,11 +1266,11 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
     if (!direct) {
         for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
         if (!grid_barrier(s)) return false;
-        for (int k = w0; k < nF; k += nw) patch_warp<kNet>(s, k, nF, false, par, ovf);
+        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, par, ovf);
         return true;
     }
     for (int w = w0; w < 2 * nF; w += nw) {
-        if (w < nF) patch_warp<kNet>(s, w, nF, true, par, ovf);
+        if (w < nF) patch_warp(s, w, nF, true, par, ovf);
         else move_warp(s, s.fid[w - nF], s.fref[w - nF]);
     }
     return true;
@@ -1337,13 +1282,9 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
 // half-step (ia) instead.  Launched cooperatively with every block resident.
 // Per-step counts live in two slots chosen by the step's parity, so that the
 // slots of the next step can be cleared while this one is read.  The list
-// is final when the kernel ends (and before the tail).  kNet: the form for
-// the learned policy (update_pending); the other form serves every policy
-// too, evaluating the network one particle per warp.  The non-inlined
-// passes take kNet only so that each form has its own copies: callees
-// shared by the two forms were allocated with more spills in the plain one.
+// is final when the kernel ends (and before the tail).
 // ---------------------------------------------------------------------------
-template <bool kFused, class Tail, bool kNet>
+template <bool kFused, class Tail>
 __global__ void __launch_bounds__(kStepMaxThreads, 1)
 k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, DevState sp,
        IntegrateArgs ia, Tail tail)
@@ -1374,9 +1315,9 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     int *ovf = &c->ovf[par];
 
     if constexpr (kFused)
-        check_pass_fused<kNet>(s, vel, acc, ia, inc, step, &c->nF_acc[par]);
+        check_pass_fused(s, vel, acc, ia, inc, step, &c->nF_acc[par]);
     else
-        check_pass_stream<kNet>(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
+        check_pass_stream(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
     if (!grid_barrier(s)) return;
     const int nF = *(volatile int *)&c->nF_acc[par];
     if (s.sc_cnt && blockIdx.x == 0)   // the next step's scene counters
@@ -1415,15 +1356,19 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     bool changed = false;
     if (inc) {
         if (nF > 0) {
-            if (!partial_pass<kNet>(s, nF, par, ovf)) return;
+            if (deferred_update(s)) {
+                update_pass(s, nF, pos, vel, acc, step);
+                if (!grid_barrier(s)) return;
+            }
+            if (!partial_pass(s, nF, par, ovf)) return;
             changed = true;
         }
     } else if (upd > 0 && !store_failed(s)) {
-        full_update_pass<kNet>(s, pos, vel);
+        full_update_pass(s, pos, vel);
         if (!grid_barrier(s)) return;
-        full_insert_pass<kNet>(s);
+        full_insert_pass(s);
         if (!grid_barrier(s)) return;
-        all_rows_pass<kNet>(s, 1, ovf);
+        all_rows_pass(s, 1, ovf);
         changed = true;
     }
     if (changed) {
@@ -1434,11 +1379,11 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
             trace_add(c, TR_REBUILD, t1, t2);
         }
         if (*(volatile int *)ovf && !store_failed(s)) {
-            if (!relayout_pass<kNet>(s)) return;
+            if (!relayout_pass(s)) return;
             if (s.trace && lead) trace_add(c, TR_RELAYOUT, t2, global_ns());
         }
     }
-    if (s.log_on) log_pass<kNet>(s, pos, step);
+    if (s.log_on) log_pass(s, pos, step);
     if (Tail::kActive) {
         const unsigned long long t3 = (s.trace && lead) ? global_ns() : 0ULL;
         tail(blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);

@@ -122,9 +122,8 @@ def _learned_setup(lvb, s, seed=3):
 
 @pytest.mark.parametrize("log", [False, True])
 def test_learned_policy_broad_phase_parity(orc, log):
-    # with the rebuild log off each lane evaluates the network for its own
-    # flagged particle; with it on a warp evaluates it one particle at a
-    # time: both must give the oracle's skins bit for bit
+    # with the rebuild log on or off (the log adds a pass and samples, and
+    # must change nothing else): the oracle's skins bit for bit
     lvb = _lvb()
     from oracle.statemachine import OracleLVB
     s = scenes.ballistic(n=2000, seed=17, vsigma=1.0)
