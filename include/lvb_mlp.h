@@ -11,12 +11,19 @@
  *   h1_o = bf16(relu(b1_o + sum_{k=0..7}  W1[o][k] z_k))     sums in k order
  *   h2_o = bf16(relu(b2_o + sum_{k=0..31} W2[o][k] h1_k))
  *   y    = b3 + sum_{k=0..31} w3[k] h2_k
- *   skin = (2 r) * fminf(fmaxf(y, y_lo), y_hi), then the cap of lvb.h
- * relu(x) = x if x > 0 else 0; fmaxf / fminf return the other operand when
- * one is NaN.  Products of bfloat16 values are exact in binary32, so the
- * result does not depend on fused multiply-add use.  The output range
- * [y_lo, y_hi] (in diameters) keeps every proposal positive and bounded:
- * the network is used on states its training data may not cover.
+ *   yc   = fminf(fmaxf(y, y_lo), y_hi)
+ *   skin = (2 r) * yc                       (diameter form, y_steps = 0)
+ *   skin = (2 r) * (f0 * (yc * y_steps))    (travel form, y_steps > 0)
+ * then the cap of lvb.h; each product is rounded once, in the order
+ * written.  relu(x) = x if x > 0 else 0; fmaxf / fminf return the other
+ * operand when one is NaN.  Products of bfloat16 values are exact in
+ * binary32, so the result does not depend on fused multiply-add use.  The
+ * output range [y_lo, y_hi] keeps every proposal positive and bounded: the
+ * network is used on states its training data may not cover.  In the
+ * diameter form y is the skin in diameters; in the travel form it is the
+ * skin in units of the particle's travel over y_steps steps at its present
+ * speed (f0 d = |v| dt), a per-particle factor K / y_steps of the paper's
+ * rule K |v| dt.
  *
  * Features f (binary32, at the step that flags the particle, from the state
  * before its update; d = 2 r, dt the policy's time step):
@@ -61,8 +68,8 @@ typedef struct {
     float b3;
     float mu[LVB_MLP_IN];
     float isd[LVB_MLP_IN];
-    float y_lo, y_hi;    /* output range, in diameters */
-    float pad;
+    float y_lo, y_hi;    /* output range (in the output's unit) */
+    float y_steps;       /* 0: diameter form; > 0: travel form over y_steps steps */
 } lvb_mlp_weights;
 
 /*
@@ -70,17 +77,21 @@ typedef struct {
  *   params : host, LVB_MLP_PARAMS binary32 in the order W1, b1, W2, b2, w3, b3.
  *   mu, isd: host, LVB_MLP_IN each (feature offset and inverse scale).
  *   y_range: host, {y_lo, y_hi} with y_lo <= y_hi, or NULL for {0, +inf}
- *            (then skin = d * max(y, 0)).
+ *            (then yc = max(y, 0)).
+ *   y_steps: 0 for the diameter form, else the travel form's step count
+ *            (finite, > 0).
  *   out    : host or device lvb_mlp_weights (weights rounded to bfloat16).
- * Errors: EINVAL (NULL pointer, y_lo > y_hi or NaN), EDEVICE.
+ * Errors: EINVAL (NULL pointer, y_lo > y_hi or NaN, y_steps negative, NaN
+ * or infinite), EDEVICE.
  */
 int lvb_mlp_pack(const float *params, const float *mu, const float *isd, const float *y_range,
-                 lvb_mlp_weights *out);
+                 float y_steps, lvb_mlp_weights *out);
 
 /*
- * lvb_mlp_infer -- the network on n feature rows: skin[i] = d[i] * max(y, 0)
- * (no cap) and y[i].  feats: device n x 8; diam, skin, y: device n (y may be
- * NULL); w: device weights.  Enqueues on `stream`.
+ * lvb_mlp_infer -- the network on n feature rows: skin[i] by the weights'
+ * output form with d = diam[i] and f0 = feats[i][0] (no cap), and y[i].
+ * feats: device n x 8; diam, skin, y: device n (y may be NULL); w: device
+ * weights.  Enqueues on `stream`.
  */
 int lvb_mlp_infer(const float *feats, const float *diam, int64_t n, const lvb_mlp_weights *w,
                   float *skin, float *y, void *stream);

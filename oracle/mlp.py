@@ -15,10 +15,15 @@ bits):
     h1_o = bf16( relu( b1_o + sum_k W1_ok z_k ) )      k = 0..7 in order
     h2_o = bf16( relu( b2_o + sum_k W2_ok h1_k ) )     k = 0..31 in order
     y    = b3 + sum_k w3_k h2_k                        k = 0..31 in order
-    skin = d * fmin(fmax(y, y_lo), y_hi)               (then the cap)
-(fmax / fmin return the other operand when one is NaN.)  The output range
-[y_lo, y_hi] belongs to the weights; y_lo = 0, y_hi = +inf gives
-d * max(y, 0).
+    yc   = fmin(fmax(y, y_lo), y_hi)
+    skin = d * yc                          diameter form (y_steps = 0)
+    skin = d * (f0 * (yc * y_steps))       travel form (y_steps > 0)
+(each product one binary32 rounding, in that order; then the cap; fmax /
+fmin return the other operand when one is NaN.)  The output range
+[y_lo, y_hi] and y_steps belong to the weights; y_lo = 0, y_hi = +inf gives
+yc = max(y, 0).  Since f0 d is the particle's travel |v| dt in one step,
+the travel form is the paper's rule K |v| dt with a per-particle factor
+K = yc * y_steps proposed by the network.
 Weights and biases are bfloat16 / binary32; each product of two bfloat16
 values is exact in binary32, and each sum is one binary32 rounding, taken
 in the order written, starting from the bias.
@@ -52,7 +57,7 @@ def bf16_round(x):
 class Weights:
     """Parameters in binary32 master form."""
 
-    def __init__(self, W1, b1, W2, b2, w3, b3, mu, isd, y_lo=0.0, y_hi=np.inf):
+    def __init__(self, W1, b1, W2, b2, w3, b3, mu, isd, y_lo=0.0, y_hi=np.inf, y_steps=0.0):
         self.W1 = np.asarray(W1, np.float32).reshape(N_H, N_IN)
         self.b1 = np.asarray(b1, np.float32).reshape(N_H)
         self.W2 = np.asarray(W2, np.float32).reshape(N_H, N_H)
@@ -63,6 +68,7 @@ class Weights:
         self.isd = np.asarray(isd, np.float32).reshape(N_IN)
         self.y_lo = np.float32(y_lo)
         self.y_hi = np.float32(y_hi)
+        self.y_steps = np.float32(y_steps)
 
     @staticmethod
     def random(seed=0, scale=0.3):
@@ -76,7 +82,7 @@ class Weights:
                                [self.b3]]).astype(np.float32)
 
     @staticmethod
-    def from_flat(p, mu, isd, y_lo=0.0, y_hi=np.inf):
+    def from_flat(p, mu, isd, y_lo=0.0, y_hi=np.inf, y_steps=0.0):
         p = np.asarray(p, np.float32)
         o = 0
         W1 = p[o:o + N_H * N_IN]; o += N_H * N_IN
@@ -85,7 +91,7 @@ class Weights:
         b2 = p[o:o + N_H]; o += N_H
         w3 = p[o:o + N_H]; o += N_H
         b3 = p[o]
-        return Weights(W1, b1, W2, b2, w3, b3, mu, isd, y_lo, y_hi)
+        return Weights(W1, b1, W2, b2, w3, b3, mu, isd, y_lo, y_hi, y_steps)
 
 
 def _dot_fixed(bias, w, x):
@@ -108,6 +114,9 @@ def infer(W: Weights, feats, diam):
     h2 = bf16_round(np.maximum(_dot_fixed(W.b2, bf16_round(W.W2), h1), np.float32(0)))
     y = _dot_fixed(np.array([W.b3], np.float32), bf16_round(W.w3)[None, :], h2)[:, 0]
     yc = np.fmin(np.fmax(y, W.y_lo), W.y_hi).astype(np.float32)
+    if W.y_steps > 0:
+        k = (yc * W.y_steps).astype(np.float32)
+        yc = (f[:, 0] * k).astype(np.float32)
     return (np.asarray(diam, np.float32) * yc).astype(np.float32), y
 
 

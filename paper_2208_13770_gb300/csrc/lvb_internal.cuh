@@ -221,6 +221,17 @@ __device__ __forceinline__ float mlp_y_warp(const lvb_mlp_weights *__restrict__ 
     return y;
 }
 
+// The network's skin proposal from its output y for a particle of diameter
+// d with travel feature f0 (lvb_mlp.h): diameter form (y_steps = 0) or
+// travel form, each product rounded once in the header's order.
+__device__ __forceinline__ float mlp_skin(const lvb_mlp_weights *__restrict__ W, float y, float d,
+                                          float f0)
+{
+    const float yc = fminf(fmaxf(y, W->y_lo), W->y_hi);
+    const float u = W->y_steps > 0.0f ? __fmul_rn(f0, __fmul_rn(yc, W->y_steps)) : yc;
+    return __fmul_rn(d, u);
+}
+
 // Slack rule of the row store: capacity for a row of `len` entries (room
 // for the row to grow by half, and by 8 however short it is, before the
 // store is re-laid out).

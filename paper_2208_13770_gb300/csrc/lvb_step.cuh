@@ -186,7 +186,7 @@ __device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g
     float prop = 0.0f;
     if (s.skin_kind == LVB_SKIN_LEARNED) {
         const float y = mlp_y_warp(s.mlp, f);
-        prop = __fmul_rn(__fmul_rn(2.0f, r), fminf(fmaxf(y, s.mlp->y_lo), s.mlp->y_hi));
+        prop = mlp_skin(s.mlp, y, __fmul_rn(2.0f, r), f[0]);
     }
     return skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
 }

@@ -51,7 +51,7 @@ __global__ void k_mlp_infer(const float *__restrict__ feats, const float *__rest
         for (int k = 0; k < NI; ++k) f[k] = feats[i * NI + k];
         const float y = mlp_y_warp(W, f);
         if ((threadIdx.x & 31) == 0) {
-            skin[i] = __fmul_rn(diam[i], fminf(fmaxf(y, W->y_lo), W->y_hi));
+            skin[i] = mlp_skin(W, y, diam[i], f[0]);
             if (yout) yout[i] = y;
         }
     }
@@ -265,14 +265,16 @@ constexpr int64_t kGradChunk = 1024 * kTB;   // samples per pass of lvb_mlp_grad
 extern "C" {
 
 int lvb_mlp_pack(const float *params, const float *mu, const float *isd, const float *y_range,
-                 lvb_mlp_weights *out)
+                 float y_steps, lvb_mlp_weights *out)
 {
     if (!params || !mu || !isd || !out) return LVB_EINVAL;
     if (y_range && !(y_range[0] <= y_range[1])) return LVB_EINVAL;
+    if (!(y_steps >= 0.0f) || !std::isfinite(y_steps)) return LVB_EINVAL;
     lvb_mlp_weights w;
     memset(&w, 0, sizeof(w));
     w.y_lo = y_range ? y_range[0] : 0.0f;
     w.y_hi = y_range ? y_range[1] : INFINITY;
+    w.y_steps = y_steps;
     for (int k = 0; k < NH * NI; ++k) w.W1[k] = bf16_host_rn(params[OFF_W1 + k]);
     for (int k = 0; k < NH; ++k) w.b1[k] = params[OFF_B1 + k];
     for (int k = 0; k < NH * NH; ++k) w.W2[k] = bf16_host_rn(params[OFF_W2 + k]);

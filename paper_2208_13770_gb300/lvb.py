@@ -96,7 +96,7 @@ _SIGS = {
     "lvb_set_stream": ([_p, _p], ctypes.c_int),
     "lvb_destroy": ([_p], ctypes.c_int),
     "lvb_strerror": ([ctypes.c_int], ctypes.c_char_p),
-    "lvb_mlp_pack": ([_p, _p, _p, _p, _p], ctypes.c_int),
+    "lvb_mlp_pack": ([_p, _p, _p, _p, ctypes.c_float, _p], ctypes.c_int),
     "lvb_mlp_infer": ([_p, _p, _i64, _p, _p, _p, _p], ctypes.c_int),
     "lvb_mlp_grad": ([_p, _i64, _p, _p, _p, ctypes.c_float, _p, ctypes.POINTER(ctypes.c_double),
                       _p], ctypes.c_int),
@@ -302,8 +302,8 @@ LVB_MLP_LOSS_SQUARED, LVB_MLP_LOSS_RELATIVE = 0, 1
 MLP_WEIGHTS_BYTES = 4 * (32 * 8 + 32 + 32 * 32 + 32 + 32 + 1 + 8 + 8 + 3)
 
 
-def lvb_mlp_pack(params, mu, isd, y_range, out):
-    return _lib.lvb_mlp_pack(params, mu, isd, y_range, out)
+def lvb_mlp_pack(params, mu, isd, y_range, y_steps, out):
+    return _lib.lvb_mlp_pack(params, mu, isd, y_range, y_steps, out)
 
 
 def lvb_mlp_infer(feats, diam, n, w, skin, y, stream=None):
@@ -615,10 +615,11 @@ class DEM:
 
 
 # ------------------------------------------------------------ skin network
-def mlp_weights_device(params, mu, isd, y_range=None):
+def mlp_weights_device(params, mu, isd, y_range=None, y_steps=0.0):
     """Pack master parameters (+ normalisation, + output range {y_lo, y_hi}
-    or None for {0, inf}) into a device lvb_mlp_weights record; returns the
-    torch byte tensor holding it."""
+    or None for {0, inf}, + y_steps: 0 for the diameter form of the output,
+    else the travel form's step count) into a device lvb_mlp_weights record;
+    returns the torch byte tensor holding it."""
     import torch
     buf = torch.empty(MLP_WEIGHTS_BYTES, dtype=torch.uint8, device="cuda")
     p = np.ascontiguousarray(params, np.float32)
@@ -626,7 +627,7 @@ def mlp_weights_device(params, mu, isd, y_range=None):
     d = np.ascontiguousarray(isd, np.float32)
     yr = None if y_range is None else np.ascontiguousarray(y_range, np.float32)
     _check(lvb_mlp_pack(_np_ptr(p), _np_ptr(m), _np_ptr(d), None if yr is None else _np_ptr(yr),
-                        buf.data_ptr()), "lvb_mlp_pack")
+                        float(y_steps), buf.data_ptr()), "lvb_mlp_pack")
     return buf
 
 

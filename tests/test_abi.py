@@ -84,6 +84,20 @@ def test_argument_checks_without_gpu():
     assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_PAPER_KVDT, 200.0, 0.0, None), vel=p) == E
     # the network needs weights, velocities and accelerations
     assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_LEARNED, 0.0, 1e-5, None), vel=p) == E
+    # the network's weights: a bad output range or travel step count
+    prm = np.zeros(lvb.LVB_MLP_PARAMS, np.float32)
+    one = np.ones(lvb.LVB_MLP_IN, np.float32)
+    rec = np.zeros(lvb.MLP_WEIGHTS_BYTES, np.uint8)
+
+    def pack(yr=None, steps=0.0):
+        yp = None if yr is None else np.asarray(yr, np.float32)
+        return lvb._lib.lvb_mlp_pack(prm.ctypes.data, one.ctypes.data, one.ctypes.data,
+                                     None if yp is None else yp.ctypes.data, steps,
+                                     rec.ctypes.data)
+    assert pack(yr=(0.5, 0.1)) == E
+    assert pack(steps=-1.0) == E
+    assert pack(steps=float("nan")) == E
+    assert pack(steps=float("inf")) == E
     assert lvb._lib.lvb_step(None, p, None, None) == E
     assert lvb._lib.lvb_step_host(None, p, None, None, None, None) == E
     assert lvb._lib.lvb_sync(None) == E

@@ -38,16 +38,20 @@ def _weights(seed):
     return W
 
 
-def test_inference_bit_exact():
+@pytest.mark.parametrize("y_steps", [0.0, 400.0])
+def test_inference_bit_exact(y_steps):
+    # diameter form and travel form of the output
     lvb = _lvb()
     from oracle import mlp
     W = _weights(1)
     W.y_lo, W.y_hi = np.float32(0.05), np.float32(0.8)
+    W.y_steps = np.float32(y_steps)
     rng = np.random.default_rng(2)
     n = 5000
     f = rng.normal(0, 2, (n, 8)).astype(np.float32)
+    f[:, 0] = np.abs(f[:, 0]) * np.float32(1e-3)
     d = rng.uniform(1e-3, 4e-3, n).astype(np.float32)
-    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi))
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi), y_steps)
     skin = torch.empty(n, device="cuda")
     y = torch.empty(n, device="cuda")
     fd, dd = _dev(f), _dev(d)
@@ -120,15 +124,17 @@ def _learned_setup(lvb, s, seed=3):
     return W, grid
 
 
-@pytest.mark.parametrize("log", [False, True])
-def test_learned_policy_broad_phase_parity(orc, log):
+@pytest.mark.parametrize("log,y_steps", [(False, 0.0), (True, 0.0), (False, 300.0)])
+def test_learned_policy_broad_phase_parity(orc, log, y_steps):
     # with the rebuild log on or off (the log adds a pass and samples, and
-    # must change nothing else): the oracle's skins bit for bit
+    # must change nothing else), and in the travel form of the output: the
+    # oracle's skins bit for bit
     lvb = _lvb()
     from oracle.statemachine import OracleLVB
     s = scenes.ballistic(n=2000, seed=17, vsigma=1.0)
     W, grid = _learned_setup(lvb, s)
-    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi))
+    W.y_steps = np.float32(y_steps)
+    wbuf = lvb.mlp_weights_device(W.flat(), W.mu, W.isd, (W.y_lo, W.y_hi), y_steps)
     acc = np.zeros_like(s.pos)
     acc[:, 2] = -9.81
     ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_LEARNED, 0.0, s.dt,

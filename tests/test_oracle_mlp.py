@@ -67,6 +67,41 @@ def test_one_path_network_closed_form():
     assert np.array_equal(skin3, (d * np.float32(0.3)).astype(np.float32))
 
 
+def test_travel_form_is_the_paper_rule_per_particle():
+    # a network with constant output c in the travel form over S steps
+    # proposes skin = d (f0 (c S)) with f0 = (|v| dt) / d: the paper's rule
+    # K |v| dt (Eq. skin_formulus1) with K = c S, up to the roundings of f0
+    # and of the three products (each at most half an ulp)
+    rng = np.random.default_rng(5)
+    n = 4000
+    v = rng.normal(0, 0.5, (n, 3)).astype(np.float32)
+    r = rng.uniform(0.5e-3, 2e-3, n).astype(np.float32)
+    dt = np.float32(1e-6)
+    d = (np.float32(2) * r).astype(np.float32)
+    vm = np.sqrt(((v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1]).astype(np.float32)
+                  + v[:, 2] * v[:, 2]).astype(np.float32))
+    f = np.zeros((n, mlp.N_IN), np.float32)
+    f[:, 0] = ((vm * dt).astype(np.float32) / d).astype(np.float32)
+    f[:, 1] = rng.normal(0, 1, n)          # the other features play no part
+    c, S = np.float32(1.5), np.float32(400.0)
+    p = np.zeros(mlp.N_PARAMS, np.float32)
+    p[-1] = c
+    W = mlp.Weights.from_flat(p, np.zeros(mlp.N_IN), np.ones(mlp.N_IN), 0.0, np.inf, S)
+    skin, y = mlp.infer(W, f, d)
+    assert (y == c).all()
+    rule = 600.0 * vm.astype(np.float64) * float(dt)
+    assert np.abs(skin / rule - 1).max() < 6 * 2.0 ** -24
+    # the range applies to y before the scaling: y_lo above c gives K = y_lo S
+    W.y_lo = np.float32(2.0)
+    skin2, _ = mlp.infer(W, f, d)
+    assert np.abs(skin2 / (800.0 * vm.astype(np.float64) * float(dt)) - 1).max() < 6 * 2.0 ** -24
+    # a particle at rest gets no skin; the diameter form ignores f0
+    f[:3, 0] = 0
+    assert (mlp.infer(W, f, d)[0][:3] == 0).all()
+    W.y_steps = np.float32(0)
+    assert np.array_equal(mlp.infer(W, f, d)[0], (d * np.float32(2.0)).astype(np.float32))
+
+
 @pytest.mark.parametrize("rel_floor", [0.0, 0.15])
 def test_backward_matches_finite_differences(rel_floor):
     # squared error, and relative error with a floor that some labels fall below
