@@ -58,7 +58,10 @@ extern "C" {
 
 /* Device layout of the weights given to LVB_SKIN_LEARNED (lvb_skin_policy.mlp).
  * W1, W2, w3 hold bfloat16 values stored as binary32 (lvb_mlp_pack rounds
- * them); row-major [out][in]. */
+ * them).  W1 and W2 are stored input-major, [in][out] (W1[k * 32 + o] is
+ * the weight from input k to hidden unit o), so that the 32 units' weights
+ * of one input lie together; the master parameters of lvb_mlp_pack and of
+ * training are [out][in]. */
 typedef struct {
     float W1[LVB_MLP_HIDDEN * LVB_MLP_IN];
     float b1[LVB_MLP_HIDDEN];

@@ -187,9 +187,11 @@ __device__ __forceinline__ unsigned lanemask_lt()
 
 // ---------------------------------------------------------------------------
 // The skin network (lvb_mlp.h), one warp per particle: lane o computes hidden
-// unit o of each layer; every sum runs in index order from its bias, so the
-// result is the same on every lane and equal to the CPU evaluation.  The
-// weights hold bfloat16 values, so fmaf(w, x, acc) = acc + w*x rounded once.
+// unit o of each layer (its weights of input k are one coalesced line for
+// the warp, the layout being input-major); every sum runs in index order
+// from its bias, so the result is the same on every lane and equal to the
+// CPU evaluation.  The weights hold bfloat16 values, so fmaf(w, x, acc) =
+// acc + w*x rounded once.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float bf16_rn(float x)
 {
@@ -208,12 +210,12 @@ __device__ __forceinline__ float mlp_y_warp(const lvb_mlp_weights *__restrict__ 
         z[k] = bf16_rn(__fmul_rn(__fsub_rn(f[k], W->mu[k]), W->isd[k]));
     float acc = W->b1[lane];
 #pragma unroll
-    for (int k = 0; k < LVB_MLP_IN; ++k) acc = fmaf(W->W1[lane * LVB_MLP_IN + k], z[k], acc);
+    for (int k = 0; k < LVB_MLP_IN; ++k) acc = fmaf(W->W1[k * LVB_MLP_HIDDEN + lane], z[k], acc);
     const float h1 = bf16_rn(relu(acc));
     float acc2 = W->b2[lane];
 #pragma unroll
     for (int k = 0; k < LVB_MLP_HIDDEN; ++k)
-        acc2 = fmaf(W->W2[lane * LVB_MLP_HIDDEN + k], __shfl_sync(FULL, h1, k), acc2);
+        acc2 = fmaf(W->W2[k * LVB_MLP_HIDDEN + lane], __shfl_sync(FULL, h1, k), acc2);
     const float h2 = bf16_rn(relu(acc2));
     float y = W->b3;
 #pragma unroll

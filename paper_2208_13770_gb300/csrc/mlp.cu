@@ -275,9 +275,12 @@ int lvb_mlp_pack(const float *params, const float *mu, const float *isd, const f
     w.y_lo = y_range ? y_range[0] : 0.0f;
     w.y_hi = y_range ? y_range[1] : INFINITY;
     w.y_steps = y_steps;
-    for (int k = 0; k < NH * NI; ++k) w.W1[k] = bf16_host_rn(params[OFF_W1 + k]);
+    // input-major device layout (lvb_mlp.h) from the [out][in] master form
+    for (int o = 0; o < NH; ++o)
+        for (int k = 0; k < NI; ++k) w.W1[k * NH + o] = bf16_host_rn(params[OFF_W1 + o * NI + k]);
     for (int k = 0; k < NH; ++k) w.b1[k] = params[OFF_B1 + k];
-    for (int k = 0; k < NH * NH; ++k) w.W2[k] = bf16_host_rn(params[OFF_W2 + k]);
+    for (int o = 0; o < NH; ++o)
+        for (int k = 0; k < NH; ++k) w.W2[k * NH + o] = bf16_host_rn(params[OFF_W2 + o * NH + k]);
     for (int k = 0; k < NH; ++k) w.b2[k] = params[OFF_B2 + k];
     for (int k = 0; k < NH; ++k) w.w3[k] = bf16_host_rn(params[OFF_W3 + k]);
     w.b3 = params[OFF_B3];
