@@ -212,13 +212,15 @@ __device__ __forceinline__ float mlp_y_warp(const lvb_mlp_weights *__restrict__ 
 #pragma unroll
     for (int k = 0; k < LVB_MLP_IN; ++k) acc = fmaf(W->W1[k * LVB_MLP_HIDDEN + lane], z[k], acc);
     const float h1 = bf16_rn(relu(acc));
+    // unrolled by 8 only: enough loads in flight, and few registers held
+    // (the step kernel's callers run at 64 registers a thread)
     float acc2 = W->b2[lane];
-#pragma unroll
+#pragma unroll 8
     for (int k = 0; k < LVB_MLP_HIDDEN; ++k)
         acc2 = fmaf(W->W2[k * LVB_MLP_HIDDEN + lane], __shfl_sync(FULL, h1, k), acc2);
     const float h2 = bf16_rn(relu(acc2));
     float y = W->b3;
-#pragma unroll
+#pragma unroll 8
     for (int k = 0; k < LVB_MLP_HIDDEN; ++k) y = fmaf(W->w3[k], __shfl_sync(FULL, h2, k), y);
     return y;
 }

@@ -192,69 +192,89 @@ __device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g
 }
 
 
-// Live partners of row i (entries >= 0), counted by the warp.
-__device__ __forceinline__ int row_live_warp(const DevState &s, int i)
+// Live partners of row i (entries >= 0), counted by one lane.
+__device__ __forceinline__ int row_live_lane(const DevState &s, int i)
 {
-    const int lane = threadIdx.x & 31;
     const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
     int c = 0;
-    for (int e0 = 0; e0 < len; e0 += 32) {
-        const int e = e0 + lane;
-        c += __popc(__ballot_sync(FULL, e < len && s.col[off + e] >= 0));
-    }
+    for (int e = 0; e < len; ++e) c += s.col[off + e] >= 0;
     return c;
 }
 
-// a2 for flagged particle i by one warp, after the check pass (PARTIAL
-// trigger, deferred_update): new reference position and skin (the policy's
-// features come from the state before the update -- rows and cells change
-// only in the rebuild that follows; `step` is the number of the step being
-// taken), kept with the old state at index k of the flagged list.  (pos and
+// a2 for the m <= 32 flagged particles at list indices k0 .. k0 + m - 1,
+// after the check pass (PARTIAL trigger, deferred_update): lane t takes
+// particle fid[k0 + t] -- its loads and features (from the state before
+// the update: rows and cells change only in the rebuild that follows;
+// `step` is the number of the step being taken) in flight with the other
+// lanes' -- and the warp evaluates the network for the m particles one
+// after another; each lane then writes its particle's new reference
+// position and skin, kept with the old state at its list index.  (pos and
 // vel may have been written earlier in the same kernel by the DEM position
 // half-step, so they are read through plain coherent loads.)
-static __device__ __noinline__ void update_warp(const DevState &s, int i, int k, const float4 *pos,
-                                                const float4 *vel, const float4 *acc, int step)
+__device__ __forceinline__ void update_group(const DevState &s, int k0, int m,
+                                                 const float4 *pos, const float4 *vel,
+                                                 const float4 *acc, int step)
 {
     const int lane = threadIdx.x & 31;
+    const bool act = lane < m;
+    const int i = act ? s.fid[k0 + lane] : 0;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float f[LVB_MLP_IN];
+#pragma unroll
+    for (int t = 0; t < LVB_MLP_IN; ++t) f[t] = 0.0f;
+    if (act && (s.skin_kind == LVB_SKIN_LEARNED || s.log_on)) {
+        const float4 p = pos[i];
+        const SceneGeom &g = geom_of(s, i);
+        const int nc = cell_key(g, p.x, p.y, p.z);
+        skin_features(s, p, vel ? vel[i] : zero, acc ? acc[i] : zero, s.rad[i], g, s.ref[i],
+                      row_live_lane(s, i), step - s.born[i], s.cell_live[nc], f);
+    }
+    float y = 0.0f;
+    if (s.skin_kind == LVB_SKIN_LEARNED) {
+        for (int t = 0; t < m; ++t) {
+            float ft[LVB_MLP_IN];
+#pragma unroll
+            for (int k = 0; k < LVB_MLP_IN; ++k) ft[k] = __shfl_sync(FULL, f[k], t);
+            const float yt = mlp_y_warp(s.mlp, ft);
+            if (lane == t) y = yt;
+        }
+    }
+    if (!act) return;
+    // the particle's state again (cached): fewer registers held across the
+    // network's evaluation
+    const int k = k0 + lane;
     const float4 p = pos[i];
     const float r = s.rad[i];
-    const float4 v = vel ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 v = vel ? vel[i] : zero;
     const float4 q = s.ref[i];
     const SceneGeom &g = geom_of(s, i);
-    float f[LVB_MLP_IN];
-    if (s.skin_kind == LVB_SKIN_LEARNED || s.log_on) {
-        const float4 a = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int nc = cell_key(g, p.x, p.y, p.z);
-        skin_features(s, p, v, a, r, g, q, row_live_warp(s, i), step - s.born[i],
-                      s.cell_live[nc], f);
+    const float prop =
+        s.skin_kind == LVB_SKIN_LEARNED ? mlp_skin(s.mlp, y, __fmul_rn(2.0f, r), f[0]) : 0.0f;
+    const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
+    const float4 qn = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
+    s.ref[i] = make_float4(p.x, p.y, p.z, sk);
+    s.born[i] = step;
+    s.fref[k] = qn;
+    s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
+    if (s.sc_cnt) {
+        const int sc = s.scene_of[i];
+        const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
+        s.sfid[slot] = i;
+        s.sfref[slot] = qn;
     }
-    const float sk = warp_skin(s, g, r, v, f);
-    if (lane == 0) {
-        const float4 qn = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
-        s.ref[i] = make_float4(p.x, p.y, p.z, sk);
-        s.born[i] = step;
-        s.fref[k] = qn;
-        s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
-        if (s.sc_cnt) {
-            const int sc = s.scene_of[i];
-            const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
-            s.sfid[slot] = i;
-            s.sfref[slot] = qn;
-        }
-        if (s.log_on && s.lg_t[i] < 0) {
-            s.lg_t[i] = step;
-            s.lg_x[i] = p;
-            s.lg_m[i] = 0.0f;
+    if (s.log_on && s.lg_t[i] < 0) {
+        s.lg_t[i] = step;
+        s.lg_x[i] = p;
+        s.lg_m[i] = 0.0f;
 #pragma unroll
-            for (int t = 0; t < LVB_MLP_IN; ++t) s.lg_feat[(long long)i * LVB_MLP_IN + t] = f[t];
-        }
+        for (int t = 0; t < LVB_MLP_IN; ++t) s.lg_feat[(long long)i * LVB_MLP_IN + t] = f[t];
     }
 }
 
 // a2 for up to 32 flagged particles at once, one per lane (lane t takes
-// particle id[t], list index k0 + t, t < m): the same update as update_warp for
-// the policies that need neither the network nor the rebuild log, with all
-// the lanes' loads in flight together.
+// particle id[t], list index k0 + t, t < m), inside the check pass: the same
+// update as update_group for the policies that need neither the network
+// nor the rebuild log.
 static __device__ __noinline__ void update_lanes(const DevState &s, const int *id, int k0, int m,
                                                  const float4 *pos, const float4 *vel, int step)
 {
@@ -1239,14 +1259,17 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
 }
 
 // The deferred a2 (deferred_update) for the nF flagged particles of the
-// step, one warp per particle, items spread over the blocks first as in
-// partial_pass; list index k keeps the check's order.
+// step: each warp takes groups of c = ceil(nF / warps) <= 32 consecutive
+// list entries (update_group), the groups spread over the blocks first as
+// in partial_pass.
 static __device__ __noinline__ void update_pass(const DevState &s, int nF, const float4 *pos,
                                                 const float4 *vel, const float4 *acc, int step)
 {
     const int w0 = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int k = w0; k < nF; k += nw) update_warp(s, s.fid[k], k, pos, vel, acc, step);
+    const int c = min(32, (nF + nw - 1) / nw);
+    for (long long k0 = (long long)w0 * c; k0 < nF; k0 += (long long)nw * c)
+        update_group(s, (int)k0, min(c, nF - (int)k0), pos, vel, acc, step);
 }
 
 // The rebuild of a partial step (nF flagged).  Up to s.direct_max
