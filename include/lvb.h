@@ -87,7 +87,8 @@ typedef struct {
     float value;         /* s_g [m], alpha [-] or K [steps], by kind */
     float dt;            /* time step for LVB_SKIN_PAPER_KVDT [s] */
     const void *mlp;     /* LVB_SKIN_LEARNED: device pointer to packed
-                            weights (lvb_mlp.h layout); else NULL */
+                            weights (lvb_mlp.h layout), 16-byte aligned;
+                            else NULL */
 } lvb_skin_policy;
 
 typedef struct {

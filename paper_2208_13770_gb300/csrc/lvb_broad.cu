@@ -743,7 +743,8 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (trigger == LVB_TRIGGER_GLOBAL && nscenes > 1) return LVB_EINVAL;
     if (skin->kind < LVB_SKIN_GLOBAL || skin->kind > LVB_SKIN_LEARNED) return LVB_EINVAL;
     if (skin->kind == LVB_SKIN_LEARNED &&
-        (!skin->mlp || !vel || !acc || trigger != LVB_TRIGGER_PARTIAL || !(skin->dt > 0.0f)))
+        (!skin->mlp || !aligned16(skin->mlp) || !vel || !acc ||
+         trigger != LVB_TRIGGER_PARTIAL || !(skin->dt > 0.0f)))
         return LVB_EINVAL;
     if (acc && !aligned16(acc)) return LVB_EINVAL;
     if (!(skin->value >= 0.0f) || !std::isfinite(skin->value)) return LVB_EINVAL;

@@ -192,6 +192,29 @@ __device__ __forceinline__ float warp_skin(const DevState &s, const SceneGeom &g
 }
 
 
+// The network's weights in shared memory for the step: copied
+// asynchronously (16-byte cp.async pieces) when the kernel starts, so the
+// copy runs under the check pass; the issuing threads wait for their pieces
+// before the first grid barrier, whose block barrier then publishes them.
+static_assert(sizeof(lvb_mlp_weights) % 16 == 0, "weights are copied in 16-byte pieces");
+
+__device__ __forceinline__ void weights_copy_async(lvb_mlp_weights *dst,
+                                                   const lvb_mlp_weights *src)
+{
+    const char *g = reinterpret_cast<const char *>(src);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    for (int t = threadIdx.x; t < (int)(sizeof(lvb_mlp_weights) / 16); t += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * t),
+                     "l"(g + 16 * t)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void weights_copy_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Live partners of row i (entries >= 0), counted by one lane.
 __device__ __forceinline__ int row_live_lane(const DevState &s, int i)
 {
@@ -211,9 +234,9 @@ __device__ __forceinline__ int row_live_lane(const DevState &s, int i)
 // position and skin, kept with the old state at its list index.  (pos and
 // vel may have been written earlier in the same kernel by the DEM position
 // half-step, so they are read through plain coherent loads.)
-__device__ __forceinline__ void update_group(const DevState &s, int k0, int m,
-                                                 const float4 *pos, const float4 *vel,
-                                                 const float4 *acc, int step)
+__device__ __forceinline__ void update_group(const DevState &s, const lvb_mlp_weights *W, int k0,
+                                             int m, const float4 *pos, const float4 *vel,
+                                             const float4 *acc, int step)
 {
     const int lane = threadIdx.x & 31;
     const bool act = lane < m;
@@ -235,7 +258,7 @@ __device__ __forceinline__ void update_group(const DevState &s, int k0, int m,
             float ft[LVB_MLP_IN];
 #pragma unroll
             for (int k = 0; k < LVB_MLP_IN; ++k) ft[k] = __shfl_sync(FULL, f[k], t);
-            const float yt = mlp_y_warp(s.mlp, ft);
+            const float yt = mlp_y_warp(W, ft);
             if (lane == t) y = yt;
         }
     }
@@ -249,7 +272,7 @@ __device__ __forceinline__ void update_group(const DevState &s, int k0, int m,
     const float4 q = s.ref[i];
     const SceneGeom &g = geom_of(s, i);
     const float prop =
-        s.skin_kind == LVB_SKIN_LEARNED ? mlp_skin(s.mlp, y, __fmul_rn(2.0f, r), f[0]) : 0.0f;
+        s.skin_kind == LVB_SKIN_LEARNED ? mlp_skin(W, y, __fmul_rn(2.0f, r), f[0]) : 0.0f;
     const float sk = skin_of(s.skin_kind, s.skin_value, s.skin_dt, g.H, r, v, prop);
     const float4 qn = make_float4(p.x, p.y, p.z, __fadd_rn(r, sk));
     s.ref[i] = make_float4(p.x, p.y, p.z, sk);
@@ -1262,14 +1285,15 @@ __device__ __forceinline__ void trace_add(DevCounters *c, int slot, unsigned lon
 // step: each warp takes groups of c = ceil(nF / warps) <= 32 consecutive
 // list entries (update_group), the groups spread over the blocks first as
 // in partial_pass.
-static __device__ __noinline__ void update_pass(const DevState &s, int nF, const float4 *pos,
-                                                const float4 *vel, const float4 *acc, int step)
+static __device__ __noinline__ void update_pass(const DevState &s, const lvb_mlp_weights *W,
+                                                int nF, const float4 *pos, const float4 *vel,
+                                                const float4 *acc, int step)
 {
     const int w0 = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int c = min(32, (nF + nw - 1) / nw);
     for (long long k0 = (long long)w0 * c; k0 < nF; k0 += (long long)nw * c)
-        update_group(s, (int)k0, min(c, nF - (int)k0), pos, vel, acc, step);
+        update_group(s, W, (int)k0, min(c, nF - (int)k0), pos, vel, acc, step);
 }
 
 // The rebuild of a partial step (nF flagged).  Up to s.direct_max
@@ -1333,6 +1357,9 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     if (err & DERR_SYNC) return;   // a barrier failed earlier: the context is unusable
     const bool inc = s.trigger == LVB_TRIGGER_PARTIAL && !(err & DERR_STORE);
     const int step = (int)c->steps + 1, par = step & 1;
+    __shared__ __align__(16) lvb_mlp_weights w_sh;
+    const bool net = s.skin_kind == LVB_SKIN_LEARNED;
+    if (net) weights_copy_async(&w_sh, s.mlp);
     grid_barrier_begin(s, par);
     const float4 *pos = kFused ? ia.pos : pos_in;
     int *ovf = &c->ovf[par];
@@ -1341,6 +1368,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         check_pass_fused(s, vel, acc, ia, inc, step, &c->nF_acc[par]);
     else
         check_pass_stream(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
+    if (net) weights_copy_wait();
     if (!grid_barrier(s)) return;
     const int nF = *(volatile int *)&c->nF_acc[par];
     if (s.sc_cnt && blockIdx.x == 0)   // the next step's scene counters
@@ -1380,7 +1408,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     if (inc) {
         if (nF > 0) {
             if (deferred_update(s)) {
-                update_pass(s, nF, pos, vel, acc, step);
+                update_pass(s, &w_sh, nF, pos, vel, acc, step);
                 if (!grid_barrier(s)) return;
             }
             if (!partial_pass(s, nF, par, ovf)) return;

@@ -62,10 +62,10 @@ def test_argument_checks_without_gpu():
     box = lvb.lvb_box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
     skin = lvb.lvb_skin_policy(lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, 1e-5, None)
 
-    def init(n=8, ptr=p, b=box, s=skin, trigger=0, cf=1.25, vel=None):
+    def init(n=8, ptr=p, b=box, s=skin, trigger=0, cf=1.25, vel=None, acc=None):
         ctx = lvb.ctypes.c_void_p()
         return lvb._lib.lvb_init(lvb.ctypes.byref(ctx), n, ptr, lvb.ctypes.byref(b),
-                                 lvb.ctypes.byref(s), trigger, cf, vel, None, None)
+                                 lvb.ctypes.byref(s), trigger, cf, vel, acc, None)
 
     E = lvb.LVB_EINVAL
     assert init(n=0) == E                      # empty
@@ -84,6 +84,9 @@ def test_argument_checks_without_gpu():
     assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_PAPER_KVDT, 200.0, 0.0, None), vel=p) == E
     # the network needs weights, velocities and accelerations
     assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_LEARNED, 0.0, 1e-5, None), vel=p) == E
+    # ... and 16-byte aligned weights (the step kernel copies them in pieces)
+    assert init(s=lvb.lvb_skin_policy(lvb.LVB_SKIN_LEARNED, 0.0, 1e-5, p + 8), vel=p,
+                acc=p) == E
     # the network's weights: a bad output range or travel step count
     prm = np.zeros(lvb.LVB_MLP_PARAMS, np.float32)
     one = np.ones(lvb.LVB_MLP_IN, np.float32)
