@@ -205,8 +205,8 @@ BATCH_STEPS = 2000
 # one ncu capture of the current kernel on each workload (mean of two
 # launches; the command and the counters are in profiles/).  They go stale
 # when the kernel changes: set them to None until the capture is repeated.
-NCU_TRAFFIC_SETTLING = 6.77e6      # profiles/k_step_settling200k_ncu.txt
-NCU_TRAFFIC_BATCHED = 213.7e6      # profiles/k_step_batched512_ncu.txt
+NCU_TRAFFIC_SETTLING = None      # profiles/k_step_settling200k_ncu.txt (re-capture pending)
+NCU_TRAFFIC_BATCHED = None      # profiles/k_step_batched512_ncu.txt (re-capture pending)
 
 
 def _narrow_phase(n, entries, ms, hbm_peak):
@@ -299,7 +299,8 @@ def _batched(lvb, torch, hbm_peak, warmup):
 
 LEARN_N = 1_000_000
 LEARN_H = 400           # horizon of the rebuild-log labels, and K of the paper's rule
-LEARN_MARGIN = 1.3      # labels scaled by this margin before training
+LEARN_MARGIN = 2.0      # labels scaled by this margin before training
+LEARN_CLIP = 0.99       # labels clipped at this quantile
 LEARN_STEPS = 1500      # steps of the logged training run and of each timed run
 LEARN_LOSS = "squared"   # training loss: squared error of the label (or "relative")
 
@@ -340,11 +341,18 @@ def _timed_advance(lvb, torch, scene, kind, value, mlp=None, log=None, steps=LEA
 
 
 def _train_skin(lvb, torch, samples, seed):
-    """Network weights trained on the GPU on rebuild-log samples (labels
-    scaled by LEARN_MARGIN); returns (device weights, info)."""
+    """Network weights trained on the GPU on rebuild-log samples, for the
+    travel form of the output over LEARN_H steps (skin = y LEARN_H |v| dt,
+    a per-particle factor of the paper's rule): each label (largest
+    displacement over the horizon, in diameters) becomes label /
+    (f0 LEARN_H) -- the displacement in units of the particle's travel over
+    the horizon at its speed when updated -- scaled by LEARN_MARGIN and
+    clipped at the LEARN_CLIP quantile; samples of particles at rest are
+    left out.  Returns (device weights, info)."""
     import time
-    smp = np.ascontiguousarray(samples).copy()
-    smp[:, 8] *= np.float32(LEARN_MARGIN)
+    smp = np.ascontiguousarray(samples[samples[:, 0] > 0]).copy()
+    y = smp[:, 8].astype(np.float64) * LEARN_MARGIN / (smp[:, 0].astype(np.float64) * LEARN_H)
+    smp[:, 8] = np.minimum(y, np.quantile(y, LEARN_CLIP)).astype(np.float32)
     rng = np.random.default_rng(seed)
     p0 = (rng.standard_normal(lvb.LVB_MLP_PARAMS) * 0.1).astype(np.float32)
     yr = np.zeros(2, np.float32)
@@ -356,8 +364,8 @@ def _train_skin(lvb, torch, samples, seed):
     info = {"samples": int(len(smp)), "epochs": 20, "loss": LEARN_LOSS,
             "loss_first": float(losses[0]),
             "loss_last": float(losses[-1]), "seconds": time.time() - t0,
-            "y_range": [float(yr[0]), float(yr[1])]}
-    return lvb.mlp_weights_device(p, mu, isd, yr), info
+            "y_range": [float(yr[0]), float(yr[1])], "y_steps": LEARN_H}
+    return lvb.mlp_weights_device(p, mu, isd, yr, float(LEARN_H)), info
 
 
 def _learned(lvb, torch):
@@ -395,8 +403,11 @@ def _learned(lvb, torch):
         "workload": "drum R 0.3 m x 0.1 m, %d lognormal spheres (median 1 mm, sigma_ln 0.35), "
                     "10 rpm, dt 1e-6 s, %d steps per run" % (sc.n, LEARN_STEPS),
         "training": {"source": "plain local buffer (0.1 d_i), then the network's own run",
-                     "label": "largest displacement over the next %d steps / d, x %.1f"
-                              % (LEARN_H, LEARN_MARGIN),
+                     "output": "travel form: skin = y * %d |v| dt (y clamped to its "
+                               "range), a per-particle K = %d y of the paper's rule" % (LEARN_H, LEARN_H),
+                     "label": "largest displacement over the next %d steps / (%d |v| dt), "
+                              "x %.1f, clipped at the %.2f quantile"
+                              % (LEARN_H, LEARN_H, LEARN_MARGIN, LEARN_CLIP),
                      "selection": "fastest of 3 weight draws x 2 training stages on this "
                                   "scene",
                      "last_stage1": info1, "last_stage2": info2},
