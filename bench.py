@@ -205,8 +205,8 @@ BATCH_STEPS = 2000
 # one ncu capture of the current kernel on each workload (mean of two
 # launches; the command and the counters are in profiles/).  They go stale
 # when the kernel changes: set them to None until the capture is repeated.
-NCU_TRAFFIC_SETTLING = None      # profiles/k_step_settling200k_ncu.txt (re-capture pending)
-NCU_TRAFFIC_BATCHED = None      # profiles/k_step_batched512_ncu.txt (re-capture pending)
+NCU_TRAFFIC_SETTLING = 7.18e6      # profiles/k_step_settling200k_ncu.txt
+NCU_TRAFFIC_BATCHED = 210.4e6      # profiles/k_step_batched512_ncu.txt
 
 
 def _narrow_phase(n, entries, ms, hbm_peak):
