@@ -67,6 +67,49 @@ def test_one_path_network_closed_form():
     assert np.array_equal(skin3, (d * np.float32(0.3)).astype(np.float32))
 
 
+def test_bfloat16_roundings_closed_form():
+    # three one-path units whose sums are not bfloat16 numbers, so that each
+    # rounding of the inference formula (z, h1, h2) changes y; by hand,
+    # with u = 1 + 3 * 2^-9 (bfloat16 neighbours 1 and 1 + 2^-7, u nearer
+    # the upper one):
+    #   unit 0: a1 = 1 * 1 + 3*2^-9 = u -> h1 = 1 + 2^-7; a2 = h1 - 1 = 2^-7
+    #   unit 1: h1 = 1; a2 = h1 + 3*2^-9 = u -> h2 = 1 + 2^-7
+    #   unit 2: z = bf16(u) = 1 + 2^-7; a1 = z - 1 = 2^-7 = h1 = h2
+    #   y = ((-1 + 2^-7) + (1 + 2^-7)) + 2^-7 = 3 * 2^-7 (exact)
+    u = 1 + 3 * 2.0 ** -9
+    W1 = np.zeros((mlp.N_H, mlp.N_IN), np.float32)
+    W1[0, 0] = W1[1, 0] = W1[2, 1] = 1.0
+    b1 = np.zeros(mlp.N_H, np.float32)
+    b1[0], b1[2] = 3 * 2.0 ** -9, -1.0
+    W2 = np.zeros((mlp.N_H, mlp.N_H), np.float32)
+    W2[0, 0] = W2[1, 1] = W2[2, 2] = 1.0
+    b2 = np.zeros(mlp.N_H, np.float32)
+    b2[0], b2[1] = -1.0, 3 * 2.0 ** -9
+    w3 = np.zeros(mlp.N_H, np.float32)
+    w3[:3] = 1.0
+    W = mlp.Weights(W1, b1, W2, b2, w3, -1.0, np.zeros(mlp.N_IN), np.ones(mlp.N_IN))
+    f = np.zeros((1, mlp.N_IN), np.float32)
+    f[0, 0], f[0, 1] = 1.0, u
+    _, y = mlp.infer(W, f, np.ones(1, np.float32))
+    assert y[0] == np.float32(3 * 2.0 ** -7)
+    # the training forward pass (binary64 sums, same roundings) agrees here
+    y64, _ = mlp.forward64(W, f, quantize=True)
+    assert y64[0] == 3 * 2.0 ** -7
+
+
+def test_training_forward_matches_inference():
+    # the binary64 training forward with the bfloat16 roundings evaluates
+    # the same network as the binary32 inference formula: equal up to the
+    # sums' roundings (which may move a hidden value by one bfloat16 step)
+    rng = np.random.default_rng(21)
+    W = mlp.Weights.random(seed=22, scale=0.5)
+    f = rng.normal(0, 1, (3000, mlp.N_IN)).astype(np.float32)
+    _, y = mlp.infer(W, f, np.ones(len(f), np.float32))
+    y64, _ = mlp.forward64(W, f, quantize=True)
+    d = np.abs(y64 - y.astype(np.float64)) / (np.abs(y64) + 1e-3)
+    assert np.median(d) < 1e-6 and np.quantile(d, 0.99) < 1e-2
+
+
 def test_travel_form_is_the_paper_rule_per_particle():
     # a network with constant output c in the travel form over S steps
     # proposes skin = d (f0 (c S)) with f0 = (|v| dt) / d: the paper's rule
