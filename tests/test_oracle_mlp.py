@@ -195,3 +195,75 @@ def test_relative_loss_special_cases():
     lr, gr = mlp.loss_and_grad64(W, f, lo, quantize=True, rel_floor=0.125)
     assert lr == pytest.approx(l2 / 0.125 ** 2, rel=1e-12)
     assert np.allclose(gr, g2 / 0.125 ** 2, rtol=1e-12, atol=0)
+
+
+def test_features_closed_form():
+    # one particle with representable values, the eight features by hand:
+    # r = 2^-8 (d = 2^-7), v = (3, 4, 0) (|v| = 5), a = (0, 0, -8), dt = 2^-10,
+    # moved by (3, 4, 0) 2^-12 from its old reference (skin 2^-9), in the box
+    # [0, 1]^3 at (1/4, 1/2, 1/8), H = 2^-6
+    pos = np.array([[0.25, 0.5, 0.125, 2.0 ** -8]], np.float32)
+    vel = np.array([[3.0, 4.0, 0.0, 0.0]], np.float32)
+    acc = np.array([[0.0, 0.0, -8.0, 0.0]], np.float32)
+    ref_old = np.array([[0.25 - 3 * 2.0 ** -12, 0.5 - 4 * 2.0 ** -12, 0.125, 2.0 ** -9]],
+                       np.float32)
+    grid = {"lo": np.zeros(3, np.float32), "hi": np.ones(3, np.float32),
+            "H": np.float32(2.0 ** -6)}
+    f = mlp.features(pos, vel, acc, 2.0 ** -10, grid, ref_old, [7], [12], [3])[0]
+    want = [5 * 2.0 ** -10 / 2.0 ** -7,          # f0 = |v| dt / d = 5/8
+            8 * 2.0 ** -20 / 2.0 ** -7,          # f1 = |a| dt^2 / d = 2^-10
+            2.0 ** -8 / 2.0 ** -6,               # f2 = r / H = 1/4
+            7, 12,                               # f3 partners, f4 age
+            5 * 2.0 ** -12 / 2.0 ** -9,          # f5 = travel / old skin = 5/8
+            3,                                   # f6 occupancy
+            (0.125 - 2.0 ** -8) / 2.0 ** -7]     # f7 = nearest wall gap / d = 15.5
+    assert np.array_equal(f, np.array(want, np.float32))
+    # no old skin: f5 = 0
+    ref0 = ref_old.copy()
+    ref0[0, 3] = 0
+    assert mlp.features(pos, vel, acc, 2.0 ** -10, grid, ref0, [7], [12], [3])[0][5] == 0
+
+
+def test_state_machine_learned_feature_counts():
+    # a learned context of five particles (r = 1 mm, skin 0.1 d from a
+    # constant network): A (index 2) at the middle of cell (4, 4, 4),
+    # partners B, C (lower indices) and E within the cutoff 2 (r + skin) =
+    # 2.4 mm of it and of no other (B-C 3.1 mm, B-E 3.3 mm, C-E 2.6 mm), D
+    # far away; E's reference lies in A's cell, 0.1 mm above its lower x
+    # face.  At step 1, A moves 0.3 mm (> its 0.2 mm skin) and E 0.15 mm
+    # (< its skin) across that face into cell 3; A moves 0.3 mm again at
+    # step 3.  A's features then count, from the state before its update: 3
+    # live partners (B, C, E), 2 reference positions in the cell of its new
+    # position (its own and E's, whose current position has left it), and
+    # the steps since its last update (1, then 2)
+    from oracle.statemachine import OracleLVB
+    import oracle
+    lo, hi = (0.0, 0.0, 0.0), (0.1, 0.1, 0.1)
+    grid = mlp.grid_params(1e-3, 1.25, lo, hi)
+    L = 1.0 / float(grid["invL"])
+    a = 4.5 * L
+    pos = np.array([[a + 2.1e-3, a, a], [a, a + 2.3e-3, a], [a, a, a], [0.05, 0.05, 0.05],
+                    [4 * L + 0.1e-3, a, a]])
+    pos4 = np.concatenate([pos, np.full((5, 1), 1e-3)], axis=1).astype(np.float32)
+    p = np.zeros(mlp.N_PARAMS, np.float32)
+    p[-1] = 0.1
+    W = mlp.Weights.from_flat(p, np.zeros(mlp.N_IN), np.ones(mlp.N_IN))
+    z4 = np.zeros_like(pos4)
+    sm = OracleLVB(pos4, oracle.SKIN_LEARNED, 0.0, 1e-6, grid["H"], 0, vel4=z4,
+                   learned={"weights": W, "grid": grid}, acc4=z4)
+    assert np.allclose(sm.ref[:, 3], 2e-4, rtol=1e-6)
+    assert set(zip(sm.pi.tolist(), sm.pj.tolist())) == {(0, 2), (1, 2), (2, 4)}
+    p1 = pos4.copy()
+    p1[2, 0] += np.float32(3e-4)
+    p1[4, 0] -= np.float32(1.5e-4)
+    f, _ = sm.step(p1, vel4=z4, acc4=z4)
+    assert f.tolist() == [False, False, True, False, False]
+    idx, feats = sm.last_features
+    assert idx.tolist() == [2] and feats[0, 3] == 3 and feats[0, 4] == 1 and feats[0, 6] == 2
+    sm.step(p1, vel4=z4, acc4=z4)                # nothing moves: no update
+    p3 = p1.copy()
+    p3[2, 0] += np.float32(3e-4)
+    f, _ = sm.step(p3, vel4=z4, acc4=z4)
+    idx, feats = sm.last_features
+    assert f.tolist() == [False, False, True, False, False] and idx.tolist() == [2]
+    assert feats[0, 3] == 3 and feats[0, 4] == 2 and feats[0, 6] == 2

@@ -48,6 +48,24 @@ MUTANTS = {
     "gW2_transposed": ("gW2 = dh2.T @ h1", "gW2 = h1.T @ dh2"),
     "rel_floor_ignored": ("w = 1.0 / np.maximum(t, float(np.float32(rel_floor))) ** 2",
                           "w = 1.0 / t ** 2"),
+    # features: the speed feature from the acceleration, one dt too few,
+    # the wall gap without the radius, the travel over the new skin
+    "f0_from_acc": ("f[:, 0] = ((_norm3(vel4) * dt)", "f[:, 0] = ((_norm3(acc4) * dt)"),
+    "f1_one_dt": ("f[:, 1] = ((((_norm3(acc4) * dt).astype(np.float32)) * dt).astype(np.float32) / d)",
+                  "f[:, 1] = (((_norm3(acc4) * dt).astype(np.float32)) / d)"),
+    "f7_gap_without_radius": ("lo_gap = ((pos4[:, k] - grid[\"lo\"][k]).astype(np.float32) - r)",
+                              "lo_gap = ((pos4[:, k] - grid[\"lo\"][k]).astype(np.float32) - 0)"),
+}
+
+# the learned state machine: partners counted on one side of the pair list
+# only, occupancy from current instead of reference positions, age off by one
+SM_SRC = os.path.join(os.path.dirname(oracle.__file__), "statemachine.py")
+SM_MUTANTS = {
+    "nrow_one_side": ("np.bincount(np.concatenate([self.pi, self.pj]), minlength=self.n)",
+                      "np.bincount(self.pi, minlength=self.n)"),
+    "occ_from_positions": ("mlp.cell_index(self.ref[:, :3], grid)",
+                           "mlp.cell_index(pos4[:, :3], grid)"),
+    "age_off_by_one": ("step - self.born[idx], occ)", "step - 1 - self.born[idx], occ)"),
 }
 
 
@@ -70,6 +88,8 @@ def _pins():
         lambda: P.test_backward_matches_finite_differences(0.0),
         lambda: P.test_backward_matches_finite_differences(0.15),
         P.test_relative_loss_special_cases,
+        P.test_features_closed_form,
+        P.test_state_machine_learned_feature_counts,
     ]
     for c in checks:
         try:
@@ -91,3 +111,17 @@ def test_mutant_is_caught(monkeypatch, name):
 def test_unmutated_passes_pins(monkeypatch):
     monkeypatch.setattr(P, "mlp", _load(open(SRC).read(), "none"))
     assert _pins()
+
+
+@pytest.mark.parametrize("name", sorted(SM_MUTANTS))
+def test_state_machine_mutant_is_caught(monkeypatch, name):
+    import oracle.statemachine as SM
+    before, after = SM_MUTANTS[name]
+    src = open(SM_SRC).read()
+    assert src.count(before) == 1, name
+    mod = types.ModuleType("oracle.statemachine_mutant_" + name)
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(before, after), "<state machine mutant %s>" % name, "exec"),
+         mod.__dict__)
+    monkeypatch.setattr(SM, "OracleLVB", mod.OracleLVB)
+    assert not _pins(), "mutant %s survived the pins" % name
