@@ -152,6 +152,35 @@ def test_flags_partial_updates_repeat_with_period(orc):
     assert [i + 1 for i, x in enumerate(hist) if x] == [4, 8, 12, 16]
 
 
+def test_trigger_modes_update_sets(orc):
+    # the same two particles as above (one moving 2^-20 a step with a skin
+    # of 3.5 steps, one static) under the three triggers: the local buffer
+    # updates the violating particle alone; the global one (Def. autoverlet)
+    # updates both whenever one violates, so the static particle's skin is
+    # reset too; with no buffer every particle is updated every step
+    from oracle.statemachine import OracleLVB, TRIGGER_PARTIAL, TRIGGER_GLOBAL, TRIGGER_ALWAYS
+    h = np.float32(2.0 ** -20)
+    pos = np.array([[0.5, 0.25, 0.25, 1e-3], [0.25, 0.5, 0.25, 1e-3]], dtype=np.float32)
+    got = {}
+    for trig in (TRIGGER_PARTIAL, TRIGGER_GLOBAL, TRIGGER_ALWAYS):
+        sm = OracleLVB(pos, 0, 3.5 * h, 0.0, np.float32(1.0), trig)
+        rows = []
+        for step in range(1, 9):
+            p = pos.copy()
+            p[0, 0] = np.float32(0.5) + np.float32(step) * h
+            f, upd = sm.step(p)
+            rows.append((f.tolist(), upd.tolist()))
+        got[trig] = (rows, sm.updates, sm.rebuild_steps)
+    rows, upd_total, rb = got[TRIGGER_PARTIAL]
+    assert [r[1] for r in rows] == [[k in (4, 8), False] for k in range(1, 9)]
+    assert (upd_total, rb) == (2, 2)
+    rows, upd_total, rb = got[TRIGGER_GLOBAL]
+    assert [r[1] for r in rows] == [[k in (4, 8)] * 2 for k in range(1, 9)]
+    assert (upd_total, rb) == (4, 2)
+    rows, upd_total, rb = got[TRIGGER_ALWAYS]
+    assert all(r[1] == [True, True] for r in rows) and (upd_total, rb) == (16, 8)
+
+
 def test_flags_k_zero_is_every_step(orc):
     # K = 0 in skin = K |v| dt: every moving particle is flagged every step
     from oracle.statemachine import OracleLVB, TRIGGER_PARTIAL

@@ -61,3 +61,30 @@ def test_mutant_is_caught(orc, tmp_path, name):
 
 def test_unmutated_passes_pins(orc):
     assert _pins(orc)
+
+
+# the state machine's triggers: the global buffer updating only the
+# violating particles, the no-buffer mode updating only on a violation
+SM_SRC = os.path.join(os.path.dirname(oracle.__file__), "statemachine.py")
+SM_MUTANTS = {
+    "global_updates_flagged_only": ("upd = np.full(self.n, bool(f.any()))", "upd = f.copy()"),
+    "always_only_on_violation": ("            upd = np.ones(self.n, dtype=bool)",
+                                 "            upd = np.full(self.n, bool(f.any()))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SM_MUTANTS))
+def test_state_machine_trigger_mutant_is_caught(orc, monkeypatch, name):
+    import types
+    import oracle.statemachine as SM
+    import tests.test_oracle_broadphase as B
+    before, after = SM_MUTANTS[name]
+    src = open(SM_SRC).read()
+    assert src.count(before) == 1, name
+    mod = types.ModuleType("oracle.statemachine_mutant_" + name)
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(before, after), "<state machine mutant %s>" % name, "exec"),
+         mod.__dict__)
+    monkeypatch.setattr(SM, "OracleLVB", mod.OracleLVB)
+    with pytest.raises(AssertionError):
+        B.test_trigger_modes_update_sets(orc)
