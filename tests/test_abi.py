@@ -101,6 +101,18 @@ def test_argument_checks_without_gpu():
     assert pack(steps=-1.0) == E
     assert pack(steps=float("nan")) == E
     assert pack(steps=float("inf")) == E
+    # inference, gradient and training entry points: null buffers, negative
+    # or empty sample counts, a negative relative floor, a bad loss kind
+    buf = np.zeros(64, np.float32).ctypes.data
+    dbl = lvb.ctypes.byref(lvb.ctypes.c_double(0.0))
+    L = lvb._lib
+    assert L.lvb_mlp_infer(None, buf, 4, buf, buf, None, None) == E
+    assert L.lvb_mlp_infer(buf, buf, -1, buf, buf, None, None) == E
+    assert L.lvb_mlp_grad(buf, 0, buf, buf, buf, 0.0, buf, dbl, None) == E
+    assert L.lvb_mlp_grad(buf, 4, buf, buf, buf, -1.0, buf, dbl, None) == E
+    assert L.lvb_mlp_grad(buf, 4, None, buf, buf, 0.0, buf, dbl, None) == E
+    assert L.lvb_mlp_train(buf, 0, 1, 8, 1e-3, 1, 0, buf, buf, buf, buf, buf, None) == E
+    assert L.lvb_mlp_train(buf, 4, 1, 8, 1e-3, 1, 7, buf, buf, buf, buf, buf, None) == E
     assert lvb._lib.lvb_step(None, p, None, None) == E
     assert lvb._lib.lvb_step_host(None, p, None, None, None, None) == E
     assert lvb._lib.lvb_sync(None) == E
