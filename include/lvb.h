@@ -117,7 +117,15 @@ typedef struct {
     int64_t block_threads;   /* threads per block of the step kernel */
     int64_t compaction;      /* LVB_COMPACT_* in use */
     int64_t n_scenes;        /* independent scenes in the context */
-    int64_t reserved[4];
+    /* work of the partial rebuilds so far (PARTIAL trigger), the counts
+     * behind the algorithmic bytes of a step: */
+    int64_t rebuild_candidates; /* stencil candidates read (cell slot id +
+                                   reference record each) */
+    int64_t rebuild_direct;  /* flagged-list records read by the direct test
+                                of the flagged particles against each other */
+    int64_t rebuild_edits;   /* edits of unflagged particles' rows (a pair
+                                removed or inserted) */
+    int64_t reserved[1];
     float cell_edge;         /* L [m] (scene 0) */
     float rnl_max;           /* cap H on R_NL = r + skin [m] (scene 0) */
     int32_t grid[3];         /* cells per axis (scene 0) */
@@ -196,6 +204,20 @@ int lvb_scene_info(lvb_ctx *ctx, int32_t scene, lvb_scene_info_t *out);
 int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *ref4,
                     const lvb_box *box, const lvb_skin_policy *skin, int32_t trigger,
                     float cell_factor, const float *vel, const float *acc, void *stream);
+
+/*
+ * lvb_batch_init_resume -- lvb_batch_init with every particle's reference
+ * state taken from ref4 (device float4 (xref, yref, zref, skin), n records,
+ * e.g. saved by lvb_get_ref of a batched context), as lvb_init_resume does
+ * for one scene: the list of each scene is built on those references, so a
+ * batched run resumes where the saved context stood.  Same checks as
+ * lvb_init_resume (each skin within the cap of its own scene, else
+ * LVB_EINVAL) and as lvb_batch_init.
+ */
+int lvb_batch_init_resume(lvb_ctx **out, int32_t n_scenes, const int64_t *offsets,
+                          const float *pos_r, const float *ref4, const lvb_box *boxes,
+                          const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
+                          const float *vel, const float *acc, void *stream);
 
 /*
  * lvb_step -- one step of the automatic Verlet update at the positions

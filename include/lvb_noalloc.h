@@ -30,9 +30,10 @@ extern "C" {
 /*
  * lvb_pairs_noalloc -- every pair i < j with
  *   |xref_i - xref_j|^2 <= (R_NL,i + R_NL,j)^2,   R_NL = r + skin
- * (Def. verletlist on the reference positions, evaluated in binary32 as
- * lvb.h states), i.e. the pair set that lvb_get_pairs_ij returns for a
- * context holding the same reference state, in no particular order.
+ * on the reference positions, each sum, difference and product rounded to
+ * binary32 in the order lvb.h gives (no fused multiply-add), i.e. the pair
+ * set that lvb_get_pairs_ij returns for a context holding the same
+ * reference state, in no particular order.
  *
  *   n       : number of particles, 1 <= n <= LVB_NOALLOC_MAX_N.
  *   pos4    : device, n float4 records (x, y, z, r); only r is read.
@@ -54,6 +55,9 @@ extern "C" {
  * n > LVB_NOALLOC_MAX_N (nothing is launched); LVB_EINVAL for NULL or
  * misaligned pointers, n < 1, cap < 0, a bad box, r <= 0 or skin < 0;
  * LVB_ENAN for a non-finite input; LVB_EDEVICE when a CUDA call fails.
+ * An error of the caller's own earlier CUDA work that the caller has not
+ * yet read (cudaGetLastError) is left in place: this call reads the status
+ * of each of its own launches and copies directly.
  *
  * No memory is allocated -- no cudaMalloc, cudaFree or allocating library
  * call, on the device or the host.  The first call on a device does a

@@ -29,12 +29,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (binary32 arithmetic without contraction)."""
+    """Compile the oracle with gcc (binary32 arithmetic without contraction),
+    with OpenMP where the compiler has it (the flag test and the pair search
+    then use several host threads; the results do not depend on how many)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
-               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.check_call(cmd)
+        base = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
+                "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.call(base + ["-fopenmp"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -89,6 +92,10 @@ def _configure(L):
         L.orc_dem_step64.restype = ctypes.c_int
         L.orc_improvement_pct.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_improvement_pct.restype = ctypes.c_double
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = None
+        L.orc_threads.argtypes = []
+        L.orc_threads.restype = ctypes.c_int
     return L
 
 
@@ -118,6 +125,17 @@ class use_library:
         global _lib
         _lib = self.saved
         return False
+
+
+def set_threads(t):
+    """Host threads of the flag test and the pair search (t <= 0: all
+    processors)."""
+    lib().orc_set_threads(int(t))
+
+
+def threads():
+    """Host threads the oracle's parallel loops use (1 without OpenMP)."""
+    return int(lib().orc_threads())
 
 
 def _f32x4(a):

@@ -35,8 +35,45 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------ */
+/* Threads.  When built with OpenMP the flag test and the linked-cell   */
+/* pair search split their loops over particles / cells across host    */
+/* threads; every result is the same set in the same (sorted) order     */
+/* whatever the thread count, since each decision is the fixed formula  */
+/* on one particle or one pair.                                         */
+/* ------------------------------------------------------------------ */
+ORC_API void orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(t > 0 ? t : omp_get_num_procs());
+#else
+    (void)t;
+#endif
+}
+
+ORC_API int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* binary32 building blocks                                            */
@@ -69,6 +106,7 @@ ORC_API int64_t orc_flags(int64_t n, const float *pos4, const float *ref4,
                           uint8_t *flag)
 {
     int64_t nf = 0;
+#pragma omp parallel for reduction(+ : nf) schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         float d2 = sqdist_f32(pos4 + 4 * i, ref4 + 4 * i);
         float s = ref4[4 * i + 3];
@@ -187,14 +225,6 @@ ORC_API int64_t orc_pairs_brute(int64_t n, const float *ref4, const float *rad,
 /* ------------------------------------------------------------------ */
 typedef struct { int32_t i, j; } ipair;
 
-static int cmp_ipair(const void *a, const void *b)
-{
-    const ipair *x = (const ipair *)a, *y = (const ipair *)b;
-    if (x->i != y->i) return x->i < y->i ? -1 : 1;
-    if (x->j != y->j) return x->j < y->j ? -1 : 1;
-    return 0;
-}
-
 /* Cell grid over a set of points; counting sort of particle ids by cell. */
 typedef struct {
     double lo[3];
@@ -294,8 +324,13 @@ ORC_API int64_t orc_pairs_cells(int64_t n, const float *ref4, const float *rad,
     if (!(edge > 0.0)) edge = 1.0;
     cellgrid g;
     if (grid_build(&g, n, ref4, edge) != 0) { grid_free(&g); return -1; }
-    pairbuf pb = {0};
+    /* one pair buffer per host thread; the cells are split among them */
+    int nt = orc_threads();
+    pairbuf *pbs = (pairbuf *)calloc((size_t)nt, sizeof(pairbuf));
+    if (!pbs) { grid_free(&g); return -1; }
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t ca = 0; ca < g.ncell; ++ca) {
+        pairbuf *pb = &pbs[thread_id()];
         int64_t ax = ca % g.dim[0];
         int64_t ay = (ca / g.dim[0]) % g.dim[1];
         int64_t az = ca / (g.dim[0] * g.dim[1]);
@@ -314,20 +349,49 @@ ORC_API int64_t orc_pairs_cells(int64_t n, const float *ref4, const float *rad,
                     if (cb == ca && b >= a) continue;   /* same cell: once */
                     if (pair_test(ref4 + 4 * (int64_t)a, rad[a],
                                   ref4 + 4 * (int64_t)b, rad[b]))
-                        pb_push(&pb, a, b);
+                        pb_push(pb, a, b);
                 }
             }
         }
     }
     grid_free(&g);
-    if (pb.oom) { free(pb.buf); return -1; }
-    if (pb.n > 1) qsort(pb.buf, (size_t)pb.n, sizeof(ipair), cmp_ipair);
-    for (int64_t k = 0; k < pb.n && k < cap; ++k) {
-        pi[k] = pb.buf[k].i;
-        pj[k] = pb.buf[k].j;
+    int64_t np = 0;
+    int oom = 0;
+    for (int t = 0; t < nt; ++t) { np += pbs[t].n; oom |= pbs[t].oom; }
+    int64_t *start = oom ? NULL : (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t *col = oom ? NULL : (int32_t *)malloc((size_t)(np > 0 ? np : 1) * sizeof(int32_t));
+    if (oom || !start || !col) {
+        for (int t = 0; t < nt; ++t) free(pbs[t].buf);
+        free(pbs); free(start); free(col);
+        return -1;
     }
-    int64_t np = pb.n;
-    free(pb.buf);
+    /* (i, j) order: bucket the pairs by i (counting sort), then sort each
+     * bucket's j ascending */
+    for (int t = 0; t < nt; ++t)
+        for (int64_t k = 0; k < pbs[t].n; ++k) start[pbs[t].buf[k].i + 1]++;
+    for (int64_t i = 0; i < n; ++i) start[i + 1] += start[i];
+    for (int t = 0; t < nt; ++t) {
+        for (int64_t k = 0; k < pbs[t].n; ++k) col[start[pbs[t].buf[k].i]++] = pbs[t].buf[k].j;
+        free(pbs[t].buf);
+    }
+    free(pbs);
+    for (int64_t i = n; i > 0; --i) start[i] = start[i - 1];   /* back to bucket starts */
+    start[0] = 0;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t a = start[i] + 1; a < start[i + 1]; ++a) {   /* insertion sort */
+            int32_t v = col[a];
+            int64_t b = a;
+            for (; b > start[i] && col[b - 1] > v; --b) col[b] = col[b - 1];
+            col[b] = v;
+        }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = start[i]; k < start[i + 1] && k < cap; ++k) {
+            pi[k] = (int32_t)i;
+            pj[k] = col[k];
+        }
+    free(start);
+    free(col);
     return np;
 }
 

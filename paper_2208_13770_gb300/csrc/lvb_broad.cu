@@ -1023,6 +1023,16 @@ int lvb_init_resume(lvb_ctx **out, int64_t n, const float *pos_r, const float *r
                      stream);
 }
 
+int lvb_batch_init_resume(lvb_ctx **out, int32_t n_scenes, const int64_t *offsets,
+                          const float *pos_r, const float *ref4, const lvb_box *boxes,
+                          const lvb_skin_policy *skin, int32_t trigger, float cell_factor,
+                          const float *vel, const float *acc, void *stream)
+{
+    if (!offsets || !ref4 || n_scenes < 1) return LVB_EINVAL;
+    return init_impl(out, n_scenes, offsets, offsets[n_scenes], pos_r, ref4, boxes, skin,
+                     trigger, cell_factor, vel, acc, stream);
+}
+
 int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
 {
     if (!c || !pos_r || !aligned16(pos_r) || (vel && !aligned16(vel)) || (acc && !aligned16(acc)))
@@ -1349,6 +1359,9 @@ int lvb_stats(lvb_ctx *c, lvb_stats_t *o)
     o->block_threads = c->block_threads;
     o->compaction = c->s.compact_block ? LVB_COMPACT_BLOCK : LVB_COMPACT_WARP;
     o->n_scenes = c->nscenes;
+    o->rebuild_candidates = (int64_t)h.alg_cand;
+    o->rebuild_direct = (int64_t)h.alg_direct;
+    o->rebuild_edits = (int64_t)h.alg_edits;
     o->cell_edge = c->sg[0].L;
     o->rnl_max = c->sg[0].H;
     for (int k = 0; k < 3; ++k) o->grid[k] = c->sg[0].dim[k];

@@ -55,6 +55,10 @@ struct DevCounters {
     unsigned long long kernels;  // kernels of this library executed (device count)
     unsigned long long barriers; // grid barriers passed by step kernels
     long long log_n;         // rebuild-log samples closed so far
+    // work of the partial rebuilds so far (for the algorithmic byte count):
+    // stencil candidates read, flagged-list records read by the direct
+    // test, and edits (removals + insertions) of unflagged partners' rows
+    unsigned long long alg_cand, alg_direct, alg_edits;
     // per-phase / per-kernel device time (LVB_OPT_TRACE): sums over steps;
     // separate kernels record first block entry / last block exit first
     unsigned long long tr_start[kTraceSlots], tr_end[kTraceSlots];

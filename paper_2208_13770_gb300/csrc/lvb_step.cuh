@@ -525,7 +525,7 @@ __device__ __forceinline__ void lane_edit(const DevState &s, int jr, int ji, int
 // The edits of other rows run one per lane, in parallel; the first 32 old
 // partners and the first 32 stencil candidates are loaded together.
 static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF, bool direct,
-                                               int par, int *ovf)
+                                               int par, int *ovf, unsigned (&work)[3])
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -582,7 +582,9 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         }
         if (len0 <= 32) jr0 = rm ? j : -1;
         else if (rm) lane_remove(s, j, i);
+        work[2] += __popc(__ballot_sync(FULL, rm));
     }
+    work[0] += total;
     // 2. stencil (+ direct test) and 3. insertions
     int found = 0;
     if (total == 0 && jr0 >= 0) lane_remove(s, jr0, i);
@@ -614,6 +616,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
             if (p < cap) s.col[off + p] = j;
         }
         found += __popc(m);
+        work[2] += __popc(__ballot_sync(FULL, ins));
         if (b0 == 0) {
             lane_edit(s, jr0, ins ? j : -1, i, ovf);
         } else if (ins) {
@@ -629,6 +632,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         const float4 *lst = own ? s.sfref + g.first : s.fref;
         const int *ids = own ? s.sfid + g.first : s.fid;
         const int m = own ? s.sc_cnt[par * s.nscenes + s.scene_of[i]] : nF;
+        work[1] += m;
         for (int b0 = 0; b0 < m; b0 += 32 * kDirectUnroll) {
             float4 rf[kDirectUnroll];
 #pragma unroll
@@ -757,6 +761,10 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 // the barrier state of this block (used by its thread 0 only)
 static __shared__ unsigned long long s_bar_need;   // arrivals up to the last barrier
 static __shared__ int s_bar_par;                   // parity of the step
+// the block's share of the partial rebuild's work counts (DevCounters
+// alg_*), gathered by its warps with shared-memory atomics and added to the
+// context's counters by thread 0 once per step
+static __shared__ unsigned long long s_work[3];
 
 // Called by every thread at the start of the step kernel, before any barrier.
 __device__ __forceinline__ void grid_barrier_begin(const DevState &s, int par)
@@ -764,6 +772,7 @@ __device__ __forceinline__ void grid_barrier_begin(const DevState &s, int par)
     if (threadIdx.x == 0) {
         s_bar_need = 0;
         s_bar_par = par;
+        s_work[0] = s_work[1] = s_work[2] = 0ULL;
         if (blockIdx.x == 0) s.cnt->bar_cnt[par ^ 1] = 0;
     }
 }
@@ -1310,17 +1319,34 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
     const int w0 = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool direct = nF <= s.direct_max;
+    unsigned work[3] = {0u, 0u, 0u};
     if (!direct) {
         for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
         if (!grid_barrier(s)) return false;
-        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, par, ovf);
-        return true;
+        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, par, ovf, work);
+    } else {
+        for (int w = w0; w < 2 * nF; w += nw) {
+            if (w < nF) patch_warp(s, w, nF, true, par, ovf, work);
+            else move_warp(s, s.fid[w - nF], s.fref[w - nF]);
+        }
     }
-    for (int w = w0; w < 2 * nF; w += nw) {
-        if (w < nF) patch_warp(s, w, nF, true, par, ovf);
-        else move_warp(s, s.fid[w - nF], s.fref[w - nF]);
-    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (work[q]) atomicAdd(&s_work[q], (unsigned long long)work[q]);
     return true;
+}
+
+// Adds the block's rebuild work counts to the context's (thread 0, after a
+// block barrier that follows partial_pass).
+__device__ __forceinline__ void flush_work(const DevState &s)
+{
+    if (threadIdx.x == 0) {
+        DevCounters *c = s.cnt;
+        if (s_work[0]) atomicAdd(&c->alg_cand, s_work[0]);
+        if (s_work[1]) atomicAdd(&c->alg_direct, s_work[1]);
+        if (s_work[2]) atomicAdd(&c->alg_edits, s_work[2]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1424,6 +1450,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
     }
     if (changed) {
         if (!grid_barrier(s)) return;
+        flush_work(s);
         unsigned long long t2 = 0;
         if (s.trace && lead) {
             t2 = global_ns();

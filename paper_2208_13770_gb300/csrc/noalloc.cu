@@ -219,6 +219,24 @@ k_na_pairs(NaScratch *sc, const float4 *__restrict__ ref4, const float4 *__restr
     }
 }
 
+// Launches fn<<<grid, threads, 0, st>>>(args...) and returns the launch's
+// own status (cudaLaunchKernelEx reports it directly), so that no call here
+// needs cudaGetLastError -- which would also read and clear an error of the
+// caller's own earlier work that the caller has not yet collected.
+template <typename... P, typename... A>
+cudaError_t na_launch(void (*fn)(P...), int grid, int threads, cudaStream_t st, A... args)
+{
+    static_assert(sizeof...(P) == sizeof...(A), "argument count");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, fn, static_cast<P>(args)...);
+}
+
 // Device address of the scratch, looked up once per device (with that
 // device current) and kept for the life of the process.
 constexpr int kNaMaxDevices = 64;
@@ -285,7 +303,6 @@ int lvb_pairs_noalloc(int64_t n, const float *pos4, const float *ref4, const lvb
             return LVB_EINVAL;
     if (n > kNaMaxN) return LVB_ELIMIT;
 
-    cudaGetLastError();
     NaScratch *sc = nullptr;
     if (int rc = na_scratch(&sc)) return rc;
     const cudaStream_t st = (cudaStream_t)stream;
@@ -294,10 +311,9 @@ int lvb_pairs_noalloc(int64_t n, const float *pos4, const float *ref4, const lvb
     const int nn = (int)n;
     const int grid = std::min((nn + kNaThreads - 1) / kNaThreads, kNaBlocks);
 
-    k_na_reset<<<1, 1, 0, st>>>(sc);
-    k_na_extent<<<grid, kNaThreads, 0, st>>>(sc, r4, p4, nn);
+    cudaError_t e = na_launch(k_na_reset, 1, 1, st, sc);
+    if (e == cudaSuccess) e = na_launch(k_na_extent, grid, kNaThreads, st, sc, r4, p4, nn);
     unsigned ext[2] = {0u, 0u};   // rnl_max_bits, bad (adjacent in NaScratch)
-    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ext, &sc->rnl_max_bits, sizeof(ext), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -310,13 +326,13 @@ int lvb_pairs_noalloc(int64_t n, const float *pos4, const float *ref4, const lvb
     const NaGrid g = na_grid(*box, rnl_max);
     const int gc = std::min((g.ncells + kNaThreads - 1) / kNaThreads, kNaBlocks);
     const int gw = std::min((nn + 7) / 8, 4 * kNaBlocks);   // 8 warps (particles) per block
-    k_na_clear<<<gc, kNaThreads, 0, st>>>(sc, g.ncells);
-    k_na_count<<<grid, kNaThreads, 0, st>>>(sc, r4, nn, g);
-    k_na_scan<<<1, kNaThreads, 0, st>>>(sc, g.ncells);
-    k_na_fill<<<grid, kNaThreads, 0, st>>>(sc, r4, p4, nn, g);
-    k_na_pairs<<<gw, kNaThreads, 0, st>>>(sc, r4, p4, nn, g, pi, pj, cap);
+    e = na_launch(k_na_clear, gc, kNaThreads, st, sc, g.ncells);
+    if (e == cudaSuccess) e = na_launch(k_na_count, grid, kNaThreads, st, sc, r4, nn, g);
+    if (e == cudaSuccess) e = na_launch(k_na_scan, 1, kNaThreads, st, sc, g.ncells);
+    if (e == cudaSuccess) e = na_launch(k_na_fill, grid, kNaThreads, st, sc, r4, p4, nn, g);
+    if (e == cudaSuccess)
+        e = na_launch(k_na_pairs, gw, kNaThreads, st, sc, r4, p4, nn, g, pi, pj, cap);
     unsigned long long np = 0;
-    e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&np, &sc->npairs, sizeof(np), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

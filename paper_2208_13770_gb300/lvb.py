@@ -43,8 +43,8 @@ class lvb_stats_t(ctypes.Structure):
                 ("n", "steps", "rebuild_steps", "flagged_total", "updated_total", "last_flagged",
                  "entries", "pairs", "relayouts", "grows", "cell_capacity", "row_store_capacity",
                  "kernels_executed", "barriers", "step_blocks", "block_threads", "compaction",
-                 "n_scenes")] + \
-               [("reserved", ctypes.c_int64 * 4)] + \
+                 "n_scenes", "rebuild_candidates", "rebuild_direct", "rebuild_edits")] + \
+               [("reserved", ctypes.c_int64 * 1)] + \
                [("cell_edge", ctypes.c_float), ("rnl_max", ctypes.c_float),
                 ("grid", ctypes.c_int32 * 3), ("pad", ctypes.c_int32)]
 
@@ -81,6 +81,9 @@ _SIGS = {
     "lvb_init_resume": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(lvb_box),
                          ctypes.POINTER(lvb_skin_policy), ctypes.c_int32, ctypes.c_float, _p, _p,
                          _p], ctypes.c_int),
+    "lvb_batch_init_resume": ([ctypes.POINTER(_p), ctypes.c_int32, _p, _p, _p,
+                               ctypes.POINTER(lvb_box), ctypes.POINTER(lvb_skin_policy),
+                               ctypes.c_int32, ctypes.c_float, _p, _p, _p], ctypes.c_int),
     "lvb_step": ([_p, _p, _p, _p], ctypes.c_int),
     "lvb_step_host": ([_p, _p, _p, _p, _p, _p], ctypes.c_int),
     "lvb_sync": ([_p], ctypes.c_int),
@@ -178,6 +181,17 @@ def lvb_init_resume(n, pos_r, ref4, box, skin, trigger, cell_factor, vel=None, a
                               ctypes.byref(skin), int(trigger), float(cell_factor), vel, acc,
                               stream)
     _check(rc, "lvb_init_resume")
+    return ctx
+
+
+def lvb_batch_init_resume(n_scenes, offsets, pos_r, ref4, boxes, skin, trigger, cell_factor,
+                          vel=None, acc=None, stream=None):
+    ctx = _p()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    rc = _lib.lvb_batch_init_resume(ctypes.byref(ctx), int(n_scenes), off.ctypes.data, pos_r,
+                                    ref4, boxes, ctypes.byref(skin), int(trigger),
+                                    float(cell_factor), vel, acc, stream)
+    _check(rc, "lvb_batch_init_resume")
     return ctx
 
 
@@ -365,8 +379,13 @@ class LVB:
             for q in range(ns):
                 for k in range(3):
                     boxes[q].lo[k], boxes[q].hi[k] = float(box_lo[q][k]), float(box_hi[q][k])
-            self.ctx = lvb_batch_init(ns, offsets, _dptr(pos), boxes, skin, trigger, cell_factor,
-                                      _dptr(vel), _dptr(acc), stream)
+            if ref is None:
+                self.ctx = lvb_batch_init(ns, offsets, _dptr(pos), boxes, skin, trigger,
+                                          cell_factor, _dptr(vel), _dptr(acc), stream)
+            else:
+                self.ctx = lvb_batch_init_resume(ns, offsets, _dptr(pos), _dptr(ref), boxes, skin,
+                                                 trigger, cell_factor, _dptr(vel), _dptr(acc),
+                                                 stream)
             return
         box = lvb_box()
         for k in range(3):

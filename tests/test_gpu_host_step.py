@@ -27,8 +27,10 @@ def _dev(a):
                                                    (1, 0.1, False)],
                          ids=["diameter", "paper_rule", "pageable_outputs"])
 def test_step_host_matches_oracle_step_by_step(orc, kind, value, pinned_out):
-    # page-locked outputs are written by the step kernel itself, pageable
-    # ones are copied back after each step
+    # the step writes its flag words into a device staging slot, which a
+    # copy stream of the context copies out to the caller's buffers while
+    # the next step runs; page-locked outputs overlap that copy, pageable
+    # ones make it synchronous
     lvb = _lvb()
     from oracle.statemachine import OracleLVB
     s = scenes.ballistic(n=3000, seed=21, vsigma=1.0)

@@ -4,9 +4,10 @@ Collected last on purpose: the entry point's working memory is one fixed
 device array shared by every call, so these tests also show that it works
 after the rest of the suite has used the device, and that one call leaves
 nothing behind that changes the next (two calls in a row, on different and
-on repeated inputs).  The reference is lvb_get_pairs_ij of a context that
-holds the same reference state (Def. verletlist); pairs come back in no
-particular order, so the sets are compared.
+on repeated inputs).  Every call's pair set is compared with two others:
+the CPU oracle's pair set for the same reference state (its own brute-force
+or linked-cell search), and lvb_get_pairs_ij of a context that holds that
+state.  Pairs come back in no particular order, so the sets are compared.
 """
 import ctypes
 
@@ -53,10 +54,15 @@ def _keys(n, pi, pj):
 
 
 def _check_against_context(lvb, ctx, pos_d, box):
-    """One call through the C-ABI; its pair set must be the context's."""
+    """One call through the C-ABI; its pair set must be the oracle's and the
+    context's."""
+    import oracle
     ei, ej = ctx.pairs_ij()
     n = ctx.n
-    ref_d = _dev(ctx.ref())
+    ref = ctx.ref()
+    oi, oj = oracle.pairs(ref, pos_d.cpu().numpy()[:, 3])
+    assert np.array_equal(_keys(n, ei, ej), _keys(n, oi, oj))
+    ref_d = _dev(ref)
     rc, cnt, pi, pj = _noalloc(lvb, pos_d, ref_d, box, len(ei) + 64)
     assert rc == lvb.LVB_OK, lvb.lvb_strerror(rc)
     assert cnt == len(ei)
