@@ -288,6 +288,17 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 rows from the final cells.  0 .. 2^20
                                 (default 4096) */
 
+#define LVB_OPT_STENCIL_REACH 9 /* which of the 27 stencil cells a row build
+                                scans (Algorithm 1 visits all 27): 0 all of
+                                them; 1 those whose box lies within R_NL,i + H
+                                of the particle (H the cap on any R_NL); 2
+                                (default) also skips a cell whose box lies
+                                beyond R_NL,i plus the largest R_NL stored in
+                                that cell.  Every partner lies within
+                                R_NL,i + R_NL,j, so each choice gives the same
+                                list; 1 and 2 read fewer candidates with
+                                polydisperse radii */
+
 /* Values of LVB_OPT_COMPACT. */
 #define LVB_COMPACT_WARP  0  /* flagged ids gather in a per-warp list during
                                 the check; the list takes its indices with

@@ -135,6 +135,29 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
                   float *y_range, float *losses, void *stream);
 
 /*
+ * lvb_mlp_travel_labels -- rebuild-log samples turned into training samples
+ * for the travel form of the output over `horizon` steps (y_steps =
+ * horizon): the label becomes the largest displacement in units of the
+ * particle's travel over the horizon at its speed when updated, times a
+ * margin, clipped at a quantile.
+ *   samples : device n x 9 (8 features, label), e.g. from lvb_log_read.
+ *   out     : device, room for n x 9; must not overlap samples.  Receives,
+ *             in their input order, the samples with f0 > 0 (a particle at
+ *             rest has no travel and is left out), features unchanged and
+ *             label
+ *               y = (label * margin) / (f0 * horizon)     (binary32, each
+ *                                                          operation rounded)
+ *             then y = fminf(y, c), c the order statistic k = floor(clip_q
+ *             (m - 1)) (0-based, ascending, binary64 product) of the m
+ *             values y.
+ *   horizon : >= 1 (the log's horizon); margin > 0, finite; 0 < clip_q <= 1.
+ *   n_out   : host out, m.
+ * Synchronises.  Errors: EINVAL, ENOMEM, EDEVICE.
+ */
+int lvb_mlp_travel_labels(const float *samples, int64_t n, int32_t horizon, float margin,
+                          float clip_q, float *out, int64_t *n_out, void *stream);
+
+/*
  * lvb_log_enable -- start recording training samples from a broad-phase
  * context (PARTIAL trigger): each particle's update opens a record with its
  * features; `horizon` steps later the record closes with its label and is

@@ -243,3 +243,28 @@ def features(pos4, vel4, acc4, dt, grid, ref_old, nrow, age, occ):
         w = m if w is None else np.minimum(w, m)
     f[:, 7] = (w / d).astype(np.float32)
     return f
+
+
+# ----------------------------------------------------------------- labels
+def travel_labels(samples, horizon, margin, clip_q):
+    """Rebuild-log samples (n, 9: eight features, label = largest
+    displacement over the horizon / d) as training samples of the travel
+    form over `horizon` steps.  In the order given, the samples with
+    f0 > 0 are kept (f0 d = |v| dt is the particle's travel per step; one at
+    rest has none); each label t becomes y = (t * margin) / (f0 * horizon),
+    every operation rounded to binary32 -- the displacement in units of the
+    travel over the horizon, times a margin -- and then y = min(y, c) with c
+    the value of rank k = floor(clip_q (m - 1)) (0-based) among the m values
+    y in ascending order."""
+    s = np.asarray(samples, dtype=np.float32).reshape(-1, N_IN + 1)
+    kept = s[s[:, 0] > np.float32(0)].copy()
+    m = len(kept)
+    if m == 0:
+        return kept
+    t = (kept[:, N_IN] * np.float32(margin)).astype(np.float32)
+    u = (kept[:, 0] * np.float32(horizon)).astype(np.float32)
+    y = (t / u).astype(np.float32)
+    k = int(np.floor(float(np.float32(clip_q)) * float(m - 1)))
+    c = np.sort(y)[k]
+    kept[:, N_IN] = np.minimum(y, c)
+    return kept

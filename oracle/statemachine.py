@@ -113,3 +113,78 @@ class OracleLVB:
                              step - self.born[idx], occ)
         self.last_features = (idx, feats)
         return mlp.infer(self.learned["weights"], feats, np.float32(2.0) * pos4[idx, 3])[0]
+
+
+class RebuildLog:
+    """The rebuild log (the skin network's training data, lvb_log_enable) as
+    a plain procedure over an OracleLVB with the partial trigger.
+
+    At every step, before the state machine updates anything:
+      * the particles it is about to update (the flagged ones, Eq. update)
+        that have no open record each open one: the step number, the
+        position x_open, a running maximum m = 0, and the eight features of
+        lvb_mlp.h from the state before the update (old reference state,
+        partners in the current list, steps since the last update,
+        reference positions in the cell of x);
+    then the state machine steps; then, for every open record (including
+    those just opened), m = max(m, |x - x_open|^2) at this step's position
+    (binary32, fixed association), and a record opened `horizon` steps ago
+    closes: it yields the sample (features, sqrt(m) / d) -- the largest
+    displacement over the horizon in diameters -- and the particle may open
+    a new record at a later update.
+
+    grid: the cell grid of the features (oracle.mlp.grid_params)."""
+
+    def __init__(self, sm, grid, horizon):
+        if sm.trigger != TRIGGER_PARTIAL:
+            raise ValueError("the rebuild log follows the partial trigger")
+        self.sm, self.grid, self.horizon = sm, grid, int(horizon)
+        n = sm.n
+        self.t_open = np.full(n, -1, dtype=np.int64)
+        self.x_open = np.zeros((n, 4), dtype=np.float32)
+        self.m = np.zeros(n, dtype=np.float32)
+        self.feat = np.zeros((n, 8), dtype=np.float32)
+        self.samples = []
+
+    def step(self, pos4, vel4=None, acc4=None, proposal=None):
+        from . import mlp
+        sm = self.sm
+        pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
+        zero = np.zeros((sm.n, 4), dtype=np.float32)
+        vel = zero if vel4 is None else np.asarray(vel4, dtype=np.float32)
+        acc = zero if acc4 is None else np.asarray(acc4, dtype=np.float32)
+        step = sm.steps + 1
+        upd = _flags(pos4, sm.ref)
+        idx = np.nonzero(upd & (self.t_open < 0))[0]
+        if len(idx):
+            nrow = np.bincount(np.concatenate([sm.pi, sm.pj]), minlength=sm.n)[idx]
+            ncell = int(np.prod(self.grid["dims"]))
+            occ_all = np.bincount(mlp.cell_index(sm.ref[:, :3], self.grid), minlength=ncell)
+            occ = occ_all[mlp.cell_index(pos4[idx, :3], self.grid)]
+            self.feat[idx] = mlp.features(pos4[idx], vel[idx], acc[idx], sm.dt, self.grid,
+                                          sm.ref[idx], nrow, step - sm.born[idx], occ)
+            self.t_open[idx] = step
+            self.x_open[idx] = pos4[idx]
+            self.m[idx] = np.float32(0)
+        out = sm.step(pos4, vel4=vel4, proposal=proposal, acc4=acc4)
+        o = np.nonzero(self.t_open >= 0)[0]
+        if len(o):
+            d = (pos4[o, :3] - self.x_open[o, :3]).astype(np.float32)
+            d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]).astype(np.float32)
+            d2 = (d2 + d[:, 2] * d[:, 2]).astype(np.float32)
+            m = np.fmax(self.m[o], d2).astype(np.float32)
+            close = (step - self.t_open[o]) >= self.horizon
+            c = o[close]
+            if len(c):
+                diam = (np.float32(2.0) * sm.rad[c]).astype(np.float32)
+                lab = (np.sqrt(m[close]).astype(np.float32) / diam).astype(np.float32)
+                self.samples.append(np.concatenate([self.feat[c], lab[:, None]], axis=1))
+                self.t_open[c] = -1
+            self.m[o[~close]] = m[~close]
+        return out
+
+    def log(self):
+        """The closed records so far, (k, 9) binary32, in closing order."""
+        if not self.samples:
+            return np.zeros((0, 9), dtype=np.float32)
+        return np.concatenate(self.samples).astype(np.float32)

@@ -17,6 +17,8 @@ ever missed (Theorem 1 holds for any skin).
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 
 CELL_FACTORS = (1.0, 1.25, 1.5)
 BLOCK_THREADS = (1024, 512, 256)
@@ -55,11 +57,52 @@ def _trial(torch, lvb, scene_list, choice, warm, steps):
         dem.close()
 
 
-def tune(scene_list, warm=200, steps=400):
-    """Returns (best Choice, list of trials {choice fields, ms_per_step})."""
+def _cache_path():
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "lvb_autotune.json")
+
+
+def cache_key(kind, n, gpu_name):
+    """(scene kind, particle-count bucket (powers of two), GPU name)."""
+    return "%s|n2^%d|%s" % (kind, max(0, int(n) - 1).bit_length(), gpu_name)
+
+
+def _cache_load():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _cache_store(key, choice, trials):
+    d = _cache_load()
+    d[key] = {"choice": dataclasses.asdict(choice), "trials": trials}
+    try:
+        os.makedirs(os.path.dirname(_cache_path()), exist_ok=True)
+        tmp = _cache_path() + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(d, f)
+        os.replace(tmp, _cache_path())
+    except OSError:
+        pass
+
+
+def tune(scene_list, warm=200, steps=400, key=None):
+    """Returns (best Choice, list of trials {choice fields, ms_per_step}).
+    With key (a scene kind), the choice is looked up in a per-user cache
+    under (kind, particle-count bucket, GPU name) and stored there after a
+    search, so that a second run on the same kind of workload and GPU skips
+    the search (its trials list is then the cached one)."""
     import torch
     from . import lvb
     trials = []
+    ck = None
+    if key is not None:
+        ck = cache_key(key, sum(q.n for q in scene_list), torch.cuda.get_device_name())
+        hit = _cache_load().get(ck)
+        if hit is not None:
+            return Choice(**hit["choice"]), hit["trials"]
 
     def run(choice):
         ms = _trial(torch, lvb, scene_list, choice, warm, steps)
@@ -89,4 +132,6 @@ def tune(scene_list, warm=200, steps=400):
         ms = run(c)
         if ms < best_ms:
             best, best_ms = c, ms
+    if ck is not None:
+        _cache_store(ck, best, trials)
     return best, trials

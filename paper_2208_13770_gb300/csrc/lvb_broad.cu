@@ -899,6 +899,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     s.n = (int)n;
     s.bar_spins = kBarrierSpins;
     s.direct_max = kFlaggedDirectMax;
+    s.reach = 2;
     s.nwords = c->nwords;
     s.trigger = trigger;
     s.skin_kind = skin->kind;
@@ -1148,6 +1149,9 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     } else if (option == LVB_OPT_DIRECT_MAX) {
         if (value < 0 || value > (1 << 20)) return LVB_EINVAL;
         c->s.direct_max = (int)value;
+    } else if (option == LVB_OPT_STENCIL_REACH) {
+        if (value < 0 || value > 2) return LVB_EINVAL;
+        c->s.reach = (int)value;
     } else {
         return LVB_EINVAL;
     }

@@ -98,6 +98,8 @@ struct DevState {
     unsigned bar_spins;   // polls before a barrier gives up
     int direct_max;       // largest flagged count rebuilt in one phase with
                           // the direct flagged-pair test (LVB_OPT_DIRECT_MAX)
+    int reach;            // stencil cells skipped by distance (LVB_OPT_STENCIL_REACH):
+                          // 0 none, 1 by the cap H, 2 by H and the cell's own bound
     // second destination of this step's flag words and flagged count
     // (lvb_step_host: a staging slot copied out while the next step runs),
     // or null
@@ -541,11 +543,12 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     if (lane < 27) {
         const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
         if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
-            const float dd = cell_dist2(g, x, y, z, qn);
-            if (within_reach(g, dd, qn.w, g.H)) {
+            const float dd = s.reach ? cell_dist2(g, x, y, z, qn) : 0.0f;
+            if (s.reach == 0 || within_reach(g, dd, qn.w, g.H)) {
                 cid = g.cell_base + (z * d1 + y) * d0 + x;
                 cnt_l = s.cell_cnt[cid];
-                if (!within_reach(g, dd, qn.w, __int_as_float(s.cell_rmax[cid]))) cnt_l = 0;
+                if (s.reach == 2 && !within_reach(g, dd, qn.w, __int_as_float(s.cell_rmax[cid])))
+                    cnt_l = 0;
             }
         }
     }
@@ -689,11 +692,13 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill,
         if (lane < 27) {
             const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
             if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
-                const float dd = cell_dist2(g, x, y, z, qi);
-                if (within_reach(g, dd, qi.w, g.H)) {
+                const float dd = s.reach ? cell_dist2(g, x, y, z, qi) : 0.0f;
+                if (s.reach == 0 || within_reach(g, dd, qi.w, g.H)) {
                     cid = g.cell_base + (z * d1 + y) * d0 + x;
                     cnt_l = min(s.cell_cnt[cid], ccap);
-                    if (!within_reach(g, dd, qi.w, __int_as_float(s.cell_rmax[cid]))) cnt_l = 0;
+                    if (s.reach == 2 &&
+                        !within_reach(g, dd, qi.w, __int_as_float(s.cell_rmax[cid])))
+                        cnt_l = 0;
                 }
             }
         }

@@ -431,3 +431,156 @@ int lvb_mlp_train(const float *samples, int64_t n, int32_t epochs, int32_t batch
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Travel-form labels (lvb_mlp_travel_labels): samples with f0 > 0 kept in
+// their order (chunked stable compaction: block b owns a contiguous chunk
+// and writes its kept samples after those of the blocks before it), label
+// t -> (t * margin) / (f0 * horizon), then clipped at an order statistic
+// found by bisection over the binary32 bit patterns (non-negative values
+// order like their bits).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kTlThreads = 256;
+constexpr int kTlBlocks = 256;
+
+__device__ __forceinline__ bool tl_keep(const float *s) { return s[0] > 0.0f; }
+
+__global__ void __launch_bounds__(kTlThreads)
+k_tl_count(const float *__restrict__ smp, int64_t n, int64_t chunk, int *blk_cnt)
+{
+    const int64_t a = (int64_t)blockIdx.x * chunk, b = min(n, a + chunk);
+    int c = 0;
+    for (int64_t i = a + threadIdx.x; i < b; i += kTlThreads) c += tl_keep(smp + i * kSamp);
+    __shared__ int ws[kTlThreads / 32];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kTlThreads / 32; ++w) t += ws[w];
+        blk_cnt[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kTlThreads)
+k_tl_scatter(const float *__restrict__ smp, int64_t n, int64_t chunk, const int *blk_cnt,
+             int horizon, float margin, float *__restrict__ out)
+{
+    __shared__ int ws[kTlThreads / 32];
+    __shared__ int s_base;
+    if (threadIdx.x == 0) {
+        int base = 0;
+        for (int q = 0; q < (int)blockIdx.x; ++q) base += blk_cnt[q];
+        s_base = base;
+    }
+    __syncthreads();
+    int base = s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t a = (int64_t)blockIdx.x * chunk, b = min(n, a + chunk);
+    const float hz = (float)horizon;
+    for (int64_t t0 = a; t0 < b; t0 += kTlThreads) {
+        const int64_t i = t0 + threadIdx.x;
+        const bool keep = i < b && tl_keep(smp + i * kSamp);
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (lane == 0) ws[warp] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kTlThreads / 32; ++w) {
+            before += w < warp ? ws[w] : 0;
+            total += ws[w];
+        }
+        if (keep) {
+            const float *s = smp + i * kSamp;
+            float *o = out + (int64_t)(base + before + __popc(m & lanemask_lt())) * kSamp;
+#pragma unroll
+            for (int k = 0; k < NI; ++k) o[k] = s[k];
+            o[NI] = __fdiv_rn(__fmul_rn(s[NI], margin), __fmul_rn(s[0], hz));
+        }
+        base += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kTlThreads)
+k_tl_count_le(const float *__restrict__ out, int64_t m, unsigned t, unsigned long long *cnt)
+{
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kTlThreads + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * kTlThreads)
+        c += __float_as_uint(out[i * kSamp + NI]) <= t;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+__global__ void __launch_bounds__(kTlThreads)
+k_tl_clip(float *out, int64_t m, float c)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kTlThreads + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * kTlThreads)
+        out[i * kSamp + NI] = fminf(out[i * kSamp + NI], c);
+}
+
+}  // namespace
+
+extern "C" int lvb_mlp_travel_labels(const float *samples, int64_t n, int32_t horizon,
+                                     float margin, float clip_q, float *out, int64_t *n_out,
+                                     void *stream)
+{
+    if (n_out) *n_out = 0;
+    if (!samples || !out || !n_out || n < 0 || horizon < 1 || samples == out) return LVB_EINVAL;
+    if (!(margin > 0.0f) || !std::isfinite(margin) || !(clip_q > 0.0f) || !(clip_q <= 1.0f))
+        return LVB_EINVAL;
+    if (n == 0) return LVB_OK;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int64_t chunk = (n + kTlBlocks - 1) / kTlBlocks;
+    int *blk = nullptr;
+    unsigned long long *cnt = nullptr;
+    cudaError_t e = cudaMalloc((void **)&blk, sizeof(int) * kTlBlocks);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&cnt, sizeof(unsigned long long));
+    auto done = [&](int rc) {
+        cudaStreamSynchronize(st);
+        if (blk) cudaFree(blk);
+        if (cnt) cudaFree(cnt);
+        return rc;
+    };
+    if (e != cudaSuccess) return done(e == cudaErrorMemoryAllocation ? LVB_ENOMEM : LVB_EDEVICE);
+    k_tl_count<<<kTlBlocks, kTlThreads, 0, st>>>(samples, n, chunk, blk);
+    k_tl_scatter<<<kTlBlocks, kTlThreads, 0, st>>>(samples, n, chunk, blk, horizon, margin, out);
+    std::vector<int> bc(kTlBlocks);
+    e = cudaMemcpyAsync(bc.data(), blk, sizeof(int) * kTlBlocks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(LVB_EDEVICE);
+    int64_t m = 0;
+    for (int v : bc) m += v;
+    if (m > 0) {
+        // order statistic k (0-based, ascending): the smallest bit pattern
+        // t with at least k + 1 labels <= t
+        const int64_t k = (int64_t)std::floor((double)clip_q * (double)(m - 1));
+        const int g = (int)std::min<int64_t>((m + kTlThreads - 1) / kTlThreads, 4 * 152);
+        unsigned lo = 0u, hi = 0x7fffffffu;
+        while (lo < hi && e == cudaSuccess) {
+            const unsigned mid = lo + (hi - lo) / 2;
+            unsigned long long c = 0;
+            e = cudaMemsetAsync(cnt, 0, sizeof(c), st);
+            if (e == cudaSuccess) {
+                k_tl_count_le<<<g, kTlThreads, 0, st>>>(out, m, mid, cnt);
+                e = cudaMemcpyAsync(&c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if ((int64_t)c >= k + 1) hi = mid;
+            else lo = mid + 1;
+        }
+        if (e != cudaSuccess) return done(LVB_EDEVICE);
+        float c;
+        memcpy(&c, &lo, sizeof(c));
+        k_tl_clip<<<g, kTlThreads, 0, st>>>(out, m, c);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return done(LVB_EDEVICE);
+    *n_out = m;
+    return done(LVB_OK);
+}

@@ -105,6 +105,8 @@ _SIGS = {
                       _p], ctypes.c_int),
     "lvb_mlp_train": ([_p, _i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
                        ctypes.c_int32, _p, _p, _p, _p, _p, _p], ctypes.c_int),
+    "lvb_mlp_travel_labels": ([_p, _i64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _p,
+                               _pi64, _p], ctypes.c_int),
     "lvb_log_enable": ([_p, ctypes.c_int32, _i64], ctypes.c_int),
     "lvb_log_read": ([_p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_pairs_noalloc": ([_i64, _p, _p, ctypes.POINTER(lvb_box), _p, _p, _i64, _pi64, _p],
@@ -207,6 +209,7 @@ def lvb_step_host(ctx, pos_r, vel=None, acc=None, bits=None, n_flagged=None):
 LVB_OPT_TRACE, LVB_OPT_BLOCK_THREADS, LVB_OPT_COMPACT = 3, 4, 5
 LVB_OPT_BARRIER_EXTRA, LVB_OPT_BARRIER_SPINS = 6, 7
 LVB_OPT_DIRECT_MAX = 8
+LVB_OPT_STENCIL_REACH = 9
 LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
 TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]
 
@@ -333,6 +336,11 @@ def lvb_mlp_train(samples, n, epochs, batch, lr, seed, loss_kind, params, mu, is
                   losses, stream=None):
     return _lib.lvb_mlp_train(samples, int(n), int(epochs), int(batch), float(lr), int(seed),
                               int(loss_kind), params, mu, isd, y_range, losses, stream)
+
+
+def lvb_mlp_travel_labels(samples, n, horizon, margin, clip_q, out, n_out, stream=None):
+    return _lib.lvb_mlp_travel_labels(samples, int(n), int(horizon), float(margin),
+                                      float(clip_q), out, n_out, stream)
 
 
 def lvb_log_enable(ctx, horizon, capacity):
@@ -667,3 +675,21 @@ def mlp_train(samples_dev, epochs, batch, lr, seed, params0, y_range_out=None,
                          _np_ptr(losses)),
            "lvb_mlp_train")
     return p, mu, isd, losses
+
+
+def mlp_travel_labels(samples, horizon, margin, clip_q):
+    """lvb_mlp_travel_labels on an (n, 9) float32 array (host) or device
+    tensor; returns the kept samples as a host array (m, 9)."""
+    import torch
+    if isinstance(samples, np.ndarray):
+        src = torch.from_numpy(np.ascontiguousarray(samples, dtype=np.float32)).cuda()
+    else:
+        src = samples.contiguous()
+    out = torch.empty_like(src)
+    m = ctypes.c_int64(0)
+    _check(lvb_mlp_travel_labels(src.data_ptr() if src.numel() else None, src.shape[0],
+                                 horizon, margin, clip_q,
+                                 out.data_ptr() if out.numel() else None, ctypes.byref(m),
+                                 torch.cuda.current_stream().cuda_stream),
+           "lvb_mlp_travel_labels")
+    return out[:m.value].cpu().numpy()

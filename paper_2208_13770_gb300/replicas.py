@@ -1,12 +1,12 @@
 """Runs over several GPUs of one node: one process per GPU.
 
 The broad phase of one scene does not shard (the paper's method has no
-exchange step), so N GPUs run N independent replicas of the workload --
-each rank its own seeded copy -- with no collective on the data path
-(weak scaling).  The only collectives are the timing ones: a barrier
-before the timed region and the maximum of the ranks' times after it, so
-that the job's time is its slowest rank's and its throughput counts the
-particle-steps of all ranks.
+exchange step), but a batch of independent scenes does: the scenes are
+split over the ranks, greedily by particle count (shard_greedy), and every
+rank advances its share with no collective on the data path.  The only
+collectives are the timing ones: a barrier before the timed region and the
+maximum of the ranks' times after it, so that the job's time is its
+slowest rank's and its throughput counts the particle-steps of all ranks.
 """
 from __future__ import annotations
 
@@ -42,3 +42,18 @@ def job_throughput(world: int, n: int, steps: int, ms: float) -> float:
     """Units per second of the whole job: world ranks x n units x steps, over
     the slowest rank's time in milliseconds."""
     return world * n * steps / (ms * 1e-3)
+
+
+def shard_greedy(sizes, world: int):
+    """Scene indices of each rank: scenes taken largest first, each to the
+    rank with the fewest particles so far (ties: the lowest rank); every
+    rank's list in ascending scene order."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for q in sorted(range(len(sizes)), key=lambda q: (-int(sizes[q]), q)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[r].append(q)
+        load[r] += int(sizes[q])
+    return [sorted(x) for x in out]

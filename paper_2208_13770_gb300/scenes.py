@@ -134,23 +134,17 @@ def settling(n=200_000, seed=SEED_BASE + 1, rmin=0.5e-3, rmax=2e-3, footprint=0.
                  skin_value=skin_value, cell_factor=cell_factor)
 
 
-def drum(n=2_000_000, seed=SEED_BASE + 2, R=0.3, length=0.20, rpm=10.0, median=1e-3,
-         sigma_ln=0.35, rclip=(0.4e-3, 3e-3), dt=1e-6, steps=5000, skin_kind=1,
-         skin_value=0.1, cell_factor=1.25) -> Scene:
-    """A horizontal drum (axis along y, centre (0, 0) in x-z) holding a dense
-    bed, stratified by size: radii are sorted large-first and laid in
-    horizontal lattice layers from the bottom, each layer's spacing the
-    largest diameter in it.  The bed starts in solid-body rotation."""
-    rng = _rng(seed)
-    radii = np.exp(rng.normal(math.log(median), sigma_ln, size=n))
-    radii = np.clip(radii, rclip[0], rclip[1])
-    radii = np.sort(radii)[::-1].copy()
+def _drum_layers(rng, radii, z0, R, length, margin):
+    """Horizontal lattice layers inside the circle of radius R (x-z plane)
+    from height z0 up: each layer's spacing is `margin` times the largest
+    diameter among the next particles (radii sorted large-first), sites
+    chosen at random and jittered within their free play.  Returns (xyz,
+    height of the top of the last layer)."""
+    n = len(radii)
     xyz = np.zeros((n, 3))
     placed = 0
-    z = -R
-    margin = 1.0001
+    z = z0
     while placed < n:
-        # spacing of this layer: largest diameter among the next candidates
         a = 2.0 * radii[placed] * margin
         zc = z + 0.5 * a
         if zc + 0.5 * a > R:
@@ -174,14 +168,72 @@ def drum(n=2_000_000, seed=SEED_BASE + 2, R=0.3, length=0.20, rpm=10.0, median=1
             xyz[placed:placed + take, 2] = zc + rng.uniform(-1, 1, take) * play
             placed += take
         z += a
+    return xyz, z
+
+
+def drum(n=2_000_000, seed=SEED_BASE + 2, R=0.3, length=0.20, rpm=10.0, median=1e-3,
+         sigma_ln=0.35, rclip=(0.4e-3, 3e-3), dt=1e-6, steps=5000, skin_kind=1,
+         skin_value=0.1, cell_factor=1.25, tilt_deg=0.0, cascade=0.0,
+         cascade_speed=0.3, cascade_spacing=1.6) -> Scene:
+    """A horizontal drum (axis along y, centre (0, 0) in x-z) holding a dense
+    bed, stratified by size: radii are sorted large-first and laid in
+    horizontal lattice layers from the bottom, each layer's spacing the
+    largest diameter in it.  The bed starts in solid-body rotation.
+
+    tilt_deg turns the whole load about the drum axis, so that the bed's free
+    surface slopes as in a drum rotating in the rolling regime.  cascade > 0
+    takes that fraction of the particles (a random subset of the radii) out
+    of the bed and lays them, the same way but with cascade_spacing times the
+    spacing (a packing fraction about cascade_spacing^-3 of the bed's), in
+    layers on top of the bed, moving down the slope at cascade_speed [m/s]
+    plus N(0, 0.05 m/s) per component: the dense bed and dilute cascading
+    layer of a rotating drum, made by construction because a real drum needs
+    about a revolution (6e6 steps of 1 us) to develop them."""
+    rng = _rng(seed)
+    radii = np.exp(rng.normal(math.log(median), sigma_ln, size=n))
+    radii = np.clip(radii, rclip[0], rclip[1])
+    n_c = int(round(cascade * n))
+    r_c = np.zeros(0)
+    if n_c > 0:
+        pick = np.zeros(n, dtype=bool)
+        pick[rng.choice(n, size=n_c, replace=False)] = True
+        r_c = np.sort(radii[pick])[::-1].copy()
+        radii = radii[~pick]
+    radii = np.sort(radii)[::-1].copy()
+    xyz, top = _drum_layers(rng, radii, -R, R, length, 1.0001)
     omega = rpm * 2.0 * math.pi / 60.0
+    vel3 = np.zeros((len(radii), 3))
+    # solid-body rotation about +y: v = omega x (x - c) with c on the axis
+    vel3[:, 0] = omega * xyz[:, 2]
+    vel3[:, 2] = -omega * xyz[:, 0]
+    if n_c:
+        xc, _ = _drum_layers(rng, r_c, top, R, length, cascade_spacing)
+        vc = rng.normal(0.0, 0.05, size=(n_c, 3))
+        xyz = np.concatenate([xyz, xc])
+        vel3 = np.concatenate([vel3, vc])
+        radii = np.concatenate([radii, r_c])
+    th = math.radians(tilt_deg)
+    if th:
+        # turn positions and velocities about +y by th (distances from the
+        # axis are kept, so every particle stays inside the drum)
+        c, s_ = math.cos(th), math.sin(th)
+        x, z = xyz[:, 0].copy(), xyz[:, 2].copy()
+        xyz[:, 0], xyz[:, 2] = c * x - s_ * z, s_ * x + c * z
+        vx, vz = vel3[:, 0].copy(), vel3[:, 2].copy()
+        vel3[:, 0], vel3[:, 2] = c * vx - s_ * vz, s_ * vx + c * vz
+    if n_c:
+        # downhill along the turned surface: the surface direction (cos th,
+        # sin th) in x-z, signed so that it points down
+        down = np.array([math.cos(th), math.sin(th)])
+        if down[1] > 0:
+            down = -down
+        vel3[-n_c:, 0] += cascade_speed * down[0]
+        vel3[-n_c:, 2] += cascade_speed * down[1]
     pos = np.zeros((n, 4), dtype=np.float32)
     pos[:, :3] = xyz
     pos[:, 3] = radii
     vel = np.zeros((n, 4), dtype=np.float32)
-    # solid-body rotation about +y: v = omega x (x - c) with c on the axis
-    vel[:, 0] = omega * xyz[:, 2]
-    vel[:, 2] = -omega * xyz[:, 0]
+    vel[:, :3] = vel3
     lo = (-R, 0.0, -R)
     hi = (R, length, R)
     return Scene("drum", pos, vel, lo, hi, dt, steps, "drum", gravity=(0.0, 0.0, -9.81),

@@ -7,8 +7,10 @@
 * training on the GPU lowers the loss;
 * the LEARNED skin policy inside the broad phase: the oracle recomputes every
   feature and proposal and must get the same skins, flags and pair sets;
-* the rebuild log: samples carry the features of the update and the label
-  (largest displacement over the horizon / d).
+* the rebuild log: the samples of a context's log equal the oracle's
+  rebuild log (oracle.statemachine.RebuildLog) bit for bit, on a ballistic
+  run and on a packed bed run by the DEM driver;
+* the travel-form labels of the library equal the oracle's.
 """
 import numpy as np
 import pytest
@@ -193,22 +195,103 @@ def test_learned_policy_full_size_drum_parity(orc):
     ctx.close()
 
 
-def test_rebuild_log_samples(orc):
+def _sorted_rows(a):
+    a = np.asarray(a, np.float32)
+    return a[np.lexsort(a.T[::-1])]
+
+
+def test_rebuild_log_matches_oracle_ballistic(orc):
+    # the log of a context (features of each update, largest displacement
+    # over the horizon) against the oracle's rebuild log on the same
+    # positions, velocities and accelerations: the same samples bit for bit
+    # (the device appends them in no particular order, so sorted rows are
+    # compared)
     lvb = _lvb()
+    from oracle import mlp
+    from oracle.statemachine import OracleLVB, RebuildLog
     s = scenes.ballistic(n=2000, seed=23, vsigma=1.0)
-    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, 1, 0.1, s.dt, 0, s.cell_factor)
+    acc = np.zeros_like(s.pos)
+    acc[:, 2] = -9.81
     horizon = 10
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_PAPER_KVDT, 60.0, s.dt,
+                  lvb.LVB_TRIGGER_PARTIAL, s.cell_factor, vel=_dev(s.vel), acc=_dev(acc))
     ctx.log_enable(horizon, 100000)
-    traj = list(scenes.ballistic_trajectory(s, 80))
-    for pos, _ in traj:
-        ctx.step(_dev(pos))
-    smp = ctx.log_samples()
-    assert len(smp) > 20
-    # labels are the largest displacement over the horizon in diameters:
-    # bounded by |v| * horizon * dt / d for ballistic motion between walls
-    vmax = np.linalg.norm(s.vel[:, :3], axis=1).max()
-    assert (smp[:, 8] >= 0).all()
-    assert smp[:, 8].max() <= vmax * horizon * s.dt / (2 * 1e-3) * 1.001
-    # features f2 = r / H, f4 = age > 0 after the first update
-    assert np.allclose(smp[:, 2], np.float32(1e-3) / ctx.stats()["rnl_max"])
+    grid = mlp.grid_params(s.pos[:, 3].max(), s.cell_factor, s.lo, s.hi)
+    assert np.float32(ctx.stats()["rnl_max"]) == grid["H"]
+    sm = OracleLVB(s.pos, orc.SKIN_PAPER_KVDT, 60.0, s.dt, grid["H"], 0, vel4=s.vel)
+    log = RebuildLog(sm, grid, horizon)
+    for pos, vel in scenes.ballistic_trajectory(s, 80):
+        ctx.step(_dev(pos), _dev(vel), _dev(acc))
+        log.step(pos, vel4=vel, acc4=acc)
+    got, want = ctx.log_samples(), log.log()
+    assert len(want) > 100
+    assert got.shape == want.shape
+    assert np.array_equal(_sorted_rows(got), _sorted_rows(want))
     ctx.close()
+
+
+def test_rebuild_log_matches_oracle_packed_dem(orc):
+    # the same on a packed bed run by the DEM driver, phase by phase: the
+    # oracle is fed the driver's own state after each position half-step
+    # (x', v* and a, what the broad phase sees)
+    lvb = _lvb()
+    from oracle import mlp
+    from oracle.statemachine import OracleLVB, RebuildLog
+    s = scenes.packed(n=4000, seed=31, vsigma=0.2)
+    horizon = 7
+    dem = lvb.DEM(s)
+    dem.lvb.log_enable(horizon, 100000)
+    H = np.float32(dem.lvb.stats()["rnl_max"])
+    grid = mlp.grid_params(s.pos[:, 3].max(), s.cell_factor, s.lo, s.hi)
+    assert grid["H"] == H
+    sm = OracleLVB(s.pos, orc.SKIN_DIAMETER_FACTOR, s.skin_value, s.dt, H, 0,
+                   ref4=dem.lvb.ref())
+    log = RebuildLog(sm, grid, horizon)
+    for _ in range(60):
+        dem.phase(lvb.DEM_PHASE_INTEGRATE)
+        x, _, a, vstar = dem.state()
+        dem.phase(lvb.DEM_PHASE_BROAD)
+        dem.phase(lvb.DEM_PHASE_FORCES)
+        log.step(x, vel4=vstar, acc4=a)
+    got, want = dem.lvb.log_samples(), log.log()
+    assert len(want) > 100
+    assert got.shape == want.shape
+    assert np.array_equal(_sorted_rows(got), _sorted_rows(want))
+    assert np.array_equal(dem.lvb.ref(), sm.ref)
+    dem.close()
+
+
+def test_travel_labels_match_oracle(orc):
+    # lvb_mlp_travel_labels against the oracle's travel_labels: random
+    # samples with some particles at rest (f0 = 0), and a real log
+    lvb = _lvb()
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    smp = rng.uniform(0.0, 2.0, size=(200_003, 9)).astype(np.float32)
+    smp[rng.random(len(smp)) < 0.1, 0] = 0.0
+    for h, margin, q in ((400, 2.0, 0.99), (7, 1.5, 0.5), (1, 1.0, 1.0)):
+        got = lvb.mlp_travel_labels(smp, h, margin, q)
+        want = mlp.travel_labels(smp, h, margin, q)
+        assert got.shape == want.shape
+        assert np.array_equal(got, want), (h, margin, q)
+    s = scenes.ballistic(n=2000, seed=29, vsigma=1.0)
+    ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, s.dt,
+                  lvb.LVB_TRIGGER_PARTIAL, s.cell_factor, vel=_dev(s.vel))
+    ctx.log_enable(10, 100000)
+    for pos, vel in scenes.ballistic_trajectory(s, 60):
+        ctx.step(_dev(pos), _dev(vel))
+    real = ctx.log_samples()
+    ctx.close()
+    assert len(real) > 50
+    assert np.array_equal(lvb.mlp_travel_labels(real, 10, 2.0, 0.99),
+                          mlp.travel_labels(real, 10, 2.0, 0.99))
+    # argument checks
+    import ctypes
+    m = ctypes.c_int64(0)
+    d = _dev(smp[:10])
+    o = torch.empty_like(d)
+    for args in ((0, 2.0, 0.5), (10, 0.0, 0.5), (10, 2.0, 0.0), (10, 2.0, 1.5)):
+        rc = lvb.lvb_mlp_travel_labels(d.data_ptr(), 10, *args, o.data_ptr(), ctypes.byref(m))
+        assert rc == lvb.LVB_EINVAL, args
+    rc = lvb.lvb_mlp_travel_labels(d.data_ptr(), 10, 10, 2.0, 0.5, d.data_ptr(), ctypes.byref(m))
+    assert rc == lvb.LVB_EINVAL
