@@ -67,10 +67,8 @@ T0 = 1000                 # the timed window starts after step T0 of the batch's
 T0_SETTLING = 10_000      # and after step T0_SETTLING of the 200k settling box's run
 # 1 GiB: well above the 129 MB L2 (for the workloads that fit in it)
 L2_FLUSH_BYTES = 1 << 30
-M_E2E = 16                # steps of the window the e2e leg replays
-M_CPU = 32                # steps of the window the CPU baseline replays
-CPU_SAMPLE_N = 600_000    # particles (whole scenes from scene 0) the CPU baseline replays
-CPU_BUDGET_S = 12.0       # seconds of oracle time per thread setting
+M_E2E = 16                # steps of the window the e2e and CPU legs replay
+CPU_BUDGET_S = 15.0       # seconds of oracle time per thread setting (whole scenes)
 REF_SAMPLE_N = 40_000     # particles of the reference arm's sample (scenes > 4096 each)
 
 
@@ -292,9 +290,8 @@ def _tune(lvb, torch, sc):
 def _headline(lvb, torch, sc, choice, steps, warmup, record=True, profile=False):
     """The batch from step T0 - warmup: warm-up steps, then `steps` timed
     steps phase by phase.  Records (for the e2e and CPU legs) the reference
-    state and positions at the window's start, all positions over the first
-    M_E2E steps and the positions of a block of whole scenes from scene 0
-    over the first M_CPU steps."""
+    state and positions at the window's start and all positions over the
+    first M_E2E steps."""
     n = int(sum(q.n for q in sc))
     dem = lvb.DEM(sc, cell_factor=choice.cell_factor)
     choice.apply(dem, lvb)
@@ -305,23 +302,16 @@ def _headline(lvb, torch, sc, choice, steps, warmup, record=True, profile=False)
     on_step = None
     if record:
         off = dem.offsets
-        q1 = int(np.searchsorted(off, CPU_SAMPLE_N, side="right")) - 1
-        q1 = max(1, min(q1, len(sc)))
-        nb = int(off[q1])
-        m_e2e, m_cpu = min(M_E2E, steps), min(M_CPU, steps)
-        rec = {"ref0": dem.lvb.ref(), "pos0": dem.state()[0], "m_e2e": m_e2e, "m_cpu": m_cpu,
-               "q1": q1, "nb": nb,
+        m_e2e = min(M_E2E, steps)
+        rec = {"ref0": dem.lvb.ref(), "pos0": dem.state()[0], "m_e2e": m_e2e,
                "pos_e2e": torch.empty((m_e2e, n, 4), dtype=torch.float32, pin_memory=True),
-               "pos_cpu": torch.empty((m_cpu, nb, 4), dtype=torch.float32, pin_memory=True),
-               "rnl_max": [dem.lvb.scene_info(q)["rnl_max"] for q in range(q1)],
+               "rnl_max": [dem.lvb.scene_info(q)["rnl_max"] for q in range(len(sc))],
                "offsets": off}
         dpos = dem.device_pos_tensor(torch)
 
         def on_step(k):
             if k < m_e2e:
                 rec["pos_e2e"][k].copy_(dpos, non_blocking=True)
-            if k < m_cpu:
-                rec["pos_cpu"][k].copy_(dpos[:nb], non_blocking=True)
     s0 = dem.lvb.stats()
     if profile:
         torch.cuda.synchronize()
@@ -388,19 +378,20 @@ def _e2e_batch(lvb, torch, sc, choice, rec):
 
 def _oracle_replay(sc, rec, threads, budget_s):
     """The oracle's broad phase (flags, skins, pair set by linked cells) on
-    the GPU run's own states: each scene of the recorded block starts from
-    the run's reference state at the window's start and steps through the
-    recorded positions.  Scenes are replayed one after another until the
-    time budget is spent; returns particle-steps/s and what was covered."""
+    the GPU run's own states: each scene starts from the run's reference
+    state at the window's start and steps through the recorded positions of
+    the window's first steps.  Scenes are replayed one after another, from
+    scene 0, until the time budget is spent; returns particle-steps/s and
+    what was covered."""
     import oracle
     from oracle.statemachine import OracleLVB
     oracle.set_threads(threads)
     used = oracle.threads()
     off = rec["offsets"]
-    pos = rec["pos_cpu"].numpy()
-    m = rec["m_cpu"]
+    pos = rec["pos_e2e"].numpy()
+    m = rec["m_e2e"]
     done_ps, el, scenes_done = 0, 0.0, 0
-    for q in range(rec["q1"]):
+    for q in range(len(sc)):
         a, b = int(off[q]), int(off[q + 1])
         s0 = sc[q]
         sm = OracleLVB(rec["pos0"][a:b], s0.skin_kind, s0.skin_value, s0.dt, rec["rnl_max"][q],

@@ -299,6 +299,31 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 list; 1 and 2 read fewer candidates with
                                 polydisperse radii */
 
+#define LVB_OPT_CELL_CAPACITY 12 /* slots per cell of at least value (rounded
+                                up to a multiple of 32, at most 65536): the
+                                cells are re-laid out before the next step
+                                (no effect if they already have as many).
+                                The library sizes the slots from the initial
+                                occupancy and a dense packing of the mean
+                                particle volume, and doubles them between
+                                steps when a cell passes 75%; a caller that
+                                moves many particles into one cell within
+                                one step raises them first */
+
+/* Test hooks for the overflow paths (they make a store fill up without a
+ * device fault; the results of a context that reports LVB_EOVERFLOW are
+ * invalid, as always): */
+#define LVB_OPT_GROW 10       /* 1 (default): the host grows the cell slots and
+                                the row store between steps when a kernel
+                                finds them over 75% / 60% full; 0: requests
+                                are ignored, so a cell that fills up reports
+                                LVB_EOVERFLOW */
+#define LVB_OPT_STORE_LIMIT 11 /* entries of the row store a re-layout may use:
+                                0 (default) the whole allocation, else
+                                min(value, allocation); a re-layout that does
+                                not fit even without slack reports
+                                LVB_EOVERFLOW */
+
 /* Values of LVB_OPT_COMPACT. */
 #define LVB_COMPACT_WARP  0  /* flagged ids gather in a per-warp list during
                                 the check; the list takes its indices with

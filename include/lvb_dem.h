@@ -106,6 +106,24 @@ int dem_phase(dem_ctx *ctx, int32_t phase);
  * records; any pointer may be NULL).  Synchronises. */
 int dem_get_state(dem_ctx *ctx, float *pos_r, float *vel, float *acc, float *vstar);
 
+/*
+ * dem_get_contact_forces -- the contacts of the current state and the
+ * normal force of each, as the forces phase evaluates them (the narrow
+ * phase of Eq. delta on the list, the linear spring-dashpot law above):
+ * every pair i < j of the list with delta_ij > 0 at the current positions
+ * (x' of the last step), in no particular order, with
+ *   force3 : the force on i, (k_n delta - gamma v_n) n_ij (3 floats a pair;
+ *            the force on j is its negation),
+ *   delta  : the overlap (compensated binary32).
+ * ci, cj, force3, delta: host or device, cap entries (force3: 3 cap
+ * floats); *n_contacts: the number of contacts (LVB_ECAPACITY if over cap,
+ * the first cap written).  Allocates temporary device memory.
+ * Synchronises.  Errors: EINVAL, ECAPACITY, ENOMEM, EDEVICE and the broad
+ * phase's device errors.
+ */
+int dem_get_contact_forces(dem_ctx *ctx, int32_t *ci, int32_t *cj, float *force3, float *delta,
+                           int64_t cap, int64_t *n_contacts);
+
 /* dem_set_state -- overwrite x, v, a (host or device float4 records; radii
  * in pos_r must equal the initial ones).  The broad phase keeps its
  * reference state, so the next step's check sees the new positions. */

@@ -90,6 +90,9 @@ def _configure(L):
         L.orc_dem_step64.argtypes = [i64, p, p, p, p, ctypes.c_double,
                                      ctypes.POINTER(DemParams), p, p, p, p, p, p, p]
         L.orc_dem_step64.restype = ctypes.c_int
+        L.orc_dem_contacts64.argtypes = [i64, p, p, p, ctypes.POINTER(DemParams), p, p, p, p,
+                                         p, i64]
+        L.orc_dem_contacts64.restype = i64
         L.orc_improvement_pct.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_improvement_pct.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -328,6 +331,31 @@ def dem_step(x4, v4, a4, dt, P, x_in=None, vstar_in=None, with_fmag=False):
     return dem_step64(x4, v4, a4, x4[:, 3], dt, P,
                       None if x_in is None else _f32x4(x_in),
                       None if vstar_in is None else _f32x4(vstar_in), with_fmag=with_fmag)
+
+
+def dem_contacts(x4, v4, P):
+    """Every contact i < j of the configuration (binary64 overlap > 0) with
+    the force on i, the overlap and the scale of the force's terms, from the
+    binary32 state of the code under test widened exactly: (ci, cj, f (m,
+    3), delta, scale), sorted by (i, j)."""
+    x4, v4 = _f32x4(x4), _f32x4(v4)
+    x, v = _d3(x4), _d3(v4)
+    r = np.ascontiguousarray(x4[:, 3], dtype=np.float64)
+    n = len(x)
+    cap = max(16, 8 * n)
+    while True:
+        ci = np.empty(cap, np.int32)
+        cj = np.empty(cap, np.int32)
+        f3 = np.empty((cap, 3), np.float64)
+        dl = np.empty(cap, np.float64)
+        sc = np.empty(cap, np.float64)
+        m = lib().orc_dem_contacts64(n, _ptr(x), _ptr(r), _ptr(v), ctypes.byref(P), _ptr(ci),
+                                     _ptr(cj), _ptr(f3), _ptr(dl), _ptr(sc), cap)
+        if m < 0:
+            raise MemoryError("oracle contact search failed")
+        if m <= cap:
+            return ci[:m].copy(), cj[:m].copy(), f3[:m].copy(), dl[:m].copy(), sc[:m].copy()
+        cap = int(m)
 
 
 def improvement_pct(t_without, t_case):

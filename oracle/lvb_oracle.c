@@ -526,6 +526,88 @@ static double lsd_force(const orc_dem_params *P, double dl, double vn, double me
     return f;
 }
 
+/* Candidate pairs for the binary64 contact search: the binary32 pair search
+ * at cutoff (r_i + r_j)(1 + 2^-20) on the positions rounded to binary32
+ * (brute force when n <= 4096, the oracle's linked cells otherwise), far
+ * above the binary32 rounding of any position.  *ci / *cj are malloc'd;
+ * returns the count or -1. */
+static int64_t contact_candidates(int64_t n, const double *x, const double *r, int32_t **ci_out,
+                                  int32_t **cj_out)
+{
+    *ci_out = NULL;
+    *cj_out = NULL;
+    float *ref = (float *)malloc((size_t)(n > 0 ? n : 1) * 4 * sizeof(float));
+    float *rad = (float *)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+    if (!ref || !rad) { free(ref); free(rad); return -1; }
+    for (int64_t i = 0; i < n; ++i) {
+        ref[4 * i + 0] = (float)x[3 * i + 0];
+        ref[4 * i + 1] = (float)x[3 * i + 1];
+        ref[4 * i + 2] = (float)x[3 * i + 2];
+        ref[4 * i + 3] = (float)(r[i] * (1.0 / 1048576.0));
+        rad[i] = (float)r[i];
+    }
+    int64_t cap = 16 * n + 1024;
+    int32_t *ci = NULL, *cj = NULL;
+    int64_t np;
+    for (;;) {
+        ci = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+        cj = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+        if (!ci || !cj) { free(ci); free(cj); free(ref); free(rad); return -1; }
+        np = (n <= 4096) ? orc_pairs_brute(n, ref, rad, ci, cj, cap)
+                         : orc_pairs_cells(n, ref, rad, ci, cj, cap);
+        if (np <= cap) break;
+        cap = np;
+        free(ci); free(cj);
+    }
+    free(ref); free(rad);
+    if (np < 0) { free(ci); free(cj); return -1; }
+    *ci_out = ci;
+    *cj_out = cj;
+    return np;
+}
+
+/* Every contact i < j (delta > 0 in binary64) of a configuration, sorted by
+ * (i, j), with the force on i, f n (f = k_n delta - gamma_n v_n, n from j to
+ * i, the law of orc_dem_forces64 below), the overlap, and the scale of the
+ * terms of f, |k_n delta| + |gamma_n v_n|.  x, v: 3n; r: n.  Writes at
+ * most cap contacts; returns their number or -1.
+ * Pinned by: the head-on pair in closed form (tests). */
+ORC_API int64_t orc_dem_contacts64(int64_t n, const double *x, const double *r, const double *v,
+                                   const orc_dem_params *P, int32_t *oi, int32_t *oj,
+                                   double *f3, double *delta, double *scale, int64_t cap)
+{
+    int32_t *ci, *cj;
+    int64_t np = contact_candidates(n, x, r, &ci, &cj);
+    if (np < 0) return -1;
+    int64_t m = 0;
+    for (int64_t k = 0; k < np; ++k) {
+        int64_t i = ci[k], j = cj[k];
+        double d[3], dist2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = x[3 * i + c] - x[3 * j + c];
+            dist2 += d[c] * d[c];
+        }
+        double dist = sqrt(dist2);
+        double dl = (r[i] + r[j]) - dist;
+        if (!(dl > 0.0) || !(dist > 0.0)) continue;
+        double nrm[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+        double vn = 0.0;
+        for (int c = 0; c < 3; ++c) vn += (v[3 * i + c] - v[3 * j + c]) * nrm[c];
+        double mi = mass_of(r[i], P->rho), mj = mass_of(r[j], P->rho);
+        double f = lsd_force(P, dl, vn, mi * mj / (mi + mj));
+        if (m < cap) {
+            oi[m] = (int32_t)i;
+            oj[m] = (int32_t)j;
+            for (int c = 0; c < 3; ++c) f3[3 * m + c] = f * nrm[c];
+            delta[m] = dl;
+            scale[m] = fabs(P->kn * dl) + fabs(f - P->kn * dl);
+        }
+        ++m;
+    }
+    free(ci); free(cj);
+    return m;
+}
+
 /* Net force on every particle (binary64).  x: 3n positions, r: n radii,
  * v: 3n damping velocities.  Candidate pairs come from the binary32 pair
  * search at cutoff (r_i + r_j)(1 + 2^-20) on the positions rounded to
@@ -539,31 +621,9 @@ ORC_API int orc_dem_forces64(int64_t n, const double *x, const double *r, const 
     memset(force, 0, (size_t)n * 3 * sizeof(double));
     if (fmag) memset(fmag, 0, (size_t)n * sizeof(double));
     if (P->contacts_on && n > 1) {
-        float *ref = (float *)malloc((size_t)n * 4 * sizeof(float));
-        float *rad = (float *)malloc((size_t)n * sizeof(float));
-        if (!ref || !rad) { free(ref); free(rad); return -1; }
-        for (int64_t i = 0; i < n; ++i) {
-            ref[4 * i + 0] = (float)x[3 * i + 0];
-            ref[4 * i + 1] = (float)x[3 * i + 1];
-            ref[4 * i + 2] = (float)x[3 * i + 2];
-            ref[4 * i + 3] = (float)(r[i] * (1.0 / 1048576.0));
-            rad[i] = (float)r[i];
-        }
-        int64_t cap = 16 * n + 1024;
-        int32_t *ci = NULL, *cj = NULL;
-        int64_t np;
-        for (;;) {
-            ci = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
-            cj = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
-            if (!ci || !cj) { free(ci); free(cj); free(ref); free(rad); return -1; }
-            np = (n <= 4096) ? orc_pairs_brute(n, ref, rad, ci, cj, cap)
-                             : orc_pairs_cells(n, ref, rad, ci, cj, cap);
-            if (np <= cap) break;
-            cap = np;
-            free(ci); free(cj);
-        }
-        free(ref); free(rad);
-        if (np < 0) { free(ci); free(cj); return -1; }
+        int32_t *ci, *cj;
+        int64_t np = contact_candidates(n, x, r, &ci, &cj);
+        if (np < 0) return -1;
         for (int64_t k = 0; k < np; ++k) {
             int64_t i = ci[k], j = cj[k];
             double d[3], dist2 = 0.0;

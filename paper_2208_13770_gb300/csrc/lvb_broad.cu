@@ -258,10 +258,12 @@ k_scan_down(ScanArgs a, DevState s, int gate)
 // Init helpers.
 // ---------------------------------------------------------------------------
 // out[0] = min radius bits, out[1] = bad input, out[2 + s] = max radius
-// bits of scene s (positive floats order like their bit patterns)
+// bits of scene s (positive floats order like their bit patterns);
+// *r3sum += the sum of r^3 (binary64, for the mean particle volume)
 __global__ void k_radius_scan(const float4 *__restrict__ pos, int n, const int *scene_of,
-                              unsigned *out)
+                              unsigned *out, double *r3sum)
 {
+    double r3 = 0.0;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         const float4 p = pos[i];
         const bool ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) &&
@@ -269,7 +271,11 @@ __global__ void k_radius_scan(const float4 *__restrict__ pos, int n, const int *
         if (!ok) { atomicOr(&out[1], 1u); continue; }
         atomicMin(&out[0], __float_as_uint(p.w));
         atomicMax(&out[2 + (scene_of ? scene_of[i] : 0)], __float_as_uint(p.w));
+        r3 += (double)p.w * (double)p.w * (double)p.w;
     }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) r3 += __shfl_xor_sync(FULL, r3, o);
+    if ((threadIdx.x & 31) == 0 && r3 != 0.0) atomicAdd(r3sum, r3);
 }
 
 __global__ void k_radius_store(const float4 *__restrict__ pos, int n, float *rad)
@@ -433,6 +439,10 @@ struct lvb_ctx {
     int version = 0;                // bumped whenever the step kernel's arguments change
     HostFlags *hflags = nullptr;    // mapped pinned host memory
     long long grows = 0;            // store or cell-slot growths done
+    int grow = 1;                   // 0: requests to grow are ignored (LVB_OPT_GROW)
+    int ccap_want = 0;              // slots per cell asked for (LVB_OPT_CELL_CAPACITY)
+    long long col_alloc = 0;        // entries allocated for the row store (s.col_cap,
+                                    // the usable part, may be set lower: LVB_OPT_STORE_LIMIT)
     // lvb_step_host: two staging slots, each with device buffers for the
     // inputs (pos, vel, acc) and the outputs (flag words, flagged count);
     // the inputs come in on one copy stream and the outputs go out on
@@ -588,14 +598,14 @@ int sync_counters(lvb_ctx *c)
 int grow_if_asked(lvb_ctx *c)
 {
     volatile HostFlags *h = c->hflags;
-    if (!h->grow_store && !h->grow_cells) return LVB_OK;
+    if (!c->grow || (!h->grow_store && !h->grow_cells)) return LVB_OK;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return from_cuda(e);
     DevState &s = c->s;
     const cudaStream_t st = c->stream;
     const bool cells = h->grow_cells != 0;
     if (cells && s.ccap < (1 << 16)) {
-        const int ccap = std::min(2 * s.ccap, 1 << 16);
+        const int ccap = std::min(std::max(2 * s.ccap, c->ccap_want), 1 << 16);
         cudaFree(s.cell_id);
         cudaFree(s.cell_ref);
         s.cell_id = nullptr;
@@ -628,6 +638,7 @@ int grow_if_asked(lvb_ctx *c)
         e = dalloc(&s.col, cap);
         if (e != cudaSuccess) return from_cuda(e);
         s.col_cap = cap;
+        c->col_alloc = cap;
     }
     k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 1);
     e = cudaGetLastError();
@@ -811,15 +822,18 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     e = cudaMemcpyAsync(c->scratch, rs.data(), sizeof(unsigned) * rs.size(),
                         cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail(from_cuda(e));
+    cudaMemsetAsync(c->sum64, 0, sizeof(double), st);
     k_radius_scan<<<grid_for(n, kThreads, 4 * kNumSMs), kThreads, 0, st>>>(
-        (const float4 *)pos_r, (int)n, c->scene_of_d, c->scratch);
+        (const float4 *)pos_r, (int)n, c->scene_of_d, c->scratch, (double *)c->sum64);
+    double r3sum = 0.0;
     e = cudaMemcpyAsync(rs.data(), c->scratch, sizeof(unsigned) * rs.size(),
                         cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&r3sum, c->sum64, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(from_cuda(e));
     if (rs[1]) return fail(LVB_ENAN);
-    float rmin;
-    memcpy(&rmin, &rs[0], 4);
+    const double r3mean = r3sum / (double)n;
 
     // per-scene geometry: cell edge, cap H, grid (at most 2048 cells per axis)
     c->sg.resize((size_t)nscenes);
@@ -942,7 +956,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(from_cuda(e));
     {
-        const double vmean = 4.0 / 3.0 * M_PI * (double)rmin * rmin * rmin;
+        const double vmean = 4.0 / 3.0 * M_PI * r3mean;
         const double dense = 0.74 * Lmax * Lmax * Lmax / std::max(vmean, 1e-30);
         long long cap = std::max<long long>(2LL * maxocc + 8, 32);
         cap = std::max<long long>(cap, (long long)std::min(dense * 0.5, 4096.0));
@@ -973,6 +987,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     e = dalloc(&s.col, col_cap);
     if (e != cudaSuccess) return fail(from_cuda(e));
     s.col_cap = col_cap;
+    c->col_alloc = col_cap;
     c->s = s;
     k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 1);
     e = cudaGetLastError();
@@ -1152,6 +1167,19 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     } else if (option == LVB_OPT_STENCIL_REACH) {
         if (value < 0 || value > 2) return LVB_EINVAL;
         c->s.reach = (int)value;
+    } else if (option == LVB_OPT_CELL_CAPACITY) {
+        if (value < 1 || value > (1 << 16)) return LVB_EINVAL;
+        const int want = (int)((value + 31) / 32 * 32);
+        if (want > c->ccap) {
+            c->ccap_want = want;
+            c->hflags->grow_cells = 1;   // grown before the next step
+        }
+    } else if (option == LVB_OPT_GROW) {
+        if (value != 0 && value != 1) return LVB_EINVAL;
+        c->grow = (int)value;
+    } else if (option == LVB_OPT_STORE_LIMIT) {
+        if (value < 0) return LVB_EINVAL;
+        c->s.col_cap = value == 0 ? c->col_alloc : std::min<long long>(value, c->col_alloc);
     } else {
         return LVB_EINVAL;
     }

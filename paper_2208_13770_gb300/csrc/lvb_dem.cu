@@ -132,6 +132,41 @@ __device__ __forceinline__ float plane_force(const DemDev &d, float x, float v, 
     return F;
 }
 
+// One contact of the narrow phase (Eq. delta) and its force: particle i at
+// xi with v* and 1/m in vi, against partner j of its row.  Returns false
+// when the two do not overlap (delta <= 0); else the overlap dl (compensated
+// binary32), the unit normal n (from j to i) and the normal force f on i
+// along n (linear spring-dashpot, damping on the normal component of
+// v*_i - v*_j).
+__device__ __forceinline__ bool contact_pair(const DemDev &d, float4 xi, float4 vi, int j,
+                                             float &dl, float n[3], float &f)
+{
+    const float4 xj = d.pos[j];
+    float h[3], l[3];
+    two_diff(xi.x, xj.x, h[0], l[0]);
+    two_diff(xi.y, xj.y, h[1], l[1]);
+    two_diff(xi.z, xj.z, h[2], l[2]);
+    // cheap reject before the compensated distance
+    const float Rr = xi.w + xj.w;
+    const float d2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    if (d2 > Rr * Rr * 1.0001f) return false;
+    float s0, corr;
+    norm_dd(h, l, s0, corr);
+    float Rh, Rl;
+    two_sum(xi.w, xj.w, Rh, Rl);
+    dl = __fsub_rn(Rh, s0) + (Rl - corr);
+    if (!(dl > 0.0f) || !(s0 > 0.0f)) return false;
+    const float inv = 1.0f / (s0 + corr);
+    n[0] = (h[0] + l[0]) * inv;
+    n[1] = (h[1] + l[1]) * inv;
+    n[2] = (h[2] + l[2]) * inv;
+    const float4 vj = d.vstar[j];
+    const float vn = (vi.x - vj.x) * n[0] + (vi.y - vj.y) * n[1] + (vi.z - vj.z) * n[2];
+    const float meff = 1.0f / (vi.w + vj.w);
+    f = lsd(d, dl, vn, meff);
+    return true;
+}
+
 // Narrow phase on the row of particle i + walls + velocity finish.
 __device__ __forceinline__ void forces_one(const DemDev &d, int i)
 {
@@ -141,37 +176,19 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
     float4 v = d.vel[i];
     const float im_i = vi.w;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (d.contacts_on) {
+    // after a row store that failed even a tight re-layout (LVB_EOVERFLOW)
+    // the row offsets no longer fit the store: the rows are not read
+    if (d.contacts_on && !(d.rows.cnt->err & DERR_STORE)) {
         const int off = d.rows.row_off[i];
         const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
         for (int e = 0; e < len; ++e) {
             const int j = d.rows.col[off + e];
             if (j < 0) continue;            // a removed pair's slot
-            const float4 xj = d.pos[j];
-            float h[3], l[3];
-            two_diff(xi.x, xj.x, h[0], l[0]);
-            two_diff(xi.y, xj.y, h[1], l[1]);
-            two_diff(xi.z, xj.z, h[2], l[2]);
-            // cheap reject before the compensated distance
-            const float Rr = xi.w + xj.w;
-            const float d2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
-            if (d2 > Rr * Rr * 1.0001f) continue;
-            float s0, corr;
-            norm_dd(h, l, s0, corr);
-            float Rh, Rl;
-            two_sum(xi.w, xj.w, Rh, Rl);
-            const float dl = __fsub_rn(Rh, s0) + (Rl - corr);
-            if (!(dl > 0.0f) || !(s0 > 0.0f)) continue;
-            const float inv = 1.0f / (s0 + corr);
-            const float n0 = (h[0] + l[0]) * inv, n1 = (h[1] + l[1]) * inv,
-                        n2 = (h[2] + l[2]) * inv;
-            const float4 vj = d.vstar[j];
-            const float vn = (vi.x - vj.x) * n0 + (vi.y - vj.y) * n1 + (vi.z - vj.z) * n2;
-            const float meff = 1.0f / (im_i + vj.w);
-            const float f = lsd(d, dl, vn, meff);
-            Fx += f * n0;
-            Fy += f * n1;
-            Fz += f * n2;
+            float dl, n[3], f;
+            if (!contact_pair(d, xi, vi, j, dl, n, f)) continue;
+            Fx += f * n[0];
+            Fy += f * n[1];
+            Fz += f * n[2];
         }
     }
     const float r = xi.w;
@@ -235,6 +252,37 @@ struct DemTail {
         for (int i = t; i < d.n; i += nt) forces_one(d, i);
     }
 };
+
+// The contacts of the current state, each pair once (i < j from row i),
+// with the force on i and the overlap; positions in the output from one
+// atomic counter, so in no particular order.
+__global__ void __launch_bounds__(kThreads)
+k_contact_list(DemDev d, unsigned long long *cnt, long long cap, int *ci, int *cj, float *f3,
+               float *delta)
+{
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
+    if (i >= d.n || !d.contacts_on || (d.rows.cnt->err & DERR_STORE)) return;
+    const float4 xi = d.pos[i];
+    const float4 vi = d.vstar[i];
+    const int off = d.rows.row_off[i];
+    const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
+    for (int e = 0; e < len; ++e) {
+        const int j = d.rows.col[off + e];
+        if (j <= i) continue;               // a removed pair's slot, or the pair from j's row
+        float dl, n[3], f;
+        if (!contact_pair(d, xi, vi, j, dl, n, f)) continue;
+        const unsigned long long k = atomicAdd(cnt, 1ULL);
+        if (k < (unsigned long long)cap) {
+            ci[k] = i;
+            cj[k] = j;
+            f3[3 * k + 0] = f * n[0];
+            f3[3 * k + 1] = f * n[1];
+            f3[3 * k + 2] = f * n[2];
+            delta[k] = dl;
+        }
+    }
+}
 
 __global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                             float rho)
@@ -495,6 +543,54 @@ int dem_advance(dem_ctx *c, int64_t steps)
         if (rc) return rc;
     }
     return LVB_OK;
+}
+
+int dem_get_contact_forces(dem_ctx *c, int32_t *ci, int32_t *cj, float *force3, float *delta,
+                           int64_t cap, int64_t *n_contacts)
+{
+    if (!c || !n_contacts || cap < 0 || (cap > 0 && (!ci || !cj || !force3 || !delta)))
+        return LVB_EINVAL;
+    *n_contacts = 0;
+    refresh(c);
+    const long long cp = std::max<long long>(cap, 1);
+    int *di = nullptr, *dj = nullptr;
+    float *df = nullptr, *dd = nullptr;
+    unsigned long long *cnt = nullptr;
+    cudaError_t e = cudaMalloc((void **)&cnt, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&di, sizeof(int) * cp);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dj, sizeof(int) * cp);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&df, sizeof(float) * 3 * cp);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dd, sizeof(float) * cp);
+    unsigned long long total = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(total), c->stream);
+    if (e == cudaSuccess) {
+        k_contact_list<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d, cnt, cap, di, dj, df,
+                                                                     dd);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const long long m = std::min<long long>((long long)total, cap);
+    if (e == cudaSuccess && m > 0) {
+        e = cudaMemcpyAsync(ci, di, sizeof(int) * m, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cj, dj, sizeof(int) * m, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(force3, df, sizeof(float) * 3 * m, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(delta, dd, sizeof(float) * m, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFree(cnt);
+    cudaFree(di);
+    cudaFree(dj);
+    cudaFree(df);
+    cudaFree(dd);
+    if (e != cudaSuccess) return from_cuda(e);
+    *n_contacts = (int64_t)total;
+    const int rc = lvb_sync(c->bp);
+    if (rc) return rc;
+    return (long long)total > cap ? LVB_ECAPACITY : LVB_OK;
 }
 
 int dem_get_state(dem_ctx *c, float *pos_r, float *vel, float *acc, float *vstar)

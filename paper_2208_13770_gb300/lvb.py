@@ -121,6 +121,7 @@ _SIGS = {
     "dem_phase": ([_p, ctypes.c_int32], ctypes.c_int),
     "dem_get_state": ([_p, _p, _p, _p, _p], ctypes.c_int),
     "dem_set_state": ([_p, _p, _p, _p], ctypes.c_int),
+    "dem_get_contact_forces": ([_p, _p, _p, _p, _p, _i64, _pi64], ctypes.c_int),
     "dem_lvb": ([_p, ctypes.POINTER(_p)], ctypes.c_int),
     "dem_device_state": ([_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p),
                           ctypes.POINTER(_p)], ctypes.c_int),
@@ -210,6 +211,9 @@ LVB_OPT_TRACE, LVB_OPT_BLOCK_THREADS, LVB_OPT_COMPACT = 3, 4, 5
 LVB_OPT_BARRIER_EXTRA, LVB_OPT_BARRIER_SPINS = 6, 7
 LVB_OPT_DIRECT_MAX = 8
 LVB_OPT_STENCIL_REACH = 9
+LVB_OPT_GROW = 10
+LVB_OPT_STORE_LIMIT = 11
+LVB_OPT_CELL_CAPACITY = 12
 LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
 TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]
 
@@ -621,6 +625,25 @@ class DEM:
             __cuda_array_interface__ = {"shape": (self.n, 4), "typestr": "<f4",
                                         "data": (ptr, False), "version": 2}
         return torch.as_tensor(_View(), device="cuda")
+
+    def contact_forces(self):
+        """dem_get_contact_forces: (ci, cj, force on i (m, 3), delta), sorted
+        by (i, j)."""
+        n = ctypes.c_int64(0)
+        rc = _lib.dem_get_contact_forces(self.ctx, None, None, None, None, 0, ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "dem_get_contact_forces")
+        cap = max(n.value, 1)
+        ci = np.empty(cap, np.int32)
+        cj = np.empty(cap, np.int32)
+        f3 = np.empty((cap, 3), np.float32)
+        dl = np.empty(cap, np.float32)
+        _check(_lib.dem_get_contact_forces(self.ctx, _np_ptr(ci), _np_ptr(cj), _np_ptr(f3),
+                                           _np_ptr(dl), cap, ctypes.byref(n)),
+               "dem_get_contact_forces")
+        m = n.value
+        o = np.lexsort((cj[:m], ci[:m]))
+        return ci[:m][o], cj[:m][o], f3[:m][o], dl[:m][o]
 
     def set_state(self, pos, vel, acc):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (pos, vel, acc)]

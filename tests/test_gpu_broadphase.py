@@ -372,9 +372,13 @@ def test_crowded_cell_moves_parity(orc, direct_max, crowd):
         snaps, n_res = _crowd_moves(s, n_cells=1, per_cell=2000, seed=33)
         moved = 2000
     assert n_res > 0
+    # slots for the whole crowd (the cells are sized for the scene as it
+    # starts, and grow only between steps)
     st, _ = _run_trajectory(orc, s, snaps, 0, 1, 0.1,
-                            options=((lvb.LVB_OPT_DIRECT_MAX, direct_max),))
+                            options=((lvb.LVB_OPT_DIRECT_MAX, direct_max),
+                                     (lvb.LVB_OPT_CELL_CAPACITY, 4096)))
     assert st["flagged_total"] >= moved + n_res
+    assert st["cell_capacity"] >= 4096
 
 
 def test_near_cutoff_pairs_match_oracle(orc):

@@ -155,7 +155,47 @@ def test_ballistic_driver_matches_oracle_and_broad_phase(orc):
     dem.close()
 
 
+def test_contact_forces_match_oracle(orc):
+    # every contact's normal force (dem_get_contact_forces: the pair i < j,
+    # the force on i, the overlap) against the binary64 oracle at the
+    # driver's own x' and v*: the contact sets agree except for overlaps
+    # within 1e-14 m of zero (below the compensated binary32 overlap's
+    # error), and each force component within 1e-5 of the contact's summed
+    # terms |k_n delta| + |damping|
+    lvb = _lvb()
+    s = scenes.packed(n=6000, seed=12, vsigma=0.5)
+    P = _params(orc, s)
+    dem = lvb.DEM(s)
+    for k in range(3):
+        dem.advance(40)
+        x, _, _, vstar = dem.state()
+        gi, gj, gf, gd = dem.contact_forces()
+        oi, oj, of, od, sc = orc.dem_contacts(x, vstar, P)
+        g = set(zip(gi.tolist(), gj.tolist()))
+        o = dict(zip(zip(oi.tolist(), oj.tolist()), range(len(oi))))
+        assert len(oi) > 5000
+        only_o = [p for p in o if p not in g]
+        assert all(abs(od[o[p]]) <= 1e-14 for p in only_o), only_o[:5]
+        idx = [(t, o[p]) for t, p in enumerate(zip(gi.tolist(), gj.tolist())) if p in o]
+        assert len(idx) == len(gi) - sum(1 for p in g if p not in o)
+        for p in g:
+            if p not in o:     # a contact only the GPU sees: overlap ~0 there too
+                t = list(zip(gi.tolist(), gj.tolist())).index(p)
+                assert abs(gd[t]) <= 1e-14
+        a, b = np.array(idx).T
+        err = np.abs(gf[a].astype(np.float64) - of[b])
+        assert (err <= 1e-5 * sc[b][:, None]).all(), err.max()
+        assert np.all(np.abs(gd[a] - od[b]) <= 1e-12)
+    dem.close()
+
+
 def test_advance_graph_matches_phase_launches(orc):
+    # the fused step (dem_advance: graphs of one cooperative launch per
+    # step) and the phase-by-phase step (dem_phase) use the same arithmetic,
+    # but the order of a row's entries -- set by concurrent slot claims --
+    # orders each force sum, so the two runs agree to rounding, and a
+    # packed bed carries the difference forward: positions to 1e-9 m and
+    # velocities to 1e-4 relative after 250 steps
     lvb = _lvb()
     s = scenes.packed(n=3000, seed=4)
     a = lvb.DEM(s)
@@ -188,11 +228,11 @@ def test_settling_full_size_step_parity(orc):
 
 
 def test_drum_full_size_step_parity(orc):
-    # 2,000,000 spheres in the rotating drum: 1,000 graph-replayed steps from
-    # the lattice start (the bed settles onto the wall), then one step checked
-    # over every particle
+    # 2,000,000 spheres in the rotating drum as the benchmark runs it (bed
+    # turned 30 degrees, 5% in a dilute cascading layer): 1,000
+    # graph-replayed steps, then one step checked over every particle
     lvb = _lvb()
-    s = scenes.drum()
+    s = scenes.drum(tilt_deg=30.0, cascade=0.05)
     P = _params(orc, s)
     dem = lvb.DEM(s)
     dem.advance(1000)

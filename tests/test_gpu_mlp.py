@@ -237,7 +237,7 @@ def test_rebuild_log_matches_oracle_packed_dem(orc):
     lvb = _lvb()
     from oracle import mlp
     from oracle.statemachine import OracleLVB, RebuildLog
-    s = scenes.packed(n=4000, seed=31, vsigma=0.2)
+    s = scenes.packed(n=4000, seed=31, vsigma=3.0)
     horizon = 7
     dem = lvb.DEM(s)
     dem.lvb.log_enable(horizon, 100000)
@@ -247,7 +247,7 @@ def test_rebuild_log_matches_oracle_packed_dem(orc):
     sm = OracleLVB(s.pos, orc.SKIN_DIAMETER_FACTOR, s.skin_value, s.dt, H, 0,
                    ref4=dem.lvb.ref())
     log = RebuildLog(sm, grid, horizon)
-    for _ in range(60):
+    for _ in range(120):
         dem.phase(lvb.DEM_PHASE_INTEGRATE)
         x, _, a, vstar = dem.state()
         dem.phase(lvb.DEM_PHASE_BROAD)

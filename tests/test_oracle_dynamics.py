@@ -143,3 +143,35 @@ def test_fed_state_is_used(orc):
     m = 2500 * 4 / 3 * math.pi * r ** 3
     assert np.allclose(a[1], [1e4 * 1e-5 / m, 0, 0], rtol=1e-12)
     assert np.allclose(a[0], -a[1], rtol=1e-12)
+
+
+def test_contact_list_sums_to_the_net_forces(orc):
+    # the per-contact forces of orc_dem_contacts64, summed per particle (the
+    # force on i, its negation on j), are the net contact forces of
+    # orc_dem_forces64 (pinned by the restitution and energy cases above);
+    # and the head-on pair in closed form: f = k_n delta + gamma |v_n|
+    from paper_2208_13770_gb300 import scenes
+    s = scenes.packed(n=1500, seed=3, vsigma=0.3)
+    P = orc.dem_params(lo=s.lo, hi=s.hi, wall_kind=orc.WALL_NONE)
+    ci, cj, f3, dl, sc = orc.dem_contacts(s.pos, s.vel, P)
+    assert len(ci) > 500 and (dl > 0).all()
+    assert np.all(ci < cj) and np.all(np.diff(ci.astype(np.int64) * len(s.pos) + cj) > 0)
+    F = np.zeros((len(s.pos), 3))
+    np.add.at(F, ci, f3)
+    np.add.at(F, cj, -f3)
+    Fo = orc.dem_forces(s.pos, s.vel, P)
+    assert np.allclose(F, Fo, rtol=0, atol=1e-12 * np.abs(Fo).max())
+    r, m_rho = 1e-3, 2500.0
+    x = np.array([[0, 0, 0, r], [2 * r - 1e-5, 0, 0, r]], np.float32)
+    v = np.zeros((2, 4), np.float32)
+    v[0, 0], v[1, 0] = 0.05, -0.05
+    ci, cj, f3, dl, sc = orc.dem_contacts(x, v, orc.dem_params(wall_kind=orc.WALL_NONE))
+    # the inputs are binary32 values, widened exactly
+    r32, d32, v32 = (float(np.float32(q)) for q in (r, 2 * r - 1e-5, 0.05))
+    m = m_rho * 4.0 / 3.0 * np.pi * r32 ** 3
+    e = 0.7
+    zeta = -np.log(e) / np.sqrt(np.pi ** 2 + np.log(e) ** 2)
+    delta = 2 * r32 - d32
+    f = 1e4 * delta + 2 * zeta * np.sqrt(m / 2 * 1e4) * (2 * v32)
+    assert len(ci) == 1 and np.isclose(dl[0], delta, rtol=1e-12)
+    assert np.isclose(f3[0, 0], -f, rtol=1e-12) and f3[0, 1] == 0 and f3[0, 2] == 0
