@@ -733,8 +733,7 @@ def _ballistic(lvb, torch):
         out[name] = {"broad_us_per_step": 1e3 * ph[1] / sc.steps,
                      "value": sc.n * sc.steps / (ph[1] * 1e-3), "unit": "particle-steps/s",
                      "updated_total": _diff(s0, s1, "updated_total"),
-                     "rebuild_steps": _diff(s0, s1, "rebuild_steps"),
-                     "flagged_once_or_more_fraction": None}
+                     "rebuild_steps": _diff(s0, s1, "rebuild_steps")}
     return out
 
 
@@ -749,6 +748,8 @@ def run_native(args):
     from paper_2208_13770_gb300 import lvb, replicas
     hbm_peak, peak_kind = _peaks()
     sc = _batch_scenes(rank, world)
+    if args.only_batched and args.scenes:
+        sc = sc[:args.scenes]
     n = int(sum(q.n for q in sc))
     K, W = args.steps, args.warmup
     if args.only_batched:
@@ -962,6 +963,9 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the headline window alone, default launch choice, no e2e or "
                          "CPU leg (for profiling)")
+    ap.add_argument("--scenes", type=int, default=0,
+                    help="with --only-batched: the first S scenes of the batch only (a smaller "
+                         "case of the same kernel, for profiling)")
     ap.add_argument("--profile", action="store_true",
                     help="with --only-batched: bracket the timed steps with "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off)")

@@ -160,8 +160,9 @@ def test_contact_forces_match_oracle(orc):
     # the force on i, the overlap) against the binary64 oracle at the
     # driver's own x' and v*: the contact sets agree except for overlaps
     # within 1e-14 m of zero (below the compensated binary32 overlap's
-    # error), and each force component within 1e-5 of the contact's summed
-    # terms |k_n delta| + |damping|
+    # error), each force component within 1e-5 of the contact's summed
+    # terms |k_n delta| + |damping|, and the overlap within the rounding of
+    # the binary32 it is returned in
     lvb = _lvb()
     s = scenes.packed(n=6000, seed=12, vsigma=0.5)
     P = _params(orc, s)
@@ -185,7 +186,8 @@ def test_contact_forces_match_oracle(orc):
         a, b = np.array(idx).T
         err = np.abs(gf[a].astype(np.float64) - of[b])
         assert (err <= 1e-5 * sc[b][:, None]).all(), err.max()
-        assert np.all(np.abs(gd[a] - od[b]) <= 1e-12)
+        # the overlap, returned in binary32: within its rounding
+        assert np.all(np.abs(gd[a] - od[b]) <= 2.0 ** -23 * np.abs(od[b]) + 1e-15)
     dem.close()
 
 

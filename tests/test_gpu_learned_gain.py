@@ -7,19 +7,21 @@ rule with K = 400 runs with the rebuild log on (horizon 400 steps: label =
 largest displacement over the next 400 steps, in diameters, times a margin
 of 1.3).  The network is trained on the GPU on those samples, run once with
 the log on (stage 1), trained again on both logs -- its own states included
--- and run (stage 2), from three initial weight draws; of these six
-networks the one with the fewest updates among those whose list is no
-larger than 1.05 times the rule's is kept (training itself is repeatable,
-but row order, hence force summation order, and so the logged samples vary
-from run to run).  Against the rule it updates fewer particles -- at most
-0.7 times as many -- and the displacement check still guards every list:
-the contacts found from the list at the end equal the oracle's contacts
-over all pairs at the same positions.
+-- and run (stage 2), from three initial weight draws.  The network kept
+is chosen on a validation pack (another seed): the one with the fewest
+updates among those whose list is no larger than 1.05 times the rule's
+there.  Only then is it run on the test pack, once, against the rule: it
+updates at most 0.7 times as many particles with a list no more than 1.05
+times as long, and the displacement check still guards every list: the
+contacts found from the list at the end equal the oracle's contacts over
+all pairs at the same positions.
 
 On the rotating drum, the network in the travel form of its output (a
 per-particle factor of the paper's rule) trained on the plain local
-buffer's log rebuilds on fewer steps than the plain rule, with a shorter
-list.
+buffer's log (labels from lvb_mlp_travel_labels) and chosen on a
+validation drum rebuilds, on the test drum, on fewer steps than the plain
+rule with a shorter list; its counts against the paper's rule at K = 400
+are printed beside them.
 """
 import numpy as np
 import pytest
@@ -80,18 +82,22 @@ def _contact_keys(n, ci, cj):
 def test_learned_skin_beats_paper_rule(orc):
     lvb = _lvb()
     s = scenes.packed(n=8000)
-    rule = _run(lvb, s, lvb.LVB_SKIN_PAPER_KVDT, float(H), log=H)
-    assert len(rule["samples"]) > 5000
+    val = scenes.packed(n=8000, seed=scenes.SEED_BASE + 15)
+    vrule = _run(lvb, val, lvb.LVB_SKIN_PAPER_KVDT, float(H), log=H)
+    assert len(vrule["samples"]) > 5000
     cands = []
     for seed in (9, 10, 11):
-        w1 = _train(lvb, rule["samples"], seed)
-        r1 = _run(lvb, s, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1, log=H)
-        w2 = _train(lvb, np.concatenate([rule["samples"], r1["samples"]]), seed)
-        r2 = _run(lvb, s, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w2)
-        cands += [r1, r2]
-    fit = [r for r in cands if r["entries"] <= 1.05 * rule["entries"]]
+        w1 = _train(lvb, vrule["samples"], seed)
+        r1 = _run(lvb, val, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w1, log=H)
+        w2 = _train(lvb, np.concatenate([vrule["samples"], r1["samples"]]), seed)
+        r2 = _run(lvb, val, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w2)
+        cands += [(r1, w1), (r2, w2)]
+    fit = [c for c in cands if c[0]["entries"] <= 1.05 * vrule["entries"]]
     assert fit
-    learned = min(fit, key=lambda r: r["updates"])
+    w = min(fit, key=lambda c: c[0]["updates"])[1]
+    # the chosen network, once, on the test pack
+    rule = _run(lvb, s, lvb.LVB_SKIN_PAPER_KVDT, float(H))
+    learned = _run(lvb, s, lvb.LVB_SKIN_LEARNED, 0.0, mlp=w)
     print("paper rule K=%d: %d updates, %.0f entries; learned: %d updates, %.0f entries"
           % (H, rule["updates"], rule["entries"], learned["updates"], learned["entries"]))
     assert learned["updates"] <= 0.7 * rule["updates"]
@@ -132,13 +138,11 @@ def test_learned_travel_form_beats_plain_rule_on_drum():
         return out
 
     plain = run(lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, log=H)
-    smp = plain["samples"]
-    smp = np.ascontiguousarray(smp[smp[:, 0] > 0]).copy()
+    smp = lvb.mlp_travel_labels(plain["samples"], H, 2.0, 0.99)
     assert len(smp) > 100_000
-    y = smp[:, 8].astype(np.float64) * 2.0 / (smp[:, 0].astype(np.float64) * H)
-    smp[:, 8] = np.minimum(y, np.quantile(y, 0.99)).astype(np.float32)
+    s_test, s = s, scenes.drum(n=1_000_000, length=0.1, seed=scenes.SEED_BASE + 12)
     best = None
-    for seed in (1, 2, 3):     # the fewest rebuilds of three weight draws
+    for seed in (1, 2, 3):     # chosen on the validation drum: the fewest rebuilds
         rng = np.random.default_rng(seed)
         p0 = (rng.standard_normal(lvb.LVB_MLP_PARAMS) * 0.1).astype(np.float32)
         yr = np.zeros(2, np.float32)
@@ -147,7 +151,13 @@ def test_learned_travel_form_beats_plain_rule_on_drum():
         assert losses[-1] < 0.1 * losses[0]
         w = lvb.mlp_weights_device(p, mu, isd, yr, float(H))
         r = run(lvb.LVB_SKIN_LEARNED, 0.0, mlp=w)
-        if best is None or r["rebuild_steps"] < best["rebuild_steps"]:
-            best = r
-    assert best["rebuild_steps"] <= 0.85 * plain["rebuild_steps"], (best, plain["rebuild_steps"])
-    assert best["entries"] <= plain["entries"], (best["entries"], plain["entries"])
+        if best is None or r["rebuild_steps"] < best[0]["rebuild_steps"]:
+            best = (r, w)
+    s = s_test
+    learned = run(lvb.LVB_SKIN_LEARNED, 0.0, mlp=best[1])
+    rule = run(lvb.LVB_SKIN_PAPER_KVDT, float(H))
+    print("drum: plain %d rebuild steps, %.0f entries; paper rule K=%d %d, %.0f; learned %d, %.0f"
+          % (plain["rebuild_steps"], plain["entries"], H, rule["rebuild_steps"], rule["entries"],
+             learned["rebuild_steps"], learned["entries"]))
+    assert learned["rebuild_steps"] <= 0.85 * plain["rebuild_steps"], (learned, plain)
+    assert learned["entries"] <= plain["entries"], (learned["entries"], plain["entries"])
