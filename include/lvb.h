@@ -310,6 +310,18 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 moves many particles into one cell within
                                 one step raises them first */
 
+#define LVB_OPT_HISTORY 13  /* 1: keep one contact-history record (4 floats)
+                                beside every list entry: a partial rebuild
+                                edits a flagged particle's row in place, so
+                                every partner that stays a pair keeps its
+                                slot and record, a new pair's record starts
+                                at zero, and re-layouts and store growth
+                                carry each record to the entry's new slot
+                                (the DEM driver's tangential springs live
+                                there).  PARTIAL trigger only (else
+                                LVB_EINVAL); the lists are the same as
+                                without it.  0 (default): off */
+
 /* Test hooks for the overflow paths (they make a store fill up without a
  * device fault; the results of a context that reports LVB_EOVERFLOW are
  * invalid, as always): */
@@ -318,6 +330,10 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 finds them over 75% / 60% full; 0: requests
                                 are ignored, so a cell that fills up reports
                                 LVB_EOVERFLOW */
+#define LVB_OPT_FORCE_RELAYOUT 14 /* 1: the next step that rebuilds rows
+                                re-lays out the whole row store on the device
+                                as if a row had outgrown its slack (test hook
+                                for the re-layout path; the list is the same) */
 #define LVB_OPT_STORE_LIMIT 11 /* entries of the row store a re-layout may use:
                                 0 (default) the whole allocation, else
                                 min(value, allocation); a re-layout that does

@@ -21,6 +21,20 @@
  *         gamma_ij = 2 zeta sqrt(m_eff k_n), zeta = -ln e / sqrt(pi^2+ln^2 e),
  *         m_eff = m_i m_j / (m_i + m_j), m = rho 4/3 pi r^3
  *   a'  = F/m + g,   v' = v + (a + a') dt / 2
+ * With friction (mu > 0; the paper's LSD model with static friction, Sec.
+ * Methodology) each particle also carries an angular velocity w (moment of
+ * inertia I = 2/5 m r^2, velocity Verlet as for v: w* = w + al dt, w' = w +
+ * (al + al') dt / 2) and each contact a tangential spring xi, kept in the
+ * broad phase's contact history (LVB_OPT_HISTORY), so it survives partial
+ * rebuilds:
+ *   v_rel = (v*_i - v*_j) - (r_i w*_i + r_j w*_j) x n_ij   (contact point)
+ *   v_t   = v_rel - (v_rel . n_ij) n_ij
+ *   xi    = xi - (xi . n_ij) n_ij,  then xi = xi + v_t dt
+ *   F_t   = -k_t xi - gamma_t v_t, capped at mu max(F_n, 0) (then
+ *           xi = -(F_t + gamma_t v_t) / k_t)
+ *   force on i: F_n n_ij + F_t;  torque on i: -r_i n_ij x F_t
+ * A pair out of contact has xi = 0; both sides of a pair keep exactly
+ * opposite records (the same binary32 operations with the roles swapped).
  * Walls use the same law with m_eff = m_i: box planes (wall_kind 1), a drum
  * of radius R about the y axis through (drum_cx, drum_cz) with end caps at
  * the box's y planes (kind 2; the wall moves tangentially, which a normal-
@@ -56,6 +70,12 @@ typedef struct {
     float drum_cx, drum_cz, drum_R, drum_omega;
     int32_t contacts_on;  /* 0: particles do not interact (ballistic runs) */
     int32_t pad;
+    /* tangential law with contact history (LSD with static friction); on
+     * when mu > 0, between particles only (walls stay frictionless): */
+    float mu;             /* Coulomb coefficient: |F_t| <= mu max(F_n, 0) */
+    float kt_ratio;       /* tangential stiffness k_t = kt_ratio k_n */
+    float gt_ratio;       /* tangential damping gamma_t = gt_ratio gamma_n */
+    int32_t pad2;
 } dem_params;
 
 typedef struct dem_ctx dem_ctx;
@@ -102,6 +122,11 @@ int dem_advance(dem_ctx *ctx, int64_t steps);
  * three phases in order. */
 int dem_phase(dem_ctx *ctx, int32_t phase);
 
+/* dem_get_rot_state -- copy out w, al (angular acceleration) and w*
+ * (float4 records, w = 1/I in the first; any pointer may be NULL); all zero
+ * without friction.  Synchronises. */
+int dem_get_rot_state(dem_ctx *ctx, float *omega, float *alpha, float *omega_star);
+
 /* dem_get_state -- copy out x (pos_r, with radii), v, a and v* (float4
  * records; any pointer may be NULL).  Synchronises. */
 int dem_get_state(dem_ctx *ctx, float *pos_r, float *vel, float *acc, float *vstar);
@@ -123,6 +148,19 @@ int dem_get_state(dem_ctx *ctx, float *pos_r, float *vel, float *acc, float *vst
  */
 int dem_get_contact_forces(dem_ctx *ctx, int32_t *ci, int32_t *cj, float *force3, float *delta,
                            int64_t cap, int64_t *n_contacts);
+
+/*
+ * dem_get_contact_history -- as dem_get_contact_forces, with friction: the
+ * force on i includes the tangential force, evaluated from the contact's
+ * spring as the last step left it (F_t = -k_t xi - gamma_t v_t, which the
+ * cap leaves equal to the capped force), and xi3 (3 floats a pair) gets
+ * the spring xi of row i's record; xi3 may be NULL.  sides = 1: each pair
+ * once, i < j; sides = 2: each pair from both rows, (i, j) and (j, i)
+ * (their springs are exact negatives of each other).
+ */
+int dem_get_contact_history(dem_ctx *ctx, int32_t sides, int32_t *ci, int32_t *cj,
+                            float *force3, float *delta, float *xi3, int64_t cap,
+                            int64_t *n_contacts);
 
 /* dem_set_state -- overwrite x, v, a (host or device float4 records; radii
  * in pos_r must equal the initial ones).  The broad phase keeps its

@@ -93,6 +93,10 @@ def _configure(L):
         L.orc_dem_contacts64.argtypes = [i64, p, p, p, ctypes.POINTER(DemParams), p, p, p, p,
                                          p, i64]
         L.orc_dem_contacts64.restype = i64
+        L.orc_dem_step64f.argtypes = ([i64] + [p] * 6 + [ctypes.c_double,
+                                      ctypes.POINTER(DemParams)] + [ctypes.c_double] * 3 +
+                                     [p] * 3 + [i64] + [p] * 3 + [p] * 7 + [p] * 7 + [i64])
+        L.orc_dem_step64f.restype = i64
         L.orc_improvement_pct.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_improvement_pct.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -356,6 +360,56 @@ def dem_contacts(x4, v4, P):
         if m <= cap:
             return ci[:m].copy(), cj[:m].copy(), f3[:m].copy(), dl[:m].copy(), sc[:m].copy()
         cap = int(m)
+
+
+def dem_step_friction(x4, v4, a4, w4, al4, dt, P, mu, kt_ratio, gt_ratio, hist=None,
+                      x_in=None, vstar_in=None, wstar_in=None):
+    """One step with rotation and the tangential law with contact history
+    (orc_dem_step64f), binary64, from the binary32 state of the code under
+    test widened exactly.  hist: (hi, hj, xi (m, 3)) of the pairs in contact
+    at the previous step (i < j, sorted), or None.  x_in / vstar_in /
+    wstar_in replace x', v*, w* as the state at which forces are evaluated.
+    Returns a dict: x, vstar, a, v, wstar, al, w (n, 3); contacts ci, cj, xi
+    (m, 3), f (m, 3: force on i), scale (m,); fmag, tmag (n,)."""
+    x4, v4, a4, w4, al4 = (_f32x4(q) for q in (x4, v4, a4, w4, al4))
+    x, v, a, w, al = (_d3(q) for q in (x4, v4, a4, w4, al4))
+    r = np.ascontiguousarray(x4[:, 3], dtype=np.float64)
+    n = len(x)
+    xf, vf, wf = (None if q is None else _d3(_f32x4(q)) for q in (x_in, vstar_in, wstar_in))
+    if hist is None:
+        hi = np.zeros(0, np.int32)
+        hj = np.zeros(0, np.int32)
+        hx = np.zeros((0, 3), np.float64)
+    else:
+        hi = np.ascontiguousarray(hist[0], np.int32)
+        hj = np.ascontiguousarray(hist[1], np.int32)
+        hx = np.ascontiguousarray(np.asarray(hist[2])[:, :3], np.float64)
+    outs = [np.zeros((n, 3), np.float64) for _ in range(7)]
+    fmag = np.zeros(n, np.float64)
+    tmag = np.zeros(n, np.float64)
+    cap = max(16, 8 * n)
+    while True:
+        ci = np.empty(cap, np.int32)
+        cj = np.empty(cap, np.int32)
+        oxi = np.empty((cap, 3), np.float64)
+        of3 = np.empty((cap, 3), np.float64)
+        osc = np.empty(cap, np.float64)
+        m = lib().orc_dem_step64f(n, _ptr(x), _ptr(v), _ptr(a), _ptr(w), _ptr(al), _ptr(r),
+                                  float(dt), ctypes.byref(P), float(mu), float(kt_ratio),
+                                  float(gt_ratio), _ptr(xf), _ptr(vf), _ptr(wf), len(hi),
+                                  _ptr(hi), _ptr(hj), _ptr(hx), *[_ptr(o) for o in outs],
+                                  _ptr(ci), _ptr(cj), _ptr(oxi), _ptr(of3), _ptr(osc),
+                                  _ptr(fmag), _ptr(tmag), cap)
+        if m < 0:
+            raise MemoryError("oracle step failed")
+        if m <= cap:
+            break
+        cap = int(m)
+    keys = ("x", "vstar", "a", "v", "wstar", "al", "w")
+    out = dict(zip(keys, outs))
+    out.update(ci=ci[:m].copy(), cj=cj[:m].copy(), xi=oxi[:m].copy(), f=of3[:m].copy(),
+               scale=osc[:m].copy(), fmag=fmag, tmag=tmag)
+    return out
 
 
 def improvement_pct(t_without, t_case):

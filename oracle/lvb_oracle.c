@@ -768,6 +768,169 @@ ORC_API int orc_dem_step64(int64_t n, const double *x, const double *v, const do
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Friction with contact history, binary64 (the LSD model with static    */
+/* friction named in Sec. Methodology; the paper gives no formula, so    */
+/* this is the common linear tangential spring with a Coulomb cap):      */
+/*   per particle also w (angular velocity) and al = T / I, I = 2/5 m r^2 */
+/*   w* = w + al dt,  w' = w + (al + al') dt / 2  (velocity Verlet)       */
+/* per contact i < j (delta > 0), n from j to i:                          */
+/*   v_rel = (v*_i - v*_j) - (r_i w*_i + r_j w*_j) x n                   */
+/*   v_t   = v_rel - (v_rel . n) n                                       */
+/*   xi    = xi_prev - (xi_prev . n) n + v_t dt   (xi_prev = 0 for a     */
+/*           pair that was not in contact at the previous step)           */
+/*   F_t   = -k_t xi - gamma_t v_t,  k_t = kt_ratio k_n,                  */
+/*           gamma_t = gt_ratio gamma_n(m_eff)                            */
+/*   if |F_t| > mu max(F_n, 0): F_t *= mu max(F_n, 0) / |F_t| and         */
+/*           xi = -(F_t + gamma_t v_t) / k_t                              */
+/*   force on i F_n n + F_t (on j its negation); torque on i -r_i n x F_t, */
+/*   on j -r_j n x F_t                                                    */
+/* Walls: the normal law only.                                            */
+/* History in: nh pairs (hi < hj, sorted by (i, j)) with xi (3 each, from */
+/* i's side).  Out: every contact of the new state, sorted, with its xi,  */
+/* the force on i and the scale of its terms |k_n delta| + |gamma_n v_n|  */
+/* + |k_t xi| + |gamma_t v_t|; per particle the sums of those scales      */
+/* (fmag) and of r times the tangential ones (tmag).  xf, vf, wf, when    */
+/* given, replace x', v*, w* as the state of the force evaluation.        */
+/* Returns the number of contacts (at most cap written) or -1.            */
+/* Pinned by: a sphere sliding on a fixed one (Coulomb limit), a sticking */
+/* pair's spring growing by v_t dt per step, the antisymmetry of forces   */
+/* and the conservation of linear momentum (tests).                       */
+/* ------------------------------------------------------------------ */
+static int64_t find_pair(int64_t nh, const int32_t *hi, const int32_t *hj, int32_t i, int32_t j)
+{
+    int64_t lo = 0, up = nh;
+    while (lo < up) {
+        int64_t mid = lo + (up - lo) / 2;
+        if (hi[mid] < i || (hi[mid] == i && hj[mid] < j)) lo = mid + 1;
+        else up = mid;
+    }
+    return (lo < nh && hi[lo] == i && hj[lo] == j) ? lo : -1;
+}
+
+ORC_API int64_t orc_dem_step64f(int64_t n, const double *x, const double *v, const double *a,
+                                const double *w, const double *al, const double *r, double dt,
+                                const orc_dem_params *P, double mu, double kt_ratio,
+                                double gt_ratio, const double *xf, const double *vf,
+                                const double *wf, int64_t nh, const int32_t *hi,
+                                const int32_t *hj, const double *hxi, double *x_out,
+                                double *vstar_out, double *a_out, double *v_out,
+                                double *wstar_out, double *al_out, double *w_out, int32_t *oi,
+                                int32_t *oj, double *oxi, double *of3, double *oscale,
+                                double *fmag, double *tmag, int64_t cap)
+{
+    for (int64_t k = 0; k < 3 * n; ++k) {
+        x_out[k] = x[k] + v[k] * dt + 0.5 * a[k] * dt * dt;
+        vstar_out[k] = v[k] + a[k] * dt;
+        wstar_out[k] = w[k] + al[k] * dt;
+    }
+    const double *X = xf ? xf : x_out, *V = vf ? vf : vstar_out, *W = wf ? wf : wstar_out;
+    double *F = (double *)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));
+    double *T = (double *)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));
+    if (!F || !T) { free(F); free(T); return -1; }
+    memset(fmag, 0, (size_t)n * sizeof(double));
+    memset(tmag, 0, (size_t)n * sizeof(double));
+    int32_t *ci = NULL, *cj = NULL;
+    int64_t np = P->contacts_on ? contact_candidates(n, X, r, &ci, &cj) : 0;
+    if (np < 0) { free(F); free(T); return -1; }
+    double kt = kt_ratio * P->kn;
+    int64_t m = 0;
+    for (int64_t k = 0; k < np; ++k) {
+        int64_t i = ci[k], j = cj[k];
+        double d[3], dist2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = X[3 * i + c] - X[3 * j + c];
+            dist2 += d[c] * d[c];
+        }
+        double dist = sqrt(dist2);
+        double dl = (r[i] + r[j]) - dist;
+        if (!(dl > 0.0) || !(dist > 0.0)) continue;
+        double nr[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+        double s[3], u[3];
+        for (int c = 0; c < 3; ++c) s[c] = r[i] * W[3 * i + c] + r[j] * W[3 * j + c];
+        double sxn[3] = {s[1] * nr[2] - s[2] * nr[1], s[2] * nr[0] - s[0] * nr[2],
+                         s[0] * nr[1] - s[1] * nr[0]};
+        for (int c = 0; c < 3; ++c) u[c] = (V[3 * i + c] - V[3 * j + c]) - sxn[c];
+        double vn = u[0] * nr[0] + u[1] * nr[1] + u[2] * nr[2];
+        double vt[3] = {u[0] - vn * nr[0], u[1] - vn * nr[1], u[2] - vn * nr[2]};
+        double mi = mass_of(r[i], P->rho), mj = mass_of(r[j], P->rho);
+        double meff = mi * mj / (mi + mj);
+        double fn = lsd_force(P, dl, vn, meff);
+        double gam_n = 2.0 * zeta_of(P->restitution) * sqrt(meff * P->kn);
+        double gt = gt_ratio * gam_n;
+        double xi[3] = {0.0, 0.0, 0.0};
+        int64_t h = nh > 0 ? find_pair(nh, hi, hj, (int32_t)i, (int32_t)j) : -1;
+        if (h >= 0) for (int c = 0; c < 3; ++c) xi[c] = hxi[3 * h + c];
+        double xn = xi[0] * nr[0] + xi[1] * nr[1] + xi[2] * nr[2];
+        for (int c = 0; c < 3; ++c) xi[c] = xi[c] - xn * nr[c] + vt[c] * dt;
+        double Ft[3], fm2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            Ft[c] = -kt * xi[c] - gt * vt[c];
+            fm2 += Ft[c] * Ft[c];
+        }
+        double fm = sqrt(fm2), lim = mu * (fn > 0.0 ? fn : 0.0);
+        if (fm > lim) {
+            for (int c = 0; c < 3; ++c) {
+                Ft[c] *= lim / fm;
+                xi[c] = -(Ft[c] + gt * vt[c]) / kt;
+            }
+        }
+        double nxf[3] = {nr[1] * Ft[2] - nr[2] * Ft[1], nr[2] * Ft[0] - nr[0] * Ft[2],
+                         nr[0] * Ft[1] - nr[1] * Ft[0]};
+        double sc_t = kt * sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]) +
+                      gt * sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+        double sc = fabs(P->kn * dl) + fabs(fn - P->kn * dl) + sc_t;
+        for (int c = 0; c < 3; ++c) {
+            F[3 * i + c] += fn * nr[c] + Ft[c];
+            F[3 * j + c] -= fn * nr[c] + Ft[c];
+            T[3 * i + c] -= r[i] * nxf[c];
+            T[3 * j + c] -= r[j] * nxf[c];
+        }
+        fmag[i] += sc;
+        fmag[j] += sc;
+        tmag[i] += r[i] * sc_t;
+        tmag[j] += r[j] * sc_t;
+        if (m < cap) {
+            oi[m] = (int32_t)i;
+            oj[m] = (int32_t)j;
+            for (int c = 0; c < 3; ++c) {
+                oxi[3 * m + c] = xi[c];
+                of3[3 * m + c] = fn * nr[c] + Ft[c];
+            }
+            oscale[m] = sc;
+        }
+        ++m;
+    }
+    free(ci); free(cj);
+    /* walls: the normal law (forces at the same state) */
+    if (P->wall_kind == 1 || P->wall_kind == 2) {
+        double *Fw = (double *)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));
+        double *fw = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        orc_dem_params Q = *P;
+        Q.contacts_on = 0;
+        if (!Fw || !fw || orc_dem_forces64(n, X, r, V, &Q, Fw, fw) != 0) {
+            free(Fw); free(fw); free(F); free(T);
+            return -1;
+        }
+        for (int64_t k = 0; k < 3 * n; ++k) F[k] += Fw[k];
+        for (int64_t i = 0; i < n; ++i) fmag[i] += fw[i];
+        free(Fw); free(fw);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double mi = mass_of(r[i], P->rho), Ii = 0.4 * mi * r[i] * r[i];
+        for (int c = 0; c < 3; ++c) {
+            double an = F[3 * i + c] / mi + P->g[c];
+            a_out[3 * i + c] = an;
+            v_out[3 * i + c] = v[3 * i + c] + 0.5 * (a[3 * i + c] + an) * dt;
+            double aln = T[3 * i + c] / Ii;
+            al_out[3 * i + c] = aln;
+            w_out[3 * i + c] = w[3 * i + c] + 0.5 * (al[3 * i + c] + aln) * dt;
+        }
+    }
+    free(F); free(T);
+    return m;
+}
+
 /* Improvement of Eq. impr (Sec. Results):                               */
 /*   Improvement = (T_without - T_case) / T_without * 100                */
 /* Pinned by: the values printed in Table tab:summary.                   */

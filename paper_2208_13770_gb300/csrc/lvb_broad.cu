@@ -128,15 +128,23 @@ k_cells_insert(DevState s, int gate, int count_only)
 // Rows of every particle from the cells (init, store growth): fill = 0
 // counts only, 1 also writes.
 __global__ void __launch_bounds__(kThreads, 4)
-k_rows(DevState s, int gate, int fill)
+k_rows(DevState s, int gate, int fill, int carry = 0)
 {
     const int nitems = gated_items(s, gate);
     if (!nitems) return;
     count_kernel(s);
     tr_enter(s, TR_ROWS);
     ph_rows(s, nitems, fill, (blockIdx.x * kThreads + threadIdx.x) >> 5,
-            (gridDim.x * kThreads) >> 5, &s.cnt->row_overflow);
+            (gridDim.x * kThreads) >> 5, &s.cnt->row_overflow, carry != 0);
     tr_exit(s, TR_ROWS);
+}
+
+// Contact history: the rows copied aside before the host re-lays them out
+// (store or cell growth), for k_rows to carry each entry's record.
+__global__ void __launch_bounds__(kThreads) k_save_rows(DevState s)
+{
+    count_kernel(s);
+    save_rows_pass(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -440,6 +448,7 @@ struct lvb_ctx {
     HostFlags *hflags = nullptr;    // mapped pinned host memory
     long long grows = 0;            // store or cell-slot growths done
     int grow = 1;                   // 0: requests to grow are ignored (LVB_OPT_GROW)
+    bool history = false;           // contact history on (LVB_OPT_HISTORY)
     int ccap_want = 0;              // slots per cell asked for (LVB_OPT_CELL_CAPACITY)
     long long col_alloc = 0;        // entries allocated for the row store (s.col_cap,
                                     // the usable part, may be set lower: LVB_OPT_STORE_LIMIT)
@@ -485,7 +494,8 @@ void free_all(lvb_ctx *c)
                     s.cell_ref, s.cnt, s.blk, c->ex_cnt, c->ex_off, c->ex_i, c->ex_j, c->ex_d,
                     c->scratch, c->sum64, c->sg_d, c->scene_of_d, s.born, s.cell_live,
                     s.cell_rmax,
-                    s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf};
+                    s.lg_feat, s.lg_x, s.lg_t, s.lg_m, s.log_buf,
+                    s.hist, s.pold, s.old_off, s.old_len, s.old_col, s.old_hist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cnt_h) cudaFreeHost(c->cnt_h);
@@ -604,6 +614,8 @@ int grow_if_asked(lvb_ctx *c)
     DevState &s = c->s;
     const cudaStream_t st = c->stream;
     const bool cells = h->grow_cells != 0;
+    if (c->history)   // the rows as they are, for carrying each entry's history
+        k_save_rows<<<rows_grid(c), kThreads, 0, st>>>(s);
     if (cells && s.ccap < (1 << 16)) {
         const int ccap = std::min(std::max(2 * s.ccap, c->ccap_want), 1 << 16);
         cudaFree(s.cell_id);
@@ -630,20 +642,36 @@ int grow_if_asked(lvb_ctx *c)
     s.col_cap = cap0;
     if (rc) return rc;
     const long long need = c->cnt_h->store_needed;
+    bool grown = false;
     if (need * 5 > s.col_cap * 3) {   // over 60%: grow
         const long long cap = std::min<long long>(2 * need + 8 * c->n + 1024, INT32_MAX);
         if (need > cap) return LVB_ENOMEM;
         cudaFree(s.col);
         s.col = nullptr;
         e = dalloc(&s.col, cap);
+        if (e == cudaSuccess && c->history) {
+            cudaFree(s.hist);
+            s.hist = nullptr;
+            e = dalloc(&s.hist, cap);
+        }
         if (e != cudaSuccess) return from_cuda(e);
         s.col_cap = cap;
         c->col_alloc = cap;
+        grown = true;
     }
-    k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 1);
+    k_rows<<<rows_grid(c), kThreads, 0, st>>>(s, GATE_ALWAYS, 1, c->history ? 1 : 0);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
+    if (grown && c->history) {   // the copy-aside store follows the store's size
+        cudaFree(s.old_col);
+        cudaFree(s.old_hist);
+        s.old_col = nullptr;
+        s.old_hist = nullptr;
+        e = dalloc(&s.old_col, c->col_alloc);
+        if (e == cudaSuccess) e = dalloc(&s.old_hist, c->col_alloc);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     h->grow_store = 0;
     h->grow_cells = 0;
     c->grows += 1;
@@ -1174,6 +1202,45 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
             c->ccap_want = want;
             c->hflags->grow_cells = 1;   // grown before the next step
         }
+    } else if (option == LVB_OPT_HISTORY) {
+        if (value != 0 && value != 1) return LVB_EINVAL;
+        if (value && c->trigger != LVB_TRIGGER_PARTIAL) return LVB_EINVAL;
+        const cudaError_t ee = cudaStreamSynchronize(c->stream);
+        if (ee != cudaSuccess) return from_cuda(ee);
+        DevState &s = c->s;
+        void *ptrs[] = {s.hist, s.pold, s.old_off, s.old_len, s.old_col, s.old_hist};
+        for (void *q : ptrs)
+            if (q) cudaFree(q);
+        s.hist = s.pold = s.old_hist = nullptr;
+        s.old_off = s.old_len = s.old_col = nullptr;
+        c->history = false;
+        if (value) {
+            cudaError_t e = dalloc(&s.hist, c->col_alloc);
+            if (e == cudaSuccess) e = dalloc(&s.pold, c->n);
+            if (e == cudaSuccess) e = dalloc(&s.old_off, c->n);
+            if (e == cudaSuccess) e = dalloc(&s.old_len, c->n);
+            if (e == cudaSuccess) e = dalloc(&s.old_col, c->col_alloc);
+            if (e == cudaSuccess) e = dalloc(&s.old_hist, c->col_alloc);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(s.hist, 0, sizeof(float4) * (size_t)c->col_alloc, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                void *qs[] = {s.hist, s.pold, s.old_off, s.old_len, s.old_col, s.old_hist};
+                for (void *q : qs)
+                    if (q) cudaFree(q);
+                s.hist = s.pold = s.old_hist = nullptr;
+                s.old_off = s.old_len = s.old_col = nullptr;
+                return from_cuda(e);
+            }
+            c->history = true;
+        }
+    } else if (option == LVB_OPT_FORCE_RELAYOUT) {
+        if (value != 1) return LVB_EINVAL;
+        const int ones[2] = {1, 1};
+        const cudaError_t e = cudaMemcpyAsync(c->s.cnt->ovf, ones, sizeof(ones),
+                                              cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) return from_cuda(cudaStreamSynchronize(c->stream));
+        return from_cuda(e);
     } else if (option == LVB_OPT_GROW) {
         if (value != 0 && value != 1) return LVB_EINVAL;
         c->grow = (int)value;
@@ -1431,6 +1498,7 @@ RowsView rows_view(lvb_ctx *c)
     v.row_len = c->s.row_len;
     v.row_cap = c->s.row_cap;
     v.col = c->s.col;
+    v.hist = c->s.hist;
     v.rad = c->s.rad;
     v.kernels = &c->s.cnt->kernels;
     v.cnt = c->s.cnt;

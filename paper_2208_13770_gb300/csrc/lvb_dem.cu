@@ -39,6 +39,9 @@ struct DemDev {
     int wall_kind, clamp_tensile, contacts_on;
     float drum_cx, drum_cz, drum_R;
     float4 *pos, *vel, *acc, *vstar;   // vstar.w = 1 / m
+    // friction (mu > 0): rotation and the tangential law; omega.w = 1 / I
+    float mu, kt, gt_ratio;
+    float4 *omega, *alpha, *wstar;     // null without friction
     RowsView rows;
     int trace;                         // per-kernel trace (copied at launch)
 };
@@ -100,6 +103,9 @@ __host__ __device__ __forceinline__ IntegrateArgs integrate_args(const DemDev &d
     a.vel = d.vel;
     a.acc = d.acc;
     a.vstar = d.vstar;
+    a.omega = d.omega;
+    a.alpha = d.alpha;
+    a.wstar = d.wstar;
     a.dt = d.dt;
     a.half_dt2 = d.half_dt2;
     a.specular = d.wall_kind == DEM_WALL_SPECULAR;
@@ -167,6 +173,61 @@ __device__ __forceinline__ bool contact_pair(const DemDev &d, float4 xi, float4 
     return true;
 }
 
+__device__ __forceinline__ float dot_rn(float ax, float ay, float az, const float n[3])
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(ax, n[0]), __fmul_rn(ay, n[1])), __fmul_rn(az, n[2]));
+}
+
+// The tangential law of one contact (friction), from particle i's side:
+// updates the spring xi kept in h (row i's history record of partner j)
+// and returns the tangential force on i.  Every operation is rounded
+// explicitly (no contraction), in an order that is exactly sign-symmetric
+// under exchanging i and j (n -> -n), so that j's record stays exactly -h.
+__device__ __forceinline__ float3 tangential(const DemDev &d, float ri, float4 vi, float4 wi,
+                                             int j, const float n[3], float fn, float meff,
+                                             float4 &h)
+{
+    const float4 vj = d.vstar[j], wj = d.wstar[j];
+    const float rj = d.pos[j].w;
+    // s = r_i w_i + r_j w_j, c = s x n: the contact point's rotational velocity
+    const float sx = __fadd_rn(__fmul_rn(ri, wi.x), __fmul_rn(rj, wj.x));
+    const float sy = __fadd_rn(__fmul_rn(ri, wi.y), __fmul_rn(rj, wj.y));
+    const float sz = __fadd_rn(__fmul_rn(ri, wi.z), __fmul_rn(rj, wj.z));
+    const float cx = __fsub_rn(__fmul_rn(sy, n[2]), __fmul_rn(sz, n[1]));
+    const float cy = __fsub_rn(__fmul_rn(sz, n[0]), __fmul_rn(sx, n[2]));
+    const float cz = __fsub_rn(__fmul_rn(sx, n[1]), __fmul_rn(sy, n[0]));
+    const float ux = __fsub_rn(__fsub_rn(vi.x, vj.x), cx);
+    const float uy = __fsub_rn(__fsub_rn(vi.y, vj.y), cy);
+    const float uz = __fsub_rn(__fsub_rn(vi.z, vj.z), cz);
+    const float un = dot_rn(ux, uy, uz, n);
+    const float tx = __fsub_rn(ux, __fmul_rn(un, n[0]));
+    const float ty = __fsub_rn(uy, __fmul_rn(un, n[1]));
+    const float tz = __fsub_rn(uz, __fmul_rn(un, n[2]));
+    // the spring kept in the tangent plane, then stretched by v_t dt
+    const float hn = dot_rn(h.x, h.y, h.z, n);
+    float hx = __fadd_rn(__fsub_rn(h.x, __fmul_rn(hn, n[0])), __fmul_rn(tx, d.dt));
+    float hy = __fadd_rn(__fsub_rn(h.y, __fmul_rn(hn, n[1])), __fmul_rn(ty, d.dt));
+    float hz = __fadd_rn(__fsub_rn(h.z, __fmul_rn(hn, n[2])), __fmul_rn(tz, d.dt));
+    const float gt = __fmul_rn(d.gt_ratio, __fmul_rn(d.two_zeta, __fsqrt_rn(__fmul_rn(meff, d.kn))));
+    float Fx = -__fadd_rn(__fmul_rn(d.kt, hx), __fmul_rn(gt, tx));
+    float Fy = -__fadd_rn(__fmul_rn(d.kt, hy), __fmul_rn(gt, ty));
+    float Fz = -__fadd_rn(__fmul_rn(d.kt, hz), __fmul_rn(gt, tz));
+    const float Fm = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(Fx, Fx), __fmul_rn(Fy, Fy)),
+                                          __fmul_rn(Fz, Fz)));
+    const float lim = __fmul_rn(d.mu, fmaxf(fn, 0.0f));
+    if (Fm > lim) {   // sliding: the force at the Coulomb limit, the spring to match it
+        const float sc = __fdiv_rn(lim, Fm);
+        Fx = __fmul_rn(Fx, sc);
+        Fy = __fmul_rn(Fy, sc);
+        Fz = __fmul_rn(Fz, sc);
+        hx = -__fdiv_rn(__fadd_rn(Fx, __fmul_rn(gt, tx)), d.kt);
+        hy = -__fdiv_rn(__fadd_rn(Fy, __fmul_rn(gt, ty)), d.kt);
+        hz = -__fdiv_rn(__fadd_rn(Fz, __fmul_rn(gt, tz)), d.kt);
+    }
+    h = make_float4(hx, hy, hz, 0.0f);
+    return make_float3(Fx, Fy, Fz);
+}
+
 // Narrow phase on the row of particle i + walls + velocity finish.
 __device__ __forceinline__ void forces_one(const DemDev &d, int i)
 {
@@ -176,6 +237,9 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
     float4 v = d.vel[i];
     const float im_i = vi.w;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    float Tx = 0.f, Ty = 0.f, Tz = 0.f;
+    const bool fric = d.omega != nullptr;
+    const float4 wi = fric ? d.wstar[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     // after a row store that failed even a tight re-layout (LVB_EOVERFLOW)
     // the row offsets no longer fit the store: the rows are not read
     if (d.contacts_on && !(d.rows.cnt->err & DERR_STORE)) {
@@ -185,10 +249,26 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
             const int j = d.rows.col[off + e];
             if (j < 0) continue;            // a removed pair's slot
             float dl, n[3], f;
-            if (!contact_pair(d, xi, vi, j, dl, n, f)) continue;
+            if (!contact_pair(d, xi, vi, j, dl, n, f)) {
+                if (fric) d.rows.hist[off + e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
             Fx += f * n[0];
             Fy += f * n[1];
             Fz += f * n[2];
+            if (fric) {
+                float4 h = d.rows.hist[off + e];
+                const float meff = 1.0f / (im_i + d.vstar[j].w);
+                const float3 Ft = tangential(d, xi.w, vi, wi, j, n, f, meff, h);
+                d.rows.hist[off + e] = h;
+                Fx += Ft.x;
+                Fy += Ft.y;
+                Fz += Ft.z;
+                // torque -r_i n x F_t
+                Tx -= xi.w * (n[1] * Ft.z - n[2] * Ft.y);
+                Ty -= xi.w * (n[2] * Ft.x - n[0] * Ft.z);
+                Tz -= xi.w * (n[0] * Ft.y - n[1] * Ft.x);
+            }
         }
     }
     const float r = xi.w;
@@ -228,6 +308,16 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
     v.z += (a.z + an.z) * d.half_dt;
     d.vel[i] = v;
     d.acc[i] = an;
+    if (fric) {   // al' = T / I, w' = w + (al + al') dt / 2
+        float4 w = d.omega[i];
+        const float4 al = d.alpha[i];
+        const float4 aln = make_float4(Tx * w.w, Ty * w.w, Tz * w.w, 0.0f);
+        w.x += (al.x + aln.x) * d.half_dt;
+        w.y += (al.y + aln.y) * d.half_dt;
+        w.z += (al.z + aln.z) * d.half_dt;
+        d.omega[i] = w;
+        d.alpha[i] = aln;
+    }
 }
 
 // Forces as a separate kernel, one thread per particle.  Eight blocks per
@@ -258,28 +348,59 @@ struct DemTail {
 // atomic counter, so in no particular order.
 __global__ void __launch_bounds__(kThreads)
 k_contact_list(DemDev d, unsigned long long *cnt, long long cap, int *ci, int *cj, float *f3,
-               float *delta)
+               float *delta, float *xi3, int both)
 {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
     if (i >= d.n || !d.contacts_on || (d.rows.cnt->err & DERR_STORE)) return;
     const float4 xi = d.pos[i];
     const float4 vi = d.vstar[i];
+    const bool fric = d.omega != nullptr;
     const int off = d.rows.row_off[i];
     const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
     for (int e = 0; e < len; ++e) {
         const int j = d.rows.col[off + e];
-        if (j <= i) continue;               // a removed pair's slot, or the pair from j's row
+        // a removed pair's slot, or (one side only) the pair from j's row
+        if (j < 0 || (!both && j <= i)) continue;
         float dl, n[3], f;
         if (!contact_pair(d, xi, vi, j, dl, n, f)) continue;
+        float Ft[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
+        if (fric) {
+            // F_t = -k_t xi - gamma_t v_t from the spring as the step left it
+            const float4 r = d.rows.hist[off + e];
+            h[0] = r.x;
+            h[1] = r.y;
+            h[2] = r.z;
+            const float4 vj = d.vstar[j], wi = d.wstar[i], wj = d.wstar[j];
+            const float ri = xi.w, rj = d.pos[j].w;
+            const float sx = __fadd_rn(__fmul_rn(ri, wi.x), __fmul_rn(rj, wj.x));
+            const float sy = __fadd_rn(__fmul_rn(ri, wi.y), __fmul_rn(rj, wj.y));
+            const float sz = __fadd_rn(__fmul_rn(ri, wi.z), __fmul_rn(rj, wj.z));
+            const float u[3] = {
+                __fsub_rn(__fsub_rn(vi.x, vj.x), __fsub_rn(__fmul_rn(sy, n[2]), __fmul_rn(sz, n[1]))),
+                __fsub_rn(__fsub_rn(vi.y, vj.y), __fsub_rn(__fmul_rn(sz, n[0]), __fmul_rn(sx, n[2]))),
+                __fsub_rn(__fsub_rn(vi.z, vj.z), __fsub_rn(__fmul_rn(sx, n[1]), __fmul_rn(sy, n[0])))};
+            const float un = dot_rn(u[0], u[1], u[2], n);
+            const float meff = 1.0f / (vi.w + vj.w);
+            const float gt =
+                __fmul_rn(d.gt_ratio, __fmul_rn(d.two_zeta, __fsqrt_rn(__fmul_rn(meff, d.kn))));
+            for (int c = 0; c < 3; ++c)
+                Ft[c] = -__fadd_rn(__fmul_rn(d.kt, h[c]),
+                                   __fmul_rn(gt, __fsub_rn(u[c], __fmul_rn(un, n[c]))));
+        }
         const unsigned long long k = atomicAdd(cnt, 1ULL);
         if (k < (unsigned long long)cap) {
             ci[k] = i;
             cj[k] = j;
-            f3[3 * k + 0] = f * n[0];
-            f3[3 * k + 1] = f * n[1];
-            f3[3 * k + 2] = f * n[2];
+            f3[3 * k + 0] = f * n[0] + Ft[0];
+            f3[3 * k + 1] = f * n[1] + Ft[1];
+            f3[3 * k + 2] = f * n[2] + Ft[2];
             delta[k] = dl;
+            if (xi3) {
+                xi3[3 * k + 0] = h[0];
+                xi3[3 * k + 1] = h[1];
+                xi3[3 * k + 2] = h[2];
+            }
         }
     }
 }
@@ -296,6 +417,12 @@ __global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const floa
         d.vel[i] = make_float4(v.x, v.y, v.z, 0.0f);
         d.vstar[i] = make_float4(v.x, v.y, v.z, (float)(1.0 / m));
         d.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (d.omega) {   // at rest, I = 2/5 m r^2
+            const float iI = (float)(1.0 / (0.4 * m * r * r));
+            d.omega[i] = make_float4(0.f, 0.f, 0.f, iI);
+            d.wstar[i] = make_float4(0.f, 0.f, 0.f, iI);
+            d.alpha[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
 }
 
@@ -328,7 +455,8 @@ void dem_free(dem_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->bp) lvb_destroy(c->bp);
-    float4 *ptrs[] = {c->d.pos, c->d.vel, c->d.acc, c->d.vstar};
+    float4 *ptrs[] = {c->d.pos, c->d.vel, c->d.acc, c->d.vstar, c->d.omega, c->d.alpha,
+                      c->d.wstar};
     for (float4 *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -408,6 +536,11 @@ static int dem_init_impl(dem_ctx **out, int32_t n_scenes, const int64_t *offsets
         !(prm->restitution > 0.0f && prm->restitution <= 1.0f))
         return LVB_EINVAL;
     if (prm->wall_kind < DEM_WALL_NONE || prm->wall_kind > DEM_WALL_SPECULAR) return LVB_EINVAL;
+    if (!(prm->mu >= 0.0f) || !std::isfinite(prm->mu)) return LVB_EINVAL;
+    if (prm->mu > 0.0f && (!(prm->kt_ratio > 0.0f) || !std::isfinite(prm->kt_ratio) ||
+                           !(prm->gt_ratio >= 0.0f) || !std::isfinite(prm->gt_ratio) ||
+                           trigger != LVB_TRIGGER_PARTIAL))
+        return LVB_EINVAL;
     if (((uintptr_t)pos_r & 15u) || ((uintptr_t)vel & 15u)) return LVB_EINVAL;
     cudaGetLastError();   // clear a stale error of an unrelated earlier call
     dem_ctx *c = new (std::nothrow) dem_ctx();
@@ -429,10 +562,18 @@ static int dem_init_impl(dem_ctx **out, int32_t n_scenes, const int64_t *offsets
     d.drum_cx = prm->drum_cx;
     d.drum_cz = prm->drum_cz;
     d.drum_R = prm->drum_R;
+    d.mu = prm->mu;
+    d.kt = prm->kt_ratio * prm->kn;
+    d.gt_ratio = prm->gt_ratio;
     cudaError_t e = cudaMalloc((void **)&d.pos, sizeof(float4) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.vel, sizeof(float4) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.acc, sizeof(float4) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.vstar, sizeof(float4) * n);
+    if (prm->mu > 0.0f) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.omega, sizeof(float4) * n);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.alpha, sizeof(float4) * n);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.wstar, sizeof(float4) * n);
+    }
     if (e != cudaSuccess) {
         dem_free(c);
         delete c;
@@ -451,10 +592,21 @@ static int dem_init_impl(dem_ctx **out, int32_t n_scenes, const int64_t *offsets
         delete c;
         return rc;
     }
+    if (prm->mu > 0.0f) {   // the tangential springs live in the contact history
+        rc = lvb_set_option(c->bp, LVB_OPT_HISTORY, 1);
+        if (rc) {
+            dem_free(c);
+            delete c;
+            return rc;
+        }
+    }
     d.rows = rows_view(c->bp);
     // a0 from the forces at (x0, v0): one force pass with a = 0, dt = 0
+    // (the tangential springs start at zero: this pass leaves them alone,
+    // and al0 = 0)
     DemDev d0 = d;
     d0.half_dt = 0.0f;
+    d0.omega = d0.alpha = d0.wstar = nullptr;
     k_forces<<<grid_n(d.n), kThreads, 0, c->stream>>>(d0);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -545,8 +697,40 @@ int dem_advance(dem_ctx *c, int64_t steps)
     return LVB_OK;
 }
 
+static int contact_list(dem_ctx *c, int both, int32_t *ci, int32_t *cj, float *force3,
+                        float *delta, float *xi3, int64_t cap, int64_t *n_contacts);
+
 int dem_get_contact_forces(dem_ctx *c, int32_t *ci, int32_t *cj, float *force3, float *delta,
                            int64_t cap, int64_t *n_contacts)
+{
+    return contact_list(c, 0, ci, cj, force3, delta, nullptr, cap, n_contacts);
+}
+
+int dem_get_contact_history(dem_ctx *c, int32_t sides, int32_t *ci, int32_t *cj, float *force3,
+                            float *delta, float *xi3, int64_t cap, int64_t *n_contacts)
+{
+    if (sides != 1 && sides != 2) return LVB_EINVAL;
+    return contact_list(c, sides == 2, ci, cj, force3, delta, xi3, cap, n_contacts);
+}
+
+int dem_get_rot_state(dem_ctx *c, float *omega, float *alpha, float *omega_star)
+{
+    if (!c) return LVB_EINVAL;
+    const size_t b = sizeof(float4) * (size_t)c->d.n;
+    cudaError_t e = cudaSuccess;
+    float *outs[3] = {omega, alpha, omega_star};
+    const float4 *srcs[3] = {c->d.omega, c->d.alpha, c->d.wstar};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (!outs[k]) continue;
+        if (srcs[k]) e = cudaMemcpyAsync(outs[k], srcs[k], b, cudaMemcpyDefault, c->stream);
+        else e = cudaMemsetAsync(outs[k], 0, b, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return from_cuda(e);
+}
+
+static int contact_list(dem_ctx *c, int both, int32_t *ci, int32_t *cj, float *force3,
+                        float *delta, float *xi3, int64_t cap, int64_t *n_contacts)
 {
     if (!c || !n_contacts || cap < 0 || (cap > 0 && (!ci || !cj || !force3 || !delta)))
         return LVB_EINVAL;
@@ -554,18 +738,19 @@ int dem_get_contact_forces(dem_ctx *c, int32_t *ci, int32_t *cj, float *force3, 
     refresh(c);
     const long long cp = std::max<long long>(cap, 1);
     int *di = nullptr, *dj = nullptr;
-    float *df = nullptr, *dd = nullptr;
+    float *df = nullptr, *dd = nullptr, *dx = nullptr;
     unsigned long long *cnt = nullptr;
     cudaError_t e = cudaMalloc((void **)&cnt, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void **)&di, sizeof(int) * cp);
     if (e == cudaSuccess) e = cudaMalloc((void **)&dj, sizeof(int) * cp);
     if (e == cudaSuccess) e = cudaMalloc((void **)&df, sizeof(float) * 3 * cp);
     if (e == cudaSuccess) e = cudaMalloc((void **)&dd, sizeof(float) * cp);
+    if (e == cudaSuccess && xi3) e = cudaMalloc((void **)&dx, sizeof(float) * 3 * cp);
     unsigned long long total = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(total), c->stream);
     if (e == cudaSuccess) {
         k_contact_list<<<grid_n(c->d.n), kThreads, 0, c->stream>>>(c->d, cnt, cap, di, dj, df,
-                                                                     dd);
+                                                                     dd, dx, both);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -579,6 +764,8 @@ int dem_get_contact_forces(dem_ctx *c, int32_t *ci, int32_t *cj, float *force3, 
             e = cudaMemcpyAsync(force3, df, sizeof(float) * 3 * m, cudaMemcpyDefault, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(delta, dd, sizeof(float) * m, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess && xi3)
+            e = cudaMemcpyAsync(xi3, dx, sizeof(float) * 3 * m, cudaMemcpyDefault, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     cudaFree(cnt);
@@ -586,6 +773,7 @@ int dem_get_contact_forces(dem_ctx *c, int32_t *ci, int32_t *cj, float *force3, 
     cudaFree(dj);
     cudaFree(df);
     cudaFree(dd);
+    if (dx) cudaFree(dx);
     if (e != cudaSuccess) return from_cuda(e);
     *n_contacts = (int64_t)total;
     const int rc = lvb_sync(c->bp);

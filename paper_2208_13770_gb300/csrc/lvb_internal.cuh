@@ -261,6 +261,7 @@ namespace lvb {
 // and v* negated per axis).
 struct IntegrateArgs {
     float4 *pos, *vel, *acc, *vstar;
+    float4 *omega, *alpha, *wstar;   // rotation (friction), or null
     float dt, half_dt2;
     int specular;
     int active;     // 0: the check reads positions as they are
@@ -294,6 +295,11 @@ __device__ __forceinline__ float4 integrate_one(const IntegrateArgs &a, const Sc
     }
     a.pos[i] = x;
     a.vstar[i] = vs;
+    if (a.omega) {   // w* = w + al dt (w*.w keeps 1/I)
+        const float4 w = a.omega[i], al = a.alpha[i];
+        a.wstar[i] = make_float4(fmaf(al.x, a.dt, w.x), fmaf(al.y, a.dt, w.y),
+                                 fmaf(al.z, a.dt, w.z), w.w);
+    }
     return x;
 }
 
@@ -304,6 +310,7 @@ struct RowsView {
     const int *row_len;
     const int *row_cap;
     const int *col;
+    float4 *hist;                  // contact history beside col, or null
     const float *rad;
     unsigned long long *kernels;   // device kernel counter of the context
     DevCounters *cnt;              // counters (trace slots)

@@ -105,6 +105,15 @@ struct DevState {
     // or null
     uint32_t *bits_out;
     int *nf_out;
+    // contact history (LVB_OPT_HISTORY): one record per row entry, hist[e]
+    // beside col[e], kept with its entry through partial rebuilds,
+    // re-layouts and store growth; null when off
+    float4 *hist;
+    float4 *pold;     // per particle: the old (xref, R_NL) of a particle
+                      // updated at this step (written by its update)
+    // the rows as they were before a re-layout, for carrying history
+    int *old_off, *old_len, *old_col;
+    float4 *old_hist;
 };
 
 // gate modes of the separate full-build kernels (init, store growth)
@@ -281,6 +290,7 @@ __device__ __forceinline__ void update_group(const DevState &s, const lvb_mlp_we
     s.born[i] = step;
     s.fref[k] = qn;
     s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
+    if (s.pold) s.pold[i] = s.oref[k];
     if (s.sc_cnt) {
         const int sc = s.scene_of[i];
         const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
@@ -316,7 +326,9 @@ static __device__ __noinline__ void update_lanes(const DevState &s, const int *i
     s.ref[i] = make_float4(p.x, p.y, p.z, sk);
     s.born[i] = step;
     s.fref[k] = qn;
-    s.oref[k] = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
+    const float4 qo = make_float4(q.x, q.y, q.z, __fadd_rn(r, q.w));
+    s.oref[k] = qo;
+    if (s.pold) s.pold[i] = qo;
     if (s.sc_cnt) {
         const int sc = s.scene_of[i];
         const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
@@ -453,7 +465,10 @@ __device__ __forceinline__ void lane_insert(const DevState &s, int j, int i, int
         for (int u = 0; u < 4; ++u) v[u] = e + u < len ? s.col[off + e + u] : 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (v[u] < 0 && atomicCAS(&s.col[off + e + u], -1, i) == -1) return;
+            if (v[u] < 0 && atomicCAS(&s.col[off + e + u], -1, i) == -1) {
+                if (s.hist) s.hist[off + e + u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                return;
+            }
     }
     for (int t = 0; t <= cap; ++t) {
         const int p = atomicAdd(&s.row_len[j], 1);
@@ -461,7 +476,10 @@ __device__ __forceinline__ void lane_insert(const DevState &s, int j, int i, int
             atomicExch(ovf, 1);
             return;
         }
-        if (atomicCAS(&s.col[off + p], -1, i) == -1) return;
+        if (atomicCAS(&s.col[off + p], -1, i) == -1) {
+            if (s.hist) s.hist[off + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
     }
 }
 
@@ -496,7 +514,10 @@ __device__ __forceinline__ void lane_edit(const DevState &s, int jr, int ji, int
                 s.col[offr + e + u] = -1;
                 dr = true;
             }
-            if (!di && vi[u] < 0 && atomicCAS(&s.col[offi + e + u], -1, i) == -1) di = true;
+            if (!di && vi[u] < 0 && atomicCAS(&s.col[offi + e + u], -1, i) == -1) {
+                di = true;
+                if (s.hist) s.hist[offi + e + u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         if (e + 4 >= lenr) dr = true;
     }
@@ -507,7 +528,10 @@ __device__ __forceinline__ void lane_edit(const DevState &s, int jr, int ji, int
             atomicExch(ovf, 1);
             return;
         }
-        if (atomicCAS(&s.col[offi + p], -1, i) == -1) return;
+        if (atomicCAS(&s.col[offi + p], -1, i) == -1) {
+            if (s.hist) s.hist[offi + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
     }
 }
 
@@ -667,6 +691,149 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     }
 }
 
+// The reference record (xref, R_NL) of particle j as it was before this
+// step's updates: its old record if it was updated at this step (history
+// mode keeps it in pold), else its present one.
+__device__ __forceinline__ float4 old_record(const DevState &s, int j)
+{
+    if (bit_of(s.bits, j)) return s.pold[j];
+    const float4 r = s.ref[j];
+    return make_float4(r.x, r.y, r.z, __fadd_rn(s.rad[j], r.w));
+}
+
+// Appends the partners j of the lanes with `ins` to row i, which only this
+// warp edits: first into the row's free slots among its first 32 entries
+// (bits of *freemask), then at its end (*tail); each new entry's history
+// starts at zero.  An entry past the row's capacity is dropped and the
+// row's length records the overflow (the re-layout rebuilds the row).
+__device__ __forceinline__ void own_row_insert(const DevState &s, int off, int cap, bool ins,
+                                               int j, unsigned *freemask, int *tail)
+{
+    const unsigned m = __ballot_sync(FULL, ins);
+    if (!m) return;
+    const int cnt = __popc(m), nfree = __popc(*freemask);
+    const int rank = __popc(m & lanemask_lt());
+    if (ins) {
+        const int slot = rank < nfree ? (int)__fns(*freemask, 0, rank + 1) : *tail + rank - nfree;
+        if (slot < cap) {
+            s.col[off + slot] = j;
+            s.hist[off + slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    const int used = min(cnt, nfree);
+    for (int t = 0; t < used; ++t) *freemask &= *freemask - 1;   // lowest bits taken
+    *tail += cnt - used;
+}
+
+// a4 + a5 for flagged particle k with contact history (LVB_OPT_HISTORY):
+// the same pair decisions as patch_warp, but row i is edited in place, as
+// the unflagged rows are, so that a partner that stays a pair keeps its
+// slot -- and its history -- through the rebuild:
+//   1. each old entry j no longer a pair under the new reference states of
+//      i and j (this step's updates are all written) becomes -1, and i
+//      leaves row j if j is unflagged (a flagged j edits its own row);
+//   2. each partner found by the stencil (+ the direct flagged test) that
+//      is a pair now and was not one under the old states (the old record
+//      of a flagged partner is kept in pold) joins row i with zero
+//      history, and an unflagged partner gets i in its row.
+static __device__ __noinline__ void patch_warp_hist(const DevState &s, int k, int nF, bool direct,
+                                                    int par, int *ovf, unsigned (&work)[3])
+{
+    const int lane = threadIdx.x & 31;
+    const int ccap = s.ccap;
+    const int i = s.fid[k];
+    const float4 qn = s.fref[k], qo = s.oref[k];
+    const int off = s.row_off[i], cap = s.row_cap[i], len0 = min(s.row_len[i], cap);
+    const SceneGeom &g = geom_of(s, i);
+    const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
+    const int ci = cell_key(g, qn.x, qn.y, qn.z) - g.cell_base;
+    const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
+    int cnt_l = 0, cid = 0;
+    if (lane < 27) {
+        const int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+        if (x >= 0 && x < d0 && y >= 0 && y < d1 && z >= 0 && z < d2) {
+            const float dd = s.reach ? cell_dist2(g, x, y, z, qn) : 0.0f;
+            if (s.reach == 0 || within_reach(g, dd, qn.w, g.H)) {
+                cid = g.cell_base + (z * d1 + y) * d0 + x;
+                cnt_l = s.cell_cnt[cid];
+                if (s.reach == 2 && !within_reach(g, dd, qn.w, __int_as_float(s.cell_rmax[cid])))
+                    cnt_l = 0;
+            }
+        }
+    }
+    cnt_l = min(cnt_l, ccap);
+    const int incl = warp_incl_scan(cnt_l);
+    const int excl = incl - cnt_l;
+    const int total = __shfl_sync(FULL, incl, 31);
+    work[0] += total;
+    // 1. old entries
+    unsigned freemask = 0u;
+    for (int e0 = 0; e0 < len0; e0 += 32) {
+        const int e = e0 + lane;
+        const int j = e < len0 ? s.col[off + e] : -2;
+        bool rm = false;
+        if (j >= 0) {
+            const float4 rj = s.ref[j];
+            rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
+            if (rm) {
+                s.col[off + e] = -1;
+                if (!bit_of(s.bits, j)) lane_remove(s, j, i);
+            }
+        }
+        const unsigned fm = __ballot_sync(FULL, e < len0 && (j == -1 || rm));
+        if (e0 == 0) freemask = fm;
+        work[2] += __popc(__ballot_sync(FULL, rm));
+    }
+    int tail = len0;
+    // 2. stencil
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const int kk = b0 + lane;
+        int c = 0;
+#pragma unroll
+        for (int st = 16; st >= 1; st >>= 1)
+            c += (__shfl_sync(FULL, incl, c + st - 1) <= kk) ? st : 0;
+        const int cc = __shfl_sync(FULL, cid, c);
+        const int ex = __shfl_sync(FULL, excl, c);
+        int j = -1;
+        float4 rj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kk < total) {
+            const long long idx = (long long)cc * ccap + (kk - ex);
+            j = s.cell_id[idx];
+            rj = s.cell_ref[idx];
+        }
+        bool ins = false, fj = false;
+        if (kk < total && j >= 0 && j != i) {
+            fj = bit_of(s.bits, j);
+            if (!(direct && fj) && pair_hit(qn, rj))
+                ins = !pair_hit(qo, fj ? s.pold[j] : rj);
+        }
+        own_row_insert(s, off, cap, ins, j, &freemask, &tail);
+        work[2] += __popc(__ballot_sync(FULL, ins && !fj));
+        if (ins && !fj) lane_insert(s, j, i, ovf);
+    }
+    if (direct) {
+        const bool own = s.sc_cnt != nullptr;
+        const float4 *lst = own ? s.sfref + g.first : s.fref;
+        const int *ids = own ? s.sfid + g.first : s.fid;
+        const int m = own ? s.sc_cnt[par * s.nscenes + s.scene_of[i]] : nF;
+        work[1] += m;
+        for (int b0 = 0; b0 < m; b0 += 32) {
+            const int kk = b0 + lane;
+            int j = -1;
+            if (kk < m && pair_hit(qn, lst[kk])) {
+                j = ids[kk];
+                if (j == i || j < g.first || j >= g.first + g.count) j = -1;
+            }
+            const bool ins = j >= 0 && !pair_hit(qo, s.pold[j]);
+            own_row_insert(s, off, cap, ins, j, &freemask, &tail);
+        }
+    }
+    if (lane == 0) {
+        s.row_len[i] = tail;
+        if (tail > cap) atomicExch(ovf, 1);
+    }
+}
+
 // a4: rows of every particle by the 27-cell stencil, one warp per row
 // (init, store growth, re-layout, GLOBAL / ALWAYS).  Lanes 0..26 each own
 // one neighbour cell; a warp scan of their occupancies flattens the
@@ -674,9 +841,20 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
 // shuffle binary search, so lanes stay busy across cell boundaries.
 // fill = 0 counts only (row_len = count); fill = 1 also writes up to the
 // row's capacity, clears the rest of the row to -1 and raises *ovf if the
-// row does not fit.  The cells must hold the final reference states.
+// row does not fit.  The cells must hold the final reference states.  With
+// contact history each written entry's record is zero, or, with carry, the
+// record of the same partner in the particle's row as it was before
+// (old_off / old_len / old_col / old_hist; zero if not there).
+__device__ __forceinline__ float4 carried_history(const DevState &s, int i, int j)
+{
+    const int o = s.old_off[i], l = s.old_len[i];
+    for (int e = 0; e < l; ++e)
+        if (s.old_col[o + e] == j) return s.old_hist[o + e];
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill, int w0,
-                                        int wstride, int *ovf)
+                                        int wstride, int *ovf, bool carry = false)
 {
     const int lane = threadIdx.x & 31;
     const int ccap = s.ccap;
@@ -726,7 +904,12 @@ __device__ __forceinline__ void ph_rows(const DevState &s, int nitems, int fill,
             const unsigned m = __ballot_sync(FULL, hit);
             if (fill && hit) {
                 const int p = found + __popc(m & lt);
-                if (p < cap) s.col[off + p] = j;
+                if (p < cap) {
+                    s.col[off + p] = j;
+                    if (s.hist)
+                        s.hist[off + p] = carry ? carried_history(s, i, j)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
             found += __popc(m);
         }
@@ -1161,10 +1344,29 @@ static __device__ __noinline__ void full_insert_pass(const DevState &s)
     }
 }
 
-static __device__ __noinline__ void all_rows_pass(const DevState &s, int fill, int *ovf)
+static __device__ __noinline__ void all_rows_pass(const DevState &s, int fill, int *ovf,
+                                                  bool carry = false)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    ph_rows(s, s.n, fill, t >> 5, nt >> 5, ovf);
+    ph_rows(s, s.n, fill, t >> 5, nt >> 5, ovf, carry);
+}
+
+// Contact history: the rows as they stand (offsets, lengths, entries and
+// records up to the extent of the last layout) copied aside before a
+// re-layout, so that the new rows can carry each entry's history.
+static __device__ __noinline__ void save_rows_pass(const DevState &s)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    for (long long i = t; i < s.n; i += nt) {
+        s.old_off[i] = s.row_off[i];
+        s.old_len[i] = min(s.row_len[i], s.row_cap[i]);
+    }
+    const long long ext = min(*(volatile long long *)&s.cnt->store_needed, s.col_cap);
+    for (long long e = t; e < ext; e += nt) {
+        s.old_col[e] = s.col[e];
+        s.old_hist[e] = s.hist[e];
+    }
 }
 
 // Offsets of the row store by a grid-wide exclusive scan of the row sizes
@@ -1224,6 +1426,10 @@ static __device__ long long layout_scan(const DevState &s, bool tight)
 static __device__ __noinline__ bool relayout_pass(const DevState &s)
 {
     DevCounters *c = s.cnt;
+    if (s.hist) {
+        save_rows_pass(s);
+        if (!grid_barrier(s)) return false;
+    }
     all_rows_pass(s, 0, nullptr);
     if (!grid_barrier(s)) return false;
     const long long need = layout_scan(s, false);
@@ -1239,7 +1445,7 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
     if (!grid_barrier(s)) return false;
     if (!store_failed(s)) {
         int unused = 0;
-        all_rows_pass(s, 1, &unused);
+        all_rows_pass(s, 1, &unused, s.hist != nullptr);
     }
     if (!grid_barrier(s)) return false;
     if (blockIdx.x == 0 && threadIdx.x == 0 && !store_failed(s)) {
@@ -1328,11 +1534,18 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
     if (!direct) {
         for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
         if (!grid_barrier(s)) return false;
-        for (int k = w0; k < nF; k += nw) patch_warp(s, k, nF, false, par, ovf, work);
+        for (int k = w0; k < nF; k += nw) {
+            if (s.hist) patch_warp_hist(s, k, nF, false, par, ovf, work);
+            else patch_warp(s, k, nF, false, par, ovf, work);
+        }
     } else {
         for (int w = w0; w < 2 * nF; w += nw) {
-            if (w < nF) patch_warp(s, w, nF, true, par, ovf, work);
-            else move_warp(s, s.fid[w - nF], s.fref[w - nF]);
+            if (w < nF) {
+                if (s.hist) patch_warp_hist(s, w, nF, true, par, ovf, work);
+                else patch_warp(s, w, nF, true, par, ovf, work);
+            } else {
+                move_warp(s, s.fid[w - nF], s.fref[w - nF]);
+            }
         }
     }
     if ((threadIdx.x & 31) == 0)

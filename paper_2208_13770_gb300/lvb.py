@@ -61,7 +61,8 @@ class dem_params(ctypes.Structure):
                 ("clamp_tensile", ctypes.c_int32), ("drum_cx", ctypes.c_float),
                 ("drum_cz", ctypes.c_float), ("drum_R", ctypes.c_float),
                 ("drum_omega", ctypes.c_float), ("contacts_on", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("pad", ctypes.c_int32), ("mu", ctypes.c_float), ("kt_ratio", ctypes.c_float),
+                ("gt_ratio", ctypes.c_float), ("pad2", ctypes.c_int32)]
 
 
 DEM_WALL_NONE, DEM_WALL_BOX, DEM_WALL_DRUM, DEM_WALL_SPECULAR = 0, 1, 2, 3
@@ -122,6 +123,9 @@ _SIGS = {
     "dem_get_state": ([_p, _p, _p, _p, _p], ctypes.c_int),
     "dem_set_state": ([_p, _p, _p, _p], ctypes.c_int),
     "dem_get_contact_forces": ([_p, _p, _p, _p, _p, _i64, _pi64], ctypes.c_int),
+    "dem_get_contact_history": ([_p, ctypes.c_int32, _p, _p, _p, _p, _p, _i64, _pi64],
+                                ctypes.c_int),
+    "dem_get_rot_state": ([_p, _p, _p, _p], ctypes.c_int),
     "dem_lvb": ([_p, ctypes.POINTER(_p)], ctypes.c_int),
     "dem_device_state": ([_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p),
                           ctypes.POINTER(_p)], ctypes.c_int),
@@ -214,6 +218,8 @@ LVB_OPT_STENCIL_REACH = 9
 LVB_OPT_GROW = 10
 LVB_OPT_STORE_LIMIT = 11
 LVB_OPT_CELL_CAPACITY = 12
+LVB_OPT_HISTORY = 13
+LVB_OPT_FORCE_RELAYOUT = 14
 LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
 TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]
 
@@ -575,6 +581,9 @@ class DEM:
         if scene.drum is not None:
             prm.drum_cx, prm.drum_cz, prm.drum_R, prm.drum_omega = scene.drum
         prm.contacts_on = int(bool(scene.contacts))
+        prm.mu = float(getattr(scene, "mu", 0.0))
+        prm.kt_ratio = float(getattr(scene, "kt_ratio", 2.0 / 7.0))
+        prm.gt_ratio = float(getattr(scene, "gt_ratio", 0.5))
         self.prm = prm
         boxes = (lvb_box * len(scenes_))()
         for q, sc in enumerate(scenes_):
@@ -644,6 +653,36 @@ class DEM:
         m = n.value
         o = np.lexsort((cj[:m], ci[:m]))
         return ci[:m][o], cj[:m][o], f3[:m][o], dl[:m][o]
+
+    def contact_history(self, sides=1):
+        """dem_get_contact_history: (ci, cj, force on i (m, 3), delta, spring
+        xi of row i (m, 3)), sorted by (i, j); sides=2: both rows of each
+        pair."""
+        n = ctypes.c_int64(0)
+        rc = _lib.dem_get_contact_history(self.ctx, sides, None, None, None, None, None, 0,
+                                          ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "dem_get_contact_history")
+        cap = max(n.value, 1)
+        ci = np.empty(cap, np.int32)
+        cj = np.empty(cap, np.int32)
+        f3 = np.empty((cap, 3), np.float32)
+        dl = np.empty(cap, np.float32)
+        xi = np.empty((cap, 3), np.float32)
+        _check(_lib.dem_get_contact_history(self.ctx, sides, _np_ptr(ci), _np_ptr(cj),
+                                            _np_ptr(f3), _np_ptr(dl), _np_ptr(xi), cap,
+                                            ctypes.byref(n)),
+               "dem_get_contact_history")
+        m = n.value
+        o = np.lexsort((cj[:m], ci[:m]))
+        return ci[:m][o], cj[:m][o], f3[:m][o], dl[:m][o], xi[:m][o]
+
+    def rot_state(self):
+        """(omega (w, 1/I), alpha, omega*) float4 records."""
+        outs = [np.empty((self.n, 4), dtype=np.float32) for _ in range(3)]
+        _check(_lib.dem_get_rot_state(self.ctx, *[_np_ptr(o) for o in outs]),
+               "dem_get_rot_state")
+        return tuple(outs)
 
     def set_state(self, pos, vel, acc):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (pos, vel, acc)]

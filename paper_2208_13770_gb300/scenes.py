@@ -54,6 +54,9 @@ class Scene:
     skin_kind: int = 1         # diameter factor
     skin_value: float = 0.1    # alpha
     cell_factor: float = 1.25  # cell edge / largest diameter
+    mu: float = 0.0            # Coulomb friction between particles (0: none)
+    kt_ratio: float = 2.0 / 7.0  # tangential / normal stiffness
+    gt_ratio: float = 0.5      # tangential / normal damping
 
     @property
     def n(self) -> int:

@@ -175,3 +175,99 @@ def test_contact_list_sums_to_the_net_forces(orc):
     f = 1e4 * delta + 2 * zeta * np.sqrt(m / 2 * 1e4) * (2 * v32)
     assert len(ci) == 1 and np.isclose(dl[0], delta, rtol=1e-12)
     assert np.isclose(f3[0, 0], -f, rtol=1e-12) and f3[0, 1] == 0 and f3[0, 2] == 0
+
+
+def _pair(u, w0=(0.0, 0.0, 0.0)):
+    # sphere 0 at the origin, sphere 1 along +x overlapping it by 1e-5 m;
+    # sphere 0 moves along +y at u, with angular velocity w0
+    r = 1e-3
+    x = np.array([[0, 0, 0, r], [2 * r - 1e-5, 0, 0, r]], np.float32)
+    v = np.zeros((2, 4), np.float32)
+    v[0, 1] = u
+    w = np.zeros((2, 4), np.float32)
+    w[0, :3] = w0
+    z = np.zeros((2, 4), np.float32)
+    return x, v, w, z
+
+
+def _fric_consts(orc, r=1e-3, rho=2500.0, kn=1e4, e=0.7, kt_ratio=2.0 / 7.0, gt_ratio=0.5):
+    r32 = float(np.float32(r))
+    m = rho * 4.0 / 3.0 * np.pi * r32 ** 3
+    zeta = -np.log(e) / np.sqrt(np.pi ** 2 + np.log(e) ** 2)
+    gam_n = 2 * zeta * np.sqrt(m / 2 * kn)
+    return m, kt_ratio * kn, gt_ratio * gam_n
+
+
+def test_friction_oracle_sticking_pair_closed_form(orc):
+    # a slow tangential motion sticks: the spring is v_t dt after one step,
+    # F_t = -(k_t dt + gamma_t) v_t, and the torque on each sphere is
+    # -r n x F_t (n from sphere 1 to sphere 0, about -x)
+    P = orc.dem_params(wall_kind=orc.WALL_NONE, g=(0, 0, 0))
+    u, dt = 1e-3, 1e-6
+    x, v, w, z = _pair(u)
+    u = float(np.float32(u))          # the inputs are binary32 values
+    m, kt, gt = _fric_consts(orc)
+    out = orc.dem_step_friction(x, v, z, w, z, dt, P, 0.5, 2.0 / 7.0, 0.5,
+                                x_in=x, vstar_in=v, wstar_in=w)
+    assert len(out["ci"]) == 1
+    xi, f = out["xi"][0], out["f"][0]
+    assert np.isclose(xi[1], u * dt, rtol=1e-12, atol=0) and xi[0] == 0 and xi[2] == 0
+    ft = -(kt * dt + gt) * u
+    assert np.isclose(f[1], ft, rtol=1e-12, atol=0)
+    # torques: -r n x F_t with n = -x: (-x) x (F y) = -F z, so T = r F z;
+    # the same for sphere 1 (both spheres turn the same way)
+    I = 0.4 * m * float(np.float32(1e-3)) ** 2
+    assert np.isclose(out["al"][0, 2], float(np.float32(1e-3)) * ft / I, rtol=1e-12, atol=0)
+    assert np.isclose(out["al"][1, 2], out["al"][0, 2], rtol=1e-12, atol=0)
+    # three steps at the same state, history carried: the spring grows by
+    # v_t dt each step
+    hist = (out["ci"], out["cj"], out["xi"])
+    for k in range(2):
+        out = orc.dem_step_friction(x, v, z, w, z, dt, P, 0.5, 2.0 / 7.0, 0.5, hist=hist,
+                                    x_in=x, vstar_in=v, wstar_in=w)
+        hist = (out["ci"], out["cj"], out["xi"])
+    assert np.isclose(out["xi"][0, 1], 3 * u * dt, rtol=1e-12, atol=0)
+    # a rotation of sphere 0 about z at w makes its contact point (at +r x)
+    # move at w r along +y: v_rel = v - (r w x n) with n = -x gives u + r w
+    x, v, w, z = _pair(u, w0=(0.0, 0.0, 0.5))
+    out = orc.dem_step_friction(x, v, z, w, z, dt, P, 0.5, 2.0 / 7.0, 0.5,
+                                x_in=x, vstar_in=v, wstar_in=w)
+    rw = float(np.float32(1e-3)) * float(np.float32(0.5))
+    assert np.isclose(out["xi"][0, 1], (u + rw) * dt, rtol=1e-9, atol=0)
+
+
+def test_friction_oracle_sliding_pair_at_the_coulomb_limit(orc):
+    # a fast tangential motion slides: |F_t| = mu F_n, F_t against v_t, and
+    # the spring is the one that gives the capped force,
+    # xi = -(F_t + gamma_t v_t) / k_t
+    P = orc.dem_params(wall_kind=orc.WALL_NONE, g=(0, 0, 0))
+    u, dt, mu = 10.0, 1e-6, 0.4
+    x, v, w, z = _pair(u)
+    mu = float(np.float32(mu))
+    m, kt, gt = _fric_consts(orc)
+    out = orc.dem_step_friction(x, v, z, w, z, dt, P, mu, 2.0 / 7.0, 0.5,
+                                x_in=x, vstar_in=v, wstar_in=w)
+    f, xi = out["f"][0], out["xi"][0]
+    fn = -f[0]                    # normal force on sphere 0 along n = -x
+    delta = 2 * float(np.float32(1e-3)) - float(np.float32(2e-3 - 1e-5))
+    assert np.isclose(fn, 1e4 * delta, rtol=1e-12, atol=0)       # no normal motion
+    assert np.isclose(f[1], -mu * fn, rtol=1e-12, atol=0) and f[2] == 0
+    assert np.isclose(xi[1], -(f[1] + gt * u) / kt, rtol=1e-12, atol=0)
+
+
+def test_friction_oracle_conserves_momentum(orc):
+    # contact forces come in equal and opposite pairs: with no walls and no
+    # gravity the total force on a dense random pack with random velocities
+    # and spins sums to zero, and so does the change of momentum
+    from paper_2208_13770_gb300 import scenes
+    s = scenes.packed(n=1200, seed=8, vsigma=0.5)
+    rng = np.random.default_rng(2)
+    w = np.zeros_like(s.pos)
+    w[:, :3] = rng.normal(0, 50.0, size=(len(s.pos), 3))
+    z = np.zeros_like(s.pos)
+    P = orc.dem_params(lo=s.lo, hi=s.hi, wall_kind=orc.WALL_NONE, g=(0, 0, 0))
+    out = orc.dem_step_friction(s.pos, s.vel, z, w, z, 1e-6, P, 0.5, 2.0 / 7.0, 0.5)
+    assert len(out["ci"]) > 300
+    m = 2500.0 * 4.0 / 3.0 * np.pi * s.pos[:, 3].astype(np.float64) ** 3
+    ptot = (m[:, None] * out["a"]).sum(axis=0)
+    assert np.all(np.abs(ptot) <= 1e-12 * out["fmag"].sum())
