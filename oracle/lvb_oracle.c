@@ -729,16 +729,22 @@ ORC_API int orc_dem_forces(int64_t n, const float *x4, const float *v4,
  * |k_n delta| + |damping term| -- the scale of the terms summed into F,
  * against which a binary32 evaluation's rounding is measured.
  * All arrays are binary64, 3n (r, fmag: n). */
+static void half_step(int64_t n, const double *x, const double *v, const double *a, double dt,
+                      double *x_out, double *vstar_out)
+{
+    for (int64_t k = 0; k < 3 * n; ++k) {
+        x_out[k] = x[k] + v[k] * dt + 0.5 * a[k] * dt * dt;
+        vstar_out[k] = v[k] + a[k] * dt;
+    }
+}
+
 ORC_API int orc_dem_step64(int64_t n, const double *x, const double *v, const double *a,
                            const double *r, double dt, const orc_dem_params *P,
                            const double *xf, const double *vf,
                            double *x_out, double *vstar_out, double *a_out, double *v_out,
                            double *fmag)
 {
-    for (int64_t k = 0; k < 3 * n; ++k) {
-        x_out[k] = x[k] + v[k] * dt + 0.5 * a[k] * dt * dt;
-        vstar_out[k] = v[k] + a[k] * dt;
-    }
+    half_step(n, x, v, a, dt, x_out, vstar_out);
     double *F = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     if (!F) return -1;
     int rc = orc_dem_forces64(n, xf ? xf : x_out, r, vf ? vf : vstar_out, P, F, fmag);
@@ -819,11 +825,8 @@ ORC_API int64_t orc_dem_step64f(int64_t n, const double *x, const double *v, con
                                 int32_t *oj, double *oxi, double *of3, double *oscale,
                                 double *fmag, double *tmag, int64_t cap)
 {
-    for (int64_t k = 0; k < 3 * n; ++k) {
-        x_out[k] = x[k] + v[k] * dt + 0.5 * a[k] * dt * dt;
-        vstar_out[k] = v[k] + a[k] * dt;
-        wstar_out[k] = w[k] + al[k] * dt;
-    }
+    half_step(n, x, v, a, dt, x_out, vstar_out);
+    for (int64_t k = 0; k < 3 * n; ++k) wstar_out[k] = w[k] + al[k] * dt;
     const double *X = xf ? xf : x_out, *V = vf ? vf : vstar_out, *W = wf ? wf : wstar_out;
     double *F = (double *)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));
     double *T = (double *)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));

@@ -271,3 +271,25 @@ def test_friction_oracle_conserves_momentum(orc):
     m = 2500.0 * 4.0 / 3.0 * np.pi * s.pos[:, 3].astype(np.float64) ** 3
     ptot = (m[:, None] * out["a"]).sum(axis=0)
     assert np.all(np.abs(ptot) <= 1e-12 * out["fmag"].sum())
+
+
+def test_friction_oracle_without_friction_is_the_normal_step(orc):
+    # mu = 0 caps every tangential force at zero: the step is the
+    # frictionless velocity-Verlet step of orc_dem_step64 (pinned above by
+    # free fall, restitution and energy), and no particle turns
+    from paper_2208_13770_gb300 import scenes
+    s = scenes.packed(n=800, seed=4, vsigma=0.3)
+    P = orc.dem_params(lo=s.lo, hi=s.hi, wall_kind=orc.WALL_BOX)
+    rng = np.random.default_rng(1)
+    a = np.zeros_like(s.pos)
+    a[:, :3] = rng.normal(0, 1.0, size=(len(s.pos), 3))
+    w = np.zeros_like(s.pos)
+    w[:, :3] = rng.normal(0, 10.0, size=(len(s.pos), 3))
+    z = np.zeros_like(s.pos)
+    out = orc.dem_step_friction(s.pos, s.vel, a, w, z, 1e-6, P, 0.0, 2.0 / 7.0, 0.5)
+    xo, vso, ao, vo = orc.dem_step(s.pos, s.vel, a, 1e-6, P)
+    assert len(out["ci"]) > 100
+    for got, want in ((out["x"], xo), (out["vstar"], vso), (out["a"], ao), (out["v"], vo)):
+        assert np.allclose(got, want, rtol=1e-13, atol=1e-300)
+    assert np.all(out["al"] == 0)
+    assert np.array_equal(out["w"], w[:, :3].astype(np.float64))
