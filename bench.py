@@ -349,6 +349,7 @@ def _e2e_batch(lvb, torch, sc, choice, rec):
                       lvb.LVB_TRIGGER_PARTIAL, choice.cell_factor, ref=ref, offsets=off)
         ctx.set_option(lvb.LVB_OPT_BLOCK_THREADS, choice.block_threads)
         ctx.set_option(lvb.LVB_OPT_COMPACT, choice.compaction)
+        ctx.set_option(lvb.LVB_OPT_CHECK_LOADS, choice.check_loads)
         bits = torch.zeros((m + 1, nw), dtype=torch.int32, pin_memory=True)
         nf = torch.zeros((m + 1,), dtype=torch.int32, pin_memory=True)
         # untimed: the first call allocates the staging slots; a step at the
@@ -754,8 +755,12 @@ def run_native(args):
     K, W = args.steps, args.warmup
     if args.only_batched:
         from paper_2208_13770_gb300 import autotune
-        res = _headline(lvb, torch, sc, autotune.Choice(), K, W, record=False,
-                        profile=args.profile)
+        ch = autotune.Choice()
+        if args.choice:
+            f = args.choice.split(",")
+            ch = autotune.Choice(float(f[0]), int(f[1]), int(f[2]),
+                                 int(f[3]) if len(f) > 3 else 1)
+        res = _headline(lvb, torch, sc, ch, K, W, record=False, profile=args.profile)
         if rank == 0:
             ph = res["phase_ms"] / K
             print(json.dumps({"only_batched": True, "n": n, "phases_ms_per_step": list(ph),
@@ -812,7 +817,9 @@ def run_native(args):
                    if world > 1 else "single",
                    "autotuned": {"cell_factor": choice.cell_factor,
                                  "block_threads": choice.block_threads,
-                                 "compaction": choice.compaction}},
+                                 "compaction": choice.compaction,
+                                 "check_loads": "registers" if choice.check_loads else
+                                                "bulk-copy ring"}},
         "roofline": roof,
         "flagged_per_step": parts["F"],
         "rebuild_fraction": _diff(s0, s1, "updated_total") / (n * K),
@@ -966,6 +973,9 @@ def main():
     ap.add_argument("--scenes", type=int, default=0,
                     help="with --only-batched: the first S scenes of the batch only (a smaller "
                          "case of the same kernel, for profiling)")
+    ap.add_argument("--choice", default="",
+                    help="with --only-batched: launch choice 'cell_factor,block_threads,"
+                         "compaction' (default 1.25,1024,0)")
     ap.add_argument("--profile", action="store_true",
                     help="with --only-batched: bracket the timed steps with "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off)")

@@ -340,6 +340,16 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 not fit even without slack reports
                                 LVB_EOVERFLOW */
 
+#define LVB_OPT_CHECK_LOADS 15 /* how the displacement check of lvb_step reads
+                                pos and ref: LVB_CHECK_REGS (default) or
+                                LVB_CHECK_RING */
+
+/* Values of LVB_OPT_CHECK_LOADS. */
+#define LVB_CHECK_REGS 1     /* each warp loads four chunks of 32 particles
+                                into registers at once (streaming loads) */
+#define LVB_CHECK_RING 0     /* thread 0 of each block streams tiles through
+                                a four-stage shared-memory ring of bulk copies */
+
 /* Values of LVB_OPT_COMPACT. */
 #define LVB_COMPACT_WARP  0  /* flagged ids gather in a per-warp list during
                                 the check; the list takes its indices with

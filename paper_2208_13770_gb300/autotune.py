@@ -1,14 +1,15 @@
 """Autotuner for the batched DEM step: cell-size factor, block shape of the
-step kernel, and the compaction scheme of the flagged ids (one atomic per
-warp chunk, or one per block tile).
+step kernel, the compaction scheme of the flagged ids (one atomic per warp
+chunk, or one per block tile), and how the broad phase's check reads its
+inputs (register loads or a ring of bulk copies).
 
 Each candidate is a fresh context on the same batch from the same initial
 state; it runs ``warm`` steps, then ``steps`` steps timed with CUDA events
 on the context's stream (graph replays of DEM_GRAPH_STEPS steps).  The
 search is coordinate-wise: the cell factor first (it changes the grid, so a
 new context), then the block shape, then the compaction scheme, each on
-the best of the previous ones.  The block shape and the compaction scheme
-are launch choices only: the lists do not change.  The cell factor also sets
+the best of the previous ones.  The block shape, the compaction scheme and
+the check's loads are launch choices only: the lists do not change.  The cell factor also sets
 the cap on every skin (R_NL <= half a cell edge, Eq.
 skin_formulus_mincell), so at 1.0 the largest particles get smaller skins
 and update more often; the lists change with the skins, but no contact is
@@ -23,6 +24,7 @@ import os
 CELL_FACTORS = (1.0, 1.25, 1.5)
 BLOCK_THREADS = (1024, 512, 256)
 COMPACTION = (0, 1)   # LVB_COMPACT_WARP, LVB_COMPACT_BLOCK
+CHECK_LOADS = (1, 0)  # LVB_CHECK_REGS, LVB_CHECK_RING
 
 
 @dataclasses.dataclass
@@ -30,10 +32,12 @@ class Choice:
     cell_factor: float = 1.25
     block_threads: int = 1024
     compaction: int = 0
+    check_loads: int = 1
 
     def apply(self, dem, lvb):
         dem.lvb.set_option(lvb.LVB_OPT_BLOCK_THREADS, self.block_threads)
         dem.lvb.set_option(lvb.LVB_OPT_COMPACT, self.compaction)
+        dem.lvb.set_option(lvb.LVB_OPT_CHECK_LOADS, self.check_loads)
 
 
 def _trial(torch, lvb, scene_list, choice, warm, steps):
@@ -129,6 +133,14 @@ def tune(scene_list, warm=200, steps=400, key=None):
         if cp == base.compaction:
             continue
         c = dataclasses.replace(base, compaction=cp)
+        ms = run(c)
+        if ms < best_ms:
+            best, best_ms = c, ms
+    base = best
+    for ck in CHECK_LOADS:
+        if ck == base.check_loads:
+            continue
+        c = dataclasses.replace(base, check_loads=ck)
         ms = run(c)
         if ms < best_ms:
             best, best_ms = c, ms

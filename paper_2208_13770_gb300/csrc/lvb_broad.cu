@@ -942,6 +942,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     s.bar_spins = kBarrierSpins;
     s.direct_max = kFlaggedDirectMax;
     s.reach = 2;
+    s.check_regs = 1;
     s.nwords = c->nwords;
     s.trigger = trigger;
     s.skin_kind = skin->kind;
@@ -1091,7 +1092,8 @@ int lvb_step(lvb_ctx *c, const float *pos_r, const float *vel, const float *acc)
     }
     const cudaError_t e =
         launch_coop(k_step<false, NoTail>, dim3(c->step_blocks), dim3(c->block_threads),
-                    (size_t)check_smem_bytes(c->block_threads), c->stream,
+                    c->s.check_regs ? (size_t)0 : (size_t)check_smem_bytes(c->block_threads),
+                    c->stream,
                     (const float4 *)pos_r, (const float4 *)vel, a4, c->s, IntegrateArgs{},
                     NoTail{});
     return from_cuda(e);
@@ -1192,6 +1194,9 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     } else if (option == LVB_OPT_DIRECT_MAX) {
         if (value < 0 || value > (1 << 20)) return LVB_EINVAL;
         c->s.direct_max = (int)value;
+    } else if (option == LVB_OPT_CHECK_LOADS) {
+        if (value != LVB_CHECK_REGS && value != LVB_CHECK_RING) return LVB_EINVAL;
+        c->s.check_regs = value == LVB_CHECK_REGS;
     } else if (option == LVB_OPT_STENCIL_REACH) {
         if (value < 0 || value > 2) return LVB_EINVAL;
         c->s.reach = (int)value;
@@ -1236,8 +1241,8 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
         }
     } else if (option == LVB_OPT_FORCE_RELAYOUT) {
         if (value != 1) return LVB_EINVAL;
-        const int ones[2] = {1, 1};
-        const cudaError_t e = cudaMemcpyAsync(c->s.cnt->ovf, ones, sizeof(ones),
+        const int one = 1;
+        const cudaError_t e = cudaMemcpyAsync(&c->s.cnt->force_relayout, &one, sizeof(one),
                                               cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) return from_cuda(cudaStreamSynchronize(c->stream));
         return from_cuda(e);

@@ -42,6 +42,7 @@ struct DevCounters {
     int nF_acc[2];     // flagged count while the check runs (slot: step parity)
     int ovf[2];        // a row outgrew its capacity (slot: step parity)
     int row_overflow;  // same, for the separate full-build kernels
+    int force_relayout;  // the next step that rebuilds rows re-lays them out (test hook)
     unsigned err;      // sticky DERR_* bits
     int last_flagged;
     int last_updated;

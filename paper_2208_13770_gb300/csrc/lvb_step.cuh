@@ -98,6 +98,8 @@ struct DevState {
     unsigned bar_spins;   // polls before a barrier gives up
     int direct_max;       // largest flagged count rebuilt in one phase with
                           // the direct flagged-pair test (LVB_OPT_DIRECT_MAX)
+    int check_regs;       // check pass of the broad phase alone: 1 register loads,
+                          // 0 the bulk-copy ring (LVB_OPT_CHECK_LOADS)
     int reach;            // stencil cells skipped by distance (LVB_OPT_STENCIL_REACH):
                           // 0 none, 1 by the cap H, 2 by H and the cell's own bound
     // second destination of this step's flag words and flagged count
@@ -1169,6 +1171,51 @@ __device__ __forceinline__ void check_pass_fused(const DevState &s, const float4
     flush_pending_final(s, pd, ia.pos, vel, acc, inc, step, nF_acc);
 }
 
+// The check pass of the broad phase alone, register form
+// (LVB_OPT_CHECK_LOADS = LVB_CHECK_REGS): block b takes tiles b, b + grid,
+// ... of blockDim * kCheckRegsUnroll particles; each warp loads its
+// kCheckRegsUnroll chunks of 32 consecutive particles' pos and ref at once
+// (streaming loads: read once, evict first), so every warp keeps 16 loads
+// of 16 bytes in flight with no block barrier in the loop.
+constexpr int kCheckRegsUnroll = 4;
+
+__device__ __forceinline__ void check_pass_regs(const DevState &s, const float4 *__restrict__ pos,
+                                                const float4 *vel, const float4 *acc, bool inc,
+                                                int step, int *nF_acc)
+{
+    constexpr int U = kCheckRegsUnroll;
+    __shared__ int pend_id[kStepMaxThreads / 32][kPending];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Pending pd{pend_id[warp], 0};
+    const int tile = blockDim.x * U;
+    for (int t0 = blockIdx.x * tile; t0 < s.n; t0 += gridDim.x * tile) {
+        float4 p[U], q[U];
+        int cu[U];
+        bool f[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cu[u] = t0 + u * blockDim.x + warp * 32;
+            const int i = cu[u] + lane;
+            if (i < s.n) {
+                p[u] = __ldcs(pos + i);
+                q[u] = __ldcs(s.ref + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = cu[u] + lane;
+            f[u] = false;
+            if (i < s.n) {
+                f[u] = violates(p[u], q[u]);
+                if (!(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(p[u].z)))
+                    atomicOr(&s.cnt->err, DERR_NAN);
+            }
+        }
+        flag_chunks<U>(s, cu, f, pos, vel, acc, inc, step, nF_acc, pd);
+    }
+    flush_pending_final(s, pd, pos, vel, acc, inc, step, nF_acc);
+}
+
 // ---------------------------------------------------------------------------
 // Bulk copies into shared memory (cp.async.bulk, completion counted by an
 // mbarrier), for the check pass of the broad phase alone.
@@ -1449,6 +1496,7 @@ static __device__ __noinline__ bool relayout_pass(const DevState &s)
     }
     if (!grid_barrier(s)) return false;
     if (blockIdx.x == 0 && threadIdx.x == 0 && !store_failed(s)) {
+        c->force_relayout = 0;
         c->relayouts += 1;
         c->store_needed = need;
         if (need * 5 > s.col_cap * 3) {        // over 60% of the store: grow it
@@ -1610,6 +1658,8 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
 
     if constexpr (kFused)
         check_pass_fused(s, vel, acc, ia, inc, step, &c->nF_acc[par]);
+    else if (s.check_regs)
+        check_pass_regs(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
     else
         check_pass_stream(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
     if (net) weights_copy_wait();
@@ -1674,7 +1724,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
             t2 = global_ns();
             trace_add(c, TR_REBUILD, t1, t2);
         }
-        if (*(volatile int *)ovf && !store_failed(s)) {
+        if ((*(volatile int *)ovf || *(volatile int *)&c->force_relayout) && !store_failed(s)) {
             if (!relayout_pass(s)) return;
             if (s.trace && lead) trace_add(c, TR_RELAYOUT, t2, global_ns());
         }

@@ -107,7 +107,7 @@ def _check(orc, s, P, before, after, flags):
 
 def test_friction_history_survives_rebuilds(orc):
     lvb = _lvb()
-    s = scenes.packed(n=4000, seed=19, vsigma=0.6)
+    s = scenes.packed(n=4000, seed=19, vsigma=5.0)
     s.mu, s.kt_ratio, s.gt_ratio = MU, KT_RATIO, GT_RATIO
     P = _params(orc, s)
     dem = lvb.DEM(s)
