@@ -65,6 +65,8 @@ WORKLOAD = ("batched settling boxes: 512 independent scenes, N log-uniform in [1
 BATCH_STEPS = 2000
 T0 = 1000                 # the timed window starts after step T0 of the batch's run
 T0_SETTLING = 10_000      # and after step T0_SETTLING of the 200k settling box's run
+SETTLING_STEPS = 2000     # timed steps of the 200k box (at most; --steps if fewer)
+EARLY_PERMILLE = 900      # the early trigger's beta (x 1000) in the settling extra
 # 1 GiB: well above the 129 MB L2 (for the workloads that fit in it)
 L2_FLUSH_BYTES = 1 << 30
 M_E2E = 16                # steps of the window the e2e and CPU legs replay
@@ -440,11 +442,15 @@ def _settling(lvb, torch, steps, warmup, hbm_peak, peak_kind):
     out = {"workload": "settling box: 200,000 polydisperse spheres r~U[0.5,2] mm, steps "
                        "%d..%d of the 20,000-step run" % (T0_SETTLING + 1, T0_SETTLING + steps),
            "n": n, "l2": "flushed before every timed step (1 GiB write)"}
-    for name, trig, kind, val in (("local", lvb.LVB_TRIGGER_PARTIAL, scene.skin_kind,
-                                   scene.skin_value),
-                                  ("global_buffer", lvb.LVB_TRIGGER_GLOBAL,
-                                   lvb.LVB_SKIN_GLOBAL, 0.1 * dmean)):
+    for name, trig, kind, val, early in (("local", lvb.LVB_TRIGGER_PARTIAL, scene.skin_kind,
+                                          scene.skin_value, 1000),
+                                         ("local_early", lvb.LVB_TRIGGER_PARTIAL,
+                                          scene.skin_kind, scene.skin_value, EARLY_PERMILLE),
+                                         ("global_buffer", lvb.LVB_TRIGGER_GLOBAL,
+                                          lvb.LVB_SKIN_GLOBAL, 0.1 * dmean, 1000)):
         dem = lvb.DEM(scene, trigger=trig, skin_kind=kind, skin_value=val)
+        if early < 1000:
+            dem.lvb.set_option(lvb.LVB_OPT_EARLY, early)
         _advance_to(dem, T0_SETTLING - warmup)
         _phases(lvb, torch, dem, warmup, flush)
         s0 = dem.lvb.stats()
@@ -459,15 +465,19 @@ def _settling(lvb, torch, steps, warmup, hbm_peak, peak_kind):
              "rebuild_fraction": _diff(s0, s1, "updated_total") / (n * steps),
              "rebuild_step_fraction": _diff(s0, s1, "rebuild_steps") / steps,
              "entries": s1["entries"], "relayouts": s1["relayouts"]}
-        if name == "local":
+        if name.startswith("local"):
             b, parts = _bp_bytes(n, steps, s0, s1)
             r["roofline"] = _roofline("k_step (broad phase)", b, ph[1] / steps, hbm_peak,
                                       peak_kind, None, parts)
             r["narrow_phase"] = _narrow_phase(n, s1["entries"], ph[2] / steps, hbm_peak)
+            if early < 1000:
+                r["early_beta"] = early / 1000.0
         else:
             r["skin"] = "uniform 0.1 * mean diameter = %.3g m" % (0.1 * dmean)
         out[name] = r
-    out["speedup_vs_global"] = out["local"]["value"] / out["global_buffer"]["value"]
+    out["speedup_vs_global"] = {
+        "local": out["local"]["value"] / out["global_buffer"]["value"],
+        "local_early": out["local_early"]["value"] / out["global_buffer"]["value"]}
     # the driver's own form: one cooperative launch per full DEM step, graphs
     dem = lvb.DEM(scene)
     _advance_to(dem, T0_SETTLING)
@@ -797,7 +807,8 @@ def run_native(args):
     cpu = None if args.no_cpu_baseline else _cpu_baseline(sc, res["rec"])
     extras = {}
     if not args.no_extras:
-        extras["settling_200k"] = _settling(lvb, torch, min(K, 2000), W, hbm_peak, peak_kind)
+        extras["settling_200k"] = _settling(lvb, torch, max(min(K, SETTLING_STEPS), 200), W,
+                                            hbm_peak, peak_kind)
         extras["drum_2M"] = _drum(lvb, torch, hbm_peak, peak_kind)
         extras["ballistic_2k"] = _ballistic(lvb, torch)
         if not args.no_learned:
@@ -838,7 +849,9 @@ def run_native(args):
         "clocks": clk.summary(),
     }
     if "settling_200k" in extras:
-        line["speedup_vs_global"] = extras["settling_200k"]["speedup_vs_global"]
+        line["speedup_vs_global"] = extras["settling_200k"]["speedup_vs_global"]["local"]
+        line["speedup_vs_global_early"] = \
+            extras["settling_200k"]["speedup_vs_global"]["local_early"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
     line.update(extras)

@@ -340,6 +340,17 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
                                 not fit even without slack reports
                                 LVB_EOVERFLOW */
 
+#define LVB_OPT_EARLY 16      /* the early trigger, beta = value / 1000 (as
+                                binary32), 1 .. 1000 (1000, the default: off).
+                                On a step where some particle violates Eq.
+                                update, every particle with |x - xref|^2 >
+                                (beta skin)^2 (binary32: t = beta * skin,
+                                then t * t) is updated with it, so the next
+                                violation comes later and fewer steps pay a
+                                rebuild.  The list stays the pair set of the
+                                reference states; lvb_get_flags still returns
+                                the violations, lvb_stats counts both.  One
+                                scene, PARTIAL trigger (else LVB_EINVAL) */
 #define LVB_OPT_CHECK_LOADS 15 /* how the displacement check of lvb_step reads
                                 pos and ref: LVB_CHECK_REGS (default) or
                                 LVB_CHECK_RING */

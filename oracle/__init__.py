@@ -70,6 +70,8 @@ def _configure(L):
         i64 = ctypes.c_int64
         L.orc_flags.argtypes = [i64, p, p, p]
         L.orc_flags.restype = i64
+        L.orc_flags_beta.argtypes = [i64, p, p, ctypes.c_float, p]
+        L.orc_flags_beta.restype = i64
         L.orc_skin.argtypes = [i64, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, p, p, p, p]
         L.orc_skin.restype = None
@@ -160,6 +162,15 @@ def flags(pos4, ref4):
     pos4, ref4 = _f32x4(pos4), _f32x4(ref4)
     out = np.zeros(len(pos4), dtype=np.uint8)
     lib().orc_flags(len(pos4), _ptr(pos4), _ptr(ref4), _ptr(out))
+    return out.astype(bool)
+
+
+def flags_beta(pos4, ref4, beta):
+    """The early trigger's set: True where |x - xref|^2 > (beta skin)^2
+    (binary32, beta rounded to binary32)."""
+    pos4, ref4 = _f32x4(pos4), _f32x4(ref4)
+    out = np.zeros(len(pos4), dtype=np.uint8)
+    lib().orc_flags_beta(len(pos4), _ptr(pos4), _ptr(ref4), np.float32(beta), _ptr(out))
     return out.astype(bool)
 
 

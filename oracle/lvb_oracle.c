@@ -117,6 +117,27 @@ ORC_API int64_t orc_flags(int64_t n, const float *pos4, const float *ref4,
     return nf;
 }
 
+/* The early trigger's set (an option of the partial trigger; the paper  */
+/* has the per-particle violation of Eq. update and the global rebuild   */
+/* of Def. autoverlet): the particles whose displacement exceeds beta    */
+/* times their skin, |x - xref|^2 > t * t with t = beta * skin, every     */
+/* product rounded to binary32 (beta itself a binary32 value).  Strict   */
+/* ">" as in Eq. update.                                                 */
+/* Pinned by: hand cases at and around the boundary (tests).             */
+ORC_API int64_t orc_flags_beta(int64_t n, const float *pos4, const float *ref4, float beta,
+                               uint8_t *flag)
+{
+    int64_t nf = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float d2 = sqdist_f32(pos4 + 4 * i, ref4 + 4 * i);
+        float t = beta * ref4[4 * i + 3];
+        float t2 = t * t;
+        flag[i] = (uint8_t)(d2 > t2);
+        nf += flag[i];
+    }
+    return nf;
+}
+
 /* ------------------------------------------------------------------ */
 /* Skin policies.                                                       */
 /*   kind 0  global skin s_g (the paper's constant-skin comparator,     */

@@ -12,6 +12,8 @@ current positions (and velocities when the skin policy needs them):
      (the per-particle extension of the scheme; the pair set it yields is
      still correct by the triangle-inequality argument of Theorem 1,
      because every unflagged particle is within its skin of its own xref);
+     with the early trigger (early_beta < 1), on a step where F is not
+     empty, also every p with |x_p - xref_p| > early_beta * skin_p;
    * ``TRIGGER_GLOBAL``  -- if F is not empty every particle is updated: the
      paper's scheme, which re-executes the whole broad phase (Def.
      autoverlet);
@@ -30,7 +32,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import (SKIN_GLOBAL, SKIN_DIAMETER_FACTOR, SKIN_PAPER_KVDT, SKIN_LEARNED,  # noqa: F401
-               flags as _flags, skin as _skin, pairs as _pairs, contacts as _contacts)
+               flags as _flags, flags_beta as _flags_beta, skin as _skin, pairs as _pairs,
+               contacts as _contacts)
 
 TRIGGER_PARTIAL, TRIGGER_GLOBAL, TRIGGER_ALWAYS = 0, 1, 2
 
@@ -41,12 +44,16 @@ class OracleLVB:
     updated particle is then the network's, from the features of lvb_mlp.h."""
 
     def __init__(self, pos4, skin_kind, skin_value, dt, H, trigger=TRIGGER_PARTIAL,
-                 vel4=None, proposal=None, ref4=None, learned=None, acc4=None):
+                 vel4=None, proposal=None, ref4=None, learned=None, acc4=None,
+                 early_beta=1.0):
         pos4 = np.ascontiguousarray(pos4, dtype=np.float32)
         self.n = len(pos4)
         self.kind, self.value, self.dt, self.H = int(skin_kind), np.float32(skin_value), \
             np.float32(dt), np.float32(H)
         self.trigger = int(trigger)
+        # the early trigger (partial trigger only): on a step with a
+        # violation, the particles past early_beta * skin are updated too
+        self.early_beta = np.float32(early_beta)
         self.rad = pos4[:, 3].copy()
         self.learned = learned
         self.born = np.zeros(self.n, dtype=np.int64)
@@ -77,6 +84,8 @@ class OracleLVB:
         step = self.steps + 1
         if self.trigger == TRIGGER_PARTIAL:
             upd = f.copy()
+            if self.early_beta < 1 and f.any():
+                upd |= _flags_beta(pos4, self.ref, self.early_beta)
         elif self.trigger == TRIGGER_GLOBAL:
             upd = np.full(self.n, bool(f.any()))
         else:

@@ -4,8 +4,9 @@ chunk, or one per block tile), and how the broad phase's check reads its
 inputs (register loads or a ring of bulk copies).
 
 Each candidate is a fresh context on the same batch from the same initial
-state; it runs ``warm`` steps, then ``steps`` steps timed with CUDA events
-on the context's stream (graph replays of DEM_GRAPH_STEPS steps).  The
+state; it runs ``warm`` steps (graph replays of DEM_GRAPH_STEPS steps), then
+``steps`` steps phase by phase, the broad phase of each between CUDA events
+on the context's stream: the tuner minimises the broad phase's time.  The
 search is coordinate-wise: the cell factor first (it changes the grid, so a
 new context), then the block shape, then the compaction scheme, each on
 the best of the previous ones.  The block shape, the compaction scheme and
@@ -41,22 +42,30 @@ class Choice:
 
 
 def _trial(torch, lvb, scene_list, choice, warm, steps):
+    """Broad-phase time per step of one candidate: `warm` steps of the DEM
+    driver (graphs), then `steps` steps phase by phase with CUDA events
+    around each broad-phase launch (the quantity the candidates differ in:
+    the cell factor changes the grid and the skins' cap, the other choices
+    the broad phase's launch)."""
     dem = lvb.DEM(scene_list, cell_factor=choice.cell_factor)
     try:
         choice.apply(dem, lvb)
         dem.advance(warm)
         stream = torch.cuda.current_stream()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
         torch.cuda.synchronize()
-        e0.record(stream)
-        dem.advance(steps)
-        e1.record(stream)
+        for e0, e1 in evs:
+            dem.phase(lvb.DEM_PHASE_INTEGRATE)
+            e0.record(stream)
+            dem.phase(lvb.DEM_PHASE_BROAD)
+            e1.record(stream)
+            dem.phase(lvb.DEM_PHASE_FORCES)
         torch.cuda.synchronize()
         rc = dem.sync()
         if rc != 0:
             raise RuntimeError("device error %d: %s" % (rc, lvb.lvb_strerror(rc)))
-        return e0.elapsed_time(e1) / steps
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps
     finally:
         dem.close()
 
@@ -93,7 +102,8 @@ def _cache_store(key, choice, trials):
 
 
 def tune(scene_list, warm=200, steps=400, key=None):
-    """Returns (best Choice, list of trials {choice fields, ms_per_step}).
+    """Returns (best Choice, list of trials {choice fields, ms_per_step of
+    the broad phase}).
     With key (a scene kind), the choice is looked up in a per-user cache
     under (kind, particle-count bucket, GPU name) and stored there after a
     search, so that a second run on the same kind of workload and GPU skips

@@ -488,6 +488,7 @@ cudaError_t dalloc(T **p, long long count)
 void free_all(lvb_ctx *c)
 {
     DevState &s = c->s;
+    if (s.ubits && s.ubits != s.bits) cudaFree(s.ubits);
     void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.fref, s.oref, s.bits, s.fid, s.sc_cnt,
                     s.sfid, s.sfref, s.row_off,
                     s.row_len, s.row_cap, s.col, s.cell_cnt, s.cell_id,
@@ -943,6 +944,8 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
     s.direct_max = kFlaggedDirectMax;
     s.reach = 2;
     s.check_regs = 1;
+    s.ubits = s.bits;
+    s.early_beta = 1.0f;
     s.nwords = c->nwords;
     s.trigger = trigger;
     s.skin_kind = skin->kind;
@@ -1194,6 +1197,19 @@ int lvb_set_option(lvb_ctx *c, int32_t option, int64_t value)
     } else if (option == LVB_OPT_DIRECT_MAX) {
         if (value < 0 || value > (1 << 20)) return LVB_EINVAL;
         c->s.direct_max = (int)value;
+    } else if (option == LVB_OPT_EARLY) {
+        if (value < 1 || value > 1000) return LVB_EINVAL;
+        if (value < 1000 && (c->trigger != LVB_TRIGGER_PARTIAL || c->nscenes != 1))
+            return LVB_EINVAL;
+        DevState &s = c->s;
+        if (value < 1000 && s.ubits == s.bits) {
+            const cudaError_t e = dalloc(&s.ubits, c->nwords);
+            if (e != cudaSuccess) {
+                s.ubits = s.bits;
+                return from_cuda(e);
+            }
+        }
+        s.early_beta = (float)((double)value / 1000.0);
     } else if (option == LVB_OPT_CHECK_LOADS) {
         if (value != LVB_CHECK_REGS && value != LVB_CHECK_RING) return LVB_EINVAL;
         c->s.check_regs = value == LVB_CHECK_REGS;

@@ -107,6 +107,11 @@ struct DevState {
     // or null
     uint32_t *bits_out;
     int *nf_out;
+    // the particles updated at this step, one bit each: the flag words
+    // (bits) unless the early trigger is on (LVB_OPT_EARLY), which adds
+    // particles past beta * skin on steps with a flag; the rebuild reads this
+    uint32_t *ubits;
+    float early_beta;     // 1: off; < 1: the early trigger's fraction of the skin
     // contact history (LVB_OPT_HISTORY): one record per row entry, hist[e]
     // beside col[e], kept with its entry through partial rebuilds,
     // re-layouts and store growth; null when off
@@ -605,7 +610,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         const int e = e0 + lane;
         const int j = e0 == 0 ? jo0 : (e < len0 ? s.col[off + e] : -1);
         bool rm = false;
-        if (e < len0 && j >= 0 && !bit_of(s.bits, j)) {
+        if (e < len0 && j >= 0 && !bit_of(s.ubits, j)) {
             const float4 rj = s.ref[j];
             rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
         }
@@ -633,7 +638,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         }
         bool hit = false, ins = false;
         if (kk < total && j >= 0 && j != i) {
-            const bool fj = bit_of(s.bits, j);
+            const bool fj = bit_of(s.ubits, j);
             if (!(direct && fj)) {
                 hit = pair_hit(qn, rj);
                 ins = hit && !fj && !pair_hit(qo, rj);
@@ -698,7 +703,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
 // mode keeps it in pold), else its present one.
 __device__ __forceinline__ float4 old_record(const DevState &s, int j)
 {
-    if (bit_of(s.bits, j)) return s.pold[j];
+    if (bit_of(s.ubits, j)) return s.pold[j];
     const float4 r = s.ref[j];
     return make_float4(r.x, r.y, r.z, __fadd_rn(s.rad[j], r.w));
 }
@@ -779,7 +784,7 @@ static __device__ __noinline__ void patch_warp_hist(const DevState &s, int k, in
             rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
             if (rm) {
                 s.col[off + e] = -1;
-                if (!bit_of(s.bits, j)) lane_remove(s, j, i);
+                if (!bit_of(s.ubits, j)) lane_remove(s, j, i);
             }
         }
         const unsigned fm = __ballot_sync(FULL, e < len0 && (j == -1 || rm));
@@ -805,7 +810,7 @@ static __device__ __noinline__ void patch_warp_hist(const DevState &s, int k, in
         }
         bool ins = false, fj = false;
         if (kk < total && j >= 0 && j != i) {
-            fj = bit_of(s.bits, j);
+            fj = bit_of(s.ubits, j);
             if (!(direct && fj) && pair_hit(qn, rj))
                 ins = !pair_hit(qo, fj ? s.pold[j] : rj);
         }
@@ -1536,6 +1541,50 @@ static __device__ __noinline__ void log_pass(const DevState &s, const float4 *po
     }
 }
 
+// The early trigger (LVB_OPT_EARLY), on a step where some particle
+// violates Eq. update: every other particle whose displacement exceeds
+// beta times its skin, |x - xref|^2 > (beta skin)^2 in the fixed binary32
+// formula, is updated too, so that the next violation comes later (a
+// reading of Def. autoverlet's trigger between its per-particle and global
+// forms: the pair set stays the function of (xref, skin) it always is).
+// One warp per 32 consecutive particles: the updated-set word ubits = the
+// flag word | the early ones; the early ones join the flagged list (one
+// atomic per warp) and, unless the update is deferred, are updated here.
+static __device__ __noinline__ void early_pass(const DevState &s, const float4 *pos,
+                                               const float4 *vel, int step, int *nF_acc)
+{
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    __shared__ int ids_sh[kStepMaxThreads / 32][32];
+    int *ids = ids_sh[threadIdx.x >> 5];
+    for (int w = w0; w < s.nwords; w += nw) {
+        const int i = w * 32 + lane;
+        const uint32_t fw = s.bits[w];
+        bool e = false;
+        if (i < s.n && !((fw >> lane) & 1u)) {
+            const float4 p = pos[i];
+            const float4 q = s.ref[i];
+            const float t = __fmul_rn(s.early_beta, q.w);
+            e = sqdist_rn(p.x, p.y, p.z, q.x, q.y, q.z) > __fmul_rn(t, t);
+        }
+        const unsigned m = __ballot_sync(FULL, e);
+        if (lane == 0) s.ubits[w] = fw | m;
+        if (!m) continue;
+        int k0 = 0;
+        if (lane == 0) k0 = atomicAdd(nF_acc, __popc(m));
+        k0 = __shfl_sync(FULL, k0, 0);
+        const int r = __popc(m & lanemask_lt());
+        if (e) {
+            ids[r] = i;
+            s.fid[k0 + r] = i;
+        }
+        __syncwarp();
+        if (!deferred_update(s)) update_lanes(s, ids, k0, __popc(m), pos, vel, step);
+        __syncwarp();
+    }
+}
+
 // Tail of a step that only does the broad phase.
 struct NoTail {
     static constexpr bool kActive = false;
@@ -1664,25 +1713,31 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         check_pass_stream(s, pos_in, vel, acc, inc, step, &c->nF_acc[par]);
     if (net) weights_copy_wait();
     if (!grid_barrier(s)) return;
-    const int nF = *(volatile int *)&c->nF_acc[par];
+    const int nV = *(volatile int *)&c->nF_acc[par];   // violations of Eq. update
+    int nF = nV;                                        // particles updated
+    if (inc && nV > 0 && s.early_beta < 1.0f) {
+        early_pass(s, pos, vel, step, &c->nF_acc[par]);
+        if (!grid_barrier(s)) return;
+        nF = *(volatile int *)&c->nF_acc[par];
+    }
     if (s.sc_cnt && blockIdx.x == 0)   // the next step's scene counters
         for (int q = threadIdx.x; q < s.nscenes; q += blockDim.x)
             s.sc_cnt[(par ^ 1) * s.nscenes + q] = 0;
     int upd;
     if (s.trigger == LVB_TRIGGER_PARTIAL) upd = nF;
-    else if (s.trigger == LVB_TRIGGER_GLOBAL) upd = nF ? s.n : 0;
+    else if (s.trigger == LVB_TRIGGER_GLOBAL) upd = nV ? s.n : 0;
     else upd = s.n;
     unsigned long long t1 = 0;
     if (lead) {
         // stores and reductions only: no load on the step's last path
         c->nF_acc[par ^ 1] = 0;
         c->ovf[par ^ 1] = 0;
-        c->nF = nF;
-        if (s.nf_out) *s.nf_out = nF;
-        c->last_flagged = nF;
+        c->nF = nV;
+        if (s.nf_out) *s.nf_out = nV;
+        c->last_flagged = nV;
         c->last_updated = upd;
         atomicAdd((unsigned long long *)&c->steps, 1ULL);
-        atomicAdd((unsigned long long *)&c->flagged_total, (unsigned long long)nF);
+        atomicAdd((unsigned long long *)&c->flagged_total, (unsigned long long)nV);
         atomicAdd((unsigned long long *)&c->updated_total, (unsigned long long)upd);
         if (upd) atomicAdd((unsigned long long *)&c->rebuild_steps, 1ULL);
         atomicAdd(&c->kernels, 1ULL);

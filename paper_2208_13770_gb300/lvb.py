@@ -221,6 +221,7 @@ LVB_OPT_CELL_CAPACITY = 12
 LVB_OPT_HISTORY = 13
 LVB_OPT_FORCE_RELAYOUT = 14
 LVB_OPT_CHECK_LOADS = 15
+LVB_OPT_EARLY = 16
 LVB_CHECK_RING, LVB_CHECK_REGS = 0, 1
 LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
 TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]

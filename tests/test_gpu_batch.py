@@ -151,27 +151,31 @@ def test_batch_dem_matches_oracle_per_scene(orc):
 
 def test_autotuner_picks_a_measured_candidate_and_keeps_results():
     # the coordinate search times every candidate once and returns the
-    # fastest; the launch choices (block size, compaction) change no result
+    # fastest; the launch choices (block size, compaction, the check's
+    # loads) change no result
     lvb = _lvb()
     from paper_2208_13770_gb300 import autotune
     sc = _scenes(6, seed=11)
     best, trials = autotune.tune(sc, warm=20, steps=30)
     n_cf, n_bt, n_cp = len(autotune.CELL_FACTORS), len(autotune.BLOCK_THREADS), len(autotune.COMPACTION)
-    assert len(trials) == n_cf + (n_bt - 1) + (n_cp - 1)
+    n_ck = len(autotune.CHECK_LOADS)
+    assert len(trials) == n_cf + (n_bt - 1) + (n_cp - 1) + (n_ck - 1)
     assert all(t["ms_per_step"] > 0 for t in trials)
-    picked = [t for t in trials if (t["cell_factor"], t["block_threads"], t["compaction"]) ==
-              (best.cell_factor, best.block_threads, best.compaction)]
+    picked = [t for t in trials if (t["cell_factor"], t["block_threads"], t["compaction"],
+                                    t["check_loads"]) ==
+              (best.cell_factor, best.block_threads, best.compaction, best.check_loads)]
     assert picked and picked[0]["ms_per_step"] == min(t["ms_per_step"] for t in trials)
     # the chosen cell factor with two launch shapes: identical lists on the
     # same position snapshots (the broad phase is exact for any shape)
     off = np.concatenate([[0], np.cumsum([q.n for q in sc])]).astype(np.int64)
     pos0 = np.concatenate([q.pos for q in sc])
     ctxs = []
-    for threads, comp in ((1024, 0), (256, 1)):
+    for threads, comp, check in ((1024, 0, lvb.LVB_CHECK_REGS), (256, 1, lvb.LVB_CHECK_RING)):
         ctx = lvb.LVB(_dev(pos0), [q.lo for q in sc], [q.hi for q in sc], 1, 0.1, 1e-6, 0,
                       best.cell_factor, offsets=off)
         ctx.set_option(lvb.LVB_OPT_BLOCK_THREADS, threads)
         ctx.set_option(lvb.LVB_OPT_COMPACT, comp)
+        ctx.set_option(lvb.LVB_OPT_CHECK_LOADS, check)
         ctxs.append(ctx)
     for snap in _walks(sc, 20, 2e-4, seed=5):
         p = _dev(np.concatenate(snap))

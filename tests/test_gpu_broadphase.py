@@ -419,3 +419,67 @@ def test_near_cutoff_pairs_match_oracle(orc):
     assert len(oi) > 0
     assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
     ctx.close()
+
+
+@pytest.mark.parametrize("kind,value", [(1, 0.1), (2, 300.0)], ids=["diameter", "paper_rule"])
+def test_early_trigger_matches_oracle(orc, kind, value):
+    # the early trigger (beta 0.9): on a step with a violation, the
+    # particles past 0.9 of their skin are updated too; flags (the
+    # violations), reference states and pair sets equal the oracle's state
+    # machine with the same trigger at every step, and updates come on
+    # fewer steps than without it
+    lvb = _cuda()
+    from oracle.statemachine import OracleLVB
+    s = scenes.ballistic(n=3000, seed=61, vsigma=1.0)
+    H = _H(s.pos, s.cell_factor)
+    runs = {}
+    for beta in (900, 1000):
+        ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, kind, value, s.dt, lvb.LVB_TRIGGER_PARTIAL,
+                      s.cell_factor, vel=_dev(s.vel))
+        ctx.set_option(lvb.LVB_OPT_EARLY, beta)
+        sm = OracleLVB(s.pos, kind, value, s.dt, H, 0, vel4=s.vel,
+                       early_beta=np.float32(beta / 1000.0))
+        for k, (pos, vel) in enumerate(scenes.ballistic_trajectory(s, 80), start=1):
+            ctx.step(_dev(pos), _dev(vel))
+            f, upd = sm.step(pos, vel4=vel)
+            assert np.array_equal(ctx.flags(), f), k
+            if k % 8 == 0 or k > 70:
+                assert np.array_equal(ctx.ref(), sm.ref), k
+                pi, pj = ctx.pairs_ij()
+                assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj), k
+        st = ctx.stats()
+        assert st["updated_total"] == sm.updates and st["rebuild_steps"] == sm.rebuild_steps
+        runs[beta] = st
+        ctx.close()
+    assert runs[900]["rebuild_steps"] < runs[1000]["rebuild_steps"]
+    assert runs[900]["flagged_total"] < runs[900]["updated_total"]
+    with pytest.raises(lvb.LVBError):
+        ctx = lvb.LVB(_dev(s.pos), s.lo, s.hi, kind, value, s.dt, lvb.LVB_TRIGGER_GLOBAL,
+                      s.cell_factor, vel=_dev(s.vel))
+        try:
+            ctx.set_option(lvb.LVB_OPT_EARLY, 900)
+        finally:
+            ctx.close()
+
+
+def test_early_trigger_fused_dem_step(orc):
+    # the same inside the DEM driver's fused step (position half-step in the
+    # check, forces as the tail), one direct launch per step
+    lvb = _cuda()
+    from oracle.statemachine import OracleLVB
+    s = scenes.packed(n=6000, seed=63, vsigma=3.0)
+    dem = lvb.DEM(s)
+    dem.lvb.set_option(lvb.LVB_OPT_EARLY, 850)
+    H = dem.lvb.stats()["rnl_max"]
+    sm = OracleLVB(s.pos, 1, 0.1, s.dt, H, 0, ref4=dem.lvb.ref(), early_beta=np.float32(0.85))
+    for k in range(60):
+        dem.advance(1)
+        x = dem.state()[0]
+        f, _ = sm.step(x)
+        assert np.array_equal(dem.lvb.flags(), f), k
+    assert np.array_equal(dem.lvb.ref(), sm.ref)
+    pi, pj = dem.lvb.pairs_ij()
+    assert np.array_equal(pi, sm.pi) and np.array_equal(pj, sm.pj)
+    st = dem.lvb.stats()
+    assert st["updated_total"] == sm.updates and sm.updates > st["flagged_total"] > 0
+    dem.close()

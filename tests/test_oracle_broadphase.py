@@ -306,3 +306,37 @@ def test_near_cutoff_closed_form(orc):
     li, lj = orc.pairs_brute(ref, rad)
     assert (0, 1) in set(zip(li.tolist(), lj.tolist()))
     assert (6, 7) not in set(zip(li.tolist(), lj.tolist()))
+
+
+def test_early_trigger_hand_case(orc):
+    # three particles far apart, global skin 1, beta 0.75 (all values exact
+    # in binary32).  Step 1: particle 0 moves 0.8 (past 0.75 of its skin,
+    # within the skin), particle 1 moves 0.75 (exactly beta skin: not past
+    # it) -- no violation, so nothing is updated.  Step 2: particle 2 moves
+    # 1.5 (a violation): it and particle 0 are updated, particle 1 is not.
+    from oracle.statemachine import OracleLVB
+    pos = np.zeros((3, 4), np.float32)
+    pos[:, 1] = [0.0, 100.0, 200.0]
+    pos[:, 3] = 0.25
+    sm = OracleLVB(pos, orc.SKIN_GLOBAL, 1.0, 1.0, np.float32(50.0), early_beta=0.75)
+    p1 = pos.copy()
+    p1[0, 0], p1[1, 0] = 0.8, 0.75
+    f, upd = sm.step(p1)
+    assert not f.any() and not upd.any() and sm.rebuild_steps == 0
+    p2 = p1.copy()
+    p2[2, 0] = 1.5
+    f, upd = sm.step(p2)
+    assert list(f) == [False, False, True]
+    assert list(upd) == [True, False, True]
+    assert sm.ref[0, 0] == np.float32(0.8) and sm.ref[1, 0] == 0.0 and sm.ref[2, 0] == 1.5
+    # beta = 1: the plain partial trigger
+    sm1 = OracleLVB(pos, orc.SKIN_GLOBAL, 1.0, 1.0, np.float32(50.0), early_beta=1.0)
+    sm1.step(p1)
+    f, upd = sm1.step(p2)
+    assert list(upd) == [False, False, True]
+    # the set itself: strict ">" at the boundary, beta rounded to binary32
+    ref = np.zeros((2, 4), np.float32)
+    ref[:, 3] = 1.0
+    x = np.zeros((2, 4), np.float32)
+    x[0, 0], x[1, 0] = 0.75, np.nextafter(np.float32(0.75), np.float32(1))
+    assert list(orc.flags_beta(x, ref, 0.75)) == [False, True]

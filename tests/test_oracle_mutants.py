@@ -64,10 +64,13 @@ def test_unmutated_passes_pins(orc):
 
 
 # the state machine's triggers: the global buffer updating only the
-# violating particles, the no-buffer mode updating only on a violation
+# violating particles, the early trigger acting on steps without a
+# violation, the no-buffer mode updating only on a violation
 SM_SRC = os.path.join(os.path.dirname(oracle.__file__), "statemachine.py")
 SM_MUTANTS = {
     "global_updates_flagged_only": ("upd = np.full(self.n, bool(f.any()))", "upd = f.copy()"),
+    "early_without_violation": ("if self.early_beta < 1 and f.any():",
+                                "if self.early_beta < 1:"),
     "always_only_on_violation": ("            upd = np.ones(self.n, dtype=bool)",
                                  "            upd = np.full(self.n, bool(f.any()))"),
 }
@@ -86,5 +89,10 @@ def test_state_machine_trigger_mutant_is_caught(orc, monkeypatch, name):
     exec(compile(src.replace(before, after), "<state machine mutant %s>" % name, "exec"),
          mod.__dict__)
     monkeypatch.setattr(SM, "OracleLVB", mod.OracleLVB)
-    with pytest.raises(AssertionError):
-        B.test_trigger_modes_update_sets(orc)
+    caught = 0
+    for pin in (B.test_trigger_modes_update_sets, B.test_early_trigger_hand_case):
+        try:
+            pin(orc)
+        except AssertionError:
+            caught += 1
+    assert caught > 0, name
