@@ -65,7 +65,8 @@ WORKLOAD = ("batched settling boxes: 512 independent scenes, N log-uniform in [1
 BATCH_STEPS = 2000
 T0 = 1000                 # the timed window starts after step T0 of the batch's run
 T0_SETTLING = 10_000      # and after step T0_SETTLING of the 200k settling box's run
-SETTLING_STEPS = 2000     # timed steps of the 200k box (at most; --steps if fewer)
+SETTLING_STEPS = 2000     # timed steps of the 200k box (its global buffer rebuilds on
+                          # about one step in 500, so a long window)
 EARLY_PERMILLE = 900      # the early trigger's beta (x 1000) in the settling extra
 # 1 GiB: well above the 129 MB L2 (for the workloads that fit in it)
 L2_FLUSH_BYTES = 1 << 30
@@ -807,8 +808,7 @@ def run_native(args):
     cpu = None if args.no_cpu_baseline else _cpu_baseline(sc, res["rec"])
     extras = {}
     if not args.no_extras:
-        extras["settling_200k"] = _settling(lvb, torch, max(min(K, SETTLING_STEPS), 200), W,
-                                            hbm_peak, peak_kind)
+        extras["settling_200k"] = _settling(lvb, torch, SETTLING_STEPS, W, hbm_peak, peak_kind)
         extras["drum_2M"] = _drum(lvb, torch, hbm_peak, peak_kind)
         extras["ballistic_2k"] = _ballistic(lvb, torch)
         if not args.no_learned:

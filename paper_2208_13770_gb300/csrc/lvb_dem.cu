@@ -228,8 +228,10 @@ __device__ __forceinline__ float3 tangential(const DemDev &d, float ri, float4 v
     return make_float3(Fx, Fy, Fz);
 }
 
-// Narrow phase on the row of particle i + walls + velocity finish.
-__device__ __forceinline__ void forces_one(const DemDev &d, int i)
+// Narrow phase on the row of particle i + walls + velocity finish; the
+// friction form (fric) also the tangential law, torques and rotation.
+template <bool fric>
+__device__ __forceinline__ void forces_body(const DemDev &d, int i)
 {
     const float4 xi = d.pos[i];
     const float4 vi = d.vstar[i];
@@ -238,7 +240,6 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
     const float im_i = vi.w;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     float Tx = 0.f, Ty = 0.f, Tz = 0.f;
-    const bool fric = d.omega != nullptr;
     const float4 wi = fric ? d.wstar[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     // after a row store that failed even a tight re-layout (LVB_EOVERFLOW)
     // the row offsets no longer fit the store: the rows are not read
@@ -318,6 +319,19 @@ __device__ __forceinline__ void forces_one(const DemDev &d, int i)
         d.omega[i] = w;
         d.alpha[i] = aln;
     }
+}
+
+// The friction form is a separate function, so that its registers do not
+// weigh on the kernels that run without it.
+static __device__ __noinline__ void forces_one_fric(const DemDev &d, int i)
+{
+    forces_body<true>(d, i);
+}
+
+__device__ __forceinline__ void forces_one(const DemDev &d, int i)
+{
+    if (d.omega) forces_one_fric(d, i);
+    else forces_body<false>(d, i);
 }
 
 // Forces as a separate kernel, one thread per particle.  Eight blocks per

@@ -233,12 +233,19 @@ __device__ __forceinline__ void weights_copy_wait()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Live partners of row i (entries >= 0), counted by one lane.
+// Live partners of row i (entries >= 0), counted by one lane: eight
+// entries loaded at a time, so a short row costs one memory latency.
 __device__ __forceinline__ int row_live_lane(const DevState &s, int i)
 {
     const int off = s.row_off[i], len = min(s.row_len[i], s.row_cap[i]);
     int c = 0;
-    for (int e = 0; e < len; ++e) c += s.col[off + e] >= 0;
+    for (int e = 0; e < len; e += 8) {
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = e + u < len ? s.col[off + e + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c += v[u] >= 0;
+    }
     return c;
 }
 
