@@ -99,6 +99,8 @@ def _configure(L):
                                       ctypes.POINTER(DemParams)] + [ctypes.c_double] * 3 +
                                      [p] * 3 + [i64] + [p] * 3 + [p] * 7 + [p] * 7 + [i64])
         L.orc_dem_step64f.restype = i64
+        L.orc_clump_contacts.argtypes = [i64, p, p, p, p, p, p, p, p, p, i64]
+        L.orc_clump_contacts.restype = i64
         L.orc_improvement_pct.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_improvement_pct.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -421,6 +423,23 @@ def dem_step_friction(x4, v4, a4, w4, al4, dt, P, mu, kt_ratio, gt_ratio, hist=N
     out.update(ci=ci[:m].copy(), cj=cj[:m].copy(), xi=oxi[:m].copy(), f=of3[:m].copy(),
                scale=osc[:m].copy(), fmag=fmag, tmag=tmag)
     return out
+
+
+def clump_contacts(pos4, quat4, sub_off, sub4):
+    """Every sub-sphere contact between clumps i < j (brute force over all
+    pairs of clumps): (ci, ca, cj, cb, delta), in (i, a, j, b) order; ca, cb
+    index the sub-spheres within their clumps."""
+    pos4, quat4, sub4 = _f32x4(pos4), _f32x4(quat4), _f32x4(sub4)
+    off = np.ascontiguousarray(sub_off, np.int32)
+    n = len(pos4)
+    cap = max(16, 64 * n)
+    while True:
+        outs = [np.empty(cap, np.int32) for _ in range(4)] + [np.empty(cap, np.float32)]
+        m = lib().orc_clump_contacts(n, _ptr(pos4), _ptr(quat4), _ptr(off), _ptr(sub4),
+                                     *[_ptr(o) for o in outs], cap)
+        if m <= cap:
+            return tuple(o[:m].copy() for o in outs)
+        cap = int(m)
 
 
 def improvement_pct(t_without, t_case):

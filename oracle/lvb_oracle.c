@@ -955,6 +955,87 @@ ORC_API int64_t orc_dem_step64f(int64_t n, const double *x, const double *v, con
     return m;
 }
 
+/* ------------------------------------------------------------------ */
+/* Multi-sphere clumps (the clump narrow phase that follows a broad      */
+/* phase on bounding spheres, Sec. Background): sub-sphere a of clump i  */
+/* at x_i + R(q_i) b_a, q = (w, x, y, z) a unit quaternion,              */
+/*   R = [1-2(yy+zz)  2(xy-wz)  2(xz+wy)                                  */
+/*        2(xy+wz)  1-2(xx+zz)  2(yz-wx)                                  */
+/*        2(xz-wy)  2(yz+wx)  1-2(xx+yy)]                                 */
+/* in binary32 with every operation rounded in the order written, each   */
+/* component of R b as ((R_k0 b_x + R_k1 b_y) + R_k2 b_z), then added to  */
+/* x_i.  A contact: a of i and b of j, i < j, delta = (r_a + r_b) -       */
+/* sqrtf(|x_a - x_b|^2) > 0 (Eq. delta).  Brute force over every pair of  */
+/* clumps and every pair of their sub-spheres, in (i, a, j, b) order.     */
+/* Pinned by: a dumbbell turned by closed-form quaternions, and contacts  */
+/* that appear and vanish with the turn (tests).                          */
+/* ------------------------------------------------------------------ */
+static void clump_rotmat(const float *q, float R[9])
+{
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    float yy = y * y, zz = z * z, xx = x * x;
+    float xy = x * y, wz = w * z, xz = x * z, wy = w * y, yz = y * z, wx = w * x;
+    float t;
+    t = yy + zz; t = 2.0f * t; R[0] = 1.0f - t;
+    t = xy - wz; R[1] = 2.0f * t;
+    t = xz + wy; R[2] = 2.0f * t;
+    t = xy + wz; R[3] = 2.0f * t;
+    t = xx + zz; t = 2.0f * t; R[4] = 1.0f - t;
+    t = yz - wx; R[5] = 2.0f * t;
+    t = xz - wy; R[6] = 2.0f * t;
+    t = yz + wx; R[7] = 2.0f * t;
+    t = xx + yy; t = 2.0f * t; R[8] = 1.0f - t;
+}
+
+static void clump_world(const float *c4, const float R[9], const float *b4, float out4[4])
+{
+    for (int k = 0; k < 3; ++k) {
+        float p0 = R[3 * k + 0] * b4[0];
+        float p1 = R[3 * k + 1] * b4[1];
+        float p2 = R[3 * k + 2] * b4[2];
+        float s = p0 + p1;
+        s = s + p2;
+        out4[k] = c4[k] + s;
+    }
+    out4[3] = b4[3];
+}
+
+ORC_API int64_t orc_clump_contacts(int64_t n, const float *pos4, const float *quat4,
+                                   const int32_t *sub_off, const float *sub4, int32_t *ci,
+                                   int32_t *ca, int32_t *cj, int32_t *cb, float *delta,
+                                   int64_t cap)
+{
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float Ri[9];
+        clump_rotmat(quat4 + 4 * i, Ri);
+        for (int64_t j = i + 1; j < n; ++j) {
+            float Rj[9];
+            clump_rotmat(quat4 + 4 * j, Rj);
+            for (int32_t a = sub_off[i]; a < sub_off[i + 1]; ++a) {
+                float wa[4];
+                clump_world(pos4 + 4 * i, Ri, sub4 + 4 * (int64_t)a, wa);
+                for (int32_t b = sub_off[j]; b < sub_off[j + 1]; ++b) {
+                    float wb[4];
+                    clump_world(pos4 + 4 * j, Rj, sub4 + 4 * (int64_t)b, wb);
+                    float dl = overlap_f32(wa, wb);
+                    if (dl > 0.0f) {
+                        if (m < cap) {
+                            ci[m] = (int32_t)i;
+                            ca[m] = a - sub_off[i];
+                            cj[m] = (int32_t)j;
+                            cb[m] = b - sub_off[j];
+                            delta[m] = dl;
+                        }
+                        ++m;
+                    }
+                }
+            }
+        }
+    }
+    return m;
+}
+
 /* Improvement of Eq. impr (Sec. Results):                               */
 /*   Improvement = (T_without - T_case) / T_without * 100                */
 /* Pinned by: the values printed in Table tab:summary.                   */

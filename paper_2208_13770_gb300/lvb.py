@@ -112,6 +112,7 @@ _SIGS = {
     "lvb_log_read": ([_p, _p, _i64, _pi64], ctypes.c_int),
     "lvb_pairs_noalloc": ([_i64, _p, _p, ctypes.POINTER(lvb_box), _p, _p, _i64, _pi64, _p],
                           ctypes.c_int),
+    "lvb_clump_contacts": ([_p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i64, _pi64], ctypes.c_int),
     "dem_init": ([ctypes.POINTER(_p), _i64, _p, _p, ctypes.POINTER(dem_params), ctypes.c_float,
                   ctypes.POINTER(lvb_box), ctypes.POINTER(lvb_skin_policy), ctypes.c_int32,
                   ctypes.c_float, _p], ctypes.c_int),
@@ -490,6 +491,26 @@ class LVB:
         _check(lvb_get_contacts(self.ctx, _dptr(pos), _np_ptr(ci), _np_ptr(cj), _np_ptr(dl), cap,
                                 ctypes.byref(n)), "lvb_get_contacts")
         return ci[:n.value], cj[:n.value], dl[:n.value]
+
+    def clump_contacts(self, pos, quat, sub_off, sub):
+        """lvb_clump_contacts on device tensors (pos, quat: (n, 4); sub_off:
+        (n + 1,) int32; sub: (m, 4)): (ci, ca, cj, cb, delta) sorted by
+        (i, a, j, b)."""
+        n = ctypes.c_int64(0)
+        rc = _lib.lvb_clump_contacts(self.ctx, _dptr(pos), _dptr(quat), _dptr(sub_off),
+                                     _dptr(sub), None, None, None, None, None, 0,
+                                     ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_clump_contacts")
+        cap = max(n.value, 1)
+        outs = [np.empty(cap, np.int32) for _ in range(4)] + [np.empty(cap, np.float32)]
+        _check(_lib.lvb_clump_contacts(self.ctx, _dptr(pos), _dptr(quat), _dptr(sub_off),
+                                       _dptr(sub), *[_np_ptr(o) for o in outs], cap,
+                                       ctypes.byref(n)), "lvb_clump_contacts")
+        m = n.value
+        ci, ca, cj, cb, dl = (o[:m] for o in outs)
+        o = np.lexsort((cb, cj, ca, ci))
+        return ci[o], ca[o], cj[o], cb[o], dl[o]
 
     def flags(self):
         words = np.zeros((self.n + 31) // 32, dtype=np.uint32)

@@ -340,3 +340,42 @@ def test_early_trigger_hand_case(orc):
     x = np.zeros((2, 4), np.float32)
     x[0, 0], x[1, 0] = 0.75, np.nextafter(np.float32(0.75), np.float32(1))
     assert list(orc.flags_beta(x, ref, 0.75)) == [False, True]
+
+
+def _dumbbell_and_sphere(bx):
+    # clump 0: a dumbbell, sub-spheres at (-1, 0, 0) and (1, 0, 0), r 0.5;
+    # clump 1: one sphere of r 0.5 at its centre (bx, 0, 0)
+    pos = np.array([[0, 0, 0, 1.6], [bx, 0, 0, 0.6]], np.float32)
+    sub_off = np.array([0, 2, 3], np.int32)
+    sub = np.array([[-1, 0, 0, 0.5], [1, 0, 0, 0.5], [0, 0, 0, 0.5]], np.float32)
+    return pos, sub_off, sub
+
+
+def test_clump_oracle_closed_forms(orc):
+    # identity: the dumbbell's +x sphere (sub 1) at (1, 0, 0) touches the
+    # sphere at (1.75, 0, 0): delta = 1 - 0.75 = 0.25 exactly
+    pos, off, sub = _dumbbell_and_sphere(1.75)
+    ident = np.array([[1, 0, 0, 0], [1, 0, 0, 0]], np.float32)
+    ci, ca, cj, cb, dl = orc.clump_contacts(pos, ident, off, sub)
+    assert list(zip(ci, ca, cj, cb)) == [(0, 1, 1, 0)] and dl[0] == np.float32(0.25)
+    # half turns (exact quaternions): about z (w, x, y, z) = (0, 0, 0, 1) and
+    # about y (0, 0, 1, 0) swap the dumbbell's ends, so sub 0 touches; about
+    # x (0, 1, 0, 0) leaves the x axis where it is
+    for q, a in (((0, 0, 0, 1), 0), ((0, 0, 1, 0), 0), ((0, 1, 0, 0), 1)):
+        quat = np.array([q, [1, 0, 0, 0]], np.float32)
+        ci, ca, cj, cb, dl = orc.clump_contacts(pos, quat, off, sub)
+        assert list(zip(ci, ca, cj, cb)) == [(0, a, 1, 0)] and dl[0] == np.float32(0.25), q
+    # moved away: no contact (distance 1 = r_a + r_b exactly: delta 0)
+    pos, off, sub = _dumbbell_and_sphere(2.0)
+    assert len(orc.clump_contacts(pos, ident, off, sub)[0]) == 0
+    # the turned second clump's own offset: a sphere at b = (0, 0.5, 0) of
+    # clump 1 turned half about x sits at (bx, -0.5, 0)
+    pos = np.array([[0, 0, 0, 1.6], [1.5, 0.2, 0, 1.1]], np.float32)
+    off = np.array([0, 2, 3], np.int32)
+    sub = np.array([[-1, 0, 0, 0.5], [1, 0, 0, 0.5], [0, 0.5, 0, 0.5]], np.float32)
+    q = np.array([[1, 0, 0, 0], [0, 1, 0, 0]], np.float32)
+    ci, ca, cj, cb, dl = orc.clump_contacts(pos, q, off, sub)
+    # (1.5, -0.3, 0) against (1, 0, 0): |d|^2 = 0.25 + 0.09 = 0.34
+    d2 = np.float32(np.float32(0.5) * np.float32(0.5)) + np.float32(np.float32(-0.3) ** 2)
+    assert list(zip(ci, ca, cj, cb)) == [(0, 1, 1, 0)]
+    assert dl[0] == np.float32(1.0) - np.sqrt(np.float32(d2))
