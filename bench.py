@@ -67,7 +67,7 @@ T0 = 1000                 # the timed window starts after step T0 of the batch's
 T0_SETTLING = 10_000      # and after step T0_SETTLING of the 200k settling box's run
 SETTLING_STEPS = 2000     # timed steps of the 200k box (its global buffer rebuilds on
                           # about one step in 500, so a long window)
-EARLY_PERMILLE = 900      # the early trigger's beta (x 1000) in the settling extra
+EARLY_PERMILLE = 700      # the early trigger's beta (x 1000) in the settling extra
 # 1 GiB: well above the 129 MB L2 (for the workloads that fit in it)
 L2_FLUSH_BYTES = 1 << 30
 M_E2E = 16                # steps of the window the e2e and CPU legs replay

@@ -427,7 +427,7 @@ def dem_step_friction(x4, v4, a4, w4, al4, dt, P, mu, kt_ratio, gt_ratio, hist=N
 
 def clump_contacts(pos4, quat4, sub_off, sub4):
     """Every sub-sphere contact between clumps i < j (brute force over all
-    pairs of clumps): (ci, ca, cj, cb, delta), in (i, a, j, b) order; ca, cb
+    pairs of clumps): (ci, ca, cj, cb, delta), in (i, j, a, b) order; ca, cb
     index the sub-spheres within their clumps."""
     pos4, quat4, sub4 = _f32x4(pos4), _f32x4(quat4), _f32x4(sub4)
     off = np.ascontiguousarray(sub_off, np.int32)

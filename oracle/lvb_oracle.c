@@ -966,7 +966,7 @@ ORC_API int64_t orc_dem_step64f(int64_t n, const double *x, const double *v, con
 /* component of R b as ((R_k0 b_x + R_k1 b_y) + R_k2 b_z), then added to  */
 /* x_i.  A contact: a of i and b of j, i < j, delta = (r_a + r_b) -       */
 /* sqrtf(|x_a - x_b|^2) > 0 (Eq. delta).  Brute force over every pair of  */
-/* clumps and every pair of their sub-spheres, in (i, a, j, b) order.     */
+/* clumps and every pair of their sub-spheres, in (i, j, a, b) order.     */
 /* Pinned by: a dumbbell turned by closed-form quaternions, and contacts  */
 /* that appear and vanish with the turn (tests).                          */
 /* ------------------------------------------------------------------ */

@@ -495,7 +495,7 @@ class LVB:
     def clump_contacts(self, pos, quat, sub_off, sub):
         """lvb_clump_contacts on device tensors (pos, quat: (n, 4); sub_off:
         (n + 1,) int32; sub: (m, 4)): (ci, ca, cj, cb, delta) sorted by
-        (i, a, j, b)."""
+        (i, j, a, b)."""
         n = ctypes.c_int64(0)
         rc = _lib.lvb_clump_contacts(self.ctx, _dptr(pos), _dptr(quat), _dptr(sub_off),
                                      _dptr(sub), None, None, None, None, None, 0,
@@ -509,7 +509,7 @@ class LVB:
                                        ctypes.byref(n)), "lvb_clump_contacts")
         m = n.value
         ci, ca, cj, cb, dl = (o[:m] for o in outs)
-        o = np.lexsort((cb, cj, ca, ci))
+        o = np.lexsort((cb, ca, cj, ci))
         return ci[o], ca[o], cj[o], cb[o], dl[o]
 
     def flags(self):
