@@ -724,6 +724,98 @@ def _learned(lvb, torch):
     }
 
 
+def _friction(lvb, torch):
+    """Friction with contact history on the 1,000,000-sphere drum (mu 0.5,
+    k_t = 2/7 k_n, gamma_t = 0.5 gamma_n): full DEM steps in graphs with and
+    without friction from the same state, and the broad phase alone phase by
+    phase with the history on (flagged rows edited in place) and off."""
+    from paper_2208_13770_gb300 import scenes
+    sc = scenes.drum(n=LEARN_N, length=0.1)
+    out = {"workload": "drum R 0.3 m x 0.1 m, %d lognormal spheres, 10 rpm, dt 1e-6 s; "
+                       "friction mu 0.5 between particles (walls frictionless)" % sc.n}
+    stream = torch.cuda.current_stream()
+    for name, mu in (("frictionless", 0.0), ("friction", 0.5)):
+        s = sc.copy()
+        s.mu = mu
+        dem = lvb.DEM(s)
+        dem.advance(500)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dem.advance(1000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _check_rc(lvb, dem.sync())
+        ms = e0.elapsed_time(e1)
+        s0 = dem.lvb.stats()
+        ph = _phases(lvb, torch, dem, 300)
+        _check_rc(lvb, dem.sync())
+        s1 = dem.lvb.stats()
+        dem.close()
+        out[name] = {"full_step_value": sc.n * 1000 / (ms * 1e-3),
+                     "full_step_us": 1e3 * ms / 1000,
+                     "unit": "particle-steps/s (full DEM step, graphs)",
+                     "broad_us_per_step": 1e3 * ph[1] / 300,
+                     "forces_us_per_step": 1e3 * ph[2] / 300,
+                     "flagged_per_step": _diff(s0, s1, "flagged_total") / 300}
+    out["friction_cost"] = out["frictionless"]["full_step_value"] / out["friction"]["full_step_value"]
+    return out
+
+
+def _clumps(lvb, torch, n=400_000, seed=2208_13770 + 21):
+    """The clumps' narrow phase (lvb_clump_contacts) on the bounding-sphere
+    list: n rigid clumps of one to four spheres, random orientations, their
+    bounding spheres on a jittered lattice at 1.6 median bounding radii (so
+    neighbours' bounds overlap); the narrow phase's time per call between
+    CUDA events (the call includes its input checks and the copies of its
+    results)."""
+    rng = np.random.default_rng(seed)
+    k = rng.integers(1, 5, size=n)
+    off = np.concatenate([[0], np.cumsum(k)]).astype(np.int32)
+    m = int(off[-1])
+    sub = np.zeros((m, 4), np.float32)
+    sub[:, :3] = rng.normal(0, 0.5e-3, size=(m, 3))
+    sub[:, 3] = rng.uniform(0.3e-3, 0.8e-3, size=m)
+    ext = np.linalg.norm(sub[:, :3].astype(np.float64), axis=1) + sub[:, 3]
+    R = np.maximum.reduceat(ext, off[:-1])
+    R = (R / (1.0 - 2.0 ** -12) * (1.0 + 1e-6)).astype(np.float32)
+    spacing = 1.6 * float(np.median(R))   # neighbours' bounding spheres overlap
+    side = int(np.ceil(n ** (1 / 3)))
+    idx = rng.permutation(side ** 3)[:n]
+    c = np.stack([idx % side, (idx // side) % side, idx // side ** 2], 1) * spacing
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = c + rng.uniform(-0.05, 0.05, size=(n, 3)) * spacing
+    pos[:, 3] = R
+    q = rng.normal(size=(n, 4))
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    dev = lambda a, t=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", t)
+    pad = 2.0 * float(R.max())
+    ctx = lvb.LVB(dev(pos), (-pad,) * 3, (side * spacing + pad,) * 3,
+                  lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, 1e-5, lvb.LVB_TRIGGER_PARTIAL, 1.25)
+    d_pos, d_q, d_off, d_sub = dev(pos), dev(q), dev(off, torch.int32), dev(sub)
+    stream = torch.cuda.current_stream()
+    calls, ms, contacts = 10, 0.0, 0
+    for _ in range(2):
+        ctx.clump_contacts(d_pos, d_q, d_off, d_sub)
+    for _ in range(calls):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ci = ctx.clump_contacts(d_pos, d_q, d_off, d_sub)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        contacts = len(ci)
+    st = ctx.stats()
+    ctx.close()
+    return {"workload": "%d clumps of 1-4 spheres (%d sub-spheres), bounding spheres on a "
+                        "jittered lattice, random orientations" % (n, m),
+            "n_clumps": n, "n_spheres": m, "list_pairs": st["pairs"],
+            "contacts": contacts, "ms_per_call": ms / calls,
+            "clumps_per_s": n / (ms / calls * 1e-3), "unit": "clumps/s (narrow phase)"}
+
+
 def _ballistic(lvb, torch):
     """The 2,000-sphere ballistic case (r = 1 mm, phi 0.30, specular walls,
     dt 1e-5 s, 1,000 steps): local skin 0.1 d against the global skin
@@ -811,6 +903,8 @@ def run_native(args):
         extras["settling_200k"] = _settling(lvb, torch, SETTLING_STEPS, W, hbm_peak, peak_kind)
         extras["drum_2M"] = _drum(lvb, torch, hbm_peak, peak_kind)
         extras["ballistic_2k"] = _ballistic(lvb, torch)
+        extras["friction_1M"] = _friction(lvb, torch)
+        extras["clumps_400k"] = _clumps(lvb, torch)
         if not args.no_learned:
             extras["learned"] = _learned(lvb, torch)
     line = {
