@@ -768,8 +768,8 @@ def _clumps(lvb, torch, n=400_000, seed=2208_13770 + 21):
     list: n rigid clumps of one to four spheres, random orientations, their
     bounding spheres on a jittered lattice at 1.6 median bounding radii (so
     neighbours' bounds overlap); the narrow phase's time per call between
-    CUDA events (the call includes its input checks and the copies of its
-    results)."""
+    CUDA events, outputs in device memory (the call includes its input
+    checks and two synchronisations)."""
     rng = np.random.default_rng(seed)
     k = rng.integers(1, 5, size=n)
     off = np.concatenate([[0], np.cumsum(k)]).astype(np.int32)
@@ -795,18 +795,22 @@ def _clumps(lvb, torch, n=400_000, seed=2208_13770 + 21):
                   lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, 1e-5, lvb.LVB_TRIGGER_PARTIAL, 1.25)
     d_pos, d_q, d_off, d_sub = dev(pos), dev(q), dev(off, torch.int32), dev(sub)
     stream = torch.cuda.current_stream()
-    calls, ms, contacts = 10, 0.0, 0
-    for _ in range(2):
-        ctx.clump_contacts(d_pos, d_q, d_off, d_sub)
+    contacts = len(ctx.clump_contacts(d_pos, d_q, d_off, d_sub)[0])
+    cap = contacts + 1024
+    outs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(4)] + \
+        [torch.empty(cap, dtype=torch.float32, device="cuda")]
+    calls, ms = 20, 0.0
+    for _ in range(3):
+        ctx.clump_contacts_into(d_pos, d_q, d_off, d_sub, *outs)
     for _ in range(calls):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ci = ctx.clump_contacts(d_pos, d_q, d_off, d_sub)[0]
+        got = ctx.clump_contacts_into(d_pos, d_q, d_off, d_sub, *outs)
         e1.record(stream)
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
-        contacts = len(ci)
+        assert got == contacts
     st = ctx.stats()
     ctx.close()
     return {"workload": "%d clumps of 1-4 spheres (%d sub-spheres), bounding spheres on a "

@@ -56,11 +56,13 @@ extern "C" {
  *             delta[k]; in no particular order.
  *   n_contacts : out, the number of contacts (LVB_ECAPACITY if over cap,
  *             the first cap written).
- * Allocates temporary device memory.  Synchronises.  Errors: EINVAL (NULL
- * or misaligned pointers, a sub-sphere outside its bound's margin, a
- * quaternion off unit length, offsets not increasing or more than 64
- * sub-spheres), ECAPACITY, ENOMEM, EDEVICE, and the context's device
- * errors.
+ * Outputs in device memory are written in place (no allocation); if any
+ * output is in host memory, all five go through temporary device arrays
+ * of cap entries.  Synchronises.  Errors: EINVAL (NULL or misaligned
+ * pointers, a sub-sphere outside its bound's margin, a quaternion off unit
+ * length, a negative first offset, offsets not increasing or more than 64
+ * sub-spheres; nothing written), ECAPACITY, ENOMEM, EDEVICE, and the
+ * context's device errors.
  */
 int lvb_clump_contacts(lvb_ctx *ctx, const float *pos_r, const float *quat,
                        const int32_t *sub_off, const float *sub, int32_t *ci, int32_t *ca,

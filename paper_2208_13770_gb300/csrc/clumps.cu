@@ -59,7 +59,7 @@ k_clump_check(int n, const float4 *__restrict__ pos, const float4 *__restrict__ 
                           (double)q.w * q.w;
         if (!(fabs(qq - 1.0) <= 1.0 / 524288.0)) b |= CL_BAD_QUAT;
         const int a0 = off[i], a1 = off[i + 1];
-        if (!(a1 > a0) || a1 - a0 > kMaxSub) {
+        if (a0 < 0 || !(a1 > a0) || a1 - a0 > kMaxSub) {
             b |= CL_BAD_OFFSETS;
             continue;
         }
@@ -127,6 +127,16 @@ int from_cuda(cudaError_t e)
     return LVB_EDEVICE;
 }
 
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // an unknown pointer: host memory
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" int lvb_clump_contacts(lvb_ctx *ctx, const float *pos_r, const float *quat,
@@ -145,29 +155,44 @@ extern "C" int lvb_clump_contacts(lvb_ctx *ctx, const float *pos_r, const float 
     const RowsView rv = rows_view(ctx);
     const cudaStream_t st = step_stream(ctx);
     const int n = rv.n;
-    const long long cp = std::max<long long>(cap, 1);
     unsigned *bad = nullptr;
     unsigned long long *cnt = nullptr;
+    small_scratch(ctx, &bad, &cnt);
+    // outputs in device memory are written by the kernel in place; any
+    // output in host memory sends all five through device temporaries
+    bool direct = true;
+    if (cap > 0) {
+        const void *outs[5] = {ci, ca, cj, cb, delta};
+        for (const void *p : outs) direct = direct && on_device(p);
+    }
+    const long long cp = std::max<long long>(cap, 1);
     int *di = nullptr, *da = nullptr, *dj = nullptr, *db = nullptr;
     float *dd = nullptr;
     auto done = [&](int code) {
         cudaStreamSynchronize(st);
-        cudaFree(bad);
-        cudaFree(cnt);
-        cudaFree(di);
-        cudaFree(da);
-        cudaFree(dj);
-        cudaFree(db);
-        cudaFree(dd);
+        if (!direct) {
+            cudaFree(di);
+            cudaFree(da);
+            cudaFree(dj);
+            cudaFree(db);
+            cudaFree(dd);
+        }
         return code;
     };
-    cudaError_t e = cudaMalloc((void **)&bad, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&cnt, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&di, sizeof(int) * cp);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&da, sizeof(int) * cp);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&dj, sizeof(int) * cp);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&db, sizeof(int) * cp);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&dd, sizeof(float) * cp);
+    cudaError_t e = cudaSuccess;
+    if (direct) {
+        di = ci;
+        da = ca;
+        dj = cj;
+        db = cb;
+        dd = delta;
+    } else {
+        e = cudaMalloc((void **)&di, sizeof(int) * cp);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&da, sizeof(int) * cp);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&dj, sizeof(int) * cp);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&db, sizeof(int) * cp);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&dd, sizeof(float) * cp);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return done(from_cuda(e));
@@ -190,14 +215,16 @@ extern "C" int lvb_clump_contacts(lvb_ctx *ctx, const float *pos_r, const float 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return done(from_cuda(e));
     const long long m = std::min<long long>((long long)total, cap);
-    int32_t *outs[4] = {ci, ca, cj, cb};
-    int *srcs[4] = {di, da, dj, db};
-    for (int k = 0; k < 4 && e == cudaSuccess && m > 0; ++k)
-        e = cudaMemcpyAsync(outs[k], srcs[k], sizeof(int) * m, cudaMemcpyDefault, st);
-    if (e == cudaSuccess && m > 0)
-        e = cudaMemcpyAsync(delta, dd, sizeof(float) * m, cudaMemcpyDefault, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return done(from_cuda(e));
+    if (!direct && m > 0) {
+        int32_t *outs[4] = {ci, ca, cj, cb};
+        int *srcs[4] = {di, da, dj, db};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(outs[k], srcs[k], sizeof(int) * m, cudaMemcpyDefault, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(delta, dd, sizeof(float) * m, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return done(from_cuda(e));
+    }
     *n_contacts = (int64_t)total;
     return done((long long)total > cap ? LVB_ECAPACITY : LVB_OK);
 }

@@ -1547,6 +1547,12 @@ cudaStream_t step_stream(lvb_ctx *c)
     return c->stream;
 }
 
+void small_scratch(lvb_ctx *c, unsigned **u32, unsigned long long **u64)
+{
+    *u32 = c->scratch;
+    *u64 = c->sum64;
+}
+
 int grow_stores_if_asked(lvb_ctx *c)
 {
     return grow_if_asked(c);

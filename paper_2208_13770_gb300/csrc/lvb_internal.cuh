@@ -328,6 +328,9 @@ RowsView rows_view(lvb_ctx *c);
 DevState step_state(lvb_ctx *c);
 void step_shape(lvb_ctx *c, int *blocks, int *threads);
 cudaStream_t step_stream(lvb_ctx *c);
+// The context's small device scratch (at least 8 words and one 64-bit
+// word), used on its stream by calls that synchronise before returning.
+void small_scratch(lvb_ctx *c, unsigned **u32, unsigned long long **u64);
 
 // Changes whenever the step kernel's arguments change (options, logging,
 // store growth), so that a caller holding a graph of steps knows to rebuild

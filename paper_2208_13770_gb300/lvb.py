@@ -512,6 +512,18 @@ class LVB:
         o = np.lexsort((cb, ca, cj, ci))
         return ci[o], ca[o], cj[o], cb[o], dl[o]
 
+    def clump_contacts_into(self, pos, quat, sub_off, sub, ci, ca, cj, cb, delta):
+        """lvb_clump_contacts into device tensors of equal length (the
+        capacity); returns the contact count (over the capacity: only the
+        first capacity written)."""
+        n = ctypes.c_int64(0)
+        rc = _lib.lvb_clump_contacts(self.ctx, _dptr(pos), _dptr(quat), _dptr(sub_off),
+                                     _dptr(sub), _dptr(ci), _dptr(ca), _dptr(cj), _dptr(cb),
+                                     _dptr(delta), int(ci.numel()), ctypes.byref(n))
+        if rc not in (LVB_OK, LVB_ECAPACITY):
+            _check(rc, "lvb_clump_contacts")
+        return n.value
+
     def flags(self):
         words = np.zeros((self.n + 31) // 32, dtype=np.uint32)
         nf = ctypes.c_int64(0)

@@ -98,6 +98,25 @@ def test_clump_contacts_match_oracle(orc):
             total += len(want[0])
     assert total > 200
     assert ctx.stats()["flagged_total"] > 0
+    # the same contacts written in place to device outputs, and a short
+    # capacity (the count, the first cap written)
+    d_pos, d_q = _dev(pos), _dev(q)
+    want = orc.clump_contacts(pos, q, off, sub)
+    m = len(want[0])
+    for cap in (m + 7, m // 2):
+        outs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(4)] + \
+            [torch.empty(cap, dtype=torch.float32, device="cuda")]
+        assert ctx.clump_contacts_into(d_pos, d_q, d_off, d_sub, *outs) == m
+        got = [o[:min(cap, m)].cpu().numpy() for o in outs]
+        o = np.lexsort((got[3], got[1], got[2], got[0]))
+        key = lambda c: (c[0].astype(np.int64) * 64 + c[1]) * (1 << 30) + c[2].astype(np.int64) * 64 + c[3]
+        kw = key(want)
+        kg = key([g[o] for g in got])
+        if cap >= m:
+            assert np.array_equal(kg, kw)
+            assert np.array_equal(got[4][o], want[4])
+        else:
+            assert np.all(np.isin(kg, kw))
     # input checks: a bound without the margin, a quaternion off unit length
     import ctypes
     n = ctypes.c_int64(0)
@@ -106,6 +125,12 @@ def test_clump_contacts_match_oracle(orc):
     rc = lvb._lib.lvb_clump_contacts(ctx.ctx, _dev(bad).data_ptr(), _dev(q).data_ptr(),
                                      d_off.data_ptr(), d_sub.data_ptr(), None, None, None, None,
                                      None, 0, ctypes.byref(n))
+    assert rc == lvb.LVB_EINVAL
+    bad_off = off.copy()
+    bad_off[0] = -1
+    rc = lvb._lib.lvb_clump_contacts(ctx.ctx, _dev(pos).data_ptr(), _dev(q).data_ptr(),
+                                     _dev(bad_off, np.int32).data_ptr(), d_sub.data_ptr(), None,
+                                     None, None, None, None, 0, ctypes.byref(n))
     assert rc == lvb.LVB_EINVAL
     qb = q.copy()
     qb[5] *= np.float32(1.01)
