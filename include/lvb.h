@@ -376,7 +376,9 @@ int lvb_step_host(lvb_ctx *ctx, const float *pos_r, const float *vel, const floa
 /* Phases of the step kernel: 0 check (with the flagged particles'
  * updates), 1 rebuild passes, 2 re-layout, 3 tail (the DEM driver's
  * forces); separate kernels: 4 DEM integrate, 5 DEM forces, 6 full-build
- * rows (init, store growth). */
+ * rows (init, store growth); inside the partial rebuild: 7 from the first
+ * work item's start to the last one's end (patches and moves), 8 the
+ * longest single work item. */
 
 /* lvb_trace -- per-kernel device time summed over the steps traced so far
  * (ns) and the number of steps each kernel ran in; LVB_TRACE_SLOTS entries

@@ -34,6 +34,7 @@ enum : unsigned { DERR_NAN = 1u, DERR_CELL = 2u, DERR_STORE = 4u, DERR_SYNC = 8u
 // slots of the trace: phases of the step kernel, then separate kernels
 enum TraceSlot {
     TR_CHECK = 0, TR_REBUILD, TR_RELAYOUT, TR_TAIL, TR_INTEGRATE, TR_FORCES, TR_ROWS,
+    TR_ITEMS, TR_ITEM_MAX,
     kTraceSlots = 16
 };
 

@@ -967,6 +967,9 @@ static __shared__ int s_bar_par;                   // parity of the step
 // alg_*), gathered by its warps with shared-memory atomics and added to the
 // context's counters by thread 0 once per step
 static __shared__ unsigned long long s_work[3];
+// the block's rebuild work items when traced: first start, last end,
+// longest item (ItemTrace)
+static __shared__ unsigned long long s_items[3];
 
 // Called by every thread at the start of the step kernel, before any barrier.
 __device__ __forceinline__ void grid_barrier_begin(const DevState &s, int par)
@@ -975,6 +978,8 @@ __device__ __forceinline__ void grid_barrier_begin(const DevState &s, int par)
         s_bar_need = 0;
         s_bar_par = par;
         s_work[0] = s_work[1] = s_work[2] = 0ULL;
+        s_items[0] = ~0ULL;
+        s_items[1] = s_items[2] = 0ULL;
         if (blockIdx.x == 0) s.cnt->bar_cnt[par ^ 1] = 0;
     }
 }
@@ -1620,6 +1625,46 @@ static __device__ __noinline__ void update_pass(const DevState &s, const lvb_mlp
         update_group(s, W, (int)k0, min(c, nF - (int)k0), pos, vel, acc, step);
 }
 
+// Trace of the rebuild's work items (LVB_OPT_TRACE; lane 0 of each warp):
+// the first start, the last end and the longest item of the warp's items,
+// gathered per block in s_items and added to the context's trace slots
+// TR_ITEMS / TR_ITEM_MAX by items_flush before the step's last barrier.
+struct ItemTrace {
+    bool on;
+    unsigned long long ta = 0, first = ~0ULL, last = 0, longest = 0;
+    __device__ __forceinline__ void start()
+    {
+        if (on) ta = global_ns();
+    }
+    __device__ __forceinline__ void stop()
+    {
+        if (!on) return;
+        const unsigned long long tb = global_ns();
+        first = min(first, ta);
+        last = max(last, tb);
+        longest = max(longest, tb - ta);
+    }
+    __device__ __forceinline__ void to_block() const
+    {
+        if (!on || last == 0) return;
+        atomicMin(&s_items[0], first);
+        atomicMax(&s_items[1], last);
+        atomicMax(&s_items[2], longest);
+    }
+};
+
+__device__ __forceinline__ void items_flush(const DevState &s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && s_items[1] != 0) {
+        DevCounters *c = s.cnt;
+        atomicMin(&c->tr_start[TR_ITEMS], s_items[0]);
+        atomicMax(&c->tr_end[TR_ITEMS], s_items[1]);
+        atomicMin(&c->tr_start[TR_ITEM_MAX], 0ULL);
+        atomicMax(&c->tr_end[TR_ITEM_MAX], s_items[2]);
+    }
+}
+
 // The rebuild of a partial step (nF flagged).  Up to s.direct_max
 // flagged particles: moves and patches in one phase, on different warps
 // (work items 0..nF-1 patch rows, nF..2nF-1 move cell slots; the patches
@@ -1635,27 +1680,38 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool direct = nF <= s.direct_max;
     unsigned work[3] = {0u, 0u, 0u};
+    ItemTrace it{s.trace && (threadIdx.x & 31) == 0};
     if (!direct) {
-        for (int k = w0; k < nF; k += nw) move_warp(s, s.fid[k], s.fref[k]);
+        for (int k = w0; k < nF; k += nw) {
+            it.start();
+            move_warp(s, s.fid[k], s.fref[k]);
+            it.stop();
+        }
         if (!grid_barrier(s)) return false;
         for (int k = w0; k < nF; k += nw) {
+            it.start();
             if (s.hist) patch_warp_hist(s, k, nF, false, par, ovf, work);
             else patch_warp(s, k, nF, false, par, ovf, work);
+            it.stop();
         }
     } else {
         for (int w = w0; w < 2 * nF; w += nw) {
+            it.start();
             if (w < nF) {
                 if (s.hist) patch_warp_hist(s, w, nF, true, par, ovf, work);
                 else patch_warp(s, w, nF, true, par, ovf, work);
             } else {
                 move_warp(s, s.fid[w - nF], s.fref[w - nF]);
             }
+            it.stop();
         }
     }
-    if ((threadIdx.x & 31) == 0)
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q)
             if (work[q]) atomicAdd(&s_work[q], (unsigned long long)work[q]);
+        it.to_block();
+    }
     return true;
 }
 
@@ -1768,6 +1824,7 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
                 if (!grid_barrier(s)) return;
             }
             if (!partial_pass(s, nF, par, ovf)) return;
+            if (s.trace) items_flush(s);
             changed = true;
         }
     } else if (upd > 0 && !store_failed(s)) {
@@ -1785,6 +1842,12 @@ k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, 
         if (s.trace && lead) {
             t2 = global_ns();
             trace_add(c, TR_REBUILD, t1, t2);
+            for (int k = TR_ITEMS; k <= TR_ITEM_MAX; ++k) {
+                const unsigned long long a = c->tr_start[k], b = c->tr_end[k];
+                if (b != 0 && b >= a) trace_add(c, k, a, b);
+                c->tr_start[k] = ~0ULL;
+                c->tr_end[k] = 0;
+            }
         }
         if ((*(volatile int *)ovf || *(volatile int *)&c->force_relayout) && !store_failed(s)) {
             if (!relayout_pass(s)) return;

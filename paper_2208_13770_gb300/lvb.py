@@ -225,7 +225,8 @@ LVB_OPT_CHECK_LOADS = 15
 LVB_OPT_EARLY = 16
 LVB_CHECK_RING, LVB_CHECK_REGS = 0, 1
 LVB_COMPACT_WARP, LVB_COMPACT_BLOCK = 0, 1
-TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows"]
+TRACE_SLOTS = ["check", "rebuild", "relayout", "tail_forces", "integrate", "forces", "rows",
+               "rebuild_items", "rebuild_item_max"]
 
 
 def lvb_trace(ctx, sum_ns, count):
