@@ -490,7 +490,7 @@ void free_all(lvb_ctx *c)
     DevState &s = c->s;
     if (s.ubits && s.ubits != s.bits) cudaFree(s.ubits);
     void *ptrs[] = {s.ref, s.rad, s.cell_of, s.slot_of, s.fref, s.oref, s.bits, s.fid, s.sc_cnt,
-                    s.sfid, s.sfref, s.row_off,
+                    s.sfid, s.sfref, s.fsc, s.row_off,
                     s.row_len, s.row_cap, s.col, s.cell_cnt, s.cell_id,
                     s.cell_ref, s.cnt, s.blk, c->ex_cnt, c->ex_off, c->ex_i, c->ex_j, c->ex_d,
                     c->scratch, c->sum64, c->sg_d, c->scene_of_d, s.born, s.cell_live,
@@ -918,6 +918,7 @@ static int init_impl(lvb_ctx **out, int nscenes, const int64_t *offsets, int64_t
         if (e == cudaSuccess) e = dalloc(&s.sc_cnt, 2LL * nscenes);
         if (e == cudaSuccess) e = dalloc(&s.sfid, n);
         if (e == cudaSuccess) e = dalloc(&s.sfref, n);
+        if (e == cudaSuccess) e = dalloc(&s.fsc, n);
         if (e == cudaSuccess) e = cudaMemsetAsync(s.sc_cnt, 0, sizeof(int) * 2 * nscenes, st);
     }
     if (e == cudaSuccess) e = dalloc(&s.row_off, n);

@@ -65,6 +65,8 @@ struct DevState {
     int *sc_cnt;      // 2 x nscenes counters (by step parity)
     int *sfid;
     float4 *sfref;
+    int *fsc;         // scene of each flagged particle, same order as fid
+                      // (saves the rebuild a dependent load; null with one scene)
     // rows: row i is col[row_off[i], row_off[i] + row_cap[i]); entries below
     // row_len[i] are partners or -1 (a removed pair), entries at or above
     // it are -1; row_len[i] > row_cap[i] means the row overflowed
@@ -129,6 +131,12 @@ enum Gate { GATE_OVERFLOW = 1, GATE_ANY_FLAG = 2, GATE_ALWAYS = 3 };
 __device__ __forceinline__ const SceneGeom &geom_of(const DevState &s, int i)
 {
     return s.sg[s.nscenes == 1 ? 0 : s.scene_of[i]];
+}
+
+// geometry and scene of flagged list entry k (particle fid[k])
+__device__ __forceinline__ int flagged_scene(const DevState &s, int k)
+{
+    return s.nscenes == 1 ? 0 : s.fsc[k];
 }
 
 __device__ __forceinline__ bool store_failed(const DevState &s)
@@ -307,6 +315,7 @@ __device__ __forceinline__ void update_group(const DevState &s, const lvb_mlp_we
     if (s.pold) s.pold[i] = s.oref[k];
     if (s.sc_cnt) {
         const int sc = s.scene_of[i];
+        s.fsc[k] = sc;
         const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
         s.sfid[slot] = i;
         s.sfref[slot] = qn;
@@ -345,6 +354,7 @@ static __device__ __noinline__ void update_lanes(const DevState &s, const int *i
     if (s.pold) s.pold[i] = qo;
     if (s.sc_cnt) {
         const int sc = s.scene_of[i];
+        s.fsc[k] = sc;
         const int slot = g.first + atomicAdd(&s.sc_cnt[(step & 1) * s.nscenes + sc], 1);
         s.sfid[slot] = i;
         s.sfref[slot] = qn;
@@ -357,11 +367,11 @@ static __device__ __noinline__ void update_lanes(const DevState &s, const int *i
 // (compare-and-swap) or a fresh one at the end; the cells' live counts
 // follow, and the new cell's R_NL bound is raised to qn.w if below.  Slots
 // of unflagged particles never change.
-__device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn)
+__device__ __forceinline__ void move_warp(const DevState &s, int i, float4 qn, int sc)
 {
     const int lane = threadIdx.x & 31;
     const int ccap = s.ccap;
-    const SceneGeom &g = geom_of(s, i);
+    const SceneGeom &g = s.sg[sc];
     const int nc = cell_key(g, qn.x, qn.y, qn.z);
     const int oc = s.cell_of[i], so = s.slot_of[i];
     if (lane == 0) atomicMax(&s.cell_rmax[nc], __float_as_int(qn.w));
@@ -572,8 +582,9 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     const int ccap = s.ccap;
     const int i = s.fid[k];
     const float4 qn = s.fref[k], qo = s.oref[k];
+    const int sc = flagged_scene(s, k);
     const int off = s.row_off[i], cap = s.row_cap[i], len0 = min(s.row_len[i], cap);
-    const SceneGeom &g = geom_of(s, i);
+    const SceneGeom &g = s.sg[sc];
     const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
     const int ci = cell_key(g, qn.x, qn.y, qn.z) - g.cell_base;
     const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
@@ -617,9 +628,16 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         const int e = e0 + lane;
         const int j = e0 == 0 ? jo0 : (e < len0 ? s.col[off + e] : -1);
         bool rm = false;
-        if (e < len0 && j >= 0 && !bit_of(s.ubits, j)) {
+        if (e < len0 && j >= 0) {
+            // the partner's flag word, reference state and radius are
+            // loaded together (one memory latency; none of them changes
+            // during the rebuild), and only an unflagged partner's pair is
+            // tested
+            const uint32_t fw = s.ubits[j >> 5];
             const float4 rj = s.ref[j];
-            rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(s.rad[j], rj.w)));
+            const float rr = s.rad[j];
+            if (!((fw >> (j & 31)) & 1u))
+                rm = !pair_hit(qn, make_float4(rj.x, rj.y, rj.z, __fadd_rn(rr, rj.w)));
         }
         if (len0 <= 32) jr0 = rm ? j : -1;
         else if (rm) lane_remove(s, j, i);
@@ -672,7 +690,7 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         const bool own = s.sc_cnt != nullptr;
         const float4 *lst = own ? s.sfref + g.first : s.fref;
         const int *ids = own ? s.sfid + g.first : s.fid;
-        const int m = own ? s.sc_cnt[par * s.nscenes + s.scene_of[i]] : nF;
+        const int m = own ? s.sc_cnt[par * s.nscenes + sc] : nF;
         work[1] += m;
         for (int b0 = 0; b0 < m; b0 += 32 * kDirectUnroll) {
             float4 rf[kDirectUnroll];
@@ -757,8 +775,9 @@ static __device__ __noinline__ void patch_warp_hist(const DevState &s, int k, in
     const int ccap = s.ccap;
     const int i = s.fid[k];
     const float4 qn = s.fref[k], qo = s.oref[k];
+    const int sc = flagged_scene(s, k);
     const int off = s.row_off[i], cap = s.row_cap[i], len0 = min(s.row_len[i], cap);
-    const SceneGeom &g = geom_of(s, i);
+    const SceneGeom &g = s.sg[sc];
     const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
     const int ci = cell_key(g, qn.x, qn.y, qn.z) - g.cell_base;
     const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
@@ -829,7 +848,7 @@ static __device__ __noinline__ void patch_warp_hist(const DevState &s, int k, in
         const bool own = s.sc_cnt != nullptr;
         const float4 *lst = own ? s.sfref + g.first : s.fref;
         const int *ids = own ? s.sfid + g.first : s.fid;
-        const int m = own ? s.sc_cnt[par * s.nscenes + s.scene_of[i]] : nF;
+        const int m = own ? s.sc_cnt[par * s.nscenes + sc] : nF;
         work[1] += m;
         for (int b0 = 0; b0 < m; b0 += 32) {
             const int kk = b0 + lane;
@@ -968,8 +987,9 @@ static __shared__ int s_bar_par;                   // parity of the step
 // context's counters by thread 0 once per step
 static __shared__ unsigned long long s_work[3];
 // the block's rebuild work items when traced: first start, last end,
-// longest item (ItemTrace)
+// longest item (item_start / item_stop)
 static __shared__ unsigned long long s_items[3];
+static __shared__ unsigned long long s_item_t0[kStepMaxThreads / 32];
 
 // Called by every thread at the start of the step kernel, before any barrier.
 __device__ __forceinline__ void grid_barrier_begin(const DevState &s, int par)
@@ -1626,32 +1646,25 @@ static __device__ __noinline__ void update_pass(const DevState &s, const lvb_mlp
 }
 
 // Trace of the rebuild's work items (LVB_OPT_TRACE; lane 0 of each warp):
-// the first start, the last end and the longest item of the warp's items,
-// gathered per block in s_items and added to the context's trace slots
-// TR_ITEMS / TR_ITEM_MAX by items_flush before the step's last barrier.
-struct ItemTrace {
-    bool on;
-    unsigned long long ta = 0, first = ~0ULL, last = 0, longest = 0;
-    __device__ __forceinline__ void start()
-    {
-        if (on) ta = global_ns();
+// each item's start is kept in shared memory (nothing held in registers
+// across the item), and the block's first start, last end and longest item
+// gather in s_items by shared-memory atomics; items_flush adds them to the
+// context's trace slots TR_ITEMS / TR_ITEM_MAX before the step's last
+// barrier.
+__device__ __forceinline__ void item_start(const DevState &s)
+{
+    if (s.trace && (threadIdx.x & 31) == 0) s_item_t0[threadIdx.x >> 5] = global_ns();
+}
+
+__device__ __forceinline__ void item_stop(const DevState &s)
+{
+    if (s.trace && (threadIdx.x & 31) == 0) {
+        const unsigned long long tb = global_ns(), ta = s_item_t0[threadIdx.x >> 5];
+        atomicMin(&s_items[0], ta);
+        atomicMax(&s_items[1], tb);
+        atomicMax(&s_items[2], tb - ta);
     }
-    __device__ __forceinline__ void stop()
-    {
-        if (!on) return;
-        const unsigned long long tb = global_ns();
-        first = min(first, ta);
-        last = max(last, tb);
-        longest = max(longest, tb - ta);
-    }
-    __device__ __forceinline__ void to_block() const
-    {
-        if (!on || last == 0) return;
-        atomicMin(&s_items[0], first);
-        atomicMax(&s_items[1], last);
-        atomicMax(&s_items[2], longest);
-    }
-};
+}
 
 __device__ __forceinline__ void items_flush(const DevState &s)
 {
@@ -1680,37 +1693,35 @@ static __device__ __noinline__ bool partial_pass(const DevState &s, int nF, int 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool direct = nF <= s.direct_max;
     unsigned work[3] = {0u, 0u, 0u};
-    ItemTrace it{s.trace && (threadIdx.x & 31) == 0};
     if (!direct) {
         for (int k = w0; k < nF; k += nw) {
-            it.start();
-            move_warp(s, s.fid[k], s.fref[k]);
-            it.stop();
+            item_start(s);
+            move_warp(s, s.fid[k], s.fref[k], flagged_scene(s, k));
+            item_stop(s);
         }
         if (!grid_barrier(s)) return false;
         for (int k = w0; k < nF; k += nw) {
-            it.start();
+            item_start(s);
             if (s.hist) patch_warp_hist(s, k, nF, false, par, ovf, work);
             else patch_warp(s, k, nF, false, par, ovf, work);
-            it.stop();
+            item_stop(s);
         }
     } else {
         for (int w = w0; w < 2 * nF; w += nw) {
-            it.start();
+            item_start(s);
             if (w < nF) {
                 if (s.hist) patch_warp_hist(s, w, nF, true, par, ovf, work);
                 else patch_warp(s, w, nF, true, par, ovf, work);
             } else {
-                move_warp(s, s.fid[w - nF], s.fref[w - nF]);
+                move_warp(s, s.fid[w - nF], s.fref[w - nF], flagged_scene(s, w - nF));
             }
-            it.stop();
+            item_stop(s);
         }
     }
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q)
             if (work[q]) atomicAdd(&s_work[q], (unsigned long long)work[q]);
-        it.to_block();
     }
     return true;
 }
