@@ -63,8 +63,10 @@ extern "C" {
  * call, on the device or the host.  The first call on a device does a
  * one-time set-up: it looks up the device address of the working array
  * (cudaGetSymbolAddress with that device current, which may also load
- * the library's module there); make that first call before any stream
- * capture begins.  Nothing needs to start at zero: each call clears its counters
+ * the library's module there).  The call cannot be captured into a CUDA
+ * graph (it synchronises its stream and reads results to the host): on a
+ * stream that is capturing, or whose capture status cannot be read, it
+ * returns LVB_EINVAL before any launch.  Nothing needs to start at zero: each call clears its counters
  * and cell counts on the stream before use.  All calls on one device share
  * the one working array, so calls that overlap in time on that device --
  * from two host threads, or on two streams -- race on it and give wrong

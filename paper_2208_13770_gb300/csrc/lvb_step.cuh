@@ -1380,7 +1380,11 @@ __device__ __forceinline__ void check_pass_stream(const DevState &s, const float
         if (tid == 0 && j + kStages < mine) issue(issued++);
     }
     if (failed && tid == 0) {
-        // copies still in flight land before the block leaves (bounded)
+        // copies still in flight land before the block leaves.  The wait is
+        // bounded like every wait here; a copy of in-bounds memory lands in
+        // microseconds, so one that outlasts it would mean the device is
+        // already failing.  The context is marked failed (DERR_SYNC): no
+        // later step on it launches work that uses this block's stages.
         for (int k = j; k < issued; ++k)
             stage_wait(&bar[k % kStages], (unsigned)(k / kStages) & 1u);
     }

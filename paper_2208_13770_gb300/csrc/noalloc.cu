@@ -302,10 +302,15 @@ int lvb_pairs_noalloc(int64_t n, const float *pos4, const float *ref4, const lvb
         if (!std::isfinite(box->lo[k]) || !std::isfinite(box->hi[k]) || !(box->hi[k] > box->lo[k]))
             return LVB_EINVAL;
     if (n > kNaMaxN) return LVB_ELIMIT;
+    const cudaStream_t st = (cudaStream_t)stream;
+    // the call synchronises its stream and reads results to the host, so
+    // it cannot be captured into a graph: refuse before any launch
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return LVB_EINVAL;
 
     NaScratch *sc = nullptr;
     if (int rc = na_scratch(&sc)) return rc;
-    const cudaStream_t st = (cudaStream_t)stream;
     const float4 *p4 = (const float4 *)pos4;
     const float4 *r4 = (const float4 *)ref4;
     const int nn = (int)n;

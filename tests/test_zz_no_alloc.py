@@ -147,6 +147,23 @@ def test_capacity_and_limits():
     rc = lvb.lvb_pairs_noalloc(0, pos_d.data_ptr(), ref_d.data_ptr(), ctypes.byref(box),
                                None, None, 0, ctypes.byref(cnt), None)
     assert rc == lvb.LVB_EINVAL
+    # a stream being captured into a graph: refused before any launch (the
+    # call synchronises its stream, which a capture does not allow)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    x = torch.zeros(4, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        x.add_(1.0)
+        cnt = ctypes.c_int64(-1)
+        rc = lvb.lvb_pairs_noalloc(10, pos_d.data_ptr(), ref_d.data_ptr(), ctypes.byref(box),
+                                   None, None, 0, ctypes.byref(cnt), side.cuda_stream)
+        graph.capture_end()
+    assert rc == lvb.LVB_EINVAL and cnt.value == 0
+    graph.replay()
+    torch.cuda.synchronize()
+    assert x.sum().item() == 4.0
     # non-finite reference coordinate
     bad = ctx.ref()
     bad[7, 1] = np.nan
