@@ -717,6 +717,8 @@ def _learned(lvb, torch):
                                   "timed once on the benchmark drum" % (vbest, bseed, bstage),
                      "last_stage1": info1, "last_stage2": info2},
         "learned": learned, "plain_0.1d": plain, "paper_rule": rules,
+        "gain_vs_paper_default_K200": (learned["value"] / rules["K200"]["value"]
+                                       if "K200" in rules else None),
         "gain_vs_paper_rule_K%d" % LEARN_H: learned["value"] / rules["K%d" % LEARN_H]["value"],
         "gain_vs_best_paper_rule": learned["value"] / best_rule["value"],
         "gain_vs_plain": learned["value"] / plain["value"],
