@@ -128,7 +128,8 @@ int dem_phase(dem_ctx *ctx, int32_t phase);
 int dem_get_rot_state(dem_ctx *ctx, float *omega, float *alpha, float *omega_star);
 
 /* dem_get_state -- copy out x (pos_r, with radii), v, a and v* (float4
- * records; any pointer may be NULL).  Synchronises. */
+ * records; the w of v and of v* holds 1 / m; any pointer may be NULL).
+ * Synchronises. */
 int dem_get_state(dem_ctx *ctx, float *pos_r, float *vel, float *acc, float *vstar);
 
 /*
@@ -163,8 +164,9 @@ int dem_get_contact_history(dem_ctx *ctx, int32_t sides, int32_t *ci, int32_t *c
                             int64_t *n_contacts);
 
 /* dem_set_state -- overwrite x, v, a (host or device float4 records; radii
- * in pos_r must equal the initial ones).  The broad phase keeps its
- * reference state, so the next step's check sees the new positions. */
+ * in pos_r must equal the initial ones; the w of v is ignored, the driver
+ * keeps 1 / m there).  The broad phase keeps its reference state, so the
+ * next step's check sees the new positions. */
 int dem_set_state(dem_ctx *ctx, const float *pos_r, const float *vel, const float *acc);
 
 /* dem_lvb -- the broad-phase context the driver owns (valid until

@@ -38,7 +38,8 @@ struct DemDev {
     float kn, two_zeta, g[3];
     int wall_kind, clamp_tensile, contacts_on;
     float drum_cx, drum_cz, drum_R;
-    float4 *pos, *vel, *acc, *vstar;   // vstar.w = 1 / m
+    float4 *pos, *vel, *acc, *vstar;   // vel.w = vstar.w = 1 / m (the integrator
+                                       // reads it with v, not from vstar)
     // friction (mu > 0): rotation and the tangential law; omega.w = 1 / I
     float mu, kt, gt_ratio;
     float4 *omega, *alpha, *wstar;     // null without friction
@@ -119,8 +120,13 @@ k_integrate(DemDev d)
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
     dtr_enter(d, TR_INTEGRATE);
+    // the scene's geometry only for the specular walls (no load otherwise)
     if (i < d.n)
-        integrate_one(integrate_args(d), d.rows.sg[d.rows.nscenes == 1 ? 0 : d.rows.scene_of[i]], i);
+        integrate_one<true>(integrate_args(d),
+                      d.rows.sg[d.rows.nscenes == 1 || d.wall_kind != DEM_WALL_SPECULAR
+                                    ? 0
+                                    : d.rows.scene_of[i]],
+                      i);
     dtr_exit(d, TR_INTEGRATE);
 }
 
@@ -428,8 +434,9 @@ __global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const floa
         const double r = p.w;
         const double m = (double)rho * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
         d.pos[i] = p;
-        d.vel[i] = make_float4(v.x, v.y, v.z, 0.0f);
-        d.vstar[i] = make_float4(v.x, v.y, v.z, (float)(1.0 / m));
+        const float im = (float)(1.0 / m);
+        d.vel[i] = make_float4(v.x, v.y, v.z, im);
+        d.vstar[i] = make_float4(v.x, v.y, v.z, im);
         d.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (d.omega) {   // at rest, I = 2/5 m r^2
             const float iI = (float)(1.0 / (0.4 * m * r * r));
@@ -438,6 +445,13 @@ __global__ void k_dem_setup(DemDev d, const float4 *__restrict__ pos, const floa
             d.alpha[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
+}
+
+// After the caller overwrote v: 1 / m back into v.w (from v*.w).
+__global__ void k_restore_im(DemDev d)
+{
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < d.n; i += gridDim.x * kThreads)
+        d.vel[i].w = d.vstar[i].w;
 }
 
 // initial a0 = F(x0, v0)/m + g: the force kernel with a = 0 and dt = 0
@@ -816,6 +830,11 @@ int dem_set_state(dem_ctx *c, const float *pos_r, const float *vel, const float 
     cudaError_t e = cudaSuccess;
     if (pos_r) e = cudaMemcpyAsync(c->d.pos, pos_r, b, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess && vel) e = cudaMemcpyAsync(c->d.vel, vel, b, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && vel) {
+        const int grid = std::min(grid_n((int)c->d.n), 4 * kNumSMs);
+        k_restore_im<<<grid, kThreads, 0, c->stream>>>(c->d);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && acc) e = cudaMemcpyAsync(c->d.acc, acc, b, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return from_cuda(e);

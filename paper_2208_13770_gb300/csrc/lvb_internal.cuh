@@ -269,12 +269,17 @@ struct IntegrateArgs {
     int active;     // 0: the check reads positions as they are
 };
 
+// kStream (the integrator as a kernel of its own): the old state is read
+// with streaming loads (evict first), so that the L2 keeps the new
+// positions this kernel writes for the broad phase that follows; inside the
+// fused step (kStream false) the forces tail reads v and a again.
+template <bool kStream = false>
 __device__ __forceinline__ float4 integrate_one(const IntegrateArgs &a, const SceneGeom &g, int i)
 {
-    float4 x = a.pos[i];
-    float4 v = a.vel[i];
-    const float4 ac = a.acc[i];
-    const float im = a.vstar[i].w;
+    float4 x = kStream ? __ldcs(a.pos + i) : a.pos[i];
+    float4 v = kStream ? __ldcs(a.vel + i) : a.vel[i];
+    const float4 ac = kStream ? __ldcs(a.acc + i) : a.acc[i];
+    const float im = v.w;   // the driver keeps 1 / m in v.w (and v*.w)
     x.x = __fadd_rn(x.x, fmaf(ac.x, a.half_dt2, __fmul_rn(v.x, a.dt)));
     x.y = __fadd_rn(x.y, fmaf(ac.y, a.half_dt2, __fmul_rn(v.y, a.dt)));
     x.z = __fadd_rn(x.z, fmaf(ac.z, a.half_dt2, __fmul_rn(v.z, a.dt)));
