@@ -824,17 +824,21 @@ def _clumps(lvb, torch, n=400_000, seed=2208_13770 + 21):
 
 def _ballistic(lvb, torch):
     """The 2,000-sphere ballistic case (r = 1 mm, phi 0.30, specular walls,
-    dt 1e-5 s, 1,000 steps): local skin 0.1 d against the global skin
-    0.1 d; the state fits in L2, so this is a latency figure."""
+    dt 1e-5 s, 1,000 steps): local skin 0.1 d (plain, and with the early
+    trigger) against the global skin 0.1 d; the state fits in L2, so this
+    is a latency figure."""
     from paper_2208_13770_gb300 import scenes
     sc = scenes.ballistic()
     out = {"workload": "2,000 spheres r 1 mm, phi 0.30, N(0, 0.01 m/s), specular walls, "
                        "dt 1e-5 s, 1,000 steps", "n": sc.n}
-    stream = torch.cuda.current_stream()
-    for name, trig, kind, val in (("local", lvb.LVB_TRIGGER_PARTIAL, lvb.LVB_SKIN_DIAMETER_FACTOR,
-                                   0.1), ("global_buffer", lvb.LVB_TRIGGER_GLOBAL,
-                                          lvb.LVB_SKIN_GLOBAL, 0.2e-3)):
+    for name, trig, kind, val, early in (
+            ("local", lvb.LVB_TRIGGER_PARTIAL, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1, 1000),
+            ("local_early", lvb.LVB_TRIGGER_PARTIAL, lvb.LVB_SKIN_DIAMETER_FACTOR, 0.1,
+             EARLY_PERMILLE),
+            ("global_buffer", lvb.LVB_TRIGGER_GLOBAL, lvb.LVB_SKIN_GLOBAL, 0.2e-3, 1000)):
         dem = lvb.DEM(sc, trigger=trig, skin_kind=kind, skin_value=val)
+        if early < 1000:
+            dem.lvb.set_option(lvb.LVB_OPT_EARLY, early)
         s0 = dem.lvb.stats()
         ph = _phases(lvb, torch, dem, sc.steps)
         _check_rc(lvb, dem.sync())

@@ -585,6 +585,9 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
     const int sc = flagged_scene(s, k);
     const int off = s.row_off[i], cap = s.row_cap[i], len0 = min(s.row_len[i], cap);
     const SceneGeom &g = s.sg[sc];
+    // the direct test's count, loaded now (its latency under the stencil's)
+    const bool own = s.sc_cnt != nullptr;
+    const int m_dir = !direct ? 0 : own ? s.sc_cnt[par * s.nscenes + sc] : nF;
     const int d0 = g.dim[0], d1 = g.dim[1], d2 = g.dim[2];
     const int ci = cell_key(g, qn.x, qn.y, qn.z) - g.cell_base;
     const int cx = ci % d0, cy = (ci / d0) % d1, cz = ci / (d0 * d1);
@@ -683,28 +686,29 @@ static __device__ __noinline__ void patch_warp(const DevState &s, int k, int nF,
         }
     }
     if (direct) {
-        // kDirectUnroll reference states per lane in flight; the id is
-        // loaded only for a hit.  Many scenes: the scene's own segment of
+        // kDirectUnroll reference states and ids per lane in flight (one
+        // memory latency a batch).  Many scenes: the scene's own segment of
         // the flagged particles (scenes share one coordinate frame, so the
         // global list would also hold far-away twins)
-        const bool own = s.sc_cnt != nullptr;
         const float4 *lst = own ? s.sfref + g.first : s.fref;
         const int *ids = own ? s.sfid + g.first : s.fid;
-        const int m = own ? s.sc_cnt[par * s.nscenes + sc] : nF;
+        const int m = m_dir;
         work[1] += m;
         for (int b0 = 0; b0 < m; b0 += 32 * kDirectUnroll) {
             float4 rf[kDirectUnroll];
+            int jf[kDirectUnroll];
 #pragma unroll
             for (int u = 0; u < kDirectUnroll; ++u) {
                 const int kk = b0 + u * 32 + lane;
                 rf[u] = kk < m ? lst[kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+                jf[u] = kk < m ? ids[kk] : -1;
             }
 #pragma unroll
             for (int u = 0; u < kDirectUnroll; ++u) {
                 const int kk = b0 + u * 32 + lane;
                 int j = -1;
                 if (kk < m && pair_hit(qn, rf[u])) {
-                    j = ids[kk];
+                    j = jf[u];
                     if (j == i || j < g.first || j >= g.first + g.count) j = -1;
                 }
                 const unsigned msk = __ballot_sync(FULL, j >= 0);
