@@ -1756,18 +1756,13 @@ __device__ __forceinline__ void flush_work(const DevState &s)
 // ---------------------------------------------------------------------------
 template <bool kFused, class Tail>
 __global__ void __launch_bounds__(kStepMaxThreads, 1)
-k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc, DevState sp,
+k_step(const float4 *__restrict__ pos_in, const float4 *vel, const float4 *acc,
+       const __grid_constant__ DevState sp,
        IntegrateArgs ia, Tail tail)
 {
-    // the context's state in shared memory: every phase (and the functions
-    // it calls) reads its fields from there rather than from the parameter
-    // space, whose lines miss on first use in each phase
-    __shared__ __align__(16) DevState s_sh;
-    static_assert(sizeof(DevState) % 4 == 0, "DevState is copied in words");
-    for (int t = threadIdx.x; t < (int)(sizeof(DevState) / 4); t += blockDim.x)
-        reinterpret_cast<int *>(&s_sh)[t] = reinterpret_cast<const int *>(&sp)[t];
-    __syncthreads();
-    const DevState &s = s_sh;
+    // the context's state read in place from the parameter space (uniform
+    // reads through the constant cache; no copy at the start)
+    const DevState &s = sp;
     DevCounters *c = s.cnt;
     // the step's bookkeeping (counters, trace) runs on the last warp of
     // block 0, whose rebuild work items come last
