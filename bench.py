@@ -259,7 +259,7 @@ def _narrow_phase(n, entries, ms, hbm_peak):
 # headline window, from one ncu capture of the current kernel (mean of the
 # captured launches; the command and the counters are in profiles/).  None
 # when the kernel has changed since the capture.
-NCU_TRAFFIC_BATCHED = None
+NCU_TRAFFIC_BATCHED = 203.61e6   # profiles/k_step_batched512_ncu.txt
 
 
 # ----------------------------------------------------------------- headline
