@@ -214,6 +214,30 @@ def test_advance_graph_matches_phase_launches(orc):
     b.close()
 
 
+def test_set_state_keeps_inverse_mass():
+    # the driver keeps 1/m in the w of v (and of v*), which the integrator
+    # reads: dem_set_state ignores the caller's v.w and restores it, so the
+    # next position half-step is the one of a context that was not reset
+    lvb = _lvb()
+    s = scenes.packed(n=800, seed=13, vsigma=0.2)
+    dems = [lvb.DEM(s), lvb.DEM(s)]
+    for dem in dems:
+        dem.step()
+    x, v, a, vs = dems[0].state()
+    im = vs[:, 3].copy()
+    assert np.all(im > 0) and np.array_equal(v[:, 3], im)
+    v0 = v.copy()
+    v0[:, 3] = -1.0
+    dems[1].set_state(x, v0, a)
+    assert np.array_equal(dems[1].state()[1], v)
+    for dem in dems:
+        dem.phase(lvb.DEM_PHASE_INTEGRATE)
+    s0, s1 = dems[0].state(), dems[1].state()
+    assert np.array_equal(s0[0], s1[0]) and np.array_equal(s0[3], s1[3])
+    for dem in dems:
+        dem.close()
+
+
 def test_settling_full_size_step_parity(orc):
     # 200,000 polydisperse particles, graph-replayed steps, then one checked
     # step over every particle
