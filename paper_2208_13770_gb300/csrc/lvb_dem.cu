@@ -236,7 +236,11 @@ __device__ __forceinline__ float3 tangential(const DemDev &d, float ri, float4 v
 
 // Narrow phase on the row of particle i + walls + velocity finish; the
 // friction form (fric) also the tangential law, torques and rotation.
-template <bool fric>
+// kEarly (the forces as a kernel of their own, 32 registers): the row
+// bounds and the scene of i are loaded with the particle's own state, not
+// after the error word and the row walk; the fused tail keeps the late
+// loads (fewer registers held across the walk).
+template <bool fric, bool kEarly = false>
 __device__ __forceinline__ void forces_body(const DemDev &d, int i)
 {
     const float4 xi = d.pos[i];
@@ -247,11 +251,20 @@ __device__ __forceinline__ void forces_body(const DemDev &d, int i)
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     float Tx = 0.f, Ty = 0.f, Tz = 0.f;
     const float4 wi = fric ? d.wstar[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool walls = d.wall_kind == DEM_WALL_BOX || d.wall_kind == DEM_WALL_DRUM;
+    int sc_i = 0, off = 0, len = 0;
+    if (kEarly) {   // in range either way; used only as below
+        sc_i = walls && d.rows.nscenes > 1 ? d.rows.scene_of[i] : 0;
+        off = d.rows.row_off[i];
+        len = min(d.rows.row_len[i], d.rows.row_cap[i]);
+    }
     // after a row store that failed even a tight re-layout (LVB_EOVERFLOW)
     // the row offsets no longer fit the store: the rows are not read
     if (d.contacts_on && !(d.rows.cnt->err & DERR_STORE)) {
-        const int off = d.rows.row_off[i];
-        const int len = min(d.rows.row_len[i], d.rows.row_cap[i]);
+        if (!kEarly) {
+            off = d.rows.row_off[i];
+            len = min(d.rows.row_len[i], d.rows.row_cap[i]);
+        }
         for (int e = 0; e < len; ++e) {
             const int j = d.rows.col[off + e];
             if (j < 0) continue;            // a removed pair's slot
@@ -279,8 +292,9 @@ __device__ __forceinline__ void forces_body(const DemDev &d, int i)
         }
     }
     const float r = xi.w;
-    if (d.wall_kind == DEM_WALL_BOX || d.wall_kind == DEM_WALL_DRUM) {
-        const SceneGeom &g = d.rows.sg[d.rows.nscenes == 1 ? 0 : d.rows.scene_of[i]];
+    if (walls) {
+        if (!kEarly && d.rows.nscenes > 1) sc_i = d.rows.scene_of[i];
+        const SceneGeom &g = d.rows.sg[sc_i];
         const float m = 1.0f / im_i;
         if (d.wall_kind == DEM_WALL_BOX) {
             Fx += plane_force(d, xi.x, vi.x, r, g.lo[0], g.hi[0], m);
@@ -334,10 +348,11 @@ static __device__ __noinline__ void forces_one_fric(const DemDev &d, int i)
     forces_body<true>(d, i);
 }
 
+template <bool kEarly = false>
 __device__ __forceinline__ void forces_one(const DemDev &d, int i)
 {
     if (d.omega) forces_one_fric(d, i);
-    else forces_body<false>(d, i);
+    else forces_body<false, kEarly>(d, i);
 }
 
 // Forces as a separate kernel, one thread per particle.  Eight blocks per
@@ -349,7 +364,7 @@ k_forces(DemDev d)
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i == 0) atomicAdd(d.rows.kernels, 1ULL);
     dtr_enter(d, TR_FORCES);
-    if (i < d.n) forces_one(d, i);
+    if (i < d.n) forces_one<true>(d, i);
     dtr_exit(d, TR_FORCES);
 }
 
